@@ -1,0 +1,384 @@
+"""Benchmark of the GB300 DC-FSPB dose engine.
+
+One step = the whole hot path of one plan on synthetic inputs resident in HBM:
+  Algorithm A1 steps 1-6 for the plan's density (smoothing, beamlet geometry,
+  FP64 Siddon trace, depth tables; dc_fspb_set_density),
+  eq. (1) direct dose (dc_fspb_dose),
+  the dose-deposition matrix: pair count, row pointers and FP32 CSR fill
+  (dc_fspb_pair_count + dc_fspb_dose_matrix).
+Every pair of the plan is evaluated twice per step (once for the dose, once for
+its matrix entry), so the metric counts 2 x pairs voxel-beamlet evaluations.
+
+Default workload: the 9-field coplanar thorax plan on a 128 x 128 x 96 grid of
+0.25 cm voxels (0.5 cm beamlets, fields 8-15 cm, ROI 5 cm).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank computes its
+own plan (independent problems: weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "voxel-beamlet evals/s (full plan: steps 1-6 + eq. 1 dose + FP32 dose matrix)"
+UNIT = "evals/s"
+# Algorithmic work of one (voxel, beamlet) evaluation of eqs. (2)-(4) with the
+# lookups of Algorithm A1 steps 9-11 (counted from the method's definition):
+ALG_FP32_PER_PAIR = 95     # FP32 add/mul/fma/compare/convert operations
+ALG_MUFU_PER_PAIR = 9      # 8 exponentials (four p() of eq. 4) + 1 reciprocal (SAD/|r_a|)
+FP32_LANES_PER_SM = 128
+MUFU_LANES_PER_SM = 16
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--scale", type=float, default=1.0, help="grid scale of the thorax plan")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg, torch):
+    if pg is not None:
+        if torch.cuda.is_available():
+            pg.barrier(device_ids=[torch.cuda.current_device()])
+        else:
+            pg.barrier()
+
+
+def max_over_ranks(pg, torch, x):
+    if pg is None:
+        return x
+    t = torch.tensor([float(x)], device="cuda")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(pg, torch, x):
+    if pg is None:
+        return x
+    t = torch.tensor([float(x)], device="cuda")
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timings (the cpu_baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample_rate(plan_in, budget_s=12.0, seed=3):
+    """Times the FP64 oracle on a seeded sample of voxels of the workload.
+
+    Returns per-step CPU estimates: the oracle's plan set-up time (steps 1-6,
+    measured in full) and its dose + matrix time scaled from the sample by the
+    ratio of pair counts."""
+    from oracle import oracle
+    threads = oracle.default_threads()
+    t0 = time.perf_counter()
+    op = oracle.OraclePlan(plan_in, threads=threads)
+    t_create = time.perf_counter() - t0
+    rng = np.random.default_rng(seed)
+    n = 256
+    while True:
+        vox = np.sort(rng.choice(op.V, size=min(n, op.V), replace=False))
+        t0 = time.perf_counter()
+        op.dose_voxels(vox)
+        op.matrix(vox)
+        dt = time.perf_counter() - t0
+        if dt >= 0.4 * budget_s or n >= op.V:
+            break
+        n = int(min(op.V, n * max(2.0, 0.5 * budget_s / max(dt, 1e-3))))
+    pairs_sample = int(op.pairs_voxels(vox).sum())
+    return dict(op=op, t_create=t_create, t_sample=dt, n_vox=int(vox.size), pairs_sample=pairs_sample,
+                threads=threads)
+
+
+# ---------------------------------------------------------------------------
+
+def run_reference(args, world, rank, pg):
+    """The FP64 oracle as the reference arm (host cores, bounded samples)."""
+    if rank != 0:
+        return
+    from paper_1103_1164_gb300 import synth
+    from oracle import oracle
+    p = synth.config2(args.scale)
+    threads = oracle.default_threads()
+    t0 = time.perf_counter()
+    op = oracle.OraclePlan(p, threads=threads)
+    t_create = time.perf_counter() - t0
+    rng = np.random.default_rng(11)
+    vox = np.sort(rng.choice(op.V, size=min(4096, op.V), replace=False))
+    pairs = int(op.pairs_voxels(vox).sum())
+    times = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        op.dose_voxels(vox)
+        op.matrix(vox)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+    t = sum(times)
+    value = 2 * pairs * len(times) / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"thorax9 {p.grid.nx}x{p.grid.ny}x{p.grid.nz} @0.25cm, 9 fields, "
+                                   f"{p.n_beamlets} beamlets (0.5 cm), ROI 5 cm",
+                       "l2": "n/a (host)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{vox.size} seeded voxels of the plan per step "
+                                       f"({pairs} pairs; dose + matrix rows); plan set-up "
+                                       f"{t_create:.2f} s not in the step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local, pg):
+    import torch
+    from paper_1103_1164_gb300 import build, dc_fspb, synth
+    build.build()
+    dc = dc_fspb
+    dc.load()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    props = torch.cuda.get_device_properties(dev)
+    peaks, peak_kind = measured_peaks()
+
+    p = synth.config2(args.scale)
+    rho_d = torch.from_numpy(p.rho).to(dev)
+    flu_d = torch.from_numpy(p.fluence).to(dev)
+    plan = dc.dc_fspb_create_from(p, stream=stream.cuda_stream, device_density=rho_d)
+    V, B = plan.n_voxels, plan.n_beamlets
+    dose_d = torch.empty(plan.shape, device=dev)
+    pairs = dc.dc_fspb_pair_count(plan)
+    rowptr_d = torch.empty(V + 1, dtype=torch.int64, device=dev)
+    cols_d = torch.empty(max(pairs, 1), dtype=torch.int32, device=dev)
+    vals_d = torch.empty(max(pairs, 1), dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step(ev=None):
+        if ev: ev[0].record(stream)
+        dc.dc_fspb_set_density(plan, rho_d)
+        if ev: ev[1].record(stream)
+        dc.dc_fspb_dose(plan, flu_d, dose_d)
+        if ev: ev[2].record(stream)
+        n = dc.dc_fspb_pair_count(plan)
+        assert n == pairs
+        if ev: ev[3].record(stream)
+        dc.dc_fspb_dose_matrix(plan, dc.DC_F32, rowptr_d, cols_d, vals_d)
+        if ev: ev[4].record(stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    launches0 = dc.dc_fspb_launch_count()
+    barrier(pg, torch)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        w0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()                  # L2 flushed before every step (not timed)
+            step(evs[k])
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - w0
+    barrier(pg, torch)
+    launches = dc.dc_fspb_launch_count() - launches0
+    stage = np.array([[evs[k][j].elapsed_time(evs[k][j + 1]) for j in range(4)] for k in range(args.steps)])
+    step_ms = stage.sum(1)
+    t_total_ms = max_over_ranks(pg, torch, float(step_ms.sum()))
+    evals_step = 2 * pairs
+    total_evals = sum_over_ranks(pg, torch, evals_step * args.steps)
+    value = total_evals / (t_total_ms * 1e-3)
+    ms_per_step = t_total_ms / args.steps
+
+    # roofline of the dominant kernel: the direct dose kernel (ALU bound)
+    t_dose = float(stage[:, 1].mean()) * 1e-3
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_pairs = props.multi_processor_count * sm_max * 1e6 * min(
+        FP32_LANES_PER_SM / ALG_FP32_PER_PAIR, MUFU_LANES_PER_SM / ALG_MUFU_PER_PAIR)
+    achieved = pairs / t_dose
+    roofline = {"kernel": "k_dose<dose,1> (eqs. 1-4)", "bound": "alu",
+                "achieved": achieved / 1e9, "peak": peak_pairs / 1e9, "unit": "Gpair/s",
+                "frac": achieved / peak_pairs, "traffic": None,
+                "peak_basis": f"{props.multi_processor_count} SMs x {sm_max:.0f} MHz x "
+                              f"min(128/{ALG_FP32_PER_PAIR} FP32, 16/{ALG_MUFU_PER_PAIR} MUFU) per pair",
+                "dose_kernel_ms": t_dose * 1e3}
+    fill_ms = float(stage[:, 3].mean())
+    bytes_matrix = pairs * 8 + (V + 1) * 8
+    matrix = {"fill_ms": fill_ms, "fill_GBps": bytes_matrix / (fill_ms * 1e-3) / 1e9,
+              "hbm_peak_GBps": peaks.get("hbm_gbs"), "count_scan_ms": float(stage[:, 2].mean()),
+              "nnz": pairs, "bytes": bytes_matrix}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, dc, p, plan, pairs, torch)
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        est = oracle_sample_rate(p)
+        scale_pairs = pairs / max(est["pairs_sample"], 1)
+        t_cpu_step = est["t_create"] + est["t_sample"] * scale_pairs
+        cpu = {"value": evals_step / t_cpu_step, "unit": UNIT, "cores": est["threads"], "kind": "oracle",
+               "sample": f"FP64 oracle: plan set-up timed in full ({est['t_create']:.2f} s), dose + "
+                         f"matrix rows timed on {est['n_vox']} seeded voxels ({est['pairs_sample']} pairs, "
+                         f"{est['t_sample']:.2f} s) and scaled by pair count to the {pairs} pairs of the plan"}
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"thorax9 {p.grid.nx}x{p.grid.ny}x{p.grid.nz} @0.25cm, 9 fields "
+                                   f"8-15 cm, {B} beamlets (0.5 cm), ROI 5 cm, density correction on",
+                       "pairs": pairs, "voxels": V, "beamlets": B,
+                       "l2": f"flushed before each step ({L2_FLUSH_BYTES >> 20} MiB write, untimed)",
+                       "ranks": "independent plans (one per GPU)"},
+            "stages_ms": {"steps_1_6": float(stage[:, 0].mean()), "dose": float(stage[:, 1].mean()),
+                          "pair_count": float(stage[:, 2].mean()), "matrix_fill": fill_ms},
+            "wall_ms_per_step": 1e3 * wall / args.steps,
+            "roofline": roofline, "peaks": peak_kind, "dose_matrix": matrix,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
+def run_e2e(args, dc, p, plan, pairs, torch):
+    """The same step through the C ABI with pinned host buffers: every H2D/D2H
+    copy of the step's inputs and results is inside the timed region."""
+    V, B = plan.n_voxels, plan.n_beamlets
+    pin = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=True).numpy()
+    rho_h = pin(p.rho.shape, torch.float32)
+    rho_h[...] = p.rho
+    flu_h = pin((B,), torch.float32)
+    flu_h[...] = p.fluence
+    dose_h = pin(plan.shape, torch.float32)
+    rowptr_h = pin((V + 1,), torch.int64)
+    cols_h = pin((max(pairs, 1),), torch.int32)
+    vals_h = pin((max(pairs, 1),), torch.float32)
+
+    def step():
+        dc.dc_fspb_set_density(plan, rho_h)
+        dc.dc_fspb_dose(plan, flu_h, dose_h)
+        n = dc.dc_fspb_pair_count(plan)
+        dc.dc_fspb_dose_matrix(plan, dc.DC_F32, rowptr_h, cols_h, vals_h)
+        return n
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    k = max(1, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(k):
+        step()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / k
+    h2d = 4 * V + 4 * B
+    d2h = 4 * V + 8 * (V + 1) + 8 * pairs + 8
+    return {"value": 2 * pairs / dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "ms_per_step": dt * 1e3, "steps": k}
+
+
+def main():
+    args = parse()
+    world, rank, local, pg = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank, pg)
+    else:
+        run_ours(args, world, rank, local, pg)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

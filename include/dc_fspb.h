@@ -1,0 +1,225 @@
+/*
+ * dc_fspb.h - C ABI of the GB300 DC-FSPB dose engine.
+ *
+ * The engine computes the density-corrected finite-size pencil-beam dose of
+ * Gu, Jelen, Li, Jia and Jiang, "GPU-based finite-size pencil beam algorithm
+ * with 3D-density correction for radiotherapy dose calculation"
+ * (arXiv 1103.1164):
+ *
+ *   D(r)   = sum_i D_i(r) f_i                                         (eq. 1)
+ *   D_i(r) = F(x, y, omega, u_x, u_y, x0, y0) A(t_eq, theta) (SAD/|r_a|)^2 (eq. 2)
+ *   F      = sum_{i=1,2} omega_i p(x, u_ix, x0) p(y, u_iy, y0)          (eq. 3)
+ *   p      = the piecewise sinh/cosh/exp penumbra profile               (eq. 4)
+ *
+ * with the lateral density correction of Section 2.1 (u_1 = f_u1(rho) u_1^w,
+ * u_2 = f_u2(rho_hat) u_2^w, omega_i = f_omega_i(rho_hat)(omega_i^w +
+ * omega_i^corr)) and the per-beamlet radiological-depth and omega_corr tables
+ * of Algorithm A1 steps 5-6 / Algorithm A2 Kernel 4.  All compute runs in the
+ * library's own CUDA kernels for sm_103a on one GPU.
+ *
+ * Conventions (all entry points):
+ *  - lengths in cm, angles in degrees at the ABI (radians inside);
+ *  - volumes are float32 [nz][ny][nx], x fastest; voxel (i, j, k) has its
+ *    centre at (ox + i dx, oy + j dy, oz + k dz); voxel v = (k ny + j) nx + i;
+ *  - beam frame: at gantry 0 the beam travels +y with field axes e_x' = +x,
+ *    e_y' = +z; the gantry turns it about +z, the couch about +y, the
+ *    collimator turns e_x', e_y' about the beam axis; source = iso - SAD e_z';
+ *  - beamlets are numbered beam-major, then row (e_y' index n), then column
+ *    (e_x' index m): i = first(b) + n M_b + m, M_b = field_x / beamlet_x;
+ *  - unless a function says otherwise, pointer arguments are host memory; with
+ *    DC_DEVICE_PTRS in `flags` they are device memory of the plan's device;
+ *  - the caller owns every buffer it passes; the library owns the plan and
+ *    everything the plan allocates (released by dc_fspb_destroy);
+ *  - no exception crosses the ABI: each call returns a dc_status, and
+ *    dc_last_error() gives a message for the calling thread's last failure;
+ *  - calls on one plan are not thread-safe; work is ordered on the plan's
+ *    CUDA stream.  Calls given host pointers return after the result is in
+ *    host memory; calls given device pointers return once the work is queued.
+ */
+#ifndef DC_FSPB_H
+#define DC_FSPB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DC_OK = 0,
+    DC_EINVAL = 1,        /* an argument is out of range or inconsistent       */
+    DC_ENOMEM = 2,        /* a device or host allocation failed                */
+    DC_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed       */
+    DC_ETIMEOUT = 4,      /* a bounded device-side wait gave up                */
+    DC_EUNSUPPORTED = 5   /* the request is valid but not implemented          */
+} dc_status;
+
+#define DC_DEVICE_PTRS 1u  /* flags: pointer arguments are device memory */
+
+/* Value types of the dose-deposition matrix. */
+#define DC_F32 0
+#define DC_BF16 1
+
+/* Voxel grid (Section 2.3: CT resampled to a regular grid). */
+typedef struct {
+    int32_t nx, ny, nz;
+    float dx, dy, dz;      /* voxel size                                   */
+    float ox, oy, oz;      /* centre of voxel (0, 0, 0)                    */
+} dc_grid;
+
+/* One beam (Table 1: gantry/couch angles; Section 2.1: SAD). The field
+ * sizes are measured in the isocentre plane and must be whole multiples of
+ * the beamlet size. */
+typedef struct {
+    float gantry_deg, couch_deg, coll_deg;
+    float sad;             /* source-to-axis distance                     */
+    float iso[3];          /* isocentre                                   */
+    float field_x, field_y;
+} dc_beam;
+
+/*
+ * Commissioned beam model (Section 2.1; Algorithm A1 steps 9-11), as tables
+ * looked up by clamped linear interpolation:
+ *   A       [a_ntheta][a_nt]  A(t_eq = j a_dt, theta = l a_dtheta), bilinear;
+ *   water   [4][w_n]          u_1^w, u_2^w, omega_1^w, omega_2^w at t = j w_dt;
+ *   dens    [6][f_n]          f_u1, f_u2, f_omega1, f_omega2, b_1, b_2 at
+ *                             rho = f_rho0 + j f_drho (the commissioned density
+ *                             range: densities outside it are clamped into it).
+ * Every table needs at least 2 entries per axis and a positive step.
+ * roi_radius: radius of the ROI cylinder about each beamlet axis (the paper
+ * uses 5 cm, footnote to Algorithm A1). smooth_sigma: sigma of the Gaussian
+ * that gives rho_hat (step 1), truncated at ceil(3 sigma / delta) voxels per
+ * axis. rho_surface: the body surface is where a beamlet axis first/last meets
+ * a voxel of density > rho_surface (step 4). density_correction = 0 skips
+ * step 11 (conventional FSPB with depth correction only, Algorithm A2 Kernel 5).
+ * The host arrays are copied during dc_fspb_create and not kept.
+ */
+typedef struct {
+    const float* A;
+    int32_t a_nt, a_ntheta;
+    float a_dt, a_dtheta;
+    const float* water;
+    int32_t w_n;
+    float w_dt;
+    const float* dens;
+    int32_t f_n;
+    float f_rho0, f_drho;
+    float roi_radius;
+    float smooth_sigma;
+    float rho_surface;
+    int32_t density_correction;
+    int32_t reserved[3];   /* must be zero */
+} dc_kernel_coeffs;
+
+typedef struct dc_plan dc_plan;
+
+/* Message describing the calling thread's most recent failed call ("" if none). */
+const char* dc_last_error(void);
+/* Static name of a status code. */
+const char* dc_status_str(dc_status s);
+
+/*
+ * Builds a plan: uploads the density, computes rho_hat (Algorithm A1 step 1,
+ * A2 Kernel 1), the beamlet geometry and angle theta (steps 2-3, Kernel 2),
+ * the body entry/exit of every beamlet axis by an FP64 Siddon ray trace
+ * (step 4, Kernel 3) and the radiological-depth and omega_corr tables sampled
+ * every d = min(dx, dy, dz)/2 (steps 5-6, Kernel 4; Section 2.2).
+ *   ct_density  [nz][ny][nx] relative densities >= 0 and finite (host, or
+ *               device with DC_DEVICE_PTRS);
+ *   beams       n_beams >= 1 host records; the sources must lie outside the grid;
+ *   coeffs      host record and host tables;
+ *   cuda_stream cudaStream_t on which all of the plan's work runs (NULL = the
+ *               legacy default stream); it must outlive the plan.
+ * On success *out receives the plan; on failure *out is NULL and nothing leaks.
+ * Errors: DC_EINVAL (bad sizes, negative/NaN density, source inside the grid,
+ * field not a multiple of the beamlet), DC_ENOMEM, DC_ECUDA.
+ */
+dc_status dc_fspb_create(const float* ct_density, const dc_grid* grid, const dc_beam* beams,
+                         int32_t n_beams, float beamlet_x, float beamlet_y,
+                         const dc_kernel_coeffs* coeffs, uint32_t flags, void* cuda_stream,
+                         dc_plan** out);
+
+/*
+ * Replaces the plan's density with a new one on the same grid (the daily CT of
+ * online adaptive replanning, Section 1) and recomputes Algorithm A1 steps 1-6
+ * (A2 Kernels 1-4) in place, without reallocating: rho_hat, the per-voxel
+ * correction factors, every beamlet's body entry/exit and its tables.  The
+ * cached pair count and matrix pattern are invalidated.  Same density rules
+ * and pointer flags as dc_fspb_create; with host memory the call returns once
+ * the new tables are computed, with DC_DEVICE_PTRS once the work is queued.
+ */
+dc_status dc_fspb_set_density(dc_plan* plan, const float* ct_density, uint32_t flags);
+
+/* Releases the plan and all memory it owns (NULL is accepted). */
+dc_status dc_fspb_destroy(dc_plan* plan);
+
+/* Number of beamlets B (the length of a fluence vector). */
+dc_status dc_fspb_n_beamlets(const dc_plan* plan, int32_t* n);
+
+/* Number of voxels V = nx ny nz. */
+dc_status dc_fspb_n_voxels(const dc_plan* plan, int64_t* n);
+
+/*
+ * Eq. (1): dose[v] = sum_i f_i D_i(r_v) over the pairs whose voxel lies in
+ * beamlet i's ROI cylinder and between its body entry and exit (Algorithm A1
+ * steps 7-14, A2 Kernel 5), evaluated in FP32 with fast exponentials.
+ *   fluence [B] >= 0; dose [V] written in full (no accumulation).
+ * Errors: DC_EINVAL (NULL pointers), DC_ECUDA.
+ */
+dc_status dc_fspb_dose(dc_plan* plan, const float* fluence, float* dose, uint32_t flags);
+
+/*
+ * Eq. (1) for k fluence vectors at once: dose[q][v] = sum_i fluence[q][i] D_i(r_v),
+ * each D_i(r_v) evaluated once and applied to all k vectors (1 <= k <= 64).
+ *   fluence [k][B]; dose [k][V].
+ */
+dc_status dc_fspb_dose_batch(dc_plan* plan, const float* fluence, int32_t k, float* dose,
+                             uint32_t flags);
+
+/*
+ * Number of (voxel, beamlet) pairs that eq. (1) sums (the nonzero pattern of
+ * the dose-deposition matrix); computed on first use and cached. *pairs is
+ * host memory.
+ */
+dc_status dc_fspb_pair_count(dc_plan* plan, int64_t* pairs);
+
+/*
+ * Dose-deposition matrix M[v][i] = D_i(r_v) (unit fluence) over the same
+ * pairs, as CSR by voxel row with ascending beamlet columns:
+ *   rowptr [V + 1] int64, cols [nnz] int32, vals [nnz] float32 (value_dtype
+ *   DC_F32) or bfloat16 bits (DC_BF16, round-to-nearest-even of the FP32 value);
+ *   nnz = dc_fspb_pair_count().  All three buffers are caller-owned, and all
+ *   host or all device memory per `flags`.
+ */
+dc_status dc_fspb_dose_matrix(dc_plan* plan, int32_t value_dtype, int64_t* rowptr, int32_t* cols,
+                              void* vals, uint32_t flags);
+
+/* ---- Inspection of the plan's intermediate results (for verification) ---- */
+
+/* rho_hat [V] (Algorithm A1 step 1). */
+dc_status dc_fspb_get_smoothed(const dc_plan* plan, float* out, uint32_t flags);
+
+/*
+ * Per-beamlet geometry (steps 2-4), 16 floats per beamlet into rec [B][16]
+ * (host memory): n[3], e_x''[3], e_y''[3], theta, hit (0/1), L_in, L_out,
+ * K (number of table samples), 0, 0.
+ */
+dc_status dc_fspb_get_beamlets(const dc_plan* plan, float* rec);
+
+/*
+ * Beamlet i's tables (steps 5-6) at t = k d, k < min(K, kmax), into host
+ * arrays teq, w1, w2 (omega_1^corr, omega_2^corr); *K receives the sample count.
+ */
+dc_status dc_fspb_get_tables(const dc_plan* plan, int32_t i, float* teq, float* w1, float* w2,
+                             int32_t kmax, int32_t* K);
+
+/* Number of CUDA kernels this library has launched in the calling process
+ * (all plans, all threads), for accounting of GPU work. */
+dc_status dc_fspb_launch_count(uint64_t* n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DC_FSPB_H */

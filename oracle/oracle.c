@@ -601,15 +601,35 @@ void or_plan_pair(const void* h, int64_t v, int i, double* out)
     out[0] = D; out[1] = inside; out[2] = a;
 }
 
-/* Dose-deposition matrix M[v, i] = D_i(r_v) by voxel rows, columns ascending.
+/* Number of pairs (inside ROI and depth range) at listed voxels. */
+void or_plan_pairs_voxels(const void* h, const int64_t* vox, int64_t n, int64_t* counts, int nthreads)
+{
+    const OPlan* P = (const OPlan*)h;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+    for (int64_t q = 0; q < n; ++q) {
+        int64_t c = 0;
+        for (int i = 0; i < P->B; ++i) {
+            double D;
+            int a;
+            c += pair_dose(P, vox[q], i, &D, &a, NULL);
+        }
+        counts[q] = c;
+    }
+}
+
+/* Dose-deposition matrix M[v, i] = D_i(r_v) by voxel rows, columns ascending,
+ * for the listed voxels (all voxels if vox == NULL, n = V).
  * Counting pass: per row, the number of candidate entries (inside or ambiguous). */
-void or_plan_matrix_count(const void* h, int64_t* counts, int nthreads)
+void or_plan_matrix_count(const void* h, const int64_t* vox, int64_t n, int64_t* counts, int nthreads)
 {
     const OPlan* P = (const OPlan*)h;
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads > 0 ? nthreads : 1)
 #endif
-    for (int64_t v = 0; v < P->V; ++v) {
+    for (int64_t q = 0; q < n; ++q) {
+        int64_t v = vox ? vox[q] : q;
         int64_t c = 0;
         for (int i = 0; i < P->B; ++i) {
             double D;
@@ -617,20 +637,21 @@ void or_plan_matrix_count(const void* h, int64_t* counts, int nthreads)
             int inside = pair_dose(P, v, i, &D, &a, NULL);
             if (inside || a) ++c;
         }
-        counts[v] = c;
+        counts[q] = c;
     }
 }
 
 /* Fill pass: flags bit 0 = inside, bit 1 = ambiguous. */
-void or_plan_matrix_fill(const void* h, const int64_t* rowptr, int32_t* cols, double* vals,
-                         uint8_t* flags, int nthreads)
+void or_plan_matrix_fill(const void* h, const int64_t* vox, int64_t n, const int64_t* rowptr,
+                         int32_t* cols, double* vals, uint8_t* flags, int nthreads)
 {
     const OPlan* P = (const OPlan*)h;
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads > 0 ? nthreads : 1)
 #endif
-    for (int64_t v = 0; v < P->V; ++v) {
-        int64_t o = rowptr[v];
+    for (int64_t q = 0; q < n; ++q) {
+        int64_t v = vox ? vox[q] : q;
+        int64_t o = rowptr[q];
         for (int i = 0; i < P->B; ++i) {
             double D;
             int a;

@@ -68,8 +68,9 @@ def lib():
         L.or_plan_dose.argtypes = [vp, vp, vp, vp, i32]
         L.or_plan_dose_voxels.argtypes = [vp, vp, vp, i64, vp, vp, i32]
         L.or_plan_pair.argtypes = [vp, i64, i32, vp]
-        L.or_plan_matrix_count.argtypes = [vp, vp, i32]
-        L.or_plan_matrix_fill.argtypes = [vp, vp, vp, vp, vp, i32]
+        L.or_plan_matrix_count.argtypes = [vp, vp, i64, vp, i32]
+        L.or_plan_pairs_voxels.argtypes = [vp, vp, i64, vp, i32]
+        L.or_plan_matrix_fill.argtypes = [vp, vp, i64, vp, vp, vp, vp, i32]
         L.or_trace_ray.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, i32]
         L.or_smooth.argtypes = [vp, i32, i32, i32, d, d, d, d, vp, i32]
         L.or_p.restype = d
@@ -187,22 +188,34 @@ class OraclePlan:
         lib().or_plan_dose_voxels(self._h, _p(f), _p(v), v.size, _p(dose), _p(amb), self.threads)
         return (dose, amb) if with_amb else dose
 
+    def pairs_voxels(self, voxels):
+        """Number of (voxel, beamlet) pairs eq. (1) sums at each listed voxel."""
+        v = np.ascontiguousarray(voxels, np.int64)
+        out = np.empty(v.size, np.int64)
+        lib().or_plan_pairs_voxels(self._h, _p(v), v.size, _p(out), self.threads)
+        return out
+
     def pair(self, v, i):
         out = np.zeros(9)
         lib().or_plan_pair(self._h, int(v), int(i), _p(out))
         return dict(D=out[0], inside=bool(out[1]), amb=bool(out[2]), x=out[3], y=out[4],
                     t=out[5], teq=out[6], L=out[7], q2=out[8])
 
-    def matrix(self):
-        """CSR of candidate entries: (rowptr, cols, vals, flags) with flags bit0 =
-        inside ROI and depth range, bit1 = decision within rounding margin."""
-        counts = np.empty(self.V, np.int64)
-        lib().or_plan_matrix_count(self._h, _p(counts), self.threads)
-        rowptr = np.zeros(self.V + 1, np.int64)
+    def matrix(self, voxels=None):
+        """CSR of candidate entries (rowptr, cols, vals, flags), rows = all voxels
+        or the listed ones; flags bit0 = inside ROI and depth range, bit1 =
+        decision within rounding margin."""
+        v = None if voxels is None else np.ascontiguousarray(voxels, np.int64)
+        n = self.V if v is None else v.size
+        pv = None if v is None else _p(v)
+        counts = np.empty(n, np.int64)
+        lib().or_plan_matrix_count(self._h, pv, n, _p(counts), self.threads)
+        rowptr = np.zeros(n + 1, np.int64)
         np.cumsum(counts, out=rowptr[1:])
         nnz = int(rowptr[-1])
         cols = np.empty(max(nnz, 1), np.int32)
         vals = np.empty(max(nnz, 1), np.float64)
         flags = np.empty(max(nnz, 1), np.uint8)
-        lib().or_plan_matrix_fill(self._h, _p(rowptr), _p(cols), _p(vals), _p(flags), self.threads)
+        lib().or_plan_matrix_fill(self._h, pv, n, _p(rowptr), _p(cols), _p(vals), _p(flags),
+                                  self.threads)
         return rowptr, cols[:nnz], vals[:nnz], flags[:nnz]

@@ -1,0 +1,477 @@
+// C ABI of the DC-FSPB engine: argument checks, plan memory and the order of
+// the kernels on the plan's stream.  Every numerical step runs in the kernels
+// of k_prep.cu and k_dose.cu.
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+#include "dc_internal.cuh"
+
+namespace dc {
+
+static thread_local std::string g_last_error;
+static unsigned long long g_launches = 0;
+
+void count_launches(int n) { __atomic_fetch_add(&g_launches, (unsigned long long)n, __ATOMIC_RELAXED); }
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+dc_status cuda_fail(cudaError_t e, const char* what)
+{
+    set_error(std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+    return e == cudaErrorMemoryAllocation ? DC_ENOMEM : DC_ECUDA;
+}
+
+static dc_status invalid(const std::string& msg)
+{
+    set_error(msg);
+    return DC_EINVAL;
+}
+
+template <typename T>
+static cudaError_t dalloc(T** p, size_t n)
+{
+    return cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T) > 0 ? n * sizeof(T) : 16);
+}
+
+}  // namespace dc
+
+using namespace dc;
+
+dc::PlanView dc_plan::view() const
+{
+    PlanView v{};
+    v.nx = grid.nx; v.ny = grid.ny; v.nz = grid.nz;
+    v.n_beams = n_beams;
+    v.B = B;
+    v.Kmax = Kmax;
+    v.dx = grid.dx; v.dy = grid.dy; v.dz = grid.dz;
+    v.ox = grid.ox; v.oy = grid.oy; v.oz = grid.oz;
+    v.d = d;
+    v.inv_d = 1.0f / d;
+    v.roi = coeffs.roi_radius;
+    v.R2 = coeffs.roi_radius * coeffs.roi_radius;
+    v.bx = bx; v.by = by;
+    v.x0 = 0.5f * bx; v.y0 = 0.5f * by;
+    v.wscale = coeffs.density_correction ? 1.0f : 0.0f;
+    v.A = d_A; v.a_nt = coeffs.a_nt; v.a_nth = coeffs.a_ntheta; v.inv_adt = 1.0f / coeffs.a_dt;
+    v.water = d_water; v.w_n = coeffs.w_n; v.inv_wdt = 1.0f / coeffs.w_dt;
+    v.fac = d_fac;
+    v.beams = d_beams;
+    v.bl = d_bl;
+    v.tab = d_tab;
+    return v;
+}
+
+static void free_plan(dc_plan* p)
+{
+    if (!p) return;
+    void* bufs[] = {p->d_rho, p->d_rhos, p->d_tmp, p->d_fac, p->d_beams, p->d_bl, p->d_theta,
+                    p->d_tab, p->d_A, p->d_water, p->d_dens, p->d_beamin, p->d_fluence,
+                    p->d_dose, p->d_rowcount, p->d_rowptr, p->d_scan_tmp, p->d_mcols, p->d_mvals};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    delete p;
+}
+
+extern "C" {
+
+const char* dc_last_error(void) { return g_last_error.c_str(); }
+
+const char* dc_status_str(dc_status s)
+{
+    switch (s) {
+        case DC_OK: return "DC_OK";
+        case DC_EINVAL: return "DC_EINVAL";
+        case DC_ENOMEM: return "DC_ENOMEM";
+        case DC_ECUDA: return "DC_ECUDA";
+        case DC_ETIMEOUT: return "DC_ETIMEOUT";
+        case DC_EUNSUPPORTED: return "DC_EUNSUPPORTED";
+    }
+    return "DC_UNKNOWN";
+}
+
+static dc_status check_inputs(const float* ct, const dc_grid* g, const dc_beam* beams, int32_t nb,
+                              float bx, float by, const dc_kernel_coeffs* c, uint32_t flags)
+{
+    if (!ct || !g || !beams || !c) return invalid("dc_fspb_create: NULL argument");
+    if (g->nx < 1 || g->ny < 1 || g->nz < 1) return invalid("dc_fspb_create: empty grid");
+    if ((int64_t)g->nx * g->ny * g->nz > (int64_t)1 << 31)
+        return invalid("dc_fspb_create: grid larger than 2^31 voxels");
+    if (!(g->dx > 0 && g->dy > 0 && g->dz > 0) || !isfinite(g->ox) || !isfinite(g->oy) || !isfinite(g->oz))
+        return invalid("dc_fspb_create: voxel size must be positive and the origin finite");
+    if (nb < 1 || nb > 64) return invalid("dc_fspb_create: n_beams must be in [1, 64]");
+    if (!(bx > 0 && by > 0)) return invalid("dc_fspb_create: beamlet size must be positive");
+    if (!c->A || !c->water || !c->dens) return invalid("dc_fspb_create: NULL commissioning table");
+    if (c->a_nt < 2 || c->a_ntheta < 2 || c->w_n < 2 || c->f_n < 2)
+        return invalid("dc_fspb_create: every table needs at least 2 entries per axis");
+    if (!(c->a_dt > 0 && c->a_dtheta > 0 && c->w_dt > 0 && c->f_drho > 0))
+        return invalid("dc_fspb_create: table steps must be positive");
+    if (!(c->roi_radius > 0) || !(c->smooth_sigma >= 0) || !isfinite(c->rho_surface))
+        return invalid("dc_fspb_create: bad roi_radius, smooth_sigma or rho_surface");
+    if (c->reserved[0] || c->reserved[1] || c->reserved[2])
+        return invalid("dc_fspb_create: reserved fields must be zero");
+    size_t sm = sizeof(float4) * c->w_n + sizeof(float) * (size_t)c->a_nt * c->a_ntheta;
+    if (sm > 160 * 1024) {
+        set_error("dc_fspb_create: A and water tables exceed 160 KiB of shared memory");
+        return DC_EUNSUPPORTED;
+    }
+    double vmin = fmin((double)g->dx, fmin((double)g->dy, (double)g->dz));
+    if (c->smooth_sigma > 0 && ceil(3.0 * c->smooth_sigma / vmin) > 64) {
+        set_error("dc_fspb_create: smoothing radius above 64 voxels");
+        return DC_EUNSUPPORTED;
+    }
+    const double lo[3] = {g->ox - 0.5 * g->dx, g->oy - 0.5 * g->dy, g->oz - 0.5 * g->dz};
+    const double hi[3] = {g->ox + (g->nx - 0.5) * g->dx, g->oy + (g->ny - 0.5) * g->dy,
+                          g->oz + (g->nz - 0.5) * g->dz};
+    for (int b = 0; b < nb; ++b) {
+        const dc_beam& bm = beams[b];
+        if (!(bm.sad > 0) || !(bm.field_x > 0) || !(bm.field_y > 0))
+            return invalid("dc_fspb_create: beam " + std::to_string(b) + " has a non-positive SAD or field");
+        double mx = bm.field_x / bx, my = bm.field_y / by;
+        if (fabs(mx - round(mx)) > 1e-3 || fabs(my - round(my)) > 1e-3)
+            return invalid("dc_fspb_create: beam " + std::to_string(b) + " field is not a multiple of the beamlet size");
+        // beam frame (same convention as the geometry kernel) to check the source
+        const double deg = M_PI / 180.0, gt = bm.gantry_deg * deg, ct_ = bm.couch_deg * deg;
+        double ez[3] = {-sin(gt), cos(gt), 0.0};
+        double x = ez[0], z = ez[2];
+        ez[0] = cos(ct_) * x + sin(ct_) * z;
+        ez[2] = -sin(ct_) * x + cos(ct_) * z;
+        double src[3];
+        for (int q = 0; q < 3; ++q) src[q] = bm.iso[q] - bm.sad * ez[q];
+        // every grid corner must lie in front of the source
+        for (int corner = 0; corner < 8; ++corner) {
+            double p[3] = {(corner & 1) ? hi[0] : lo[0], (corner & 2) ? hi[1] : lo[1],
+                           (corner & 4) ? hi[2] : lo[2]};
+            double zz = (p[0] - src[0]) * ez[0] + (p[1] - src[1]) * ez[1] + (p[2] - src[2]) * ez[2];
+            if (!(zz > 1e-2))
+                return invalid("dc_fspb_create: beam " + std::to_string(b) +
+                               ": the grid must lie entirely in front of the source");
+        }
+    }
+    if (!(flags & DC_DEVICE_PTRS)) {
+        int64_t V = (int64_t)g->nx * g->ny * g->nz;
+        for (int64_t v = 0; v < V; ++v)
+            if (!(ct[v] >= 0.f) || !isfinite(ct[v]))
+                return invalid("dc_fspb_create: density must be finite and >= 0 (voxel " + std::to_string(v) + ")");
+    }
+    return DC_OK;
+}
+
+// Algorithm A1 steps 1-6 on the plan's stream for density `ct`.
+static dc_status compute_density_steps(dc_plan* p, const float* ct, uint32_t flags)
+{
+    cudaMemcpyKind k = (flags & DC_DEVICE_PTRS) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    DC_CUDA(cudaMemcpyAsync(p->d_rho, ct, p->V * sizeof(float), k, p->stream));
+    DC_CUDA(launch_smooth(p, p->coeffs.smooth_sigma));
+    DC_CUDA(launch_factors(p));
+    DC_CUDA(launch_beamlets(p));
+    p->pairs = -1;
+    return DC_OK;
+}
+
+static dc_status create_impl(dc_plan* p, const float* ct, uint32_t flags)
+{
+    const dc_grid& g = p->grid;
+    const dc_kernel_coeffs& c = p->coeffs;
+    const int64_t V = p->V;
+    double diag = sqrt((double)g.nx * g.dx * g.nx * g.dx + (double)g.ny * g.dy * g.ny * g.dy +
+                       (double)g.nz * g.dz * g.nz * g.dz);
+    p->Kmax = (int)ceil(diag / p->d) + 3;
+
+    DC_CUDA(dalloc(&p->d_rho, V));
+    DC_CUDA(dalloc(&p->d_rhos, V));
+    DC_CUDA(dalloc(&p->d_tmp, V));
+    DC_CUDA(dalloc(&p->d_fac, V));
+    DC_CUDA(dalloc(&p->d_beams, p->n_beams));
+    DC_CUDA(dalloc(&p->d_beamin, p->n_beams));
+    DC_CUDA(dalloc(&p->d_bl, p->B));
+    DC_CUDA(dalloc(&p->d_theta, p->B));
+    DC_CUDA(dalloc(&p->d_tab, (size_t)p->B * p->Kmax));
+    DC_CUDA(dalloc(&p->d_A, (size_t)c.a_nt * c.a_ntheta));
+    DC_CUDA(dalloc(&p->d_water, c.w_n));
+    DC_CUDA(dalloc(&p->d_dens, 6 * (size_t)c.f_n));
+    size_t nscan = (size_t)((V + 4095) / 4096) + 2;
+    DC_CUDA(cudaMalloc(&p->d_scan_tmp, nscan * sizeof(int64_t)));
+    p->scan_tmp_bytes = nscan * sizeof(int64_t);
+
+    // water table interleaved per depth sample: (u_1^w, u_2^w, omega_1^w, omega_2^w)
+    std::vector<float4> w(c.w_n);
+    for (int j = 0; j < c.w_n; ++j)
+        w[j] = make_float4(c.water[j], c.water[c.w_n + j], c.water[2 * c.w_n + j], c.water[3 * c.w_n + j]);
+    DC_CUDA(cudaMemcpyAsync(p->d_water, w.data(), w.size() * sizeof(float4), cudaMemcpyHostToDevice, p->stream));
+    DC_CUDA(cudaMemcpyAsync(p->d_A, c.A, sizeof(float) * (size_t)c.a_nt * c.a_ntheta,
+                            cudaMemcpyHostToDevice, p->stream));
+    DC_CUDA(cudaMemcpyAsync(p->d_dens, c.dens, sizeof(float) * 6 * (size_t)c.f_n, cudaMemcpyHostToDevice,
+                            p->stream));
+    DC_CUDA(cudaMemcpyAsync(p->d_beamin, p->beams.data(), sizeof(dc_beam) * p->n_beams,
+                            cudaMemcpyHostToDevice, p->stream));
+    dc_status s = compute_density_steps(p, ct, flags);
+    if (s != DC_OK) return s;
+    DC_CUDA(cudaStreamSynchronize(p->stream));
+    // the host copies of the tables are not kept
+    p->coeffs.A = nullptr;
+    p->coeffs.water = nullptr;
+    p->coeffs.dens = nullptr;
+    return DC_OK;
+}
+
+dc_status dc_fspb_create(const float* ct_density, const dc_grid* grid, const dc_beam* beams,
+                         int32_t n_beams, float beamlet_x, float beamlet_y,
+                         const dc_kernel_coeffs* coeffs, uint32_t flags, void* cuda_stream,
+                         dc_plan** out)
+{
+    if (!out) return invalid("dc_fspb_create: out is NULL");
+    *out = nullptr;
+    dc_status s = check_inputs(ct_density, grid, beams, n_beams, beamlet_x, beamlet_y, coeffs, flags);
+    if (s != DC_OK) return s;
+    dc_plan* p = new (std::nothrow) dc_plan();
+    if (!p) {
+        set_error("dc_fspb_create: host allocation failed");
+        return DC_ENOMEM;
+    }
+    p->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    p->grid = *grid;
+    p->V = (int64_t)grid->nx * grid->ny * grid->nz;
+    p->n_beams = n_beams;
+    p->bx = beamlet_x;
+    p->by = beamlet_y;
+    p->coeffs = *coeffs;
+    p->d = 0.5f * fminf(grid->dx, fminf(grid->dy, grid->dz));
+    p->beams.assign(beams, beams + n_beams);
+    int B = 0;
+    for (int b = 0; b < n_beams; ++b) {
+        int M = (int)lround(beams[b].field_x / beamlet_x), N = (int)lround(beams[b].field_y / beamlet_y);
+        p->M.push_back(M);
+        p->N.push_back(N);
+        p->first.push_back(B);
+        B += M * N;
+    }
+    p->B = B;
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) {
+        free_plan(p);
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    s = create_impl(p, ct_density, flags);
+    if (s != DC_OK) {
+        free_plan(p);
+        return s;
+    }
+    *out = p;
+    return DC_OK;
+}
+
+dc_status dc_fspb_set_density(dc_plan* plan, const float* ct_density, uint32_t flags)
+{
+    if (!plan || !ct_density) return invalid("dc_fspb_set_density: NULL argument");
+    if (!(flags & DC_DEVICE_PTRS)) {
+        for (int64_t v = 0; v < plan->V; ++v)
+            if (!(ct_density[v] >= 0.f) || !isfinite(ct_density[v]))
+                return invalid("dc_fspb_set_density: density must be finite and >= 0 (voxel " +
+                               std::to_string(v) + ")");
+    }
+    dc_status s = compute_density_steps(plan, ct_density, flags);
+    if (s != DC_OK) return s;
+    if (!(flags & DC_DEVICE_PTRS)) DC_CUDA(cudaStreamSynchronize(plan->stream));
+    return DC_OK;
+}
+
+dc_status dc_fspb_launch_count(uint64_t* n)
+{
+    if (!n) return invalid("dc_fspb_launch_count: NULL argument");
+    *n = __atomic_load_n(&g_launches, __ATOMIC_RELAXED);
+    return DC_OK;
+}
+
+dc_status dc_fspb_destroy(dc_plan* plan)
+{
+    if (plan) {
+        cudaStreamSynchronize(plan->stream);
+        free_plan(plan);
+    }
+    return DC_OK;
+}
+
+dc_status dc_fspb_n_beamlets(const dc_plan* plan, int32_t* n)
+{
+    if (!plan || !n) return invalid("dc_fspb_n_beamlets: NULL argument");
+    *n = plan->B;
+    return DC_OK;
+}
+
+dc_status dc_fspb_n_voxels(const dc_plan* plan, int64_t* n)
+{
+    if (!plan || !n) return invalid("dc_fspb_n_voxels: NULL argument");
+    *n = plan->V;
+    return DC_OK;
+}
+
+static dc_status ensure_staging(dc_plan* p, size_t nflu, size_t ndose)
+{
+    if (nflu > p->fluence_cap) {
+        if (p->d_fluence) cudaFree(p->d_fluence);
+        p->d_fluence = nullptr;
+        p->fluence_cap = 0;
+        DC_CUDA(dalloc(&p->d_fluence, nflu));
+        p->fluence_cap = nflu;
+    }
+    if (ndose > p->dose_cap) {
+        if (p->d_dose) cudaFree(p->d_dose);
+        p->d_dose = nullptr;
+        p->dose_cap = 0;
+        DC_CUDA(dalloc(&p->d_dose, ndose));
+        p->dose_cap = ndose;
+    }
+    return DC_OK;
+}
+
+dc_status dc_fspb_dose_batch(dc_plan* plan, const float* fluence, int32_t k, float* dose, uint32_t flags)
+{
+    if (!plan || !fluence || !dose) return invalid("dc_fspb_dose: NULL argument");
+    if (k < 1 || k > 64) return invalid("dc_fspb_dose_batch: k must be in [1, 64]");
+    const size_t nf = (size_t)k * plan->B, nd = (size_t)k * plan->V;
+    if (flags & DC_DEVICE_PTRS) {
+        DC_CUDA(launch_dose(plan, fluence, k, plan->B, dose, plan->V));
+        return DC_OK;
+    }
+    dc_status s = ensure_staging(plan, nf, nd);
+    if (s != DC_OK) return s;
+    DC_CUDA(cudaMemcpyAsync(plan->d_fluence, fluence, nf * sizeof(float), cudaMemcpyHostToDevice, plan->stream));
+    DC_CUDA(launch_dose(plan, plan->d_fluence, k, plan->B, plan->d_dose, plan->V));
+    DC_CUDA(cudaMemcpyAsync(dose, plan->d_dose, nd * sizeof(float), cudaMemcpyDeviceToHost, plan->stream));
+    DC_CUDA(cudaStreamSynchronize(plan->stream));
+    return DC_OK;
+}
+
+dc_status dc_fspb_dose(dc_plan* plan, const float* fluence, float* dose, uint32_t flags)
+{
+    return dc_fspb_dose_batch(plan, fluence, 1, dose, flags);
+}
+
+static dc_status ensure_pattern(dc_plan* p)
+{
+    if (p->pairs >= 0) return DC_OK;
+    if (!p->d_rowcount) DC_CUDA(dalloc(&p->d_rowcount, p->V));
+    if (!p->d_rowptr) DC_CUDA(dalloc(&p->d_rowptr, p->V + 1));
+    DC_CUDA(launch_count(p, p->d_rowcount));
+    int64_t* total = reinterpret_cast<int64_t*>(p->d_scan_tmp) + (p->scan_tmp_bytes / sizeof(int64_t) - 1);
+    DC_CUDA(launch_scan_counts(p, p->d_rowcount, p->d_rowptr, total));
+    int64_t h = 0;
+    DC_CUDA(cudaMemcpyAsync(&h, total, sizeof(int64_t), cudaMemcpyDeviceToHost, p->stream));
+    DC_CUDA(cudaStreamSynchronize(p->stream));
+    p->pairs = h;
+    return DC_OK;
+}
+
+dc_status dc_fspb_pair_count(dc_plan* plan, int64_t* pairs)
+{
+    if (!plan || !pairs) return invalid("dc_fspb_pair_count: NULL argument");
+    dc_status s = ensure_pattern(plan);
+    if (s != DC_OK) return s;
+    *pairs = plan->pairs;
+    return DC_OK;
+}
+
+dc_status dc_fspb_dose_matrix(dc_plan* plan, int32_t value_dtype, int64_t* rowptr, int32_t* cols,
+                              void* vals, uint32_t flags)
+{
+    if (!plan || !rowptr || !cols || !vals) return invalid("dc_fspb_dose_matrix: NULL argument");
+    if (value_dtype != DC_F32 && value_dtype != DC_BF16)
+        return invalid("dc_fspb_dose_matrix: value_dtype must be DC_F32 or DC_BF16");
+    dc_status s = ensure_pattern(plan);
+    if (s != DC_OK) return s;
+    const size_t nnz = (size_t)plan->pairs, vsz = value_dtype == DC_BF16 ? 2 : 4;
+    if (flags & DC_DEVICE_PTRS) {
+        DC_CUDA(cudaMemcpyAsync(rowptr, plan->d_rowptr, (plan->V + 1) * sizeof(int64_t),
+                                cudaMemcpyDeviceToDevice, plan->stream));
+        DC_CUDA(launch_fill(plan, plan->d_rowptr, cols, vals, value_dtype));
+        return DC_OK;
+    }
+    const size_t need = nnz * sizeof(int32_t) + 16;
+    if (need > plan->mstage_bytes) {
+        if (plan->d_mcols) cudaFree(plan->d_mcols);
+        if (plan->d_mvals) cudaFree(plan->d_mvals);
+        plan->d_mcols = nullptr;
+        plan->d_mvals = nullptr;
+        plan->mstage_bytes = 0;
+        DC_CUDA(cudaMalloc(&plan->d_mcols, need));
+        DC_CUDA(cudaMalloc(&plan->d_mvals, need));
+        plan->mstage_bytes = need;
+    }
+    int32_t* dcols = plan->d_mcols;
+    void* dvals = plan->d_mvals;
+    cudaError_t e = launch_fill(plan, plan->d_rowptr, dcols, dvals, value_dtype);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(rowptr, plan->d_rowptr, (plan->V + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                            plan->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(cols, dcols, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, plan->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(vals, dvals, nnz * vsz, cudaMemcpyDeviceToHost, plan->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(plan->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "dc_fspb_dose_matrix");
+    return DC_OK;
+}
+
+dc_status dc_fspb_get_smoothed(const dc_plan* plan, float* out, uint32_t flags)
+{
+    if (!plan || !out) return invalid("dc_fspb_get_smoothed: NULL argument");
+    cudaMemcpyKind k = (flags & DC_DEVICE_PTRS) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    DC_CUDA(cudaMemcpyAsync(out, plan->d_rhos, plan->V * sizeof(float), k, plan->stream));
+    DC_CUDA(cudaStreamSynchronize(plan->stream));
+    return DC_OK;
+}
+
+dc_status dc_fspb_get_beamlets(const dc_plan* plan, float* rec)
+{
+    if (!plan || !rec) return invalid("dc_fspb_get_beamlets: NULL argument");
+    std::vector<BeamletDev> bl(plan->B);
+    std::vector<float> th(plan->B);
+    DC_CUDA(cudaMemcpyAsync(bl.data(), plan->d_bl, sizeof(BeamletDev) * plan->B, cudaMemcpyDeviceToHost,
+                            plan->stream));
+    DC_CUDA(cudaMemcpyAsync(th.data(), plan->d_theta, sizeof(float) * plan->B, cudaMemcpyDeviceToHost,
+                            plan->stream));
+    DC_CUDA(cudaStreamSynchronize(plan->stream));
+    for (int i = 0; i < plan->B; ++i) {
+        float* r = rec + 16 * (size_t)i;
+        const BeamletDev& b = bl[i];
+        r[0] = b.n_lin.x; r[1] = b.n_lin.y; r[2] = b.n_lin.z;
+        r[3] = b.ex_tout.x; r[4] = b.ex_tout.y; r[5] = b.ex_tout.z;
+        r[6] = b.ey_wth.x; r[7] = b.ey_wth.y; r[8] = b.ey_wth.z;
+        r[9] = th[i];
+        r[10] = (float)b.meta.z;
+        r[11] = b.n_lin.w;
+        r[12] = b.n_lin.w + b.ex_tout.w;
+        r[13] = (float)b.meta.x;
+        r[14] = r[15] = 0.f;
+    }
+    return DC_OK;
+}
+
+dc_status dc_fspb_get_tables(const dc_plan* plan, int32_t i, float* teq, float* w1, float* w2, int32_t kmax,
+                             int32_t* K)
+{
+    if (!plan || !teq || !w1 || !w2 || !K) return invalid("dc_fspb_get_tables: NULL argument");
+    if (i < 0 || i >= plan->B) return invalid("dc_fspb_get_tables: beamlet index out of range");
+    BeamletDev b;
+    DC_CUDA(cudaMemcpyAsync(&b, plan->d_bl + i, sizeof(b), cudaMemcpyDeviceToHost, plan->stream));
+    DC_CUDA(cudaStreamSynchronize(plan->stream));
+    *K = b.meta.x;
+    int n = b.meta.x < kmax ? b.meta.x : kmax;
+    if (n <= 0) return DC_OK;
+    std::vector<float4> t(n);
+    DC_CUDA(cudaMemcpyAsync(t.data(), plan->d_tab + (size_t)i * plan->Kmax, n * sizeof(float4),
+                            cudaMemcpyDeviceToHost, plan->stream));
+    DC_CUDA(cudaStreamSynchronize(plan->stream));
+    for (int k = 0; k < n; ++k) {
+        teq[k] = t[k].x;
+        w1[k] = t[k].y;
+        w2[k] = t[k].z;
+    }
+    return DC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,127 @@
+// Internal declarations shared by the CUDA translation units of the DC-FSPB
+// engine (not part of the ABI; see include/dc_fspb.h for the public calls).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "dc_fspb.h"
+
+namespace dc {
+
+// Per-beam record written by the geometry kernel (FP32 copy of FP64 values).
+struct BeamDev {
+    float src[3];
+    float sad;
+    float ez[3];          // beam central axis (source -> isocentre)
+    float inv_cos_max;    // 1 / cos(largest beamlet angle of the field)
+    float ex[3];          // field axis e_x'
+    float half_fx;
+    float ey[3];          // field axis e_y'
+    float half_fy;
+    int M, N, first, pad;
+};
+
+// Per-beamlet record (64 bytes, four 16-byte vectors).
+struct BeamletDev {
+    float4 n_lin;     // unit direction n, L_in (source to body entry along the axis)
+    float4 ex_tout;   // lateral axis e_x'', t_out = L_out - L_in
+    float4 ey_wth;    // lateral axis e_y'', weight of the theta row l+1 in A
+    int4 meta;        // K (table samples), l (theta row of A), hit (0/1), beam
+};
+
+// Kernel-side view of a plan.
+struct PlanView {
+    int nx, ny, nz, n_beams, B, Kmax;
+    float dx, dy, dz, ox, oy, oz;
+    float d, inv_d;
+    float R2, roi;
+    float x0, y0, bx, by;
+    float wscale;                 // 1 with the density correction, 0 without
+    // commissioned tables (device copies)
+    const float* A; int a_nt, a_nth; float inv_adt;
+    const float4* water; int w_n; float inv_wdt;
+    // per-voxel factors f_u1(rho), f_u2(rho_hat), f_w1(rho_hat), f_w2(rho_hat)
+    const float4* fac;
+    const BeamDev* beams;
+    const BeamletDev* bl;
+    const float4* tab;            // [B][Kmax] (t_eq, omega_1^corr, omega_2^corr, 0)
+};
+
+}  // namespace dc
+
+struct dc_plan {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    dc_grid grid{};
+    int64_t V = 0;
+    int B = 0, n_beams = 0, Kmax = 0;
+    float bx = 0, by = 0, d = 0;
+    dc_kernel_coeffs coeffs{};
+    std::vector<dc_beam> beams;
+    std::vector<int> M, N, first;
+
+    // device memory owned by the plan
+    float* d_rho = nullptr;
+    float* d_rhos = nullptr;
+    float* d_tmp = nullptr;
+    float4* d_fac = nullptr;
+    dc::BeamDev* d_beams = nullptr;
+    dc::BeamletDev* d_bl = nullptr;
+    float* d_theta = nullptr;
+    float4* d_tab = nullptr;
+    float* d_A = nullptr;
+    float4* d_water = nullptr;
+    float* d_dens = nullptr;
+    dc_beam* d_beamin = nullptr;
+    // staging for calls with host pointers
+    float* d_fluence = nullptr;
+    size_t fluence_cap = 0;
+    float* d_dose = nullptr;
+    size_t dose_cap = 0;
+    // dose-deposition matrix pattern
+    int32_t* d_rowcount = nullptr;
+    int64_t* d_rowptr = nullptr;
+    int64_t pairs = -1;
+    void* d_scan_tmp = nullptr;
+    // device staging of the matrix for calls with host buffers
+    int32_t* d_mcols = nullptr;
+    void* d_mvals = nullptr;
+    size_t mstage_bytes = 0;
+    size_t scan_tmp_bytes = 0;
+
+    dc::PlanView view() const;
+};
+
+namespace dc {
+
+// number of kernels launched by the library (dc_fspb_launch_count)
+void count_launches(int n);
+
+// error plumbing -------------------------------------------------------------
+void set_error(const std::string& msg);
+dc_status cuda_fail(cudaError_t e, const char* what);
+
+#define DC_CUDA(call)                                                       \
+    do {                                                                    \
+        cudaError_t e_ = (call);                                            \
+        if (e_ != cudaSuccess) return dc::cuda_fail(e_, #call);             \
+    } while (0)
+
+// kernel launchers (defined in the kernel translation units) ------------------
+cudaError_t launch_smooth(const dc_plan* p, float sigma);
+cudaError_t launch_factors(const dc_plan* p);
+cudaError_t launch_beamlets(const dc_plan* p);
+cudaError_t launch_dose(const dc_plan* p, const float* fluence, int nf, int ldf, float* dose,
+                        int64_t ldd);
+cudaError_t launch_count(const dc_plan* p, int32_t* counts);
+cudaError_t launch_fill(const dc_plan* p, const int64_t* rowptr, int32_t* cols, void* vals,
+                        int value_dtype);
+cudaError_t launch_scan_counts(const dc_plan* p, const int32_t* counts, int64_t* rowptr,
+                               int64_t* total_dev);
+
+}  // namespace dc

@@ -1,0 +1,414 @@
+// Per-plan pre-pass kernels of the DC-FSPB engine:
+//   smoothing of the density (Algorithm A1 step 1 / A2 Kernel 1),
+//   per-voxel density-correction factors (the rho-dependent part of step 11),
+//   beamlet geometry, body entry/exit and depth tables (steps 2-6 / Kernels 2-4).
+#include <math.h>
+
+#include "dc_internal.cuh"
+
+namespace dc {
+namespace {
+
+constexpr int kMaxSmoothRadius = 64;
+
+struct SmoothArgs {
+    const float* in;
+    float* out;
+    int nx, ny, nz, r;
+    float w[2 * kMaxSmoothRadius + 1];
+};
+
+// One axis of the separable Gaussian (clamp-to-edge).  Threads run along x,
+// so the y and z passes read coalesced rows and the x pass hits L1.
+template <int AXIS>
+__global__ void __launch_bounds__(256) k_smooth_axis(const SmoothArgs a)
+{
+    int64_t V = (int64_t)a.nx * a.ny * a.nz;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        int i = (int)(v % a.nx);
+        int j = (int)((v / a.nx) % a.ny);
+        int k = (int)(v / ((int64_t)a.nx * a.ny));
+        float s = 0.f;
+        for (int q = -a.r; q <= a.r; ++q) {
+            int ii = i, jj = j, kk = k;
+            if (AXIS == 0) ii = min(max(i + q, 0), a.nx - 1);
+            if (AXIS == 1) jj = min(max(j + q, 0), a.ny - 1);
+            if (AXIS == 2) kk = min(max(k + q, 0), a.nz - 1);
+            s = fmaf(a.w[q + a.r], __ldg(a.in + ((int64_t)kk * a.ny + jj) * a.nx + ii), s);
+        }
+        a.out[v] = s;
+    }
+}
+
+__device__ __forceinline__ float lut1(const float* f, int n, float x0, float inv_h, float x)
+{
+    float s = fminf(fmaxf((x - x0) * inv_h, 0.f), (float)(n - 1));
+    int j = min((int)s, n - 2);
+    float w = s - (float)j;
+    float f0 = __ldg(f + j), f1 = __ldg(f + j + 1);
+    return fmaf(w, f1 - f0, f0);
+}
+
+__global__ void __launch_bounds__(256) k_factors(const float* __restrict__ rho,
+                                                 const float* __restrict__ rhos,
+                                                 const float* __restrict__ dens, int f_n,
+                                                 float f_rho0, float inv_drho, int dc, int64_t V,
+                                                 float4* __restrict__ fac)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        float4 f = make_float4(1.f, 1.f, 1.f, 1.f);
+        if (dc) {
+            float r = __ldg(rho + v), rs = __ldg(rhos + v);
+            f.x = lut1(dens + 0 * (size_t)f_n, f_n, f_rho0, inv_drho, r);
+            f.y = lut1(dens + 1 * (size_t)f_n, f_n, f_rho0, inv_drho, rs);
+            f.z = lut1(dens + 2 * (size_t)f_n, f_n, f_rho0, inv_drho, rs);
+            f.w = lut1(dens + 3 * (size_t)f_n, f_n, f_rho0, inv_drho, rs);
+        }
+        fac[v] = f;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Beamlet geometry + FP64 Siddon ray trace + depth tables, one thread per beamlet.
+
+constexpr int kMaxBeams = 64;
+
+struct BeamletArgs {
+    const dc_beam* beams;
+    const float* rho;
+    const float* dens;
+    int f_n;
+    float f_rho0, inv_drho;
+    int nx, ny, nz, B, n_beams, Kmax;
+    double dx, dy, dz, ox, oy, oz, d;
+    double bx, by;
+    float rho_surf;
+    int a_nth;
+    float inv_adth;
+    BeamDev* out_beams;
+    BeamletDev* out_bl;
+    float* out_theta;
+    float4* tab;
+    int first[kMaxBeams + 1];
+    int M[kMaxBeams];
+};
+
+__device__ __forceinline__ void rot_z(double a, double* v)
+{
+    double c = cos(a), s = sin(a), x = v[0], y = v[1];
+    v[0] = c * x - s * y;
+    v[1] = s * x + c * y;
+}
+__device__ __forceinline__ void rot_y(double a, double* v)
+{
+    double c = cos(a), s = sin(a), x = v[0], z = v[2];
+    v[0] = c * x + s * z;
+    v[2] = -s * x + c * z;
+}
+
+// Incremental (Amanatides-Woo form of Siddon's) voxel walk of the ray s + a n,
+// a in [amin, amax], calling visit(a0, a1, voxel) for every segment of positive
+// length.  The crossing parameters are FP64.
+struct Walk {
+    int idx[3], step[3];
+    double anext[3], adelta[3];
+    double acur, amax;
+};
+
+__device__ bool walk_init(const BeamletArgs& A, const double* s, const double* n, Walk& w)
+{
+    const int dims[3] = {A.nx, A.ny, A.nz};
+    const double del[3] = {A.dx, A.dy, A.dz};
+    const double org[3] = {A.ox, A.oy, A.oz};
+    double amin = 0.0, amax = 1e300;
+    for (int a = 0; a < 3; ++a) {
+        double p0 = org[a] - 0.5 * del[a], p1 = org[a] + (dims[a] - 0.5) * del[a];
+        if (fabs(n[a]) < 1e-15) {
+            if (s[a] <= p0 || s[a] >= p1) return false;
+            continue;
+        }
+        double t0 = (p0 - s[a]) / n[a], t1 = (p1 - s[a]) / n[a];
+        amin = fmax(amin, fmin(t0, t1));
+        amax = fmin(amax, fmax(t0, t1));
+    }
+    if (!(amin < amax)) return false;
+    for (int a = 0; a < 3; ++a) {
+        double p0 = org[a] - 0.5 * del[a];
+        double pos = s[a] + amin * n[a];
+        double f = (pos - p0) / del[a];
+        int id = (int)floor(f);
+        if (n[a] < 0 && f == floor(f)) id -= 1;
+        id = min(max(id, 0), dims[a] - 1);
+        w.idx[a] = id;
+        if (fabs(n[a]) < 1e-15) {
+            w.step[a] = 0;
+            w.anext[a] = 1e300;
+            w.adelta[a] = 1e300;
+        } else if (n[a] > 0) {
+            w.step[a] = 1;
+            w.anext[a] = (p0 + (id + 1) * del[a] - s[a]) / n[a];
+            w.adelta[a] = del[a] / n[a];
+        } else {
+            w.step[a] = -1;
+            w.anext[a] = (p0 + id * del[a] - s[a]) / n[a];
+            w.adelta[a] = -del[a] / n[a];
+        }
+    }
+    w.acur = amin;
+    w.amax = amax;
+    return true;
+}
+
+template <typename F>
+__device__ void walk_run(const BeamletArgs& A, Walk w, F&& visit)
+{
+    const int dims[3] = {A.nx, A.ny, A.nz};
+    const int maxit = A.nx + A.ny + A.nz + 8;
+    for (int it = 0; it < maxit; ++it) {
+        int ax = 0;
+        double an = w.anext[0];
+        if (w.anext[1] < an) { an = w.anext[1]; ax = 1; }
+        if (w.anext[2] < an) { an = w.anext[2]; ax = 2; }
+        bool last = an >= w.amax;
+        if (last) an = w.amax;
+        if (an > w.acur)
+            visit(w.acur, an, ((int64_t)w.idx[2] * A.ny + w.idx[1]) * A.nx + w.idx[0]);
+        if (last) return;
+        w.idx[ax] += w.step[ax];
+        if (w.idx[ax] < 0 || w.idx[ax] >= dims[ax]) return;
+        w.anext[ax] += w.adelta[ax];
+        w.acur = an;
+    }
+}
+
+__device__ __forceinline__ float lut_dens(const BeamletArgs& A, int q, float r)
+{
+    return lut1(A.dens + (size_t)q * A.f_n, A.f_n, A.f_rho0, A.inv_drho, r);
+}
+
+// Cumulative integrals of rho, b_1(rho), b_2(rho) from L_in, sampled at
+// L_in + k d for k < K.  Acc is float for rays up to 40 cm in the grid and
+// double beyond.
+template <typename Acc>
+__device__ void fill_tables(const BeamletArgs& A, const Walk& w0, double L_in, int K,
+                            float4* __restrict__ tab)
+{
+    Acc cT = 0, c1 = 0, c2 = 0;
+    int k = 0;
+    walk_run(A, w0, [&](double a0, double a1, int64_t vox) {
+        if (a1 <= L_in || k >= K) return;
+        double lo = fmax(a0, L_in);
+        float r = __ldg(A.rho + vox);
+        Acc vr = (Acc)r, v1 = (Acc)lut_dens(A, 4, r), v2 = (Acc)lut_dens(A, 5, r);
+        while (k < K) {
+            double sk = L_in + k * A.d;
+            if (sk > a1) break;
+            Acc len = (Acc)(sk - lo);
+            tab[k] = make_float4((float)(cT + vr * len), (float)(c1 + v1 * len),
+                                 (float)(c2 + v2 * len), 0.f);
+            ++k;
+        }
+        Acc len = (Acc)(a1 - lo);
+        cT += vr * len;
+        c1 += v1 * len;
+        c2 += v2 * len;
+    });
+    for (; k < K; ++k) tab[k] = make_float4((float)cT, (float)c1, (float)c2, 0.f);
+}
+
+__global__ void __launch_bounds__(128) k_beamlets(const BeamletArgs A)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= A.B) return;
+    int b = 0;
+    while (b + 1 < A.n_beams && A.first[b + 1] <= i) ++b;
+    const dc_beam bm = A.beams[b];
+    const double deg = M_PI / 180.0;
+
+    // beam frame: gantry about +z, couch about +y, collimator about the axis
+    double ex[3] = {1, 0, 0}, ey[3] = {0, 0, 1}, ez[3] = {0, 1, 0};
+    rot_z(bm.gantry_deg * deg, ex); rot_z(bm.gantry_deg * deg, ey); rot_z(bm.gantry_deg * deg, ez);
+    rot_y(bm.couch_deg * deg, ex); rot_y(bm.couch_deg * deg, ey); rot_y(bm.couch_deg * deg, ez);
+    double cc = cos(bm.coll_deg * deg), sc = sin(bm.coll_deg * deg);
+    double fx_[3], fy_[3];
+    for (int q = 0; q < 3; ++q) {
+        fx_[q] = cc * ex[q] + sc * ey[q];
+        fy_[q] = -sc * ex[q] + cc * ey[q];
+    }
+    const double sad = bm.sad;
+    double src[3], iso[3] = {bm.iso[0], bm.iso[1], bm.iso[2]};
+    for (int q = 0; q < 3; ++q) src[q] = iso[q] - sad * ez[q];
+
+    const int M = A.M[b];
+    const int local = i - A.first[b];
+    const int n = local / M, m = local % M;
+    const double hfx = 0.5 * (double)bm.field_x, hfy = 0.5 * (double)bm.field_y;
+    const double a = -hfx + (m + 0.5) * A.bx, c = -hfy + (n + 0.5) * A.by;
+
+    double nv[3];
+    for (int q = 0; q < 3; ++q) nv[q] = iso[q] + a * fx_[q] + c * fy_[q] - src[q];
+    double nn = sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+    for (int q = 0; q < 3; ++q) nv[q] /= nn;
+    const double theta = atan2(sqrt(a * a + c * c), sad);
+    double exx[3], en = fx_[0] * nv[0] + fx_[1] * nv[1] + fx_[2] * nv[2];
+    for (int q = 0; q < 3; ++q) exx[q] = fx_[q] - en * nv[q];
+    double ne = sqrt(exx[0] * exx[0] + exx[1] * exx[1] + exx[2] * exx[2]);
+    for (int q = 0; q < 3; ++q) exx[q] /= ne;
+    double eyy[3] = {exx[1] * nv[2] - exx[2] * nv[1], exx[2] * nv[0] - exx[0] * nv[2],
+                     exx[0] * nv[1] - exx[1] * nv[0]};
+
+    if (local == 0) {
+        BeamDev o;
+        for (int q = 0; q < 3; ++q) {
+            o.src[q] = (float)src[q];
+            o.ez[q] = (float)ez[q];
+            o.ex[q] = (float)fx_[q];
+            o.ey[q] = (float)fy_[q];
+        }
+        o.sad = (float)sad;
+        o.inv_cos_max = (float)(sqrt(sad * sad + hfx * hfx + hfy * hfy) / sad);
+        o.half_fx = (float)hfx;
+        o.half_fy = (float)hfy;
+        o.M = M;
+        o.N = (A.first[b + 1] - A.first[b]) / M;
+        o.first = A.first[b];
+        o.pad = 0;
+        A.out_beams[b] = o;
+    }
+
+    // row of A(t_eq, theta) and the weight of the next row
+    float rl = fminf(fmaxf((float)theta * A.inv_adth, 0.f), (float)(A.a_nth - 1));
+    int l = min((int)rl, A.a_nth - 2);
+    float wl = rl - (float)l;
+
+    // steps 4-6: Siddon walk in FP64
+    Walk w;
+    int hit = 0, K = 0;
+    double L_in = 0, L_out = 0;
+    if (walk_init(A, src, nv, w)) {
+        double first_a = -1, last_a = -1;
+        const float surf = A.rho_surf;
+        walk_run(A, w, [&](double a0, double a1, int64_t vox) {
+            if (__ldg(A.rho + vox) > surf) {
+                if (first_a < 0) first_a = a0;
+                last_a = a1;
+            }
+        });
+        if (first_a >= 0) {
+            hit = 1;
+            L_in = first_a;
+            L_out = last_a;
+            K = max(2, (int)ceil((L_out - L_in) / A.d) + 1);
+            K = min(K, A.Kmax);
+            float4* tb = A.tab + (size_t)i * A.Kmax;
+            if (w.amax - w.acur > 40.0)
+                fill_tables<double>(A, w, L_in, K, tb);
+            else
+                fill_tables<float>(A, w, L_in, K, tb);
+        }
+    }
+    BeamletDev r;
+    r.n_lin = make_float4((float)nv[0], (float)nv[1], (float)nv[2], (float)L_in);
+    r.ex_tout = make_float4((float)exx[0], (float)exx[1], (float)exx[2], (float)(L_out - L_in));
+    r.ey_wth = make_float4((float)eyy[0], (float)eyy[1], (float)eyy[2], wl);
+    r.meta = make_int4(K, l, hit, b);
+    A.out_bl[i] = r;
+    A.out_theta[i] = (float)theta;
+}
+
+int grid_for(int64_t n, int threads)
+{
+    int64_t g = (n + threads - 1) / threads;
+    return (int)(g > 152 * 64 ? 152 * 64 : (g < 1 ? 1 : g));
+}
+
+void gauss_weights(double sigma, double delta, int* r, float* w)
+{
+    int rr = sigma > 0 ? (int)ceil(3.0 * sigma / delta) : 0;
+    double tmp[2 * kMaxSmoothRadius + 1], s = 0.0;
+    for (int j = -rr; j <= rr; ++j) {
+        tmp[j + rr] = sigma > 0 ? exp(-(j * delta) * (j * delta) / (2.0 * sigma * sigma)) : 1.0;
+        s += tmp[j + rr];
+    }
+    for (int j = 0; j < 2 * rr + 1; ++j) w[j] = (float)(tmp[j] / s);
+    *r = rr;
+}
+
+}  // namespace
+
+int smooth_radius(double sigma, double delta)
+{
+    return sigma > 0 ? (int)ceil(3.0 * sigma / delta) : 0;
+}
+
+cudaError_t launch_smooth(const dc_plan* p, float sigma)
+{
+    const dc_grid& g = p->grid;
+    SmoothArgs a;
+    a.nx = g.nx; a.ny = g.ny; a.nz = g.nz;
+    int gsz = grid_for(p->V, 256);
+    // x pass: rho -> rhos, y pass: rhos -> tmp, z pass: tmp -> rhos
+    gauss_weights(sigma, g.dx, &a.r, a.w);
+    a.in = p->d_rho; a.out = p->d_rhos;
+    k_smooth_axis<0><<<gsz, 256, 0, p->stream>>>(a);
+    gauss_weights(sigma, g.dy, &a.r, a.w);
+    a.in = p->d_rhos; a.out = p->d_tmp;
+    k_smooth_axis<1><<<gsz, 256, 0, p->stream>>>(a);
+    gauss_weights(sigma, g.dz, &a.r, a.w);
+    a.in = p->d_tmp; a.out = p->d_rhos;
+    k_smooth_axis<2><<<gsz, 256, 0, p->stream>>>(a);
+    count_launches(3);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_factors(const dc_plan* p)
+{
+    const dc_kernel_coeffs& c = p->coeffs;
+    k_factors<<<grid_for(p->V, 256), 256, 0, p->stream>>>(
+        p->d_rho, p->d_rhos, p->d_dens, c.f_n, c.f_rho0, 1.0f / c.f_drho, c.density_correction,
+        p->V, p->d_fac);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_beamlets(const dc_plan* p)
+{
+    if (p->n_beams > kMaxBeams) return cudaErrorInvalidValue;
+    BeamletArgs A;
+    const dc_grid& g = p->grid;
+    const dc_kernel_coeffs& c = p->coeffs;
+    A.beams = p->d_beamin;
+    A.rho = p->d_rho;
+    A.dens = p->d_dens;
+    A.f_n = c.f_n;
+    A.f_rho0 = c.f_rho0;
+    A.inv_drho = 1.0f / c.f_drho;
+    A.nx = g.nx; A.ny = g.ny; A.nz = g.nz;
+    A.B = p->B;
+    A.n_beams = p->n_beams;
+    A.Kmax = p->Kmax;
+    A.dx = g.dx; A.dy = g.dy; A.dz = g.dz;
+    A.ox = g.ox; A.oy = g.oy; A.oz = g.oz;
+    A.d = 0.5 * fmin((double)g.dx, fmin((double)g.dy, (double)g.dz));
+    A.bx = p->bx;
+    A.by = p->by;
+    A.rho_surf = c.rho_surface;
+    A.a_nth = c.a_ntheta;
+    A.inv_adth = 1.0f / c.a_dtheta;
+    A.out_beams = p->d_beams;
+    A.out_bl = p->d_bl;
+    A.out_theta = p->d_theta;
+    A.tab = p->d_tab;
+    for (int b = 0; b < p->n_beams; ++b) {
+        A.first[b] = p->first[b];
+        A.M[b] = p->M[b];
+    }
+    A.first[p->n_beams] = p->B;
+    k_beamlets<<<(p->B + 127) / 128, 128, 0, p->stream>>>(A);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace dc

@@ -1,0 +1,276 @@
+"""Python binding of the C-ABI library libdc_fspb.so (include/dc_fspb.h).
+
+Argument marshalling only: every step of the dose computation runs in the
+library's CUDA kernels.  Each ``dc_fspb_*`` function here has the name and the
+meaning of the C entry point it calls.  Arrays may be NumPy arrays (host
+memory) or contiguous float32 torch CUDA tensors (device memory; the
+DC_DEVICE_PTRS flag is then set for the call).  There is no CPU fallback: if
+the library is not built, loading it raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+DC_OK, DC_EINVAL, DC_ENOMEM, DC_ECUDA, DC_ETIMEOUT, DC_EUNSUPPORTED = range(6)
+DC_DEVICE_PTRS = 1
+DC_F32, DC_BF16 = 0, 1
+
+_lib = None
+
+
+class DcError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_STATUS = {0: "DC_OK", 1: "DC_EINVAL", 2: "DC_ENOMEM", 3: "DC_ECUDA", 4: "DC_ETIMEOUT",
+           5: "DC_EUNSUPPORTED"}
+
+
+class dc_grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("dx", C.c_float), ("dy", C.c_float), ("dz", C.c_float),
+                ("ox", C.c_float), ("oy", C.c_float), ("oz", C.c_float)]
+
+
+class dc_beam(C.Structure):
+    _fields_ = [("gantry_deg", C.c_float), ("couch_deg", C.c_float), ("coll_deg", C.c_float),
+                ("sad", C.c_float), ("iso", C.c_float * 3), ("field_x", C.c_float),
+                ("field_y", C.c_float)]
+
+
+class dc_kernel_coeffs(C.Structure):
+    _fields_ = [("A", C.c_void_p), ("a_nt", C.c_int32), ("a_ntheta", C.c_int32),
+                ("a_dt", C.c_float), ("a_dtheta", C.c_float),
+                ("water", C.c_void_p), ("w_n", C.c_int32), ("w_dt", C.c_float),
+                ("dens", C.c_void_p), ("f_n", C.c_int32), ("f_rho0", C.c_float), ("f_drho", C.c_float),
+                ("roi_radius", C.c_float), ("smooth_sigma", C.c_float), ("rho_surface", C.c_float),
+                ("density_correction", C.c_int32), ("reserved", C.c_int32 * 3)]
+
+
+EXPORTS = ["dc_last_error", "dc_status_str", "dc_fspb_create", "dc_fspb_destroy",
+           "dc_fspb_n_beamlets", "dc_fspb_n_voxels", "dc_fspb_dose", "dc_fspb_dose_batch",
+           "dc_fspb_pair_count", "dc_fspb_dose_matrix", "dc_fspb_get_smoothed",
+           "dc_fspb_get_beamlets", "dc_fspb_get_tables", "dc_fspb_set_density",
+           "dc_fspb_launch_count"]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Loads the built library (raises if it is missing: no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is not built; run paper_1103_1164_gb300.build.build() "
+                           "(nvcc for sm_103a) first")
+    L = C.CDLL(path)
+    vp, i32, i64, u32 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32
+    L.dc_last_error.restype = C.c_char_p
+    L.dc_status_str.restype = C.c_char_p
+    L.dc_status_str.argtypes = [C.c_int]
+    L.dc_fspb_create.argtypes = [vp, C.POINTER(dc_grid), C.POINTER(dc_beam), i32, C.c_float,
+                                 C.c_float, C.POINTER(dc_kernel_coeffs), u32, vp, C.POINTER(vp)]
+    L.dc_fspb_destroy.argtypes = [vp]
+    L.dc_fspb_n_beamlets.argtypes = [vp, C.POINTER(i32)]
+    L.dc_fspb_n_voxels.argtypes = [vp, C.POINTER(i64)]
+    L.dc_fspb_dose.argtypes = [vp, vp, vp, u32]
+    L.dc_fspb_dose_batch.argtypes = [vp, vp, i32, vp, u32]
+    L.dc_fspb_pair_count.argtypes = [vp, C.POINTER(i64)]
+    L.dc_fspb_dose_matrix.argtypes = [vp, i32, vp, vp, vp, u32]
+    L.dc_fspb_get_smoothed.argtypes = [vp, vp, u32]
+    L.dc_fspb_get_beamlets.argtypes = [vp, vp]
+    L.dc_fspb_get_tables.argtypes = [vp, i32, vp, vp, vp, i32, C.POINTER(i32)]
+    L.dc_fspb_set_density.argtypes = [vp, vp, u32]
+    L.dc_fspb_launch_count.argtypes = [C.POINTER(C.c_uint64)]
+    for name in EXPORTS:
+        if name not in ("dc_last_error", "dc_status_str"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(status):
+    if status != DC_OK:
+        raise DcError(status, load().dc_last_error().decode())
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a, dtype=np.float32):
+    """(pointer, device flag) of a host NumPy array or a CUDA torch tensor."""
+    if _is_torch(a):
+        if not a.is_cuda or not a.is_contiguous():
+            raise ValueError("torch tensors must be contiguous CUDA tensors")
+        return C.c_void_p(a.data_ptr()), DC_DEVICE_PTRS
+    if not (isinstance(a, np.ndarray) and a.flags.c_contiguous and a.dtype == dtype):
+        raise ValueError(f"host arrays must be C-contiguous {np.dtype(dtype).name} NumPy arrays")
+    return a.ctypes.data_as(C.c_void_p), 0
+
+
+def _same_kind(*flags):
+    if len(set(flags)) != 1:
+        raise ValueError("all array arguments of one call must be host arrays or all CUDA tensors")
+    return flags[0]
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return 0
+
+
+class Plan:
+    """Owns a dc_plan*; freed by dc_fspb_destroy (or when garbage-collected)."""
+
+    def __init__(self, handle, n_beamlets, n_voxels, grid_shape, keep=()):
+        self.handle = handle
+        self.n_beamlets = n_beamlets
+        self.n_voxels = n_voxels
+        self.shape = grid_shape
+        self._keep = keep
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.dc_fspb_destroy(self.handle)
+            self.handle = None
+
+
+def make_coeffs(comm):
+    """dc_kernel_coeffs from a synth.Commissioning (arrays kept alive by the caller)."""
+    A = np.ascontiguousarray(comm.A, np.float32)
+    W = np.ascontiguousarray(comm.water, np.float32)
+    D = np.ascontiguousarray(comm.dens, np.float32)
+    c = dc_kernel_coeffs(A.ctypes.data, A.shape[1], A.shape[0], comm.a_dt, comm.a_dtheta,
+                         W.ctypes.data, W.shape[1], comm.w_dt, D.ctypes.data, D.shape[1],
+                         comm.f_rho0, comm.f_drho, comm.roi_radius, comm.smooth_sigma,
+                         comm.rho_surface, int(comm.density_correction), (C.c_int32 * 3)(0, 0, 0))
+    return c, (A, W, D)
+
+
+def dc_fspb_create(ct_density, grid, beams, beamlet_x, beamlet_y, comm, stream=None) -> Plan:
+    """Builds a plan (ct_density: [nz, ny, nx] float32, host array or CUDA tensor)."""
+    L = load()
+    p_rho, flag = _ptr(ct_density)
+    g = dc_grid(grid.nx, grid.ny, grid.nz, grid.dx, grid.dy, grid.dz, grid.ox, grid.oy, grid.oz)
+    arr = (dc_beam * len(beams))()
+    for q, b in enumerate(beams):
+        arr[q] = dc_beam(b.gantry_deg, b.couch_deg, b.coll_deg, b.sad, (C.c_float * 3)(*b.iso),
+                         b.field_x, b.field_y)
+    coeffs, keep = make_coeffs(comm)
+    h = C.c_void_p()
+    s = _current_stream() if stream is None else stream
+    _check(L.dc_fspb_create(p_rho, C.byref(g), arr, len(beams), beamlet_x, beamlet_y,
+                            C.byref(coeffs), flag, C.c_void_p(s), C.byref(h)))
+    nb, nv = C.c_int32(), C.c_int64()
+    _check(L.dc_fspb_n_beamlets(h, C.byref(nb)))
+    _check(L.dc_fspb_n_voxels(h, C.byref(nv)))
+    return Plan(h, nb.value, nv.value, (grid.nz, grid.ny, grid.nx))
+
+
+def dc_fspb_create_from(plan_inputs, stream=None, device_density=None) -> Plan:
+    """dc_fspb_create from a synth.Plan."""
+    rho = plan_inputs.rho if device_density is None else device_density
+    return dc_fspb_create(np.ascontiguousarray(rho, np.float32) if device_density is None else rho,
+                          plan_inputs.grid, plan_inputs.beams, plan_inputs.beamlet_x,
+                          plan_inputs.beamlet_y, plan_inputs.comm, stream)
+
+
+def dc_fspb_set_density(plan: Plan, ct_density):
+    """Recomputes steps 1-6 of the plan for a new density on the same grid."""
+    p, flag = _ptr(ct_density)
+    _check(load().dc_fspb_set_density(plan.handle, p, flag))
+
+
+def dc_fspb_launch_count() -> int:
+    n = C.c_uint64()
+    _check(load().dc_fspb_launch_count(C.byref(n)))
+    return n.value
+
+
+def dc_fspb_destroy(plan: Plan):
+    if plan.handle:
+        _check(load().dc_fspb_destroy(plan.handle))
+        plan.handle = None
+
+
+def dc_fspb_dose(plan: Plan, fluence, dose=None):
+    """Eq. (1) into `dose` ([V] float32; allocated on the host if None)."""
+    if dose is None:
+        dose = np.empty(plan.shape, np.float32)
+    pf, f1 = _ptr(fluence)
+    pd, f2 = _ptr(dose)
+    if fluence.shape[-1] != plan.n_beamlets or int(np.prod(dose.shape)) != plan.n_voxels:
+        raise ValueError("fluence must have B entries and dose V entries")
+    _check(load().dc_fspb_dose(plan.handle, pf, pd, _same_kind(f1, f2)))
+    return dose
+
+
+def dc_fspb_dose_batch(plan: Plan, fluence, dose=None):
+    """Eq. (1) for k fluence vectors: fluence [k, B] -> dose [k, V]."""
+    k = fluence.shape[0]
+    if dose is None:
+        dose = np.empty((k,) + tuple(plan.shape), np.float32)
+    pf, f1 = _ptr(fluence)
+    pd, f2 = _ptr(dose)
+    _check(load().dc_fspb_dose_batch(plan.handle, pf, k, pd, _same_kind(f1, f2)))
+    return dose
+
+
+def dc_fspb_pair_count(plan: Plan) -> int:
+    n = C.c_int64()
+    _check(load().dc_fspb_pair_count(plan.handle, C.byref(n)))
+    return n.value
+
+
+def dc_fspb_dose_matrix(plan: Plan, value_dtype=DC_F32, rowptr=None, cols=None, vals=None):
+    """CSR (rowptr int64 [V+1], cols int32 [nnz], vals float32 or bf16 bits) of M[v, i] = D_i(r_v)."""
+    nnz = dc_fspb_pair_count(plan)
+    if rowptr is None:
+        rowptr = np.empty(plan.n_voxels + 1, np.int64)
+        cols = np.empty(max(nnz, 1), np.int32)
+        vals = np.empty(max(nnz, 1), np.float32 if value_dtype == DC_F32 else np.uint16)
+    pr, f1 = _ptr(rowptr, np.int64)
+    pc, f2 = _ptr(cols, np.int32)
+    pv, f3 = _ptr(vals, vals.dtype if not _is_torch(vals) else None)
+    _check(load().dc_fspb_dose_matrix(plan.handle, value_dtype, pr, pc, pv, _same_kind(f1, f2, f3)))
+    return rowptr, cols[:nnz] if not _is_torch(cols) else cols, vals[:nnz] if not _is_torch(vals) else vals
+
+
+def dc_fspb_get_smoothed(plan: Plan):
+    out = np.empty(plan.shape, np.float32)
+    p, _ = _ptr(out)
+    _check(load().dc_fspb_get_smoothed(plan.handle, p, 0))
+    return out
+
+
+def dc_fspb_get_beamlets(plan: Plan):
+    rec = np.empty((plan.n_beamlets, 16), np.float32)
+    p, _ = _ptr(rec)
+    _check(load().dc_fspb_get_beamlets(plan.handle, p))
+    return rec
+
+
+def dc_fspb_get_tables(plan: Plan, i: int, kmax: int = 1 << 16):
+    T, W1, W2 = (np.zeros(kmax, np.float32) for _ in range(3))
+    K = C.c_int32()
+    _check(load().dc_fspb_get_tables(plan.handle, int(i), _ptr(T)[0], _ptr(W1)[0], _ptr(W2)[0],
+                                     kmax, C.byref(K)))
+    k = min(K.value, kmax)
+    return T[:k], W1[:k], W2[:k]
