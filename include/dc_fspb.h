@@ -214,6 +214,22 @@ dc_status dc_fspb_get_beamlets(const dc_plan* plan, float* rec);
 dc_status dc_fspb_get_tables(const dc_plan* plan, int32_t i, float* teq, float* w1, float* w2,
                              int32_t kmax, int32_t* K);
 
+/*
+ * Autotuner of the plan's work decomposition.  The pair traversal of
+ * dc_fspb_dose / dc_fspb_dose_matrix bins, per beam, the voxels by their
+ * projection into the isocentre plane (tiles of `tile` cm) and their depth
+ * along the beam axis (slabs of `slab` cm), 32 voxels per warp.  This call
+ * times dc_fspb_dose for each candidate (tile in {0.35, 0.5, 0.75} cm, slab in
+ * {1, 2, 4} cm) with `fluence` [B] (host, or device with DC_DEVICE_PTRS), keeps
+ * the fastest for the plan, and returns it in *tile, *slab and its time in
+ * *best_ms (each output may be NULL).  Results do not depend on the choice
+ * (every voxel sums the same pairs in the same order).
+ * dc_fspb_set_density keeps the chosen cell size.  Synchronises the plan's
+ * stream.  Errors: DC_EINVAL, DC_ECUDA.
+ */
+dc_status dc_fspb_autotune(dc_plan* plan, const float* fluence, uint32_t flags, float* tile, float* slab,
+                           float* best_ms);
+
 /* Number of CUDA kernels this library has launched in the calling process
  * (all plans, all threads), for accounting of GPU work. */
 dc_status dc_fspb_launch_count(uint64_t* n);

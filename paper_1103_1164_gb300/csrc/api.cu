@@ -57,12 +57,13 @@ dc::PlanView dc_plan::view() const
     v.bx = bx; v.by = by;
     v.x0 = 0.5f * bx; v.y0 = 0.5f * by;
     v.wscale = coeffs.density_correction ? 1.0f : 0.0f;
-    v.A = d_A; v.a_nt = coeffs.a_nt; v.a_nth = coeffs.a_ntheta; v.inv_adt = 1.0f / coeffs.a_dt;
+    v.arow = d_arow; v.a_nt = coeffs.a_nt; v.inv_adt = 1.0f / coeffs.a_dt;
     v.water = d_water; v.w_n = coeffs.w_n; v.inv_wdt = 1.0f / coeffs.w_dt;
     v.fac = d_fac;
     v.beams = d_beams;
     v.bl = d_bl;
     v.tab = d_tab;
+    v.tabm = d_tabm;
     return v;
 }
 
@@ -70,8 +71,10 @@ static void free_plan(dc_plan* p)
 {
     if (!p) return;
     void* bufs[] = {p->d_rho, p->d_rhos, p->d_tmp, p->d_fac, p->d_beams, p->d_bl, p->d_theta,
-                    p->d_tab, p->d_A, p->d_water, p->d_dens, p->d_beamin, p->d_fluence,
-                    p->d_dose, p->d_rowcount, p->d_rowptr, p->d_scan_tmp, p->d_mcols, p->d_mvals};
+                    p->d_tab, p->d_arow, p->d_tabm, p->d_A, p->d_water, p->d_dens, p->d_beamin, p->d_fluence,
+                    p->d_dose, p->d_rowcount, p->d_rowptr, p->d_scan_tmp, p->d_mcols, p->d_mvals,
+                    p->d_bin, p->d_bounds, p->d_cellof, p->d_hist, p->d_nitems, p->d_base, p->d_work,
+                    p->d_items, p->d_part, p->d_bcount};
     for (void* b : bufs)
         if (b) cudaFree(b);
     delete p;
@@ -94,6 +97,82 @@ const char* dc_status_str(dc_status s)
     return "DC_UNKNOWN";
 }
 
+// Beam frame in FP64, same convention as the geometry kernel: at gantry 0 the
+// beam travels +y with e_x' = +x, e_y' = +z; gantry about +z, couch about +y,
+// collimator about the beam axis; source = iso - SAD e_z'.
+static void beam_frame_host(const dc_beam& bm, double* ex, double* ey, double* ez, double* src)
+{
+    const double deg = M_PI / 180.0;
+    double fx[3] = {1, 0, 0}, fy[3] = {0, 0, 1}, fz[3] = {0, 1, 0};
+    double* v3[3] = {fx, fy, fz};
+    const double cg = cos(bm.gantry_deg * deg), sg = sin(bm.gantry_deg * deg);
+    const double cc = cos(bm.couch_deg * deg), sc = sin(bm.couch_deg * deg);
+    for (double* v : v3) {
+        double x = v[0], y = v[1];
+        v[0] = cg * x - sg * y;
+        v[1] = sg * x + cg * y;
+        x = v[0];
+        double z = v[2];
+        v[0] = cc * x + sc * z;
+        v[2] = -sc * x + cc * z;
+    }
+    const double ck = cos(bm.coll_deg * deg), sk = sin(bm.coll_deg * deg);
+    for (int q = 0; q < 3; ++q) {
+        ex[q] = ck * fx[q] + sk * fy[q];
+        ey[q] = -sk * fx[q] + ck * fy[q];
+        ez[q] = fz[q];
+        src[q] = bm.iso[q] - bm.sad * fz[q];
+    }
+}
+
+// Beam's-eye-view binning: default cell size and the autotuner's candidates
+// (finest first: the plan's buffers are sized for the first pair).
+static const float kDefaultTile = 0.5f, kDefaultSlab = 2.0f;
+static const float kTuneTiles[] = {0.35f, 0.5f, 0.75f};
+static const float kTuneSlabs[] = {1.0f, 2.0f, 4.0f};
+
+// Beam's-eye-view binning grid of each beam (see k_bin.cu).
+static void bin_geometry(dc_plan* p, float tile, float slab)
+{
+    p->bin_tile = tile;
+    p->bin_slab = slab;
+    const dc_grid& g = p->grid;
+    p->bin_host.clear();
+    p->tiles_max = 0;
+    p->cells_max = 0;
+    for (int b = 0; b < p->n_beams; ++b) {
+        const dc_beam& bm = p->beams[b];
+        double ex[3], ey[3], ez[3], src[3];
+        beam_frame_host(bm, ex, ey, ez, src);
+        double zmin = 1e300, zmax = -1e300;
+        for (int corner = 0; corner < 8; ++corner) {
+            const double c[3] = {g.ox + ((corner & 1) ? (g.nx - 1) * (double)g.dx : 0.0),
+                                 g.oy + ((corner & 2) ? (g.ny - 1) * (double)g.dy : 0.0),
+                                 g.oz + ((corner & 4) ? (g.nz - 1) * (double)g.dz : 0.0)};
+            const double zz = (c[0] - src[0]) * ez[0] + (c[1] - src[1]) * ez[1] + (c[2] - src[2]) * ez[2];
+            zmin = fmin(zmin, zz);
+            zmax = fmax(zmax, zz);
+        }
+        const double hfx = 0.5 * bm.field_x, hfy = 0.5 * bm.field_y, sad = bm.sad;
+        const double inv_cos = sqrt(sad * sad + hfx * hfx + hfy * hfy) / sad;
+        BinGeom G;
+        G.tile = tile;
+        G.slab = slab;
+        G.rw_max = (float)(p->coeffs.roi_radius * (sad / zmin) * inv_cos * 1.001 + 2e-3);
+        const double ea = hfx + G.rw_max + tile, ec = hfy + G.rw_max + tile;
+        G.a0 = (float)-ea;
+        G.c0 = (float)-ec;
+        G.nta = (int)ceil(2 * ea / tile);
+        G.ntc = (int)ceil(2 * ec / tile);
+        G.zz0 = (float)(zmin - 1e-3);
+        G.nzs = std::max(1, (int)ceil((zmax - zmin + 2e-3) / slab));
+        G.cells = G.nta * G.ntc * G.nzs;
+        p->bin_host.push_back(G);
+        p->tiles_max = std::max(p->tiles_max, G.nta * G.ntc);
+        p->cells_max = std::max(p->cells_max, G.cells);
+    }
+}
+
 static dc_status check_inputs(const float* ct, const dc_grid* g, const dc_beam* beams, int32_t nb,
                               float bx, float by, const dc_kernel_coeffs* c, uint32_t flags)
 {
@@ -114,9 +193,9 @@ static dc_status check_inputs(const float* ct, const dc_grid* g, const dc_beam* 
         return invalid("dc_fspb_create: bad roi_radius, smooth_sigma or rho_surface");
     if (c->reserved[0] || c->reserved[1] || c->reserved[2])
         return invalid("dc_fspb_create: reserved fields must be zero");
-    size_t sm = sizeof(float4) * c->w_n + sizeof(float) * (size_t)c->a_nt * c->a_ntheta;
-    if (sm > 160 * 1024) {
-        set_error("dc_fspb_create: A and water tables exceed 160 KiB of shared memory");
+    size_t sm = 2 * sizeof(float4) * c->w_n;
+    if (sm > 96 * 1024) {
+        set_error("dc_fspb_create: the water table exceeds 96 KiB of shared memory (w_n > 3072)");
         return DC_EUNSUPPORTED;
     }
     double vmin = fmin((double)g->dx, fmin((double)g->dy, (double)g->dz));
@@ -134,14 +213,8 @@ static dc_status check_inputs(const float* ct, const dc_grid* g, const dc_beam* 
         double mx = bm.field_x / bx, my = bm.field_y / by;
         if (fabs(mx - round(mx)) > 1e-3 || fabs(my - round(my)) > 1e-3)
             return invalid("dc_fspb_create: beam " + std::to_string(b) + " field is not a multiple of the beamlet size");
-        // beam frame (same convention as the geometry kernel) to check the source
-        const double deg = M_PI / 180.0, gt = bm.gantry_deg * deg, ct_ = bm.couch_deg * deg;
-        double ez[3] = {-sin(gt), cos(gt), 0.0};
-        double x = ez[0], z = ez[2];
-        ez[0] = cos(ct_) * x + sin(ct_) * z;
-        ez[2] = -sin(ct_) * x + cos(ct_) * z;
-        double src[3];
-        for (int q = 0; q < 3; ++q) src[q] = bm.iso[q] - bm.sad * ez[q];
+        double ex[3], ey[3], ez[3], src[3];
+        beam_frame_host(bm, ex, ey, ez, src);
         // every grid corner must lie in front of the source
         for (int corner = 0; corner < 8; ++corner) {
             double p[3] = {(corner & 1) ? hi[0] : lo[0], (corner & 2) ? hi[1] : lo[1],
@@ -169,6 +242,7 @@ static dc_status compute_density_steps(dc_plan* p, const float* ct, uint32_t fla
     DC_CUDA(launch_smooth(p, p->coeffs.smooth_sigma));
     DC_CUDA(launch_factors(p));
     DC_CUDA(launch_beamlets(p));
+    DC_CUDA(launch_binning(p));
     p->pairs = -1;
     return DC_OK;
 }
@@ -190,18 +264,52 @@ static dc_status create_impl(dc_plan* p, const float* ct, uint32_t flags)
     DC_CUDA(dalloc(&p->d_beamin, p->n_beams));
     DC_CUDA(dalloc(&p->d_bl, p->B));
     DC_CUDA(dalloc(&p->d_theta, p->B));
-    DC_CUDA(dalloc(&p->d_tab, (size_t)p->B * p->Kmax));
+    DC_CUDA(dalloc(&p->d_tab, 2 * (size_t)p->B * p->Kmax));
+    DC_CUDA(dalloc(&p->d_arow, (size_t)p->B * c.a_nt));
+    p->merged = c.w_dt == p->d;
+    if (p->merged) DC_CUDA(dalloc(&p->d_tabm, 3 * (size_t)p->B * p->Kmax));
     DC_CUDA(dalloc(&p->d_A, (size_t)c.a_nt * c.a_ntheta));
-    DC_CUDA(dalloc(&p->d_water, c.w_n));
+    DC_CUDA(dalloc(&p->d_water, 2 * (size_t)c.w_n));
     DC_CUDA(dalloc(&p->d_dens, 6 * (size_t)c.f_n));
     size_t nscan = (size_t)((V + 4095) / 4096) + 2;
     DC_CUDA(cudaMalloc(&p->d_scan_tmp, nscan * sizeof(int64_t)));
     p->scan_tmp_bytes = nscan * sizeof(int64_t);
 
-    // water table interleaved per depth sample: (u_1^w, u_2^w, omega_1^w, omega_2^w)
-    std::vector<float4> w(c.w_n);
-    for (int j = 0; j < c.w_n; ++j)
-        w[j] = make_float4(c.water[j], c.water[c.w_n + j], c.water[2 * c.w_n + j], c.water[3 * c.w_n + j]);
+    // beam's-eye-view voxel lists and per-beam partial results
+    // capacity for the finest binning the autotuner may choose, then the default
+    bin_geometry(p, kTuneTiles[0], kTuneSlabs[0]);
+    const size_t nb = (size_t)p->n_beams;
+    DC_CUDA(dalloc(&p->d_bounds, nb * p->tiles_max));
+    DC_CUDA(dalloc(&p->d_hist, nb * p->cells_max));
+    p->tiles_cap = p->tiles_max;
+    p->cells_cap = p->cells_max;
+    bin_geometry(p, kDefaultTile, kDefaultSlab);
+    DC_CUDA(dalloc(&p->d_bin, nb));
+    DC_CUDA(dalloc(&p->d_cellof, nb * V));
+    DC_CUDA(dalloc(&p->d_nitems, nb));
+    DC_CUDA(dalloc(&p->d_base, nb + 1));
+    DC_CUDA(dalloc(&p->d_work, 2));
+    DC_CUDA(dalloc(&p->d_items, nb * (V + 32)));
+    DC_CUDA(dalloc(&p->d_part, nb * V));
+    p->part_cap = nb * V;
+    DC_CUDA(dalloc(&p->d_bcount, nb * V));
+    DC_CUDA(cudaMemcpyAsync(p->d_bin, p->bin_host.data(), nb * sizeof(BinGeom), cudaMemcpyHostToDevice,
+                            p->stream));
+
+    // water table per depth sample as value + slope to the next sample:
+    // (u_1^w, du_1^w, u_2^w, du_2^w), (omega_1^w, domega_1^w, omega_2^w, domega_2^w)
+    std::vector<float4> w(2 * (size_t)c.w_n);
+    auto vs = [&](int q, int j, float* val, float* slope) {
+        const float* r = c.water + (size_t)q * c.w_n;
+        *val = r[j];
+        *slope = j + 1 < c.w_n ? r[j + 1] - r[j] : 0.f;
+    };
+    for (int j = 0; j < c.w_n; ++j) {
+        float a[8];
+        for (int q = 0; q < 4; ++q) vs(q, j, &a[2 * q], &a[2 * q + 1]);
+        w[2 * j] = make_float4(a[0], a[1], a[2], a[3]);
+        w[2 * j + 1] = make_float4(a[4], a[5], a[6], a[7]);
+    }
     DC_CUDA(cudaMemcpyAsync(p->d_water, w.data(), w.size() * sizeof(float4), cudaMemcpyHostToDevice, p->stream));
     DC_CUDA(cudaMemcpyAsync(p->d_A, c.A, sizeof(float) * (size_t)c.a_nt * c.a_ntheta,
                             cudaMemcpyHostToDevice, p->stream));
@@ -280,6 +388,79 @@ dc_status dc_fspb_set_density(dc_plan* plan, const float* ct_density, uint32_t f
     return DC_OK;
 }
 
+static dc_status ensure_staging(dc_plan* p, size_t nflu, size_t ndose);
+
+// Re-bins every beam's voxels with the given cell size (see k_bin.cu).
+static dc_status rebin(dc_plan* p, float tile, float slab)
+{
+    bin_geometry(p, tile, slab);
+    if (p->tiles_max > p->tiles_cap || p->cells_max > p->cells_cap) {
+        set_error("rebin: binning grid larger than allocated");
+        return DC_EINVAL;
+    }
+    DC_CUDA(cudaMemcpyAsync(p->d_bin, p->bin_host.data(), p->bin_host.size() * sizeof(BinGeom),
+                            cudaMemcpyHostToDevice, p->stream));
+    DC_CUDA(launch_binning(p));
+    p->pairs = -1;
+    return DC_OK;
+}
+
+dc_status dc_fspb_autotune(dc_plan* plan, const float* fluence, uint32_t flags, float* tile, float* slab,
+                           float* best_ms)
+{
+    if (!plan || !fluence) return invalid("dc_fspb_autotune: NULL argument");
+    const float* f = fluence;
+    dc_status s = ensure_staging(plan, (size_t)plan->B, (size_t)plan->V);
+    if (s != DC_OK) return s;
+    if (!(flags & DC_DEVICE_PTRS)) {
+        DC_CUDA(cudaMemcpyAsync(plan->d_fluence, fluence, plan->B * sizeof(float), cudaMemcpyHostToDevice,
+                                plan->stream));
+        f = plan->d_fluence;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    DC_CUDA(cudaEventCreate(&e0));
+    cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(ce, "cudaEventCreate");
+    }
+    float best = 3.0e38f, bt = kDefaultTile, bs = kDefaultSlab;
+    s = DC_OK;
+    for (float t : kTuneTiles) {
+        for (float sl : kTuneSlabs) {
+            s = rebin(plan, t, sl);
+            if (s != DC_OK) break;
+            float ms = 0.f;
+            ce = launch_dose(plan, f, 1, plan->B, plan->d_dose, plan->V);
+            if (ce == cudaSuccess) ce = cudaEventRecord(e0, plan->stream);
+            if (ce == cudaSuccess) ce = launch_dose(plan, f, 1, plan->B, plan->d_dose, plan->V);
+            if (ce == cudaSuccess) ce = cudaEventRecord(e1, plan->stream);
+            if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+            if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+            if (ce != cudaSuccess) {
+                s = cuda_fail(ce, "dc_fspb_autotune");
+                break;
+            }
+            if (ms < best) {
+                best = ms;
+                bt = t;
+                bs = sl;
+            }
+        }
+        if (s != DC_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != DC_OK) return s;
+    s = rebin(plan, bt, bs);
+    if (s != DC_OK) return s;
+    DC_CUDA(cudaStreamSynchronize(plan->stream));
+    if (tile) *tile = bt;
+    if (slab) *slab = bs;
+    if (best_ms) *best_ms = best;
+    return DC_OK;
+}
+
 dc_status dc_fspb_launch_count(uint64_t* n)
 {
     if (!n) return invalid("dc_fspb_launch_count: NULL argument");
@@ -334,6 +515,16 @@ dc_status dc_fspb_dose_batch(dc_plan* plan, const float* fluence, int32_t k, flo
     if (!plan || !fluence || !dose) return invalid("dc_fspb_dose: NULL argument");
     if (k < 1 || k > 64) return invalid("dc_fspb_dose_batch: k must be in [1, 64]");
     const size_t nf = (size_t)k * plan->B, nd = (size_t)k * plan->V;
+    // per-beam partial doses: 16 fluence vectors per pass when k > 1
+    const size_t need = (size_t)plan->n_beams * (k > 1 ? 16 : 1) * plan->V;
+    if (need > plan->part_cap) {
+        DC_CUDA(cudaStreamSynchronize(plan->stream));
+        cudaFree(plan->d_part);
+        plan->d_part = nullptr;
+        plan->part_cap = 0;
+        DC_CUDA(dalloc(&plan->d_part, need));
+        plan->part_cap = need;
+    }
     if (flags & DC_DEVICE_PTRS) {
         DC_CUDA(launch_dose(plan, fluence, k, plan->B, dose, plan->V));
         return DC_OK;
@@ -444,7 +635,7 @@ dc_status dc_fspb_get_beamlets(const dc_plan* plan, float* rec)
         r[9] = th[i];
         r[10] = (float)b.meta.z;
         r[11] = b.n_lin.w;
-        r[12] = b.n_lin.w + b.ex_tout.w;
+        r[12] = b.ex_tout.w;
         r[13] = (float)b.meta.x;
         r[14] = r[15] = 0.f;
     }
@@ -462,14 +653,14 @@ dc_status dc_fspb_get_tables(const dc_plan* plan, int32_t i, float* teq, float* 
     *K = b.meta.x;
     int n = b.meta.x < kmax ? b.meta.x : kmax;
     if (n <= 0) return DC_OK;
-    std::vector<float4> t(n);
-    DC_CUDA(cudaMemcpyAsync(t.data(), plan->d_tab + (size_t)i * plan->Kmax, n * sizeof(float4),
+    std::vector<float4> t(2 * (size_t)n);
+    DC_CUDA(cudaMemcpyAsync(t.data(), plan->d_tab + 2 * (size_t)i * plan->Kmax, 2 * n * sizeof(float4),
                             cudaMemcpyDeviceToHost, plan->stream));
     DC_CUDA(cudaStreamSynchronize(plan->stream));
     for (int k = 0; k < n; ++k) {
-        teq[k] = t[k].x;
-        w1[k] = t[k].y;
-        w2[k] = t[k].z;
+        teq[k] = t[2 * k].x;
+        w1[k] = t[2 * k].z;
+        w2[k] = t[2 * k + 1].x;
     }
     return DC_OK;
 }

@@ -29,12 +29,30 @@ struct BeamDev {
 // Per-beamlet record (64 bytes, four 16-byte vectors).
 struct BeamletDev {
     float4 n_lin;     // unit direction n, L_in (source to body entry along the axis)
-    float4 ex_tout;   // lateral axis e_x'', t_out = L_out - L_in
+    float4 ex_tout;   // lateral axis e_x'', L_out (-1 if the axis misses the body)
     float4 ey_wth;    // lateral axis e_y'', weight of the theta row l+1 in A
     int4 meta;        // K (table samples), l (theta row of A), hit (0/1), beam
 };
 
+// Beam's-eye-view binning grid of one beam (see k_bin.cu): tiles of `tile` cm
+// in the isocentre plane starting at (a0, c0), depth slabs of `slab` cm
+// starting at zz0; cell = (tc * nta + ta) * nzs + slab index.
+struct BinGeom {
+    float a0, c0, tile, zz0, slab, rw_max;
+    int nta, ntc, nzs, cells;
+};
+
+constexpr int kMaxBeams = 64;
+
 // Kernel-side view of a plan.
+//
+// Table layouts (value + slope to the next sample, so one load and one fma
+// give a linear interpolation, and a sample index never needs a clamp):
+//   tab   [B][Kmax][2] float4: (t_eq, dt_eq, W1, dW1), (W2, dW2, 0, 0) at t = k d
+//   arow  [B][a_nt]    float2: (A_i, dA_i) at t_eq = j a_dt, where A_i is A
+//                      already interpolated at the beamlet's theta (the bilinear
+//                      lookup of A factors into theta then t_eq)
+//   water [w_n][2]     float4: (u1w, du1w, u2w, du2w), (w1w, dw1w, w2w, dw2w)
 struct PlanView {
     int nx, ny, nz, n_beams, B, Kmax;
     float dx, dy, dz, ox, oy, oz;
@@ -42,14 +60,18 @@ struct PlanView {
     float R2, roi;
     float x0, y0, bx, by;
     float wscale;                 // 1 with the density correction, 0 without
-    // commissioned tables (device copies)
-    const float* A; int a_nt, a_nth; float inv_adt;
+    int a_nt; float inv_adt;
+    const float2* arow;
     const float4* water; int w_n; float inv_wdt;
     // per-voxel factors f_u1(rho), f_u2(rho_hat), f_w1(rho_hat), f_w2(rho_hat)
     const float4* fac;
     const BeamDev* beams;
     const BeamletDev* bl;
-    const float4* tab;            // [B][Kmax] (t_eq, omega_1^corr, omega_2^corr, 0)
+    const float4* tab;
+    // when the water tables' step equals d: [B][Kmax][3] float4
+    //   (t_eq, dt_eq, O1, dO1), (O2, dO2, u1w, du1w), (u2w, du2w, 0, 0)
+    // with O_i = omega_i^w + omega_i^corr (times 0 without density correction)
+    const float4* tabm;
 };
 
 }  // namespace dc
@@ -74,6 +96,9 @@ struct dc_plan {
     dc::BeamletDev* d_bl = nullptr;
     float* d_theta = nullptr;
     float4* d_tab = nullptr;
+    float2* d_arow = nullptr;
+    float4* d_tabm = nullptr;        // merged depth + water tables (only when w_dt == d)
+    bool merged = false;
     float* d_A = nullptr;
     float4* d_water = nullptr;
     float* d_dens = nullptr;
@@ -83,6 +108,23 @@ struct dc_plan {
     size_t fluence_cap = 0;
     float* d_dose = nullptr;
     size_t dose_cap = 0;
+    // beam's-eye-view binning: per beam a list of voxels grouped by cell
+    std::vector<dc::BinGeom> bin_host;
+    dc::BinGeom* d_bin = nullptr;
+    int tiles_max = 0, cells_max = 0;   // of the current binning
+    int tiles_cap = 0, cells_cap = 0;   // allocated for
+    float bin_tile = 0.f, bin_slab = 0.f;
+    float2* d_bounds = nullptr;      // [n_beams][tiles_max] (min L_in, max L_out)
+    int32_t* d_cellof = nullptr;     // [n_beams][V]
+    int32_t* d_hist = nullptr;       // [n_beams][cells_max]
+    int32_t* d_nitems = nullptr;     // [n_beams]
+    int64_t* d_base = nullptr;       // [n_beams + 1] start of each beam's list (whole warps)
+    int32_t* d_work = nullptr;       // [0] warp work units, [1] work counter
+    int32_t* d_items = nullptr;      // [n_beams][V + 32]
+    float* d_part = nullptr;         // per-beam partial dose [n_beams][nf][V]
+    size_t part_cap = 0;
+    int32_t* d_bcount = nullptr;     // per-beam pair counts [n_beams][V]
+    int persist_ctas[4] = {0, 0, 0, 0};
     // dose-deposition matrix pattern
     int32_t* d_rowcount = nullptr;
     int64_t* d_rowptr = nullptr;
@@ -115,7 +157,8 @@ dc_status cuda_fail(cudaError_t e, const char* what);
 // kernel launchers (defined in the kernel translation units) ------------------
 cudaError_t launch_smooth(const dc_plan* p, float sigma);
 cudaError_t launch_factors(const dc_plan* p);
-cudaError_t launch_beamlets(const dc_plan* p);
+cudaError_t launch_beamlets(const dc_plan* p);   // also builds the theta-blended A rows
+cudaError_t launch_binning(const dc_plan* p);
 cudaError_t launch_dose(const dc_plan* p, const float* fluence, int nf, int ldf, float* dose,
                         int64_t ldd);
 cudaError_t launch_count(const dc_plan* p, int32_t* counts);

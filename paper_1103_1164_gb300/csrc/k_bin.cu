@@ -1,0 +1,200 @@
+// Beam's-eye-view binning of voxels, per beam, for the pair traversal.
+//
+// For beam b every voxel r is projected into the isocentre plane
+// (a, c) = SAD (r - s).(e_x', e_y') / (r - s).e_z' and binned into cells of
+// `tile` x `tile` cm in (a, c) and `slab` cm in depth (r - s).e_z'.  The voxels
+// of one warp then share almost the same set of beamlets whose ROI cylinder
+// can hold them (Algorithm A1 step 8), so the warp's traversal wastes few
+// lanes.  A voxel is dropped from beam b's list when no beamlet near its
+// projection can reach it in depth: every pair needs L_in <= |r_a| <= |r - s|
+// and sqrt(|r - s|^2 - R^2) <= |r_a| <= L_out, so a voxel with
+// |r - s| < min L_in or sqrt(|r - s|^2 - R^2) > max L_out over those beamlets
+// is in no pair.  The bounds are taken per tile over all beamlets whose axes
+// pass within (window radius + tile half-diagonal) of the tile centre.
+#include <math.h>
+
+#include "dc_internal.cuh"
+
+namespace dc {
+namespace {
+
+constexpr float kBig = 3.0e38f;
+
+// Per (beam, tile): min L_in and max L_out of the hit beamlets near the tile.
+__global__ void __launch_bounds__(256) k_bev_bounds(const BinGeom* __restrict__ G, int n_beams,
+                                                    const BeamDev* __restrict__ beams,
+                                                    const BeamletDev* __restrict__ bl, float bx, float by,
+                                                    float2* __restrict__ bounds, int tiles_max)
+{
+    const int b = blockIdx.y;
+    if (b >= n_beams) return;
+    const BinGeom g = G[b];
+    const int ntile = g.nta * g.ntc;
+    const int M = beams[b].M, N = beams[b].N, first = beams[b].first;
+    const float hfx = beams[b].half_fx, hfy = beams[b].half_fy;
+    const float reach = g.rw_max + 0.7072f * g.tile;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntile; t += gridDim.x * blockDim.x) {
+        const int ta = t % g.nta, tc = t / g.nta;
+        const float ca = g.a0 + (ta + 0.5f) * g.tile, cc = g.c0 + (tc + 0.5f) * g.tile;
+        const int n0 = max(0, (int)floorf((cc - reach + hfy) / by - 0.5f));
+        const int n1 = min(N - 1, (int)ceilf((cc + reach + hfy) / by - 0.5f));
+        const int m0 = max(0, (int)floorf((ca - reach + hfx) / bx - 0.5f));
+        const int m1 = min(M - 1, (int)ceilf((ca + reach + hfx) / bx - 0.5f));
+        float lmin = kBig, lmax = -kBig;
+        for (int n = n0; n <= n1; ++n) {
+            const float dc_ = cc - (-hfy + (n + 0.5f) * by);
+            for (int m = m0; m <= m1; ++m) {
+                const float da = ca - (-hfx + (m + 0.5f) * bx);
+                if (da * da + dc_ * dc_ > reach * reach) continue;
+                const BeamletDev& r = bl[first + n * M + m];
+                const float lout = __ldg(&r.ex_tout.w);
+                if (lout < 0.f) continue;            // axis misses the body
+                lmin = fminf(lmin, __ldg(&r.n_lin.w));
+                lmax = fmaxf(lmax, lout);
+            }
+        }
+        bounds[(size_t)b * tiles_max + t] = make_float2(lmin, lmax);
+    }
+}
+
+__device__ __forceinline__ int voxel_cell(const BinGeom& g, const BeamDev& bm, const float2* bounds,
+                                          float R2, float rx, float ry, float rz)
+{
+    const float vx = rx - bm.src[0], vy = ry - bm.src[1], vz = rz - bm.src[2];
+    const float zz = vx * bm.ez[0] + vy * bm.ez[1] + vz * bm.ez[2];
+    if (!(zz > 1e-3f)) return -1;
+    const float s = bm.sad / zz;
+    const float a = (vx * bm.ex[0] + vy * bm.ex[1] + vz * bm.ex[2]) * s;
+    const float c = (vx * bm.ey[0] + vy * bm.ey[1] + vz * bm.ey[2]) * s;
+    const int ta = (int)floorf((a - g.a0) / g.tile), tc = (int)floorf((c - g.c0) / g.tile);
+    if (ta < 0 || ta >= g.nta || tc < 0 || tc >= g.ntc) return -1;
+    const float2 lb = bounds[tc * g.nta + ta];
+    const float d2 = vx * vx + vy * vy + vz * vz;
+    const float dist = sqrtf(d2);
+    if (dist < lb.x - 1e-3f) return -1;
+    if (sqrtf(fmaxf(d2 - R2, 0.f)) > lb.y + 1e-3f) return -1;
+    const int zs = min(max((int)floorf((zz - g.zz0) / g.slab), 0), g.nzs - 1);
+    return (tc * g.nta + ta) * g.nzs + zs;
+}
+
+// Pass 1: cell of every (beam, voxel) (-1: not in the beam's list) and cell histograms.
+__global__ void __launch_bounds__(256) k_bin_hist(const PlanView P, const BinGeom* __restrict__ G,
+                                                  const float2* __restrict__ bounds, int tiles_max,
+                                                  int cells_max, int32_t* __restrict__ cellof,
+                                                  int32_t* __restrict__ hist)
+{
+    const int b = blockIdx.y;
+    const BinGeom g = G[b];
+    const BeamDev bm = P.beams[b];
+    const int64_t V = (int64_t)P.nx * P.ny * P.nz;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(v % P.nx), iy = (int)((v / P.nx) % P.ny), iz = (int)(v / ((int64_t)P.nx * P.ny));
+        const int cell = voxel_cell(g, bm, bounds + (size_t)b * tiles_max, P.R2, fmaf((float)ix, P.dx, P.ox),
+                                    fmaf((float)iy, P.dy, P.oy), fmaf((float)iz, P.dz, P.oz));
+        cellof[(size_t)b * V + v] = cell;
+        if (cell >= 0) atomicAdd(hist + (size_t)b * cells_max + cell, 1);
+    }
+}
+
+// Pass 2 (one CTA per beam): exclusive scan of the beam's cell histogram in
+// place (the histogram becomes the cell cursors), and the beam's item count.
+__global__ void __launch_bounds__(1024) k_bin_scan(const BinGeom* __restrict__ G, int cells_max,
+                                                   int32_t* __restrict__ hist, int32_t* __restrict__ n_items)
+{
+    __shared__ int32_t sw[33];
+    const int b = blockIdx.x;
+    const int cells = G[b].cells;
+    int32_t* h = hist + (size_t)b * cells_max;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t carry = 0;
+    for (int base = 0; base < cells; base += blockDim.x) {
+        const int q = base + threadIdx.x;
+        const int32_t x = q < cells ? h[q] : 0;
+        int32_t incl = x;
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) sw[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            int32_t w = lane < (int)(blockDim.x >> 5) ? sw[lane] : 0;
+            int32_t wi = w;
+            for (int o = 1; o < 32; o <<= 1) {
+                int32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += y;
+            }
+            sw[lane] = wi - w;
+            if (lane == 31) sw[32] = wi;
+        }
+        __syncthreads();
+        if (q < cells) h[q] = carry + incl - x + sw[warp];
+        carry += sw[32];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) n_items[b] = carry;
+}
+
+// Pass 3 (one thread): start of each beam's item list, padded to whole warps,
+// and the total number of warp work units.
+__global__ void k_bin_bases(int n_beams, const int32_t* __restrict__ n_items, int64_t* __restrict__ base,
+                            int32_t* __restrict__ work)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int64_t s = 0;
+    for (int b = 0; b < n_beams; ++b) {
+        base[b] = s;
+        s += ((int64_t)n_items[b] + 31) / 32 * 32;
+    }
+    base[n_beams] = s;
+    work[0] = (int32_t)(s / 32);
+}
+
+// Pass 4: scatter voxel indices into their beam's list, grouped by cell;
+// padding slots get -1.
+__global__ void __launch_bounds__(256) k_bin_scatter(int64_t V, int n_beams, int cells_max,
+                                                     const int32_t* __restrict__ cellof,
+                                                     int32_t* __restrict__ cursor,
+                                                     const int32_t* __restrict__ n_items,
+                                                     const int64_t* __restrict__ base,
+                                                     int32_t* __restrict__ items)
+{
+    const int b = blockIdx.y;
+    const int64_t b0 = base[b];
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int cell = cellof[(size_t)b * V + v];
+        if (cell >= 0) {
+            const int pos = atomicAdd(cursor + (size_t)b * cells_max + cell, 1);
+            items[b0 + pos] = (int32_t)v;
+        }
+    }
+    const int64_t n = n_items[b], pad_end = base[b + 1];
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b0 + n + t < pad_end) items[b0 + n + t] = -1;
+}
+
+}  // namespace
+
+cudaError_t launch_binning(const dc_plan* p)
+{
+    const PlanView P = p->view();
+    cudaError_t e = cudaMemsetAsync(p->d_hist, 0, sizeof(int32_t) * (size_t)p->n_beams * p->cells_max, p->stream);
+    if (e != cudaSuccess) return e;
+    dim3 gb((p->tiles_max + 255) / 256, p->n_beams);
+    k_bev_bounds<<<gb, 256, 0, p->stream>>>(p->d_bin, p->n_beams, p->d_beams, p->d_bl, p->bx, p->by,
+                                            p->d_bounds, p->tiles_max);
+    int gx = (int)std::min<int64_t>((p->V + 255) / 256, 2048);
+    dim3 gv(gx, p->n_beams);
+    k_bin_hist<<<gv, 256, 0, p->stream>>>(P, p->d_bin, p->d_bounds, p->tiles_max, p->cells_max, p->d_cellof,
+                                          p->d_hist);
+    k_bin_scan<<<p->n_beams, 1024, 0, p->stream>>>(p->d_bin, p->cells_max, p->d_hist, p->d_nitems);
+    k_bin_bases<<<1, 32, 0, p->stream>>>(p->n_beams, p->d_nitems, p->d_base, p->d_work);
+    k_bin_scatter<<<gv, 256, 0, p->stream>>>(p->V, p->n_beams, p->cells_max, p->d_cellof, p->d_hist,
+                                             p->d_nitems, p->d_base, p->d_items);
+    count_launches(5);
+    return cudaGetLastError();
+}
+
+}  // namespace dc

@@ -2,13 +2,19 @@
 // the per-(voxel, beamlet) evaluation of eq. (2) with the lateral kernel of
 // eqs. (3)-(4), and the fluence-weighted sum of eq. (1).
 //
-// Work decomposition (gather, no global atomics): each warp owns a 4x4x2
-// brick of voxels, one voxel per lane, and accumulates its dose in registers.
-// For each beam the warp projects its voxels into the isocentre plane and
-// walks, row by row, the union of the lanes' ROI discs over the beamlet grid;
-// each lane applies the exact ROI and depth-range test of its own pair.  The
-// same traversal, with the evaluation replaced by a counter or by a CSR
-// store, gives the dose-deposition matrix.
+// Work decomposition (gather, no global atomics): a warp takes 32 voxels of
+// one beam's list (voxels binned by their beam's-eye-view cell, k_bin.cu), one
+// voxel per lane, and accumulates that beam's dose in registers.  It projects
+// its voxels into the isocentre plane and walks, row by row, the union of the
+// lanes' ROI discs over the beamlet grid; each lane applies the exact ROI and
+// depth-range test of its own pair.  Per-beam partial doses are summed in
+// beam order afterwards.  The same traversal, with the evaluation replaced by
+// a counter or by a CSR store, gives the dose-deposition matrix.
+//
+// Hot-loop choices: table indices come from a magic-constant rounding (no
+// float->int conversion, which would share the quarter-rate pipe with the
+// exponentials); every table stores value + slope so an interpolation is one
+// load and one fma; eq. (4) is evaluated without branches.
 #include <math.h>
 
 #include "dc_internal.cuh"
@@ -19,6 +25,8 @@ namespace {
 constexpr int kWarps = 8;           // warps per CTA
 constexpr int kThreads = 32 * kWarps;
 constexpr float kLog2e = 1.4426950408889634f;
+constexpr int kStage = 16;          // CSR entries staged per lane before a coalesced flush
+constexpr int kStageLd = kStage + 1;
 
 enum Mode { kDose = 0, kCount = 1, kFill = 2 };
 
@@ -28,12 +36,15 @@ struct DoseArgs {
     int nf, ldf;
     float* dose;            // [nf][ldd]
     int64_t ldd;
-    int32_t* counts;        // kCount
+    float* part;            // kDose: per-beam partial dose [n_beams][NF][V]
+    int32_t* bcount;        // kCount: per-beam pair counts [n_beams][V]; kFill reads them
     const int64_t* rowptr;  // kFill
     int32_t* cols;
     void* vals;
     int value_dtype;
-    int bricks_x, bricks_y, bricks_z;
+    const int32_t* items;   // beam voxel lists (k_bin.cu)
+    const int64_t* base;    // [n_beams + 1]
+    int32_t* work;          // [0] work units, [1] counter
 };
 
 __device__ __forceinline__ float ex2(float x)
@@ -43,127 +54,182 @@ __device__ __forceinline__ float ex2(float x)
     return y;
 }
 
-// Eq. (4) with k = u log2(e): inside |x| <= x0 it is 1 - (e1 + e2)/2,
-// outside (e1 - e2)/2, with e1 = exp(-u ||x| - x0|), e2 = exp(-u (|x| + x0)).
-__device__ __forceinline__ float penumbra(float x, float k, float x0)
+// For 0 <= x < 2^22: an integer n with n <= x and x - n <= 1 (floor(x), or
+// floor(x) - 1 when x is an exact integer), as int and as float, by rounding
+// x - 1/2 against 1.5 * 2^23.  No conversion instruction is issued.
+__device__ __forceinline__ int grid_index(float x, float& frac)
 {
-    float ax = fabsf(x);
-    float e1 = ex2(-k * fabsf(ax - x0));
-    float e2 = ex2(-k * (ax + x0));
-    return ax <= x0 ? fmaf(-0.5f, e1 + e2, 1.0f) : 0.5f * (e1 - e2);
+    const float f = __fadd_rn(__fadd_rn(x, -0.5f), 12582912.0f);
+    frac = __fadd_rn(x, -__fadd_rn(f, -12582912.0f));
+    return __float_as_int(f) - 0x4B400000;
+}
+
+// Eq. (4) with k = u log2(e), kx0 = k x0: with e1 = exp(-u ||x| - x0|) and
+// e2 = exp(-u (|x| + x0)) it is (e1 - e2)/2 outside |x| <= x0 and
+// 1 - (e1 + e2)/2 inside, i.e. (e1 - e2)/2 + [inside] (1 - e1).
+__device__ __forceinline__ float penumbra(float x, float k, float kx0, float x0)
+{
+    const float ax = fabsf(x);
+    const float e1 = ex2(-k * fabsf(ax - x0));
+    const float e2 = ex2(fmaf(-k, ax, -kx0));
+    const float ins = ax <= x0 ? 1.0f : 0.0f;
+    return fmaf(0.5f, e1 - e2, fmaf(-ins, e1, ins));
 }
 
 struct Lane {
     float vx, vy, vz;     // r - source
-    float4 fac;           // density-correction factors of the voxel
+    float4 fac;           // log2(e) f_u1(rho), log2(e) f_u2(rho_hat), f_w1(rho_hat), f_w2(rho_hat)
     bool valid;
 };
 
 // Decides whether the lane's voxel is in beamlet i's ROI and depth range and,
 // if EVAL, returns D_i(r) of eq. (2) for unit fluence.
-template <bool EVAL>
+template <bool EVAL, bool MERGED>
 __device__ __forceinline__ bool pair(const PlanView& P, const Lane& ln, int i, float sad,
-                                     const float4* __restrict__ sW, const float* __restrict__ sA,
-                                     float& D)
+                                     const float4* __restrict__ sW, float& D)
 {
     const BeamletDev* bl = P.bl + i;
     const float4 q0 = __ldg(&bl->n_lin);
     const float4 q1 = __ldg(&bl->ex_tout);
     const float4 q2 = __ldg(&bl->ey_wth);
-    const int4 q3 = __ldg(&bl->meta);
-    float L = fmaf(ln.vx, q0.x, fmaf(ln.vy, q0.y, ln.vz * q0.z));
-    float xp = fmaf(ln.vx, q1.x, fmaf(ln.vy, q1.y, ln.vz * q1.z));
-    float yp = fmaf(ln.vx, q2.x, fmaf(ln.vy, q2.y, ln.vz * q2.z));
-    float t = L - q0.w;
-    bool in = ln.valid && q3.z && fmaf(xp, xp, yp * yp) <= P.R2 && t >= 0.f && t <= q1.w;
+    const float L = fmaf(ln.vx, q0.x, fmaf(ln.vy, q0.y, ln.vz * q0.z));
+    const float xp = fmaf(ln.vx, q1.x, fmaf(ln.vy, q1.y, ln.vz * q1.z));
+    const float yp = fmaf(ln.vx, q2.x, fmaf(ln.vy, q2.y, ln.vz * q2.z));
+    // in the ROI and between body entry and exit: L_in <= |r_a| <= L_out
+    const bool in = ln.valid && fmaf(xp, xp, yp * yp) <= P.R2 && L >= q0.w && L <= q1.w;
     if (!EVAL || !in) return in;
 
+    const float t = L - q0.w;                    // depth below the surface
     const float s = sad * __frcp_rn(L);          // SAD / |r_a|
     const float x = xp * s, y = yp * s;          // isocentre-plane coordinates
 
-    // radiological depth and omega_corr tables (steps 5-6), linear in t
-    const float kf = t * P.inv_d;
-    const int k = min((int)kf, q3.x - 2);
-    const float fr = kf - (float)k;
-    const float4* tb = P.tab + (size_t)i * P.Kmax + k;
-    const float4 e0 = __ldg(tb), e1 = __ldg(tb + 1);
-    const float teq = fmaf(fr, e1.x - e0.x, e0.x);
-    const float c1 = fmaf(fr, e1.y - e0.y, e0.y);
-    const float c2 = fmaf(fr, e1.z - e0.z, e0.z);
+    // radiological depth and omega_corr tables (steps 5-6) and the water
+    // parameters u_i^w(t), omega_i^w(t) (step 10), linear in t
+    float fr;
+    const int k = grid_index(t * P.inv_d, fr);
+    float teq, O1, O2, u1w, u2w;
+    if (MERGED) {
+        const float4* tb = P.tabm + 3 * ((size_t)i * P.Kmax + k);
+        const float4 e0 = __ldg(tb), e1 = __ldg(tb + 1), e2 = __ldg(tb + 2);
+        teq = fmaf(fr, e0.y, e0.x);
+        O1 = fmaf(fr, e0.w, e0.z);
+        O2 = fmaf(fr, e1.y, e1.x);
+        u1w = fmaf(fr, e1.w, e1.z);
+        u2w = fmaf(fr, e2.y, e2.x);
+    } else {
+        const float4* tb = P.tab + 2 * ((size_t)i * P.Kmax + k);
+        const float4 e0 = __ldg(tb), e1 = __ldg(tb + 1);
+        teq = fmaf(fr, e0.y, e0.x);
+        const float c1 = fmaf(fr, e0.w, e0.z);
+        const float c2 = fmaf(fr, e1.y, e1.x);
+        float fw;
+        const int jw = grid_index(fminf(t * P.inv_wdt, (float)(P.w_n - 1)), fw);
+        const float4 w0 = sW[2 * jw], w1 = sW[2 * jw + 1];
+        u1w = fmaf(fw, w0.y, w0.x);
+        u2w = fmaf(fw, w0.w, w0.z);
+        O1 = fmaf(P.wscale, c1, fmaf(fw, w1.y, w1.x));
+        O2 = fmaf(P.wscale, c2, fmaf(fw, w1.w, w1.z));
+    }
 
-    // water parameters u_i^w(t), omega_i^w(t) (step 10)
-    const float sw = fminf(t * P.inv_wdt, (float)(P.w_n - 1));
-    const int jw = min((int)sw, P.w_n - 2);
-    const float fw = sw - (float)jw;
-    const float4 w0 = sW[jw], w1 = sW[jw + 1];
-    const float u1w = fmaf(fw, w1.x - w0.x, w0.x);
-    const float u2w = fmaf(fw, w1.y - w0.y, w0.y);
-    const float o1w = fmaf(fw, w1.z - w0.z, w0.z);
-    const float o2w = fmaf(fw, w1.w - w0.w, w0.w);
-
-    // A(t_eq, theta), bilinear (step 9)
-    const float sa = fminf(fmaxf(teq * P.inv_adt, 0.f), (float)(P.a_nt - 1));
-    const int j = min((int)sa, P.a_nt - 2);
-    const float wt = sa - (float)j;
-    const float* Ar = sA + q3.y * P.a_nt + j;
-    const float a0 = fmaf(wt, Ar[1] - Ar[0], Ar[0]);
-    const float a1 = fmaf(wt, Ar[P.a_nt + 1] - Ar[P.a_nt], Ar[P.a_nt]);
-    const float Av = fmaf(q2.w, a1 - a0, a0);
+    // A(t_eq, theta) (step 9): the beamlet's theta-interpolated row, linear in t_eq
+    float fa;
+    const int j = grid_index(fminf(fmaxf(teq * P.inv_adt, 0.f), (float)(P.a_nt - 1)), fa);
+    const float2 ar = __ldg(P.arow + (size_t)i * P.a_nt + j);
+    const float Av = fmaf(fa, ar.y, ar.x);
 
     // density correction (step 11)
-    const float k1 = ln.fac.x * u1w * kLog2e;
-    const float k2 = ln.fac.y * u2w * kLog2e;
-    const float om1 = fmaxf(ln.fac.z * fmaf(P.wscale, c1, o1w), 0.f);
-    const float om2 = fmaxf(ln.fac.w * fmaf(P.wscale, c2, o2w), 0.f);
+    const float k1 = ln.fac.x * u1w, k2 = ln.fac.y * u2w;
+    const float om1 = fmaxf(ln.fac.z * O1, 0.f);
+    const float om2 = fmaxf(ln.fac.w * O2, 0.f);
 
     // eqs. (3) and (2)
-    const float F = fmaf(om1 * penumbra(x, k1, P.x0), penumbra(y, k1, P.y0),
-                         om2 * penumbra(x, k2, P.x0) * penumbra(y, k2, P.y0));
+    const float F = fmaf(om1 * penumbra(x, k1, k1 * P.x0, P.x0), penumbra(y, k1, k1 * P.y0, P.y0),
+                         om2 * penumbra(x, k2, k2 * P.x0, P.x0) * penumbra(y, k2, k2 * P.y0, P.y0));
     D = F * Av * (s * s);
     return true;
 }
 
-template <int MODE, int NF>
-__global__ void __launch_bounds__(kThreads) k_dose(const DoseArgs a)
+// Writes the staged CSR entries of all 32 lanes of the warp: half-warps take
+// one lane's run each, so every store covers consecutive entries of one row.
+__device__ __forceinline__ void flush_stage(const DoseArgs& a, const int* sc, const float* sv, int lane,
+                                            int& cnt, int64_t& pos, int64_t pend)
+{
+    const int half = lane >> 4, j = lane & 15;
+    __syncwarp();
+    for (int l2 = 0; l2 < 32; l2 += 2) {
+        const int owner = l2 + half;
+        const int c = __shfl_sync(0xffffffffu, cnt, owner);
+        const int64_t base = __shfl_sync(0xffffffffu, pos, owner);
+        const int64_t end = __shfl_sync(0xffffffffu, pend, owner);
+        if (j < c && base + j < end) {
+            a.cols[base + j] = sc[owner * kStageLd + j];
+            const float v = sv[owner * kStageLd + j];
+            if (a.value_dtype == DC_BF16)
+                reinterpret_cast<__nv_bfloat16*>(a.vals)[base + j] = __float2bfloat16_rn(v);
+            else
+                reinterpret_cast<float*>(a.vals)[base + j] = v;
+        }
+    }
+    __syncwarp();
+    pos += cnt;
+    cnt = 0;
+}
+
+// One warp work unit = 32 consecutive entries of one beam's voxel list (voxels
+// of one or two neighbouring beam's-eye-view cells; -1 entries are padding).
+// Persistent CTAs take units from a global counter.
+template <int MODE, int NF, bool MERGED>
+__global__ void __launch_bounds__(kThreads) k_pairs(const DoseArgs a)
 {
     extern __shared__ float4 smem[];
+    __shared__ int64_t s_base[kMaxBeams + 1];
     const PlanView& P = a.P;
     float4* sW = smem;
-    float* sA = reinterpret_cast<float*>(smem + P.w_n);
-    if (MODE != kCount) {
-        for (int q = threadIdx.x; q < P.w_n; q += blockDim.x) sW[q] = __ldg(P.water + q);
-        for (int q = threadIdx.x; q < P.a_nt * P.a_nth; q += blockDim.x) sA[q] = __ldg(P.A + q);
-        __syncthreads();
-    }
-
-    // brick of this CTA: 8 x 8 x 4 voxels, warp tiles of 4 x 4 x 2
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int bid = blockIdx.x;
-    const int bxi = bid % a.bricks_x;
-    bid /= a.bricks_x;
-    const int byi = bid % a.bricks_y;
-    const int bzi = bid / a.bricks_y;
-    const int ix = bxi * 8 + (warp & 1) * 4 + (lane & 3);
-    const int iy = byi * 8 + ((warp >> 1) & 1) * 4 + ((lane >> 2) & 3);
-    const int iz = bzi * 4 + (warp >> 2) * 2 + (lane >> 4);
+    int* sc = reinterpret_cast<int*>(smem + 2 * P.w_n) + warp * (32 * kStageLd);
+    float* sv = reinterpret_cast<float*>(smem + 2 * P.w_n) + kWarps * (32 * kStageLd) + warp * (32 * kStageLd);
+    if (MODE != kCount)
+        for (int q = threadIdx.x; q < 2 * P.w_n; q += blockDim.x) sW[q] = __ldg(P.water + q);
+    for (int q = threadIdx.x; q <= P.n_beams; q += blockDim.x) s_base[q] = a.base[q];
+    __syncthreads();
+    const int total = a.work[0];
+    const int64_t V = (int64_t)P.nx * P.ny * P.nz;
 
-    Lane ln;
-    ln.valid = ix < P.nx && iy < P.ny && iz < P.nz;
-    const int64_t v = ((int64_t)min(iz, P.nz - 1) * P.ny + min(iy, P.ny - 1)) * P.nx + min(ix, P.nx - 1);
-    // explicit fma: the count and fill passes must round these identically
-    const float rx = fmaf((float)ix, P.dx, P.ox), ry = fmaf((float)iy, P.dy, P.oy),
-                rz = fmaf((float)iz, P.dz, P.oz);
-    ln.fac = MODE == kCount ? make_float4(1, 1, 1, 1) : __ldg(P.fac + v);
+    for (;;) {
+        int w = 0;
+        if (lane == 0) w = atomicAdd(a.work + 1, 1);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if (w >= total) break;
+        const int64_t e0 = (int64_t)w * 32;
+        int b = 0;
+        while (b + 1 < P.n_beams && s_base[b + 1] <= e0) ++b;
+        const int32_t vi = __ldg(a.items + e0 + lane);
 
-    float acc[NF];
+        Lane ln;
+        ln.valid = vi >= 0;
+        const int64_t v = ln.valid ? vi : 0;
+        const int ix = (int)(v % P.nx), iy = (int)((v / P.nx) % P.ny), iz = (int)(v / ((int64_t)P.nx * P.ny));
+        // explicit fma: the count and fill passes must round these identically
+        const float rx = fmaf((float)ix, P.dx, P.ox), ry = fmaf((float)iy, P.dy, P.oy),
+                    rz = fmaf((float)iz, P.dz, P.oz);
+        if (MODE == kCount) {
+            ln.fac = make_float4(1, 1, 1, 1);
+        } else {
+            ln.fac = __ldg(P.fac + v);
+            ln.fac.x *= kLog2e;
+            ln.fac.y *= kLog2e;
+        }
+        float acc[NF];
 #pragma unroll
-    for (int q = 0; q < NF; ++q) acc[q] = 0.f;
-    int32_t cnt = 0;
-    int64_t pos = (MODE == kFill && ln.valid) ? a.rowptr[v] : 0;
-    // a fill never writes past its own row, whatever the rounding
-    const int64_t pend = (MODE == kFill && ln.valid) ? a.rowptr[v + 1] : 0;
+        for (int q = 0; q < NF; ++q) acc[q] = 0.f;
+        int32_t cnt = 0;
+        int64_t pos = 0, pend = 0;
+        if (MODE == kFill && ln.valid) {
+            pos = a.rowptr[v];
+            for (int bb = 0; bb < b; ++bb) pos += a.bcount[(size_t)bb * V + v];
+            pend = pos + a.bcount[(size_t)b * V + v];   // this beam's segment of the row
+        }
 
-    for (int b = 0; b < P.n_beams; ++b) {
         const BeamDev& bm = P.beams[b];
         const float sx = __ldg(&bm.src[0]), sy = __ldg(&bm.src[1]), sz = __ldg(&bm.src[2]);
         const float sad = __ldg(&bm.sad);
@@ -203,42 +269,63 @@ __global__ void __launch_bounds__(kThreads) k_dose(const DoseArgs a)
                 const int i = row + m;
                 if (MODE == kDose) {
                     float f[NF];
-                    bool any = false;
 #pragma unroll
-                    for (int q = 0; q < NF; ++q) {
-                        f[q] = q < a.nf ? __ldg(a.fluence + (size_t)q * a.ldf + i) : 0.f;
-                        any |= f[q] != 0.f;
-                    }
-                    if (!any) continue;
+                    for (int q = 0; q < NF; ++q) f[q] = q < a.nf ? __ldg(a.fluence + (size_t)q * a.ldf + i) : 0.f;
                     float D;
-                    if (pair<true>(P, ln, i, sad, sW, sA, D)) {
+                    if (pair<true, MERGED>(P, ln, i, sad, sW, D)) {
 #pragma unroll
                         for (int q = 0; q < NF; ++q) acc[q] = fmaf(f[q], D, acc[q]);
                     }
                 } else if (MODE == kCount) {
                     float D;
-                    cnt += pair<false>(P, ln, i, sad, sW, sA, D) ? 1 : 0;
+                    cnt += pair<false, false>(P, ln, i, sad, sW, D) ? 1 : 0;
                 } else {
                     float D;
-                    if (pair<true>(P, ln, i, sad, sW, sA, D) && pos < pend) {
-                        a.cols[pos] = i;
-                        if (a.value_dtype == DC_BF16)
-                            reinterpret_cast<__nv_bfloat16*>(a.vals)[pos] = __float2bfloat16_rn(D);
-                        else
-                            reinterpret_cast<float*>(a.vals)[pos] = D;
-                        ++pos;
+                    if (pair<true, MERGED>(P, ln, i, sad, sW, D)) {
+                        sc[lane * kStageLd + cnt] = i;
+                        sv[lane * kStageLd + cnt] = D;
+                        ++cnt;
                     }
+                    if (__any_sync(0xffffffffu, cnt == kStage)) flush_stage(a, sc, sv, lane, cnt, pos, pend);
                 }
             }
         }
-    }
-    if (!ln.valid) return;
-    if (MODE == kDose) {
+        if (MODE == kFill) {
+            flush_stage(a, sc, sv, lane, cnt, pos, pend);
+        } else if (ln.valid) {
+            if (MODE == kDose) {
 #pragma unroll
-        for (int q = 0; q < NF; ++q)
-            if (q < a.nf) a.dose[(size_t)q * a.ldd + v] = acc[q];
-    } else if (MODE == kCount) {
-        a.counts[v] = cnt;
+                for (int q = 0; q < NF; ++q)
+                    if (q < a.nf) a.part[((size_t)b * NF + q) * V + v] = acc[q];
+            } else {
+                a.bcount[(size_t)b * V + v] = cnt;
+            }
+        }
+    }
+}
+
+// dose[q][v] = sum over beams of the partial doses (fixed beam order).
+__global__ void __launch_bounds__(256) k_sum_beams(const float* __restrict__ part, int n_beams, int nfs,
+                                                   int nf, int64_t V, float* __restrict__ dose, int64_t ldd)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)nf * V;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int q = (int)(e / V);
+        const int64_t v = e % V;
+        float s = 0.f;
+        for (int b = 0; b < n_beams; ++b) s += __ldg(part + ((size_t)b * nfs + q) * V + v);
+        dose[(size_t)q * ldd + v] = s;
+    }
+}
+
+// rowcount[v] = number of pairs of voxel v over all beams.
+__global__ void __launch_bounds__(256) k_rowsum(const int32_t* __restrict__ bcount, int n_beams, int64_t V,
+                                                int32_t* __restrict__ rowcount)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
+        int32_t s = 0;
+        for (int b = 0; b < n_beams; ++b) s += __ldg(bcount + (size_t)b * V + v);
+        rowcount[v] = s;
     }
 }
 
@@ -332,28 +419,52 @@ DoseArgs make_args(const dc_plan* p)
 {
     DoseArgs a{};
     a.P = p->view();
-    a.bricks_x = (p->grid.nx + 7) / 8;
-    a.bricks_y = (p->grid.ny + 7) / 8;
-    a.bricks_z = (p->grid.nz + 3) / 4;
+    a.items = p->d_items;
+    a.base = p->d_base;
+    a.work = p->d_work;
+    a.bcount = p->d_bcount;
     return a;
 }
 
-size_t smem_bytes(const dc_plan* p)
+size_t smem_bytes(const dc_plan* p, int mode)
 {
-    return sizeof(float4) * p->coeffs.w_n + sizeof(float) * (size_t)p->coeffs.a_nt * p->coeffs.a_ntheta;
+    if (mode == kCount) return 0;
+    size_t s = 2 * sizeof(float4) * p->coeffs.w_n;
+    if (mode == kFill) s += 2 * sizeof(int) * kWarps * 32 * kStageLd;
+    return s;
+}
+
+int grid_for(int64_t n)
+{
+    int64_t g = (n + 255) / 256;
+    return (int)(g > 152 * 32 ? 152 * 32 : (g < 1 ? 1 : g));
+}
+
+// Persistent launch: as many CTAs as fit on the device at once.
+template <int MODE, int NF, bool MERGED>
+cudaError_t run_variant(const dc_plan* p, const DoseArgs& a)
+{
+    const size_t sm = smem_bytes(p, MODE);
+    auto kern = k_pairs<MODE, NF, MERGED>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, sm);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(p->d_work + 1, 0, sizeof(int32_t), p->stream);
+    if (e != cudaSuccess) return e;
+    kern<<<sms * (per_sm > 0 ? per_sm : 1), kThreads, sm, p->stream>>>(a);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 template <int MODE, int NF>
 cudaError_t run(const dc_plan* p, const DoseArgs& a)
 {
-    size_t sm = MODE == kCount ? 0 : smem_bytes(p);
-    cudaError_t e = cudaFuncSetAttribute(k_dose<MODE, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sm);
-    if (e != cudaSuccess) return e;
-    int nb = a.bricks_x * a.bricks_y * a.bricks_z;
-    k_dose<MODE, NF><<<nb, kThreads, sm, p->stream>>>(a);
-    count_launches(1);
-    return cudaGetLastError();
+    if (MODE != kCount && p->merged) return run_variant<MODE, NF, true>(p, a);
+    return run_variant<MODE, NF, false>(p, a);
 }
 
 }  // namespace
@@ -363,22 +474,33 @@ cudaError_t launch_dose(const dc_plan* p, const float* fluence, int nf, int ldf,
 {
     DoseArgs a = make_args(p);
     a.ldf = ldf;
-    a.ldd = ldd;
+    a.part = p->d_part;
     for (int q0 = 0; q0 < nf; q0 += 16) {
         a.fluence = fluence + (size_t)q0 * ldf;
-        a.dose = dose + (size_t)q0 * ldd;
         a.nf = nf - q0 < 16 ? nf - q0 : 16;
-        cudaError_t e = a.nf == 1 ? run<kDose, 1>(p, a) : run<kDose, 16>(p, a);
+        const int nfs = a.nf == 1 ? 1 : 16;
+        if (p->part_cap < (size_t)p->n_beams * nfs * p->V) return cudaErrorInvalidValue;
+        cudaError_t e = cudaMemsetAsync(p->d_part, 0, sizeof(float) * (size_t)p->n_beams * nfs * p->V, p->stream);
         if (e != cudaSuccess) return e;
+        e = nfs == 1 ? run<kDose, 1>(p, a) : run<kDose, 16>(p, a);
+        if (e != cudaSuccess) return e;
+        k_sum_beams<<<grid_for((int64_t)a.nf * p->V), 256, 0, p->stream>>>(p->d_part, p->n_beams, nfs, a.nf, p->V,
+                                                                          dose + (size_t)q0 * ldd, ldd);
+        count_launches(1);
     }
-    return cudaSuccess;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_count(const dc_plan* p, int32_t* counts)
 {
     DoseArgs a = make_args(p);
-    a.counts = counts;
-    return run<kCount, 1>(p, a);
+    cudaError_t e = cudaMemsetAsync(p->d_bcount, 0, sizeof(int32_t) * (size_t)p->n_beams * p->V, p->stream);
+    if (e != cudaSuccess) return e;
+    e = run<kCount, 1>(p, a);
+    if (e != cudaSuccess) return e;
+    k_rowsum<<<grid_for(p->V), 256, 0, p->stream>>>(p->d_bcount, p->n_beams, p->V, counts);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_fill(const dc_plan* p, const int64_t* rowptr, int32_t* cols, void* vals,

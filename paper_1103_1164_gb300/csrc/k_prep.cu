@@ -73,8 +73,6 @@ __global__ void __launch_bounds__(256) k_factors(const float* __restrict__ rho,
 // ---------------------------------------------------------------------------
 // Beamlet geometry + FP64 Siddon ray trace + depth tables, one thread per beamlet.
 
-constexpr int kMaxBeams = 64;
-
 struct BeamletArgs {
     const dc_beam* beams;
     const float* rho;
@@ -189,14 +187,25 @@ __device__ __forceinline__ float lut_dens(const BeamletArgs& A, int q, float r)
 }
 
 // Cumulative integrals of rho, b_1(rho), b_2(rho) from L_in, sampled at
-// L_in + k d for k < K.  Acc is float for rays up to 40 cm in the grid and
-// double beyond.
+// L_in + k d for k < K, stored as value + slope to the next sample:
+//   tab[2k] = (T_k, T_k+1 - T_k, W1_k, W1_k+1 - W1_k), tab[2k+1] = (W2_k, W2_k+1 - W2_k, 0, 0)
+// (zero slope at k = K - 1).  Acc is float for rays up to 40 cm in the grid
+// and double beyond.
 template <typename Acc>
 __device__ void fill_tables(const BeamletArgs& A, const Walk& w0, double L_in, int K,
                             float4* __restrict__ tab)
 {
     Acc cT = 0, c1 = 0, c2 = 0;
+    float pT = 0.f, p1 = 0.f, p2 = 0.f;
     int k = 0;
+    auto emit = [&](float T, float a, float b) {
+        if (k > 0) {
+            tab[2 * (k - 1)] = make_float4(pT, T - pT, p1, a - p1);
+            tab[2 * (k - 1) + 1] = make_float4(p2, b - p2, 0.f, 0.f);
+        }
+        pT = T; p1 = a; p2 = b;
+        ++k;
+    };
     walk_run(A, w0, [&](double a0, double a1, int64_t vox) {
         if (a1 <= L_in || k >= K) return;
         double lo = fmax(a0, L_in);
@@ -206,16 +215,62 @@ __device__ void fill_tables(const BeamletArgs& A, const Walk& w0, double L_in, i
             double sk = L_in + k * A.d;
             if (sk > a1) break;
             Acc len = (Acc)(sk - lo);
-            tab[k] = make_float4((float)(cT + vr * len), (float)(c1 + v1 * len),
-                                 (float)(c2 + v2 * len), 0.f);
-            ++k;
+            emit((float)(cT + vr * len), (float)(c1 + v1 * len), (float)(c2 + v2 * len));
         }
         Acc len = (Acc)(a1 - lo);
         cT += vr * len;
         c1 += v1 * len;
         c2 += v2 * len;
     });
-    for (; k < K; ++k) tab[k] = make_float4((float)cT, (float)c1, (float)c2, 0.f);
+    while (k < K) emit((float)cT, (float)c1, (float)c2);
+    tab[2 * (K - 1)] = make_float4(pT, 0.f, p1, 0.f);
+    tab[2 * (K - 1) + 1] = make_float4(p2, 0.f, 0.f, 0.f);
+}
+
+// Merged per-beamlet tables for plans whose water tables are sampled on the
+// same depth grid as the beamlet tables (w_dt == d): the water values at
+// sample k are the water table's knot k (clamped at its end, where its slope
+// is zero), so interpolating their sum with omega_corr in t is exactly the sum
+// of the two interpolations.
+__global__ void __launch_bounds__(256) k_merge_tables(const float4* __restrict__ tab,
+                                                      const float4* __restrict__ water, int w_n,
+                                                      const BeamletDev* __restrict__ bl, int B, int Kmax,
+                                                      float wscale, float4* __restrict__ tabm)
+{
+    const int64_t n = (int64_t)B * Kmax;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / Kmax), k = (int)(e % Kmax);
+        if (k >= __ldg(&bl[i].meta.x)) continue;
+        const float4 a = __ldg(tab + 2 * e), b = __ldg(tab + 2 * e + 1);
+        const int j = min(k, w_n - 1);
+        const float4 w0 = __ldg(water + 2 * j), w1 = __ldg(water + 2 * j + 1);
+        const float dw = k < w_n - 1 ? 1.f : 0.f;   // slope of the clamped water tables
+        tabm[3 * e] = make_float4(a.x, a.y, fmaf(wscale, a.z, w1.x), fmaf(wscale, a.w, dw * w1.y));
+        tabm[3 * e + 1] = make_float4(fmaf(wscale, b.x, w1.z), fmaf(wscale, b.y, dw * w1.w), w0.x, dw * w0.y);
+        tabm[3 * e + 2] = make_float4(w0.z, dw * w0.w, 0.f, 0.f);
+    }
+}
+
+// A(t_eq, theta) interpolated at each beamlet's theta, one row per beamlet,
+// stored as (value, slope to the next t_eq sample).
+__global__ void __launch_bounds__(256) k_arows(const float* __restrict__ A, int a_nt,
+                                               const BeamletDev* __restrict__ bl, int B,
+                                               float2* __restrict__ arow)
+{
+    const int64_t n = (int64_t)B * a_nt;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / a_nt), j = (int)(e % a_nt);
+        const int l = __ldg(&bl[i].meta.y);
+        const float w = __ldg(&bl[i].ey_wth.w);
+        const float* r0 = A + (size_t)l * a_nt;
+        const float* r1 = r0 + a_nt;
+        const float v = fmaf(w, __ldg(r1 + j) - __ldg(r0 + j), __ldg(r0 + j));
+        float dv = 0.f;
+        if (j + 1 < a_nt) dv = fmaf(w, __ldg(r1 + j + 1) - __ldg(r0 + j + 1), __ldg(r0 + j + 1)) - v;
+        arow[e] = make_float2(v, dv);
+    }
 }
 
 __global__ void __launch_bounds__(128) k_beamlets(const BeamletArgs A)
@@ -302,7 +357,7 @@ __global__ void __launch_bounds__(128) k_beamlets(const BeamletArgs A)
             L_out = last_a;
             K = max(2, (int)ceil((L_out - L_in) / A.d) + 1);
             K = min(K, A.Kmax);
-            float4* tb = A.tab + (size_t)i * A.Kmax;
+            float4* tb = A.tab + 2 * (size_t)i * A.Kmax;
             if (w.amax - w.acur > 40.0)
                 fill_tables<double>(A, w, L_in, K, tb);
             else
@@ -311,7 +366,7 @@ __global__ void __launch_bounds__(128) k_beamlets(const BeamletArgs A)
     }
     BeamletDev r;
     r.n_lin = make_float4((float)nv[0], (float)nv[1], (float)nv[2], (float)L_in);
-    r.ex_tout = make_float4((float)exx[0], (float)exx[1], (float)exx[2], (float)(L_out - L_in));
+    r.ex_tout = make_float4((float)exx[0], (float)exx[1], (float)exx[2], hit ? (float)L_out : -1.0f);
     r.ey_wth = make_float4((float)eyy[0], (float)eyy[1], (float)eyy[2], wl);
     r.meta = make_int4(K, l, hit, b);
     A.out_bl[i] = r;
@@ -408,6 +463,15 @@ cudaError_t launch_beamlets(const dc_plan* p)
     A.first[p->n_beams] = p->B;
     k_beamlets<<<(p->B + 127) / 128, 128, 0, p->stream>>>(A);
     count_launches(1);
+    k_arows<<<grid_for((int64_t)p->B * p->coeffs.a_nt, 256), 256, 0, p->stream>>>(
+        p->d_A, p->coeffs.a_nt, p->d_bl, p->B, p->d_arow);
+    count_launches(1);
+    if (p->merged) {
+        k_merge_tables<<<grid_for((int64_t)p->B * p->Kmax, 256), 256, 0, p->stream>>>(
+            p->d_tab, p->d_water, p->coeffs.w_n, p->d_bl, p->B, p->Kmax,
+            p->coeffs.density_correction ? 1.0f : 0.0f, p->d_tabm);
+        count_launches(1);
+    }
     return cudaGetLastError();
 }
 

@@ -58,7 +58,7 @@ EXPORTS = ["dc_last_error", "dc_status_str", "dc_fspb_create", "dc_fspb_destroy"
            "dc_fspb_n_beamlets", "dc_fspb_n_voxels", "dc_fspb_dose", "dc_fspb_dose_batch",
            "dc_fspb_pair_count", "dc_fspb_dose_matrix", "dc_fspb_get_smoothed",
            "dc_fspb_get_beamlets", "dc_fspb_get_tables", "dc_fspb_set_density",
-           "dc_fspb_launch_count"]
+           "dc_fspb_launch_count", "dc_fspb_autotune"]
 
 
 def library_path() -> str:
@@ -93,6 +93,8 @@ def load():
     L.dc_fspb_get_tables.argtypes = [vp, i32, vp, vp, vp, i32, C.POINTER(i32)]
     L.dc_fspb_set_density.argtypes = [vp, vp, u32]
     L.dc_fspb_launch_count.argtypes = [C.POINTER(C.c_uint64)]
+    L.dc_fspb_autotune.argtypes = [vp, vp, u32, C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                   C.POINTER(C.c_float)]
     for name in EXPORTS:
         if name not in ("dc_last_error", "dc_status_str"):
             getattr(L, name).restype = C.c_int
@@ -196,6 +198,14 @@ def dc_fspb_set_density(plan: Plan, ct_density):
     """Recomputes steps 1-6 of the plan for a new density on the same grid."""
     p, flag = _ptr(ct_density)
     _check(load().dc_fspb_set_density(plan.handle, p, flag))
+
+
+def dc_fspb_autotune(plan: Plan, fluence):
+    """Picks the plan's beam's-eye-view cell size by timing; returns (tile, slab, ms)."""
+    p, flag = _ptr(fluence)
+    t, s, ms = C.c_float(), C.c_float(), C.c_float()
+    _check(load().dc_fspb_autotune(plan.handle, p, flag, C.byref(t), C.byref(s), C.byref(ms)))
+    return t.value, s.value, ms.value
 
 
 def dc_fspb_launch_count() -> int:

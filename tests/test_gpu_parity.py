@@ -193,3 +193,17 @@ def test_edge_cases(dc, oracle_mod):
     got = dc.dc_fspb_dose(planq, q.fluence)
     want, amb = oracle_mod.OraclePlan(q).dose(with_amb=True)
     assert_dose_close(got, want, amb, label="corner")
+
+
+def test_autotune_keeps_results_identical(dc):
+    p = synth.small_plan(14, n=(30, 26, 20), vox=0.25, n_beams=3, roi=2.0, field=4.0)
+    plan = dc.dc_fspb_create_from(p)
+    before = dc.dc_fspb_dose(plan, p.fluence)
+    n0 = dc.dc_fspb_pair_count(plan)
+    tile, slab, ms = dc.dc_fspb_autotune(plan, p.fluence)
+    assert min(abs(tile - c) for c in (0.35, 0.5, 0.75)) < 1e-6 and ms > 0
+    after = dc.dc_fspb_dose(plan, p.fluence)
+    assert np.array_equal(before, after)
+    assert dc.dc_fspb_pair_count(plan) == n0
+    dc.dc_fspb_set_density(plan, p.rho)
+    assert np.array_equal(dc.dc_fspb_dose(plan, p.fluence), before)
