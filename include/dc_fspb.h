@@ -195,6 +195,39 @@ dc_status dc_fspb_pair_count(dc_plan* plan, int64_t* pairs);
 dc_status dc_fspb_dose_matrix(dc_plan* plan, int32_t value_dtype, int64_t* rowptr, int32_t* cols,
                               void* vals, uint32_t flags);
 
+/*
+ * Builds, inside the plan, the dose-deposition matrix of dc_fspb_dose_matrix
+ * (M[v][i] = D_i(r_v) over the pairs of eq. 1) with BF16 values, stored
+ * block-sparse for the tensor cores: per beam, the voxels of the beam's
+ * eye-view binning are cut into row-blocks of 128, and each row-block's
+ * nonzeros are covered by dense 128 x 16 tiles of consecutive beamlets
+ * (tile starts are multiples of 8).  Must be called again after
+ * dc_fspb_set_density or dc_fspb_autotune.  Synchronises the plan's stream.
+ * Errors: DC_ENOMEM, DC_ECUDA, DC_EUNSUPPORTED (a beam of > 32768 beamlets).
+ */
+dc_status dc_fspb_spmm_prepare(dc_plan* plan);
+
+/* Tiles (*chunks, 4 KiB each) and row-blocks of the prepared matrix. */
+dc_status dc_fspb_spmm_info(const dc_plan* plan, int64_t* chunks, int64_t* row_blocks);
+
+/*
+ * Eq. (1) for k fluence vectors at once as a sparse-dense product on the
+ * tensor cores: Y[v][q] = sum_i M[v][i] F[i][q], with M the BF16 matrix of
+ * dc_fspb_spmm_prepare, F rounded to BF16 (round-to-nearest-even), products
+ * accumulated in FP32 (tcgen05.mma, tensor memory), and the per-beam partial
+ * sums of a voxel added in beam order with compensated (Neumaier) summation.
+ *   F [B][k] float32 row-major (beamlet-major), 1 <= k <= 64;
+ *   Y [V][k] float32 row-major (voxel-major), written in full.
+ * Errors: DC_EINVAL (not prepared, bad k), DC_ECUDA, DC_ETIMEOUT (a bounded
+ * device-side wait gave up; with DC_DEVICE_PTRS this is reported by the next
+ * dc_fspb_device_status).
+ */
+dc_status dc_fspb_spmm(dc_plan* plan, const float* F, int32_t k, float* Y, uint32_t flags);
+
+/* Waits for the plan's stream and reports DC_ETIMEOUT if a bounded
+ * device-side wait of an earlier call gave up, else DC_OK. */
+dc_status dc_fspb_device_status(dc_plan* plan);
+
 /* ---- Inspection of the plan's intermediate results (for verification) ---- */
 
 /* rho_hat [V] (Algorithm A1 step 1). */

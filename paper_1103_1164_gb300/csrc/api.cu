@@ -74,9 +74,10 @@ static void free_plan(dc_plan* p)
                     p->d_tab, p->d_arow, p->d_tabm, p->d_A, p->d_water, p->d_dens, p->d_beamin, p->d_fluence,
                     p->d_dose, p->d_rowcount, p->d_rowptr, p->d_scan_tmp, p->d_mcols, p->d_mvals,
                     p->d_bin, p->d_bounds, p->d_cellof, p->d_hist, p->d_nitems, p->d_base, p->d_work,
-                    p->d_items, p->d_part, p->d_bcount};
+                    p->d_items, p->d_part, p->d_bcount, p->d_sp_fp, p->d_sp_p, p->d_err};
     for (void* b : bufs)
         if (b) cudaFree(b);
+    p->spmm_free();
     delete p;
 }
 
@@ -244,6 +245,7 @@ static dc_status compute_density_steps(dc_plan* p, const float* ct, uint32_t fla
     DC_CUDA(launch_beamlets(p));
     DC_CUDA(launch_binning(p));
     p->pairs = -1;
+    if (p->sp_ready) p->spmm_free();   // the SpMM tiles follow the voxel lists
     return DC_OK;
 }
 
@@ -402,6 +404,7 @@ static dc_status rebin(dc_plan* p, float tile, float slab)
                             cudaMemcpyHostToDevice, p->stream));
     DC_CUDA(launch_binning(p));
     p->pairs = -1;
+    if (p->sp_ready) p->spmm_free();
     return DC_OK;
 }
 
@@ -605,6 +608,75 @@ dc_status dc_fspb_dose_matrix(dc_plan* plan, int32_t value_dtype, int64_t* rowpt
     if (e == cudaSuccess) e = cudaStreamSynchronize(plan->stream);
     if (e != cudaSuccess) return cuda_fail(e, "dc_fspb_dose_matrix");
     return DC_OK;
+}
+
+static dc_status check_device_status(dc_plan* p)
+{
+    if (!p->d_err) return DC_OK;
+    int32_t h = 0;
+    DC_CUDA(cudaMemcpyAsync(&h, p->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, p->stream));
+    DC_CUDA(cudaStreamSynchronize(p->stream));
+    if (h != 0) {
+        set_error("a bounded device-side wait gave up (tensor-core pipeline did not complete)");
+        return DC_ETIMEOUT;
+    }
+    return DC_OK;
+}
+
+dc_status dc_fspb_device_status(dc_plan* plan)
+{
+    if (!plan) return invalid("dc_fspb_device_status: NULL argument");
+    DC_CUDA(cudaStreamSynchronize(plan->stream));
+    return check_device_status(plan);
+}
+
+dc_status dc_fspb_spmm_prepare(dc_plan* plan)
+{
+    if (!plan) return invalid("dc_fspb_spmm_prepare: NULL argument");
+    dc_status s = ensure_pattern(plan);
+    if (s != DC_OK) return s;
+    const size_t nnz = (size_t)plan->pairs;
+    const size_t need = nnz * sizeof(int32_t) + 16;
+    if (need > plan->mstage_bytes) {
+        if (plan->d_mcols) cudaFree(plan->d_mcols);
+        if (plan->d_mvals) cudaFree(plan->d_mvals);
+        plan->d_mcols = nullptr;
+        plan->d_mvals = nullptr;
+        plan->mstage_bytes = 0;
+        DC_CUDA(cudaMalloc(&plan->d_mcols, need));
+        DC_CUDA(cudaMalloc(&plan->d_mvals, need));
+        plan->mstage_bytes = need;
+    }
+    DC_CUDA(launch_fill(plan, plan->d_rowptr, plan->d_mcols, plan->d_mvals, DC_BF16));
+    return spmm_prepare(plan, plan->d_rowptr, plan->d_mcols, reinterpret_cast<const uint16_t*>(plan->d_mvals));
+}
+
+dc_status dc_fspb_spmm_info(const dc_plan* plan, int64_t* chunks, int64_t* row_blocks)
+{
+    if (!plan) return invalid("dc_fspb_spmm_info: NULL argument");
+    if (!plan->sp_ready) return invalid("dc_fspb_spmm_info: call dc_fspb_spmm_prepare first");
+    if (chunks) *chunks = plan->sp_chunks;
+    if (row_blocks) *row_blocks = plan->sp_n_rb;
+    return DC_OK;
+}
+
+dc_status dc_fspb_spmm(dc_plan* plan, const float* F, int32_t k, float* Y, uint32_t flags)
+{
+    if (!plan || !F || !Y) return invalid("dc_fspb_spmm: NULL argument");
+    if (k < 1 || k > 64) return invalid("dc_fspb_spmm: k must be in [1, 64]");
+    if (!plan->sp_ready) return invalid("dc_fspb_spmm: call dc_fspb_spmm_prepare first");
+    if (flags & DC_DEVICE_PTRS) {
+        DC_CUDA(spmm_run(plan, F, k, Y));
+        return DC_OK;
+    }
+    const size_t nf = (size_t)k * plan->B, ny = (size_t)k * plan->V;
+    dc_status s = ensure_staging(plan, nf, ny);
+    if (s != DC_OK) return s;
+    DC_CUDA(cudaMemcpyAsync(plan->d_fluence, F, nf * sizeof(float), cudaMemcpyHostToDevice, plan->stream));
+    DC_CUDA(spmm_run(plan, plan->d_fluence, k, plan->d_dose));
+    DC_CUDA(cudaMemcpyAsync(Y, plan->d_dose, ny * sizeof(float), cudaMemcpyDeviceToHost, plan->stream));
+    DC_CUDA(cudaStreamSynchronize(plan->stream));
+    return check_device_status(plan);
 }
 
 dc_status dc_fspb_get_smoothed(const dc_plan* plan, float* out, uint32_t flags)

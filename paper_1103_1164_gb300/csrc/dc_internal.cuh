@@ -125,6 +125,36 @@ struct dc_plan {
     size_t part_cap = 0;
     int32_t* d_bcount = nullptr;     // per-beam pair counts [n_beams][V]
     int persist_ctas[4] = {0, 0, 0, 0};
+    // block-sparse BF16 dose-deposition matrix for the tensor-core SpMM (k_spmm.cu)
+    bool sp_ready = false;
+    int sp_n_rb = 0;
+    int64_t sp_chunks = 0, sp_items_total = 0;
+    int32_t* d_sp_rbfirst = nullptr;
+    int32_t* d_sp_first = nullptr;
+    int32_t* d_sp_nchunk = nullptr;
+    int64_t* d_sp_off = nullptr;
+    int32_t* d_sp_kb = nullptr;
+    void* d_sp_tiles = nullptr;
+    int32_t* d_sp_inv = nullptr;
+    void* d_sp_fp = nullptr;
+    size_t sp_fp_cap = 0;
+    float* d_sp_p = nullptr;
+    size_t sp_p_cap = 0;
+    int32_t* d_err = nullptr;        // device status word of bounded waits
+    void spmm_free()
+    {
+        void* bufs[] = {d_sp_rbfirst, d_sp_first, d_sp_nchunk, d_sp_off, d_sp_kb, d_sp_tiles, d_sp_inv};
+        for (void* b : bufs)
+            if (b) cudaFree(b);
+        d_sp_rbfirst = d_sp_first = d_sp_nchunk = nullptr;
+        d_sp_off = nullptr;
+        d_sp_kb = nullptr;
+        d_sp_tiles = nullptr;
+        d_sp_inv = nullptr;
+        sp_ready = false;
+        sp_n_rb = 0;
+        sp_chunks = 0;
+    }
     // dose-deposition matrix pattern
     int32_t* d_rowcount = nullptr;
     int64_t* d_rowptr = nullptr;
@@ -166,5 +196,8 @@ cudaError_t launch_fill(const dc_plan* p, const int64_t* rowptr, int32_t* cols, 
                         int value_dtype);
 cudaError_t launch_scan_counts(const dc_plan* p, const int32_t* counts, int64_t* rowptr,
                                int64_t* total_dev);
+// block-sparse tensor-core SpMM (k_spmm.cu)
+dc_status spmm_prepare(dc_plan* p, const int64_t* rowptr, const int32_t* cols, const uint16_t* vals);
+cudaError_t spmm_run(dc_plan* p, const float* F, int k, float* Y);
 
 }  // namespace dc

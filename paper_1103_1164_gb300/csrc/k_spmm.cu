@@ -1,0 +1,612 @@
+// Multi-fluence dose as a block-sparse BF16 tensor-core SpMM:
+//   Y[v][q] = sum_i M[v][i] F[i][q]     (eq. 1 for k fluence vectors at once)
+// with M the dose-deposition matrix (M[v][i] = D_i(r_v), BF16) and FP32
+// accumulation in tensor memory.
+//
+// Storage.  Each beam's voxel list (k_bin.cu: voxels grouped by their cell in
+// the beam's eye view) is cut into row-blocks of 128 voxels.  A row-block's
+// nonzeros in the beam's columns are covered by K-chunks of 16 consecutive
+// beamlets starting at a multiple of 8; every chunk is a dense 128 x 16 BF16
+// tile stored in the UMMA "no swizzle" K-major core-matrix layout
+// (8 x 8 cores of 128 contiguous bytes; core (m/8, k/8) at ((m/8) * 2 + k/8) * 128),
+// so one 4 KB bulk copy puts it in shared memory ready for tcgen05.mma.  The
+// fluence matrix is converted per call into the matching K-major layout of
+// 16 x 64 tiles, contiguous for every 8-aligned chunk start.
+//
+// Kernel.  One CTA (4 warps) per row-block at a time: thread 0 streams the
+// chunks' A and F tiles through a ring of shared-memory stages with
+// cp.async.bulk (completion on mbarriers) and issues one
+// tcgen05.mma.kind::f16 (M = 128, N = 64, K = 16) per chunk into a 64-column
+// FP32 accumulator in tensor memory; after a tcgen05.commit the four warps
+// read their 32 rows back with tcgen05.ld and write them out.  Every wait is
+// bounded; a wait that gives up sets an error word and the CTA stops.
+// Per-beam partial results are combined with compensated (Neumaier) sums.
+#include <stdint.h>
+
+#include <vector>
+
+#include "dc_internal.cuh"
+
+namespace dc {
+namespace {
+
+constexpr int kRB = 128;             // rows (voxels) per row-block
+constexpr int kKC = 16;              // beamlets per K-chunk
+constexpr int kN = 64;               // fluence columns of the MMA
+constexpr int kTileA = kRB * kKC * 2;     // 4096 bytes
+constexpr int kTileB = kKC * kN * 2;      // 2048 bytes
+constexpr int kStages = 6;
+constexpr int kSpmmThreads = 128;
+constexpr long long kSpinLimit = 1ll << 26;   // bounded mbarrier waits ...
+constexpr uint64_t kWaitNs = 2000000000ull;   // ... of at most 2 s
+
+// ---------------------------------------------------------------------------
+// Small PTX helpers (sm_100 family).
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, int count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for the given phase of an mbarrier; false if the wait gave up (after
+// kWaitNs nanoseconds or kSpinLimit polls, whichever comes first).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase)
+{
+    const uint64_t t0 = global_ns();
+    for (long long it = 0; it < kSpinLimit; ++it) {
+        if (mbar_try_wait(bar, phase)) return true;
+        if ((it & 255) == 255 && global_ns() - t0 > kWaitNs) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// UMMA shared-memory matrix descriptor, no swizzle, K-major.
+__device__ __forceinline__ uint64_t smem_desc(const void* p, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((smem_u32(p) >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;   // descriptor version of the sm_100 family
+    return d;                 // base offset 0, layout type 0 (no swizzle)
+}
+
+// Instruction descriptor of tcgen05.mma.kind::f16: D FP32, A and B BF16,
+// both K-major, N = kN, M = kRB.
+__host__ __device__ constexpr uint32_t instr_desc()
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN >> 3) << 17) | ((uint32_t)(kRB >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+        "l"(da), "l"(db), "r"(instr_desc()), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// CSR -> tiles.  One CTA of 128 threads per row-block; thread t owns row t.
+
+struct TileArgs {
+    const int64_t* rowptr;
+    const int32_t* cols;
+    const uint16_t* vals;        // BF16 bits
+    const int32_t* items;
+    const int64_t* base;         // start of each beam's list
+    const int32_t* n_items;
+    const int32_t* rb_first;     // [n_beams + 1] first row-block of each beam (host-computed)
+    const int32_t* first;        // [n_beams + 1] first beamlet of each beam
+    int n_beams;
+    int32_t* nchunk;             // count pass output [n_rb]
+    const int64_t* chunk_off;    // fill pass: first chunk of each row-block
+    int32_t* chunk_kb;           // fill pass: k-block (beamlet / 8) of each chunk
+    uint16_t* tiles;             // fill pass: [chunks][128 * 16]
+};
+
+constexpr int kMaxKB = 4096;   // k-blocks of one beam (32768 beamlets)
+
+template <bool FILL>
+__global__ void __launch_bounds__(kRB) k_tiles(const TileArgs a)
+{
+    __shared__ uint32_t mark[kMaxKB / 32];
+    __shared__ int16_t chunk_of[kMaxKB];   // chunk index of each k-block (-1: none)
+    __shared__ int s_nc;
+    const int rb = blockIdx.x;
+    int b = 0;
+    while (b + 1 < a.n_beams && a.rb_first[b + 1] <= rb) ++b;
+    const int j = rb - a.rb_first[b];
+    const int nit = a.n_items[b];
+    const int t = threadIdx.x;
+    const int c0 = a.first[b], c1 = a.first[b + 1];
+    const int kb0 = c0 / 8, nkb = (c1 + 7) / 8 - kb0;
+    for (int q = t; q < kMaxKB / 32; q += blockDim.x) mark[q] = 0;
+    __syncthreads();
+    const int e = j * kRB + t;
+    const int v = e < nit ? a.items[a.base[b] + e] : -1;
+    int64_t r0 = 0, r1 = 0;
+    if (v >= 0) {
+        r0 = a.rowptr[v];
+        r1 = a.rowptr[v + 1];
+        for (int64_t q = r0; q < r1; ++q) {
+            const int c = a.cols[q];
+            if (c >= c0 && c < c1) {
+                const int kb = c / 8 - kb0;
+                atomicOr(&mark[kb >> 5], 1u << (kb & 31));
+            }
+        }
+    }
+    __syncthreads();
+    if (t == 0) {
+        // greedy cover of the marked k-blocks by pairs of consecutive k-blocks
+        int nc = 0, kb = 0;
+        while (kb < nkb) {
+            if (mark[kb >> 5] & (1u << (kb & 31))) {
+                if (FILL) {
+                    a.chunk_kb[a.chunk_off[rb] + nc] = kb0 + kb;
+                    chunk_of[kb] = (int16_t)nc;
+                    if (kb + 1 < nkb) chunk_of[kb + 1] = (int16_t)nc;
+                }
+                ++nc;
+                kb += 2;
+            } else {
+                if (FILL) chunk_of[kb] = -1;
+                ++kb;
+            }
+        }
+        s_nc = nc;
+        if (!FILL) a.nchunk[rb] = nc;
+    }
+    __syncthreads();
+    if (!FILL) return;
+    // zero this row-block's tiles, then scatter the BF16 values
+    uint16_t* tiles = a.tiles + (size_t)a.chunk_off[rb] * (kRB * kKC);
+    uint4* tz = reinterpret_cast<uint4*>(tiles);
+    const int nz = s_nc * (kTileA / 16);
+    for (int q = t; q < nz; q += blockDim.x) tz[q] = make_uint4(0, 0, 0, 0);
+    __syncthreads();
+    if (v >= 0) {
+        for (int64_t q = r0; q < r1; ++q) {
+            const int c = a.cols[q];
+            if (c < c0 || c >= c1) continue;
+            const int ch = chunk_of[c / 8 - kb0];
+            const int k = c - 8 * a.chunk_kb[a.chunk_off[rb] + ch];   // column within the chunk, 0..15
+            // element (m = t, k) of the K-major core-matrix layout
+            const int off = ((t >> 3) * 2 + (k >> 3)) * 64 + (t & 7) * 8 + (k & 7);
+            tiles[(size_t)ch * (kRB * kKC) + off] = a.vals[q];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// F [B][k] (FP32, row-major) -> BF16 K-major core tiles: element (beamlet c,
+// fluence n) at ((c / 8) * 8 + n / 8) * 64 + (n % 8) * 8 + c % 8; fluence
+// columns n >= k and beamlets c >= B are zero.
+__global__ void __launch_bounds__(256) k_pack_fluence(const float* __restrict__ F, int B, int k, int nkb,
+                                                      __nv_bfloat16* __restrict__ Fp)
+{
+    const int64_t n_el = (int64_t)nkb * 8 * kN;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_el; e += (int64_t)gridDim.x * blockDim.x) {
+        const int kb = (int)(e / (8 * kN));
+        const int r = (int)(e % (8 * kN));
+        const int nb = r / 64, n_in = (r % 64) / 8, c_in = r % 8;
+        const int c = kb * 8 + c_in, n = nb * 8 + n_in;
+        const float x = (c < B && n < k) ? __ldg(F + (size_t)c * k + n) : 0.f;
+        Fp[e] = __float2bfloat16_rn(x);
+    }
+}
+
+// ---------------------------------------------------------------------------
+struct SpmmArgs {
+    const uint16_t* tiles;
+    const int32_t* chunk_kb;
+    const int64_t* chunk_off;    // [n_rb + 1]
+    const __nv_bfloat16* Fp;
+    const int32_t* items;
+    const int64_t* base;
+    const int32_t* n_items;
+    const int32_t* rb_first;
+    int n_beams, n_rb, k;
+    float* Y;                    // single beam: [V][k]
+    float* P;                    // several beams: partial rows [item][k] per beam list position
+    int direct;
+    int vec4;                    // rows may be written as float4 (k % 4 == 0, 16-byte aligned output)
+    int32_t* err;
+};
+
+__global__ void __launch_bounds__(kSpmmThreads) k_spmm(const SpmmArgs a)
+{
+    extern __shared__ __align__(1024) uint8_t sm[];
+    __shared__ uint64_t full[kStages], empty[kStages], done;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_abort;
+    const int t = threadIdx.x, warp = t >> 5;
+
+    // stage buffers, 1 KB aligned
+    uint8_t* buf = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(sm) + 1023) & ~(uintptr_t)1023);
+    if (t == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&done, 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(kN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_base;
+
+    uint32_t g_load = 0, g_mma = 0, n_done = 0;   // chunks issued / consumed so far, row-blocks done
+    for (int rb = blockIdx.x; rb < a.n_rb; rb += gridDim.x) {
+        const int64_t ch0 = a.chunk_off[rb], nch = a.chunk_off[rb + 1] - ch0;
+        if (t == 0 && !s_abort) {
+            bool ok = true;
+            // prologue: fill up to kStages stages
+            int64_t issued = 0;
+            auto issue = [&](int64_t c) {
+                const uint32_t s = g_load % kStages;
+                if (g_load >= kStages && !mbar_wait(&empty[s], ((g_load / kStages) - 1) & 1)) {
+                    ok = false;
+                    return;
+                }
+                uint8_t* sa = buf + s * (kTileA + kTileB);
+                mbar_expect_tx(&full[s], kTileA + kTileB);
+                bulk_g2s(sa, a.tiles + (size_t)(ch0 + c) * (kRB * kKC), kTileA, &full[s]);
+                bulk_g2s(sa + kTileA, a.Fp + (size_t)a.chunk_kb[ch0 + c] * (8 * kN), kTileB, &full[s]);
+                ++g_load;
+            };
+            for (; issued < nch && issued < kStages && ok; ++issued) issue(issued);
+            for (int64_t c = 0; c < nch && ok; ++c) {
+                const uint32_t s = g_mma % kStages;
+                ok = mbar_wait(&full[s], (g_mma / kStages) & 1);
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                uint8_t* sa = buf + s * (kTileA + kTileB);
+                const uint64_t da = smem_desc(sa, 128, 256);            // A: LBO along K, SBO along M
+                const uint64_t db = smem_desc(sa + kTileA, 1024, 128);  // B: LBO along K, SBO along N
+                umma_bf16(tmem, da, db, c > 0 ? 1u : 0u);
+                umma_commit(&empty[s]);
+                ++g_mma;
+                if (issued < nch) {
+                    issue(issued);
+                    ++issued;
+                }
+            }
+            if (!ok) {
+                // give up: let the copies already issued land (bounded) so that
+                // nothing is in flight when the CTA releases its memory
+                for (; g_mma < g_load; ++g_mma) mbar_wait(&full[g_mma % kStages], (g_mma / kStages) & 1);
+                s_abort = 1;
+                atomicExch(a.err, 1);
+            }
+            umma_commit(&done);
+        }
+        // epilogue: wait for the accumulator (all MMAs of this row-block), read this warp's 32 rows
+        bool ok = mbar_wait(&done, n_done & 1);
+        ++n_done;
+        if (!ok) {
+            atomicExch(a.err, 1);
+            s_abort = 1;
+        }
+        __syncthreads();
+        if (s_abort) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (ok) {
+            int b = 0;
+            while (b + 1 < a.n_beams && a.rb_first[b + 1] <= rb) ++b;
+            const int e = (rb - a.rb_first[b]) * kRB + t;
+            const bool valid = nch > 0 && e < a.n_items[b];
+            uint32_t r[kN];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+            if (nch > 0) {
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                      "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                      "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                      "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                    : "r"(taddr));
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]),
+                      "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]),
+                      "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]),
+                      "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]),
+                      "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+                    : "r"(taddr + 32));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            } else {
+#pragma unroll
+                for (int q = 0; q < kN; ++q) r[q] = 0u;
+            }
+            if (valid) {
+                float* out;
+                if (a.direct) {
+                    const int v = a.items[a.base[b] + e];
+                    out = a.Y + (size_t)v * a.k;
+                } else {
+                    out = a.P + (size_t)(a.base[b] + e) * a.k;
+                }
+                if (a.vec4) {
+#pragma unroll
+                    for (int q = 0; q < kN; q += 4)
+                        if (q < a.k)
+                            *reinterpret_cast<float4*>(out + q) =
+                                make_float4(__uint_as_float(r[q]), __uint_as_float(r[q + 1]),
+                                            __uint_as_float(r[q + 2]), __uint_as_float(r[q + 3]));
+                } else {
+#pragma unroll
+                    for (int q = 0; q < kN; ++q)
+                        if (q < a.k) out[q] = __uint_as_float(r[q]);
+                }
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        if (s_abort) break;
+    }
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kN));
+}
+
+// Y[v][q] = sum over beams of the partial rows, in beam order, with
+// Neumaier-compensated summation.
+__global__ void __launch_bounds__(256) k_spmm_reduce(const float* __restrict__ P, const int32_t* __restrict__ inv,
+                                                     int n_beams, int64_t V, int k, float* __restrict__ Y)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < V * k; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = e / k;
+        const int q = (int)(e % k);
+        float s = 0.f, c = 0.f;
+        for (int b = 0; b < n_beams; ++b) {
+            const int32_t pos = __ldg(inv + (size_t)b * V + v);
+            if (pos < 0) continue;
+            const float x = __ldg(P + (size_t)pos * k + q);
+            const float tsum = s + x;
+            c += fabsf(s) >= fabsf(x) ? (s - tsum) + x : (x - tsum) + s;
+            s = tsum;
+        }
+        Y[e] = s + c;
+    }
+}
+
+// inv[b][v] = position of voxel v in beam b's list (-1 if absent).
+__global__ void __launch_bounds__(256) k_inverse(const int32_t* __restrict__ items, const int64_t* __restrict__ base,
+                                                 const int32_t* __restrict__ n_items, int64_t V, int32_t* __restrict__ inv)
+{
+    const int b = blockIdx.y;
+    const int n = n_items[b];
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const int v = items[base[b] + e];
+        if (v >= 0) inv[(size_t)b * V + v] = (int32_t)(base[b] + e);
+    }
+}
+
+int gsize(int64_t n)
+{
+    int64_t g = (n + 255) / 256;
+    return (int)(g > 4096 ? 4096 : (g < 1 ? 1 : g));
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host side
+
+dc_status spmm_prepare(dc_plan* p, const int64_t* rowptr, const int32_t* cols, const uint16_t* vals)
+{
+    const int nb = p->n_beams;
+    std::vector<int32_t> n_items(nb);
+    DC_CUDA(cudaMemcpyAsync(n_items.data(), p->d_nitems, nb * sizeof(int32_t), cudaMemcpyDeviceToHost, p->stream));
+    DC_CUDA(cudaStreamSynchronize(p->stream));
+    std::vector<int32_t> rb_first(nb + 1), first(nb + 1);
+    int n_rb = 0;
+    for (int b = 0; b < nb; ++b) {
+        rb_first[b] = n_rb;
+        n_rb += (n_items[b] + kRB - 1) / kRB;
+        first[b] = p->first[b];
+    }
+    rb_first[nb] = n_rb;
+    first[nb] = p->B;
+    for (int b = 0; b < nb; ++b)
+        if ((first[b + 1] + 7) / 8 - first[b] / 8 > kMaxKB) {
+            set_error("spmm: a beam has more than 32768 beamlets");
+            return DC_EUNSUPPORTED;
+        }
+    p->spmm_free();
+    p->sp_n_rb = n_rb;
+    DC_CUDA(cudaMalloc(&p->d_sp_rbfirst, (nb + 1) * sizeof(int32_t)));
+    DC_CUDA(cudaMalloc(&p->d_sp_first, (nb + 1) * sizeof(int32_t)));
+    DC_CUDA(cudaMalloc(&p->d_sp_nchunk, (size_t)(n_rb + 1) * sizeof(int32_t)));
+    DC_CUDA(cudaMalloc(&p->d_sp_off, (size_t)(n_rb + 1) * sizeof(int64_t)));
+    DC_CUDA(cudaMemcpyAsync(p->d_sp_rbfirst, rb_first.data(), (nb + 1) * sizeof(int32_t), cudaMemcpyHostToDevice,
+                            p->stream));
+    DC_CUDA(cudaMemcpyAsync(p->d_sp_first, first.data(), (nb + 1) * sizeof(int32_t), cudaMemcpyHostToDevice,
+                            p->stream));
+    TileArgs ta{};
+    ta.rowptr = rowptr;
+    ta.cols = cols;
+    ta.vals = vals;
+    ta.items = p->d_items;
+    ta.base = p->d_base;
+    ta.n_items = p->d_nitems;
+    ta.rb_first = p->d_sp_rbfirst;
+    ta.first = p->d_sp_first;
+    ta.n_beams = nb;
+    ta.nchunk = p->d_sp_nchunk;
+    if (n_rb > 0) {
+        k_tiles<false><<<n_rb, kRB, 0, p->stream>>>(ta);
+        count_launches(1);
+        DC_CUDA(cudaGetLastError());
+    }
+    std::vector<int32_t> nch(n_rb + 1, 0);
+    std::vector<int64_t> off(n_rb + 1, 0);
+    if (n_rb > 0)
+        DC_CUDA(cudaMemcpyAsync(nch.data(), p->d_sp_nchunk, n_rb * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                p->stream));
+    DC_CUDA(cudaStreamSynchronize(p->stream));
+    for (int r = 0; r < n_rb; ++r) off[r + 1] = off[r] + nch[r];
+    p->sp_chunks = off[n_rb];
+    DC_CUDA(cudaMemcpyAsync(p->d_sp_off, off.data(), (n_rb + 1) * sizeof(int64_t), cudaMemcpyHostToDevice,
+                            p->stream));
+    DC_CUDA(cudaMalloc(&p->d_sp_kb, (size_t)(p->sp_chunks + 1) * sizeof(int32_t)));
+    DC_CUDA(cudaMalloc(&p->d_sp_tiles, (size_t)(p->sp_chunks + 1) * kTileA));
+    ta.chunk_off = p->d_sp_off;
+    ta.chunk_kb = p->d_sp_kb;
+    ta.tiles = reinterpret_cast<uint16_t*>(p->d_sp_tiles);
+    if (n_rb > 0) {
+        k_tiles<true><<<n_rb, kRB, 0, p->stream>>>(ta);
+        count_launches(1);
+        DC_CUDA(cudaGetLastError());
+    }
+    if (nb > 1) {
+        DC_CUDA(cudaMalloc(&p->d_sp_inv, (size_t)nb * p->V * sizeof(int32_t)));
+        DC_CUDA(cudaMemsetAsync(p->d_sp_inv, 0xff, (size_t)nb * p->V * sizeof(int32_t), p->stream));
+        int maxn = 0;
+        for (int b = 0; b < nb; ++b) maxn = std::max(maxn, n_items[b]);
+        dim3 g(gsize(maxn), nb);
+        k_inverse<<<g, 256, 0, p->stream>>>(p->d_items, p->d_base, p->d_nitems, p->V, p->d_sp_inv);
+        count_launches(1);
+        DC_CUDA(cudaGetLastError());
+        int64_t items_total = 0;
+        for (int b = 0; b < nb; ++b) items_total += ((int64_t)n_items[b] + 31) / 32 * 32;
+        p->sp_items_total = items_total;
+    }
+    if (!p->d_err) DC_CUDA(cudaMalloc(&p->d_err, sizeof(int32_t)));
+    DC_CUDA(cudaStreamSynchronize(p->stream));
+    p->sp_ready = true;
+    return DC_OK;
+}
+
+cudaError_t spmm_run(dc_plan* p, const float* F, int k, float* Y)
+{
+    const int nkb = (p->B + 7) / 8 + 2;
+    cudaError_t e = cudaSuccess;
+    if (p->sp_fp_cap < (size_t)nkb * 8 * kN) {
+        if (p->d_sp_fp) cudaFree(p->d_sp_fp);
+        p->d_sp_fp = nullptr;
+        p->sp_fp_cap = 0;
+        e = cudaMalloc(&p->d_sp_fp, (size_t)nkb * 8 * kN * sizeof(__nv_bfloat16));
+        if (e != cudaSuccess) return e;
+        p->sp_fp_cap = (size_t)nkb * 8 * kN;
+    }
+    const bool direct = p->n_beams == 1;
+    if (!direct) {
+        const size_t need = (size_t)p->sp_items_total * k;
+        if (p->sp_p_cap < need) {
+            if (p->d_sp_p) cudaFree(p->d_sp_p);
+            p->d_sp_p = nullptr;
+            p->sp_p_cap = 0;
+            e = cudaMalloc(&p->d_sp_p, need * sizeof(float));
+            if (e != cudaSuccess) return e;
+            p->sp_p_cap = need;
+        }
+    }
+    k_pack_fluence<<<gsize((int64_t)nkb * 8 * kN), 256, 0, p->stream>>>(F, p->B, k, nkb,
+                                                                       reinterpret_cast<__nv_bfloat16*>(p->d_sp_fp));
+    count_launches(1);
+    if (direct) {
+        e = cudaMemsetAsync(Y, 0, (size_t)p->V * k * sizeof(float), p->stream);
+        if (e != cudaSuccess) return e;
+    }
+    e = cudaMemsetAsync(p->d_err, 0, sizeof(int32_t), p->stream);
+    if (e != cudaSuccess) return e;
+    SpmmArgs a{};
+    a.tiles = reinterpret_cast<const uint16_t*>(p->d_sp_tiles);
+    a.chunk_kb = p->d_sp_kb;
+    a.chunk_off = p->d_sp_off;
+    a.Fp = reinterpret_cast<const __nv_bfloat16*>(p->d_sp_fp);
+    a.items = p->d_items;
+    a.base = p->d_base;
+    a.n_items = p->d_nitems;
+    a.rb_first = p->d_sp_rbfirst;
+    a.n_beams = p->n_beams;
+    a.n_rb = p->sp_n_rb;
+    a.k = k;
+    a.Y = Y;
+    a.P = p->d_sp_p;
+    a.direct = direct ? 1 : 0;
+    float* out0 = direct ? Y : p->d_sp_p;
+    a.vec4 = (k % 4 == 0 && (reinterpret_cast<uintptr_t>(out0) & 15) == 0) ? 1 : 0;
+    a.err = p->d_err;
+    const size_t smem = (size_t)kStages * (kTileA + kTileB) + 1024 + 8192;
+    e = cudaFuncSetAttribute(k_spmm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmm, kSpmmThreads, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (e != cudaSuccess) return e;
+    per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
+    int grid = sms * per_sm;
+    if (grid > p->sp_n_rb) grid = p->sp_n_rb;
+    if (grid > 0) {
+        k_spmm<<<grid, kSpmmThreads, smem, p->stream>>>(a);
+        count_launches(1);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (!direct) {
+        k_spmm_reduce<<<gsize(p->V * k), 256, 0, p->stream>>>(p->d_sp_p, p->d_sp_inv, p->n_beams, p->V, k, Y);
+        count_launches(1);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+}  // namespace dc

@@ -58,7 +58,8 @@ EXPORTS = ["dc_last_error", "dc_status_str", "dc_fspb_create", "dc_fspb_destroy"
            "dc_fspb_n_beamlets", "dc_fspb_n_voxels", "dc_fspb_dose", "dc_fspb_dose_batch",
            "dc_fspb_pair_count", "dc_fspb_dose_matrix", "dc_fspb_get_smoothed",
            "dc_fspb_get_beamlets", "dc_fspb_get_tables", "dc_fspb_set_density",
-           "dc_fspb_launch_count", "dc_fspb_autotune"]
+           "dc_fspb_launch_count", "dc_fspb_autotune", "dc_fspb_spmm_prepare", "dc_fspb_spmm_info",
+           "dc_fspb_spmm", "dc_fspb_device_status"]
 
 
 def library_path() -> str:
@@ -95,6 +96,10 @@ def load():
     L.dc_fspb_launch_count.argtypes = [C.POINTER(C.c_uint64)]
     L.dc_fspb_autotune.argtypes = [vp, vp, u32, C.POINTER(C.c_float), C.POINTER(C.c_float),
                                    C.POINTER(C.c_float)]
+    L.dc_fspb_spmm_prepare.argtypes = [vp]
+    L.dc_fspb_spmm_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
+    L.dc_fspb_spmm.argtypes = [vp, vp, i32, vp, u32]
+    L.dc_fspb_device_status.argtypes = [vp]
     for name in EXPORTS:
         if name not in ("dc_last_error", "dc_status_str"):
             getattr(L, name).restype = C.c_int
@@ -206,6 +211,33 @@ def dc_fspb_autotune(plan: Plan, fluence):
     t, s, ms = C.c_float(), C.c_float(), C.c_float()
     _check(load().dc_fspb_autotune(plan.handle, p, flag, C.byref(t), C.byref(s), C.byref(ms)))
     return t.value, s.value, ms.value
+
+
+def dc_fspb_spmm_prepare(plan: Plan):
+    """Builds the plan's block-sparse BF16 dose-deposition matrix for dc_fspb_spmm."""
+    _check(load().dc_fspb_spmm_prepare(plan.handle))
+
+
+def dc_fspb_spmm_info(plan: Plan):
+    """(tiles of 128 x 16, row-blocks of 128 voxels) of the prepared matrix."""
+    c, r = C.c_int64(), C.c_int64()
+    _check(load().dc_fspb_spmm_info(plan.handle, C.byref(c), C.byref(r)))
+    return c.value, r.value
+
+
+def dc_fspb_spmm(plan: Plan, F, Y=None):
+    """Y [V, k] = M F for F [B, k] (k <= 64) on the tensor cores."""
+    k = F.shape[1]
+    if Y is None:
+        Y = np.empty((plan.n_voxels, k), np.float32)
+    pf, f1 = _ptr(F)
+    py, f2 = _ptr(Y)
+    _check(load().dc_fspb_spmm(plan.handle, pf, k, py, _same_kind(f1, f2)))
+    return Y
+
+
+def dc_fspb_device_status(plan: Plan):
+    _check(load().dc_fspb_device_status(plan.handle))
 
 
 def dc_fspb_launch_count() -> int:
