@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--scale", type=float, default=1.0, help="grid scale of the thorax plan")
-    ap.add_argument("--profile", default=None, choices=["dose", "fill", "prep"],
+    ap.add_argument("--profile", default=None, choices=["dose", "fill", "prep", "spmm"],
                     help="small fixed run of one stage for profiler captures (prints no bench line)")
     return ap.parse_args()
 
@@ -64,6 +64,17 @@ def run_profile(args):
     import torch
     from paper_1103_1164_gb300 import build, dc_fspb as dc, synth
     build.build()
+    if args.profile == "spmm":
+        p1 = synth.config1()
+        plan = dc.dc_fspb_create_from(p1)
+        dc.dc_fspb_spmm_prepare(plan)
+        F = torch.rand(plan.n_beamlets, 64, device="cuda")
+        Y = torch.empty(plan.n_voxels, 64, device="cuda")
+        for _ in range(args.warmup + args.steps):
+            dc.dc_fspb_spmm(plan, F, Y)
+        dc.dc_fspb_device_status(plan)
+        print(f"profile run done: spmm, {plan.n_voxels} voxels, {plan.n_beamlets} beamlets")
+        return
     p = synth.config2(args.scale)
     rho_d = torch.from_numpy(p.rho).cuda()
     flu_d = torch.from_numpy(p.fluence).cuda()
@@ -333,6 +344,7 @@ def run_ours(args, world, rank, local, pg):
               "hbm_peak_GBps": peaks.get("hbm_gbs"), "count_scan_ms": float(stage[:, 2].mean()),
               "nnz": pairs, "bytes": bytes_matrix}
 
+    forms = run_forms(args, dc, torch, stream, peaks)
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, dc, p, plan, pairs, torch)
@@ -359,9 +371,68 @@ def run_ours(args, world, rank, local, pg):
             "stages_ms": {"steps_1_6": float(stage[:, 0].mean()), "dose": float(stage[:, 1].mean()),
                           "pair_count": float(stage[:, 2].mean()), "matrix_fill": fill_ms},
             "wall_ms_per_step": 1e3 * wall / args.steps,
-            "roofline": roofline, "peaks": peak_kind, "dose_matrix": matrix,
+            "roofline": roofline, "peaks": peak_kind, "dose_matrix": matrix, "forms": forms,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
+
+
+def time_on_stream(torch, stream, fn, reps, flush):
+    """Mean device time (ms) of fn() over reps calls, L2 flushed before each (untimed)."""
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.mean(ts))
+
+
+def run_forms(args, dc, torch, stream, peaks, k=64):
+    """Multi-fluence dose of the single-beam slab plan (64 x 64 x 64 voxels, 400
+    beamlets, 64 fluence vectors U[0, 1]): plain FP32 direct evaluation
+    (dc_fspb_dose_batch) against the BF16 block-sparse tensor-core SpMM
+    (dc_fspb_spmm) on the matrix built once per plan."""
+    from paper_1103_1164_gb300 import synth
+    p1 = synth.config1()
+    rho = torch.from_numpy(p1.rho).cuda()
+    plan = dc.dc_fspb_create_from(p1, stream=stream.cuda_stream, device_density=rho)
+    F = torch.from_numpy(np.random.default_rng(synth.FLUENCE_SEED).uniform(0, 1, (plan.n_beamlets, k))
+                         .astype(np.float32)).cuda()
+    Ft = F.t().contiguous()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    dose = torch.empty((k, plan.n_voxels), device="cuda")
+    Y = torch.empty((plan.n_voxels, k), device="cuda")
+    dc.dc_fspb_autotune(plan, F[:, 0].contiguous())
+    t0 = time.perf_counter()
+    dc.dc_fspb_spmm_prepare(plan)
+    prep_s = time.perf_counter() - t0
+    chunks, rbs = dc.dc_fspb_spmm_info(plan)
+    pairs = dc.dc_fspb_pair_count(plan)
+    reps = max(3, args.steps)
+    for _ in range(2):
+        dc.dc_fspb_dose_batch(plan, Ft, dose)
+        dc.dc_fspb_spmm(plan, F, Y)
+    t_plain = time_on_stream(torch, stream, lambda: dc.dc_fspb_dose_batch(plan, Ft, dose), reps, flush)
+    t_spmm = time_on_stream(torch, stream, lambda: dc.dc_fspb_spmm(plan, F, Y), reps, flush)
+    dc.dc_fspb_device_status(plan)
+    err = float(((Y.t() - dose).abs().max(1).values / dose.abs().max(1).values).max())
+    bytes_alg = chunks * 4096 + chunks * 4 + plan.n_voxels * k * 4 + plan.n_beamlets * k * 4
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    return {"workload": f"slab64 64^3 @0.25cm, 1 beam, {plan.n_beamlets} beamlets, ROI 3 cm, {k} fluences U[0,1]",
+            "pairs": pairs,
+            "plain_fp32": {"ms": t_plain, "evals_per_s": pairs * k / (t_plain * 1e-3)},
+            "bf16_spmm": {"ms": t_spmm, "evals_per_s": pairs * k / (t_spmm * 1e-3),
+                          "tiles_128x16": chunks, "row_blocks": rbs,
+                          "tile_fill": pairs / (chunks * 2048.0), "prepare_s": prep_s,
+                          "roofline": {"bound": "hbm", "achieved": bytes_alg / (t_spmm * 1e-3) / 1e9,
+                                       "peak": hbm, "unit": "GB/s",
+                                       "frac": bytes_alg / (t_spmm * 1e-3) / 1e9 / hbm,
+                                       "bytes": bytes_alg},
+                          "max_err_vs_fp32_over_colmax": err},
+            "speedup_bf16_over_fp32": t_plain / t_spmm}
 
 
 def run_e2e(args, dc, p, plan, pairs, torch):
