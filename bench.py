@@ -37,7 +37,7 @@ METRIC = "voxel-beamlet evals/s (full plan: steps 1-6 + eq. 1 dose + FP32 dose m
 UNIT = "evals/s"
 # Algorithmic work of one (voxel, beamlet) evaluation of eqs. (2)-(4) with the
 # lookups of Algorithm A1 steps 9-11 (counted from the method's definition):
-ALG_FP32_PER_PAIR = 95     # FP32 add/mul/fma/compare/convert operations
+ALG_FP32_PER_PAIR = 98     # FP32 add/mul/fma/compare/round operations (itemised in the design doc)
 ALG_MUFU_PER_PAIR = 9      # 8 exponentials (four p() of eq. 4) + 1 reciprocal (SAD/|r_a|)
 FP32_LANES_PER_SM = 128
 MUFU_LANES_PER_SM = 16
@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--scale", type=float, default=1.0, help="grid scale of the thorax plan")
-    ap.add_argument("--profile", default=None, choices=["dose", "fill", "prep", "spmm"],
+    ap.add_argument("--profile", default=None, choices=["dose", "fill", "prep", "spmm", "step"],
                     help="small fixed run of one stage for profiler captures (prints no bench line)")
     return ap.parse_args()
 
@@ -80,6 +80,23 @@ def run_profile(args):
     flu_d = torch.from_numpy(p.fluence).cuda()
     plan = dc.dc_fspb_create_from(p, device_density=rho_d)
     dose_d = torch.empty(plan.shape, device="cuda")
+    if args.profile == "step":
+        # the benchmark's step after the same plan set-up (autotuned binning)
+        dc.dc_fspb_autotune(plan, flu_d)
+        pairs = dc.dc_fspb_pair_count(plan)
+        rowptr = torch.empty(plan.n_voxels + 1, dtype=torch.int64, device="cuda")
+        cols = torch.empty(pairs, dtype=torch.int32, device="cuda")
+        vals = torch.empty(pairs, dtype=torch.float32, device="cuda")
+        n0 = dc.dc_fspb_launch_count()
+        for _ in range(args.warmup + args.steps):
+            dc.dc_fspb_set_density(plan, rho_d)
+            dc.dc_fspb_dose(plan, flu_d, dose_d)
+            dc.dc_fspb_pair_count(plan)
+            dc.dc_fspb_dose_matrix(plan, dc.DC_F32, rowptr, cols, vals)
+        torch.cuda.synchronize()
+        per_step = (dc.dc_fspb_launch_count() - n0) // (args.warmup + args.steps)
+        print(f"profile run done: step, {per_step} library launches per step")
+        return
     if args.profile == "fill":
         pairs = dc.dc_fspb_pair_count(plan)
         rowptr = torch.empty(plan.n_voxels + 1, dtype=torch.int64, device="cuda")

@@ -42,7 +42,7 @@
  *  - omega_i = f_omega_i(rho_hat) (omega_i^w + omega_i^corr) as in the text of
  *    Section 2.1, clamped at 0; u_1 uses rho at the voxel, u_2 and omega use
  *    rho_hat at the voxel; u_ix = u_iy = u_i.
- *  - "skipping step 11" (density_correction = 0) gives u_i = u_i^w,
+ *  - omitting step 11 (density_correction = 0) gives u_i = u_i^w,
  *    omega_i = omega_i^w: the conventional FSPB with 1-D depth correction.
  *  - eq. (4) is evaluated in the algebraically identical overflow-free form
  *      |x| <= x0:  1 - (exp(-u(x0-|x|)) + exp(-u(x0+|x|)))/2
@@ -124,8 +124,8 @@ static void normalize3(double* a)
 }
 
 /* Linear interpolation in a table f[j] = f(x0 + j h), j = 0..n-1, clamped to
- * the table's domain (Algorithm A1 steps 9-10: "extract ... from the
- * commissioned parameter lookup table"). */
+ * the table's domain (Algorithm A1 steps 9-10 read A, u^w and omega^w from
+ * commissioned tables). */
 double or_lut1(const double* f, int n, double x0, double h, double x)
 {
     double s = (x - x0) / h;

@@ -587,11 +587,14 @@ cudaError_t spmm_run(dc_plan* p, const float* F, int k, float* Y)
     const size_t smem = (size_t)kStages * (kTileA + kTileB) + 1024 + 8192;
     e = cudaFuncSetAttribute(k_spmm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    int per_sm = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmm, kSpmmThreads, smem);
+    // CTAs per SM from the shared-memory budget (each holds kStages tiles in
+    // flight and 64 TMEM columns; at most 4 per SM keeps TMEM at 256 of 512 columns)
+    int smem_sm = 0, sms = 0;
+    e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, p->device);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
     if (e != cudaSuccess) return e;
+    int per_sm = smem_sm / (int)(smem + 2048);
     per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
     int grid = sms * per_sm;
     if (grid > p->sp_n_rb) grid = p->sp_n_rb;
