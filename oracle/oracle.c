@@ -83,7 +83,8 @@ typedef struct {
     const double* dens;       /* [6][f_n]: f_u1, f_u2, f_w1, f_w2, b1, b2 at rho = f_rho0 + j f_drho */
     double f_rho0, f_drho;
     double roi, sigma, rho_surf;
-    int32_t density_correction, pad;
+    int32_t density_correction;
+    int32_t lateral_mode;     /* 0: rho(r), rho_hat(r) (Section 2.1); 1: axis stencils */
 } OInputs;
 
 typedef struct {
@@ -491,6 +492,89 @@ int or_plan_table(const void* h, int i, double* T, double* W1, double* W2, int k
 }
 
 /* ------------------------------------------------------------------------ */
+/* Lateral density sampling along the beam's axes (the "AXIS" form of the
+ * step-11 correction; with lateral_mode = 0 the paper's rho(r), rho_hat(r) are
+ * used instead).  For voxel r and beam b, 16 taps along each of the beam's
+ * axes e_x', e_y', e_z' through r at s_j = (j + 1/2) d, j = -8..7; at each tap
+ * the density is interpolated trilinearly (clamp-to-edge); per axis the taps
+ * are averaged with Gaussian weights exp(-s_j^2 / 2 sigma^2) normalised to one.
+ * eff = (mean of the three axis averages, x-axis average, y-axis average): the
+ * densities at which f_omega, f_u2 along x and f_u2 along y are taken.
+ * Optionally returns the 48 taps (axis-major) and the 48 nearest-voxel
+ * densities at the same points. */
+#define N_TAPS 16
+
+static double rho_trilinear(const OPlan* P, const double* p)
+{
+    const OInputs* in = &P->in;
+    const int dims[3] = {in->nx, in->ny, in->nz};
+    const double del[3] = {in->dx, in->dy, in->dz}, org[3] = {in->ox, in->oy, in->oz};
+    int i0[3], i1[3];
+    double w[3];
+    for (int a = 0; a < 3; ++a) {
+        double u = (p[a] - org[a]) / del[a];
+        if (u < 0) u = 0;
+        if (u > dims[a] - 1) u = dims[a] - 1;
+        int f = (int)floor(u);
+        if (f > dims[a] - 2) f = dims[a] - 2;
+        if (f < 0) f = 0;
+        i0[a] = f;
+        i1[a] = dims[a] > 1 ? f + 1 : f;
+        w[a] = dims[a] > 1 ? u - f : 0.0;
+    }
+    double s = 0.0;
+    for (int c = 0; c < 8; ++c) {
+        int ix = (c & 1) ? i1[0] : i0[0], iy = (c & 2) ? i1[1] : i0[1], iz = (c & 4) ? i1[2] : i0[2];
+        double wt = ((c & 1) ? w[0] : 1 - w[0]) * ((c & 2) ? w[1] : 1 - w[1]) * ((c & 4) ? w[2] : 1 - w[2]);
+        s += wt * P->rho[((size_t)iz * in->ny + iy) * in->nx + ix];
+    }
+    return s;
+}
+
+static double rho_nearest(const OPlan* P, const double* p)
+{
+    const OInputs* in = &P->in;
+    const int dims[3] = {in->nx, in->ny, in->nz};
+    const double del[3] = {in->dx, in->dy, in->dz}, org[3] = {in->ox, in->oy, in->oz};
+    int id[3];
+    for (int a = 0; a < 3; ++a) id[a] = clampi((int)floor((p[a] - org[a]) / del[a] + 0.5), 0, dims[a] - 1);
+    return P->rho[((size_t)id[2] * in->ny + id[1]) * in->nx + id[0]];
+}
+
+static void axis_densities(const OPlan* P, int64_t v, int beam, double* taps, double* nearest, double* eff)
+{
+    const OInputs* in = &P->in;
+    const OBeam* bm = &P->beam[beam];
+    int64_t ii = v % in->nx, jj = (v / in->nx) % in->ny, kk = v / ((int64_t)in->nx * in->ny);
+    double r[3] = {in->ox + ii * in->dx, in->oy + jj * in->dy, in->oz + kk * in->dz};
+    const double* axes[3] = {bm->ex, bm->ey, bm->ez};
+    double avg[3];
+    for (int a = 0; a < 3; ++a) {
+        double sw = 0.0, s = 0.0;
+        for (int j = -N_TAPS / 2; j < N_TAPS / 2; ++j) {
+            double sj = (j + 0.5) * P->d;
+            double p[3] = {r[0] + sj * axes[a][0], r[1] + sj * axes[a][1], r[2] + sj * axes[a][2]};
+            double rv = rho_trilinear(P, p);
+            double g = in->sigma > 0 ? exp(-sj * sj / (2.0 * in->sigma * in->sigma)) : 1.0;
+            if (taps) taps[a * N_TAPS + j + N_TAPS / 2] = rv;
+            if (nearest) nearest[a * N_TAPS + j + N_TAPS / 2] = rho_nearest(P, p);
+            s += g * rv;
+            sw += g;
+        }
+        avg[a] = s / sw;
+    }
+    eff[0] = (avg[0] + avg[1] + avg[2]) / 3.0;
+    eff[1] = avg[0];
+    eff[2] = avg[1];
+}
+
+/* Exposed for the tests: the stencil of (voxel v, beam b). */
+void or_plan_axis_stencil(const void* h, int64_t v, int beam, double* taps48, double* nearest48, double* eff3)
+{
+    axis_densities((const OPlan*)h, v, beam, taps48, nearest48, eff3);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Steps 8-12 for one (voxel, beamlet) pair.  Returns 1 if the pair is in the
  * beamlet's ROI and depth range, 0 otherwise; *amb is set when either
  * decision lies within the rounding margin of its boundary.  *D is D_i(r) of
@@ -538,22 +622,31 @@ static int pair_dose(const OPlan* P, int64_t v, int i, double* D, int* amb, doub
     double w1w = or_lut1(wt + 2 * (size_t)in->w_n, in->w_n, 0.0, in->w_dt, t);
     double w2w = or_lut1(wt + 3 * (size_t)in->w_n, in->w_n, 0.0, in->w_dt, t);
     /* step 11 */
-    double u1, u2, w1, w2;
+    double u1, u2x, u2y, w1, w2;
     if (in->density_correction) {
         const double* f = P->dens;
         size_t fn = (size_t)in->f_n;
-        double rl = P->rho[v], rs = P->rhos[v];
+        double rl = P->rho[v];
+        double ru_x, ru_y, rw;   /* densities that set u_2 along x, along y, and omega */
+        if (in->lateral_mode == 1) {
+            double eff[3];
+            axis_densities(P, v, bl->beam, NULL, NULL, eff);
+            rw = eff[0]; ru_x = eff[1]; ru_y = eff[2];
+        } else {
+            ru_x = ru_y = rw = P->rhos[v];
+        }
         u1 = or_lut1(f + 0 * fn, in->f_n, in->f_rho0, in->f_drho, rl) * u1w;
-        u2 = or_lut1(f + 1 * fn, in->f_n, in->f_rho0, in->f_drho, rs) * u2w;
-        w1 = or_lut1(f + 2 * fn, in->f_n, in->f_rho0, in->f_drho, rs) * (w1w + c1);
-        w2 = or_lut1(f + 3 * fn, in->f_n, in->f_rho0, in->f_drho, rs) * (w2w + c2);
+        u2x = or_lut1(f + 1 * fn, in->f_n, in->f_rho0, in->f_drho, ru_x) * u2w;
+        u2y = or_lut1(f + 1 * fn, in->f_n, in->f_rho0, in->f_drho, ru_y) * u2w;
+        w1 = or_lut1(f + 2 * fn, in->f_n, in->f_rho0, in->f_drho, rw) * (w1w + c1);
+        w2 = or_lut1(f + 3 * fn, in->f_n, in->f_rho0, in->f_drho, rw) * (w2w + c2);
         if (w1 < 0) w1 = 0;
         if (w2 < 0) w2 = 0;
     } else {
-        u1 = u1w; u2 = u2w; w1 = w1w; w2 = w2w;
+        u1 = u1w; u2x = u2y = u2w; w1 = w1w; w2 = w2w;
     }
     /* step 12: eqs. (3) and (2) */
-    double F = w1 * or_p(x, u1, x0) * or_p(y, u1, y0) + w2 * or_p(x, u2, x0) * or_p(y, u2, y0);
+    double F = w1 * or_p(x, u1, x0) * or_p(y, u1, y0) + w2 * or_p(x, u2x, x0) * or_p(y, u2y, y0);
     double isq = (bm->sad / L) * (bm->sad / L);
     *D = F * Aval * isq;
     if (out6) { out6[0] = x; out6[1] = y; out6[2] = t; out6[3] = teq; out6[4] = L; out6[5] = q2; }

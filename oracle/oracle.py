@@ -47,7 +47,7 @@ class OInputs(C.Structure):
                 ("w_dt", C.c_double),
                 ("dens", C.c_void_p), ("f_rho0", C.c_double), ("f_drho", C.c_double),
                 ("roi", C.c_double), ("sigma", C.c_double), ("rho_surf", C.c_double),
-                ("density_correction", C.c_int32), ("pad", C.c_int32)]
+                ("density_correction", C.c_int32), ("lateral_mode", C.c_int32)]
 
 
 def lib():
@@ -70,6 +70,7 @@ def lib():
         L.or_plan_pair.argtypes = [vp, i64, i32, vp]
         L.or_plan_matrix_count.argtypes = [vp, vp, i64, vp, i32]
         L.or_plan_pairs_voxels.argtypes = [vp, vp, i64, vp, i32]
+        L.or_plan_axis_stencil.argtypes = [vp, i64, i32, vp, vp, vp]
         L.or_plan_matrix_fill.argtypes = [vp, vp, i64, vp, vp, vp, vp, i32]
         L.or_trace_ray.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp, i32]
         L.or_smooth.argtypes = [vp, i32, i32, i32, d, d, d, d, vp, i32]
@@ -105,7 +106,7 @@ def smooth(rho, grid, sigma, threads=None) -> np.ndarray:
 class OraclePlan:
     """FP64 oracle of one plan: ``dose()``, ``matrix()``, per-beamlet tables and pairs."""
 
-    def __init__(self, plan, threads=None, density_correction=None):
+    def __init__(self, plan, threads=None, density_correction=None, lateral_mode=0):
         g, cm = plan.grid, plan.comm
         self.plan = plan
         self.threads = threads or default_threads()
@@ -127,7 +128,7 @@ class OraclePlan:
                       _p(d64(cm.A)).value, cm.A.shape[1], cm.A.shape[0], cm.a_dt, cm.a_dtheta,
                       _p(d64(cm.water)).value, cm.water.shape[1], cm.dens.shape[1], cm.w_dt,
                       _p(d64(cm.dens)).value, cm.f_rho0, cm.f_drho,
-                      cm.roi_radius, cm.smooth_sigma, cm.rho_surface, int(dc), 0)
+                      cm.roi_radius, cm.smooth_sigma, cm.rho_surface, int(dc), int(lateral_mode))
         self.grid = g
         self.V = g.n_voxels
         self._h = lib().or_plan_create(C.byref(ins), self.threads)
@@ -194,6 +195,12 @@ class OraclePlan:
         out = np.empty(v.size, np.int64)
         lib().or_plan_pairs_voxels(self._h, _p(v), v.size, _p(out), self.threads)
         return out
+
+    def axis_stencil(self, v, beam):
+        """(48 trilinear taps, 48 nearest-voxel taps, (rho_omega, rho_x, rho_y)) of voxel v, beam b."""
+        taps, near, eff = np.empty(48), np.empty(48), np.empty(3)
+        lib().or_plan_axis_stencil(self._h, int(v), int(beam), _p(taps), _p(near), _p(eff))
+        return taps, near, eff
 
     def pair(self, v, i):
         out = np.zeros(9)
