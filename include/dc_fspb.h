@@ -57,6 +57,11 @@ typedef enum {
 
 #define DC_DEVICE_PTRS 1u  /* flags: pointer arguments are device memory */
 
+/* Forms of the lateral density correction (Algorithm A1 step 11). */
+#define DC_LATERAL_ISO 0   /* the paper's: f(rho(r)), f(rho_hat(r)) at the dose voxel          */
+#define DC_LATERAL_AXIS 1  /* densities sampled along the beam's axes (3 x 16 trilinear taps)  */
+#define DC_LATERAL_MLP 2   /* the trained network's prediction of the AXIS densities          */
+
 /* Value types of the dose-deposition matrix. */
 #define DC_F32 0
 #define DC_BF16 1
@@ -109,7 +114,9 @@ typedef struct {
     float smooth_sigma;
     float rho_surface;
     int32_t density_correction;
-    int32_t reserved[3];   /* must be zero */
+    int32_t lateral_mode;  /* DC_LATERAL_ISO or DC_LATERAL_AXIS at creation (DC_LATERAL_MLP
+                              needs weights: see dc_fspb_set_surrogate)                   */
+    int32_t reserved[2];   /* must be zero */
 } dc_kernel_coeffs;
 
 typedef struct dc_plan dc_plan;

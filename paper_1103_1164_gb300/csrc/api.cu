@@ -64,6 +64,16 @@ dc::PlanView dc_plan::view() const
     v.bl = d_bl;
     v.tab = d_tab;
     v.tabm = d_tabm;
+    v.lfac = d_lfac;
+    v.rho = d_rho;
+    v.dens = d_dens;
+    v.f_n = coeffs.f_n;
+    v.f_rho0 = coeffs.f_rho0;
+    v.inv_drho = 1.0f / coeffs.f_drho;
+    v.idx = 1.0f / grid.dx;
+    v.idy = 1.0f / grid.dy;
+    v.idz = 1.0f / grid.dz;
+    for (int j = 0; j < 16; ++j) v.gw[j] = gw[j];
     return v;
 }
 
@@ -74,7 +84,8 @@ static void free_plan(dc_plan* p)
                     p->d_tab, p->d_arow, p->d_tabm, p->d_A, p->d_water, p->d_dens, p->d_beamin, p->d_fluence,
                     p->d_dose, p->d_rowcount, p->d_rowptr, p->d_scan_tmp, p->d_mcols, p->d_mvals,
                     p->d_bin, p->d_bounds, p->d_cellof, p->d_hist, p->d_nitems, p->d_base, p->d_work,
-                    p->d_items, p->d_part, p->d_bcount, p->d_sp_fp, p->d_sp_p, p->d_err};
+                    p->d_items, p->d_part, p->d_bcount, p->d_sp_fp, p->d_sp_p, p->d_err,
+                    p->d_lfac, p->d_mlp_frag, p->d_mlp_bias, p->d_nfall};
     for (void* b : bufs)
         if (b) cudaFree(b);
     p->spmm_free();
@@ -192,8 +203,11 @@ static dc_status check_inputs(const float* ct, const dc_grid* g, const dc_beam* 
         return invalid("dc_fspb_create: table steps must be positive");
     if (!(c->roi_radius > 0) || !(c->smooth_sigma >= 0) || !isfinite(c->rho_surface))
         return invalid("dc_fspb_create: bad roi_radius, smooth_sigma or rho_surface");
-    if (c->reserved[0] || c->reserved[1] || c->reserved[2])
+    if (c->reserved[0] || c->reserved[1])
         return invalid("dc_fspb_create: reserved fields must be zero");
+    if (c->lateral_mode != DC_LATERAL_ISO && c->lateral_mode != DC_LATERAL_AXIS)
+        return invalid("dc_fspb_create: lateral_mode must be DC_LATERAL_ISO or DC_LATERAL_AXIS "
+                       "(the network form is enabled with dc_fspb_set_surrogate)");
     size_t sm = 2 * sizeof(float4) * c->w_n;
     if (sm > 96 * 1024) {
         set_error("dc_fspb_create: the water table exceeds 96 KiB of shared memory (w_n > 3072)");
@@ -244,15 +258,31 @@ static dc_status compute_density_steps(dc_plan* p, const float* ct, uint32_t fla
     DC_CUDA(launch_factors(p));
     DC_CUDA(launch_beamlets(p));
     DC_CUDA(launch_binning(p));
+    if (p->coeffs.density_correction && p->lateral_mode != DC_LATERAL_ISO) DC_CUDA(launch_lateral(p));
     p->pairs = -1;
     if (p->sp_ready) p->spmm_free();   // the SpMM tiles follow the voxel lists
     return DC_OK;
+}
+
+// Normalised Gaussian weights of the 16 lateral-stencil taps at (j - 7.5) d.
+static void stencil_weights(dc_plan* p)
+{
+    double w[16], s = 0.0;
+    const double sg = p->coeffs.smooth_sigma;
+    for (int j = 0; j < 16; ++j) {
+        const double x = (j - 7.5) * (double)p->d;
+        w[j] = sg > 0 ? exp(-x * x / (2.0 * sg * sg)) : 1.0;
+        s += w[j];
+    }
+    for (int j = 0; j < 16; ++j) p->gw[j] = (float)(w[j] / s);
 }
 
 static dc_status create_impl(dc_plan* p, const float* ct, uint32_t flags)
 {
     const dc_grid& g = p->grid;
     const dc_kernel_coeffs& c = p->coeffs;
+    stencil_weights(p);
+    p->lateral_mode = c.lateral_mode;
     const int64_t V = p->V;
     double diag = sqrt((double)g.nx * g.dx * g.nx * g.dx + (double)g.ny * g.dy * g.ny * g.dy +
                        (double)g.nz * g.dz * g.nz * g.dz);
@@ -295,6 +325,8 @@ static dc_status create_impl(dc_plan* p, const float* ct, uint32_t flags)
     DC_CUDA(dalloc(&p->d_part, nb * V));
     p->part_cap = nb * V;
     DC_CUDA(dalloc(&p->d_bcount, nb * V));
+    DC_CUDA(dalloc(&p->d_lfac, nb * (V + 32)));
+    DC_CUDA(dalloc(&p->d_nfall, 1));
     DC_CUDA(cudaMemcpyAsync(p->d_bin, p->bin_host.data(), nb * sizeof(BinGeom), cudaMemcpyHostToDevice,
                             p->stream));
 
@@ -403,6 +435,7 @@ static dc_status rebin(dc_plan* p, float tile, float slab)
     DC_CUDA(cudaMemcpyAsync(p->d_bin, p->bin_host.data(), p->bin_host.size() * sizeof(BinGeom),
                             cudaMemcpyHostToDevice, p->stream));
     DC_CUDA(launch_binning(p));
+    if (p->coeffs.density_correction && p->lateral_mode != DC_LATERAL_ISO) DC_CUDA(launch_lateral(p));
     p->pairs = -1;
     if (p->sp_ready) p->spmm_free();
     return DC_OK;

@@ -72,6 +72,16 @@ struct PlanView {
     //   (t_eq, dt_eq, O1, dO1), (O2, dO2, u1w, du1w), (u2w, du2w, 0, 0)
     // with O_i = omega_i^w + omega_i^corr (times 0 without density correction)
     const float4* tabm;
+    // per-(voxel, beam) lateral factors for every voxel-list entry (axis and
+    // network forms): (log2 e f_u2 along x, along y, f_w1, f_w2)
+    const float4* lfac;
+    // density and density-function tables for the lateral stencils
+    const float* rho;
+    const float* dens;
+    int f_n;
+    float f_rho0, inv_drho;
+    float idx, idy, idz;          // 1 / voxel size
+    float gw[16];                 // normalised Gaussian weights of the 16 stencil taps
 };
 
 }  // namespace dc
@@ -99,6 +109,15 @@ struct dc_plan {
     float2* d_arow = nullptr;
     float4* d_tabm = nullptr;        // merged depth + water tables (only when w_dt == d)
     bool merged = false;
+    // lateral form of step 11 (DC_LATERAL_*) and its per-entry factors
+    int lateral_mode = 0;
+    float4* d_lfac = nullptr;        // [n_beams][V + 32]
+    uint2* d_mlp_frag = nullptr;     // BF16 B fragments of the surrogate network
+    float* d_mlp_bias = nullptr;
+    float mlp_lo = 0.f, mlp_hi = 0.f;
+    bool mlp_ready = false;
+    int32_t* d_nfall = nullptr;      // entries that fell back to the plain stencil
+    float gw[16] = {0};
     float* d_A = nullptr;
     float4* d_water = nullptr;
     float* d_dens = nullptr;
@@ -196,6 +215,19 @@ cudaError_t launch_fill(const dc_plan* p, const int64_t* rowptr, int32_t* cols, 
                         int value_dtype);
 cudaError_t launch_scan_counts(const dc_plan* p, const int32_t* counts, int64_t* rowptr,
                                int64_t* total_dev);
+// lateral factors, stencil samples and the surrogate network (k_lateral.cu)
+cudaError_t launch_lateral(const dc_plan* p);
+cudaError_t launch_stencils(const dc_plan* p, const int32_t* vox, const int32_t* beam, int n, float* X, float* T);
+cudaError_t launch_mlp_predict_bf16(cudaStream_t s, const float* X, int n, const uint2* wfrag, const float* bias,
+                                    float* Y);
+cudaError_t launch_mlp_grad(cudaStream_t s, int nctas, const float* theta, const float* X, const float* T, int n,
+                            float* partial, float* loss_part);
+cudaError_t launch_mlp_adam(cudaStream_t s, const float* partial, int nparts, float* theta, float* m1, float* m2,
+                            float* grad, float lr, float b1, float b2, float eps, int step);
+constexpr int kMlpParams = 7491;
+constexpr int kMlpFragU2 = (3 * 8 + 4 * 8 + 4) * 32;
+constexpr int kMlpBias = 64 + 64 + 3;
+void mlp_pack(const float* theta, std::vector<uint2>& frag, std::vector<float>& bias);
 // block-sparse tensor-core SpMM (k_spmm.cu)
 dc_status spmm_prepare(dc_plan* p, const int64_t* rowptr, const int32_t* cols, const uint16_t* vals);
 cudaError_t spmm_run(dc_plan* p, const float* F, int k, float* Y);

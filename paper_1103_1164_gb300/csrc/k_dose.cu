@@ -76,15 +76,23 @@ __device__ __forceinline__ float penumbra(float x, float k, float kx0, float x0)
     return fmaf(0.5f, e1 - e2, fmaf(-ins, e1, ins));
 }
 
+// Lateral correction of step 11: the paper's rho(r), rho_hat(r) per voxel
+// (kIso), or per-(voxel, beam) factors precomputed for every entry of the
+// beam's voxel list by the axis-stencil pass or by the trained network
+// (k_lateral.cu), loaded once per work unit (kItem).
+enum Lateral { kIso = 0, kItem = 1 };
+
 struct Lane {
     float vx, vy, vz;     // r - source
-    float4 fac;           // log2(e) f_u1(rho), log2(e) f_u2(rho_hat), f_w1(rho_hat), f_w2(rho_hat)
+    // correction factors of the voxel for the current beam:
+    // log2(e) f_u1(rho), log2(e) f_u2 along x and along y, f_w1, f_w2
+    float cu1, cu2x, cu2y, cw1, cw2;
     bool valid;
 };
 
 // Decides whether the lane's voxel is in beamlet i's ROI and depth range and,
 // if EVAL, returns D_i(r) of eq. (2) for unit fluence.
-template <bool EVAL, bool MERGED>
+template <bool EVAL, bool MERGED, int LAT>
 __device__ __forceinline__ bool pair(const PlanView& P, const Lane& ln, int i, float sad,
                                      const float4* __restrict__ sW, float& D)
 {
@@ -138,13 +146,14 @@ __device__ __forceinline__ bool pair(const PlanView& P, const Lane& ln, int i, f
     const float Av = fmaf(fa, ar.y, ar.x);
 
     // density correction (step 11)
-    const float k1 = ln.fac.x * u1w, k2 = ln.fac.y * u2w;
-    const float om1 = fmaxf(ln.fac.z * O1, 0.f);
-    const float om2 = fmaxf(ln.fac.w * O2, 0.f);
+    const float k1 = ln.cu1 * u1w, k2 = ln.cu2x * u2w;
+    const float k2y = LAT == kIso ? k2 : ln.cu2y * u2w;
+    const float om1 = fmaxf(ln.cw1 * O1, 0.f);
+    const float om2 = fmaxf(ln.cw2 * O2, 0.f);
 
     // eqs. (3) and (2)
     const float F = fmaf(om1 * penumbra(x, k1, k1 * P.x0, P.x0), penumbra(y, k1, k1 * P.y0, P.y0),
-                         om2 * penumbra(x, k2, k2 * P.x0, P.x0) * penumbra(y, k2, k2 * P.y0, P.y0));
+                         om2 * penumbra(x, k2, k2 * P.x0, P.x0) * penumbra(y, k2y, k2y * P.y0, P.y0));
     D = F * Av * (s * s);
     return true;
 }
@@ -178,7 +187,7 @@ __device__ __forceinline__ void flush_stage(const DoseArgs& a, const int* sc, co
 // One warp work unit = 32 consecutive entries of one beam's voxel list (voxels
 // of one or two neighbouring beam's-eye-view cells; -1 entries are padding).
 // Persistent CTAs take units from a global counter.
-template <int MODE, int NF, bool MERGED>
+template <int MODE, int NF, bool MERGED, int LAT>
 __global__ void __launch_bounds__(kThreads) k_pairs(const DoseArgs a)
 {
     extern __shared__ float4 smem[];
@@ -212,12 +221,21 @@ __global__ void __launch_bounds__(kThreads) k_pairs(const DoseArgs a)
         // explicit fma: the count and fill passes must round these identically
         const float rx = fmaf((float)ix, P.dx, P.ox), ry = fmaf((float)iy, P.dy, P.oy),
                     rz = fmaf((float)iz, P.dz, P.oz);
-        if (MODE == kCount) {
-            ln.fac = make_float4(1, 1, 1, 1);
-        } else {
-            ln.fac = __ldg(P.fac + v);
-            ln.fac.x *= kLog2e;
-            ln.fac.y *= kLog2e;
+        const BeamDev& bm = P.beams[b];
+        if (MODE != kCount) {
+            const float4 fac = __ldg(P.fac + v);   // f_u1(rho), f_u2(rho_hat), f_w1(rho_hat), f_w2(rho_hat)
+            ln.cu1 = kLog2e * fac.x;
+            ln.cu2x = ln.cu2y = kLog2e * fac.y;
+            ln.cw1 = fac.z;
+            ln.cw2 = fac.w;
+            if (LAT == kItem) {
+                // (log2(e) f_u2 along x, along y, f_w1, f_w2) of this (voxel, beam)
+                const float4 lf = __ldg(P.lfac + e0 + lane);
+                ln.cu2x = lf.x;
+                ln.cu2y = lf.y;
+                ln.cw1 = lf.z;
+                ln.cw2 = lf.w;
+            }
         }
         float acc[NF];
 #pragma unroll
@@ -230,7 +248,6 @@ __global__ void __launch_bounds__(kThreads) k_pairs(const DoseArgs a)
             pend = pos + a.bcount[(size_t)b * V + v];   // this beam's segment of the row
         }
 
-        const BeamDev& bm = P.beams[b];
         const float sx = __ldg(&bm.src[0]), sy = __ldg(&bm.src[1]), sz = __ldg(&bm.src[2]);
         const float sad = __ldg(&bm.sad);
         ln.vx = rx - sx; ln.vy = ry - sy; ln.vz = rz - sz;
@@ -272,16 +289,16 @@ __global__ void __launch_bounds__(kThreads) k_pairs(const DoseArgs a)
 #pragma unroll
                     for (int q = 0; q < NF; ++q) f[q] = q < a.nf ? __ldg(a.fluence + (size_t)q * a.ldf + i) : 0.f;
                     float D;
-                    if (pair<true, MERGED>(P, ln, i, sad, sW, D)) {
+                    if (pair<true, MERGED, LAT>(P, ln, i, sad, sW, D)) {
 #pragma unroll
                         for (int q = 0; q < NF; ++q) acc[q] = fmaf(f[q], D, acc[q]);
                     }
                 } else if (MODE == kCount) {
                     float D;
-                    cnt += pair<false, false>(P, ln, i, sad, sW, D) ? 1 : 0;
+                    cnt += pair<false, false, kIso>(P, ln, i, sad, sW, D) ? 1 : 0;
                 } else {
                     float D;
-                    if (pair<true, MERGED>(P, ln, i, sad, sW, D)) {
+                    if (pair<true, MERGED, LAT>(P, ln, i, sad, sW, D)) {
                         sc[lane * kStageLd + cnt] = i;
                         sv[lane * kStageLd + cnt] = D;
                         ++cnt;
@@ -441,11 +458,11 @@ int grid_for(int64_t n)
 }
 
 // Persistent launch: as many CTAs as fit on the device at once.
-template <int MODE, int NF, bool MERGED>
+template <int MODE, int NF, bool MERGED, int LAT>
 cudaError_t run_variant(const dc_plan* p, const DoseArgs& a)
 {
     const size_t sm = smem_bytes(p, MODE);
-    auto kern = k_pairs<MODE, NF, MERGED>;
+    auto kern = k_pairs<MODE, NF, MERGED, LAT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     int per_sm = 0, sms = 0;
@@ -463,8 +480,11 @@ cudaError_t run_variant(const dc_plan* p, const DoseArgs& a)
 template <int MODE, int NF>
 cudaError_t run(const dc_plan* p, const DoseArgs& a)
 {
-    if (MODE != kCount && p->merged) return run_variant<MODE, NF, true>(p, a);
-    return run_variant<MODE, NF, false>(p, a);
+    if (MODE == kCount) return run_variant<kCount, 1, false, kIso>(p, a);
+    // per-item factors exist for the axis and network forms with the density correction on
+    const bool item = p->coeffs.density_correction && p->lateral_mode != DC_LATERAL_ISO;
+    if (p->merged) return item ? run_variant<MODE, NF, true, kItem>(p, a) : run_variant<MODE, NF, true, kIso>(p, a);
+    return item ? run_variant<MODE, NF, false, kItem>(p, a) : run_variant<MODE, NF, false, kIso>(p, a);
 }
 
 }  // namespace

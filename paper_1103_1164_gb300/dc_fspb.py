@@ -19,6 +19,8 @@ from . import build as _build
 DC_OK, DC_EINVAL, DC_ENOMEM, DC_ECUDA, DC_ETIMEOUT, DC_EUNSUPPORTED = range(6)
 DC_DEVICE_PTRS = 1
 DC_F32, DC_BF16 = 0, 1
+DC_LATERAL_ISO, DC_LATERAL_AXIS, DC_LATERAL_MLP = 0, 1, 2
+MLP_PARAMS = 7491
 
 _lib = None
 
@@ -51,7 +53,8 @@ class dc_kernel_coeffs(C.Structure):
                 ("water", C.c_void_p), ("w_n", C.c_int32), ("w_dt", C.c_float),
                 ("dens", C.c_void_p), ("f_n", C.c_int32), ("f_rho0", C.c_float), ("f_drho", C.c_float),
                 ("roi_radius", C.c_float), ("smooth_sigma", C.c_float), ("rho_surface", C.c_float),
-                ("density_correction", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("density_correction", C.c_int32), ("lateral_mode", C.c_int32),
+                ("reserved", C.c_int32 * 2)]
 
 
 EXPORTS = ["dc_last_error", "dc_status_str", "dc_fspb_create", "dc_fspb_destroy",
@@ -59,7 +62,10 @@ EXPORTS = ["dc_last_error", "dc_status_str", "dc_fspb_create", "dc_fspb_destroy"
            "dc_fspb_pair_count", "dc_fspb_dose_matrix", "dc_fspb_get_smoothed",
            "dc_fspb_get_beamlets", "dc_fspb_get_tables", "dc_fspb_set_density",
            "dc_fspb_launch_count", "dc_fspb_autotune", "dc_fspb_spmm_prepare", "dc_fspb_spmm_info",
-           "dc_fspb_spmm", "dc_fspb_device_status"]
+           "dc_fspb_spmm", "dc_fspb_device_status", "dc_fspb_set_surrogate",
+           "dc_fspb_set_lateral_mode", "dc_fspb_lateral_fallbacks", "dc_fspb_stencils",
+           "dc_mlp_create", "dc_mlp_destroy", "dc_mlp_get_params", "dc_mlp_gradient", "dc_mlp_train",
+           "dc_mlp_predict"]
 
 
 def library_path() -> str:
@@ -100,6 +106,16 @@ def load():
     L.dc_fspb_spmm_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
     L.dc_fspb_spmm.argtypes = [vp, vp, i32, vp, u32]
     L.dc_fspb_device_status.argtypes = [vp]
+    L.dc_fspb_set_surrogate.argtypes = [vp, vp, C.c_float, C.c_float]
+    L.dc_fspb_set_lateral_mode.argtypes = [vp, i32]
+    L.dc_fspb_lateral_fallbacks.argtypes = [vp, C.POINTER(i64)]
+    L.dc_fspb_stencils.argtypes = [vp, vp, vp, i32, vp, vp, u32]
+    L.dc_mlp_create.argtypes = [vp, vp, C.POINTER(vp)]
+    L.dc_mlp_destroy.argtypes = [vp]
+    L.dc_mlp_get_params.argtypes = [vp, vp]
+    L.dc_mlp_gradient.argtypes = [vp, vp, vp, i32, vp, C.POINTER(C.c_float), u32]
+    L.dc_mlp_train.argtypes = [vp, vp, vp, i32, i32, i32, C.c_float, C.POINTER(C.c_float), u32]
+    L.dc_mlp_predict.argtypes = [vp, vp, i32, vp, u32, vp]
     for name in EXPORTS:
         if name not in ("dc_last_error", "dc_status_str"):
             getattr(L, name).restype = C.c_int
@@ -159,7 +175,7 @@ class Plan:
             self.handle = None
 
 
-def make_coeffs(comm):
+def make_coeffs(comm, lateral_mode=DC_LATERAL_ISO):
     """dc_kernel_coeffs from a synth.Commissioning (arrays kept alive by the caller)."""
     A = np.ascontiguousarray(comm.A, np.float32)
     W = np.ascontiguousarray(comm.water, np.float32)
@@ -167,11 +183,13 @@ def make_coeffs(comm):
     c = dc_kernel_coeffs(A.ctypes.data, A.shape[1], A.shape[0], comm.a_dt, comm.a_dtheta,
                          W.ctypes.data, W.shape[1], comm.w_dt, D.ctypes.data, D.shape[1],
                          comm.f_rho0, comm.f_drho, comm.roi_radius, comm.smooth_sigma,
-                         comm.rho_surface, int(comm.density_correction), (C.c_int32 * 3)(0, 0, 0))
+                         comm.rho_surface, int(comm.density_correction), int(lateral_mode),
+                         (C.c_int32 * 2)(0, 0))
     return c, (A, W, D)
 
 
-def dc_fspb_create(ct_density, grid, beams, beamlet_x, beamlet_y, comm, stream=None) -> Plan:
+def dc_fspb_create(ct_density, grid, beams, beamlet_x, beamlet_y, comm, stream=None,
+                   lateral_mode=DC_LATERAL_ISO) -> Plan:
     """Builds a plan (ct_density: [nz, ny, nx] float32, host array or CUDA tensor)."""
     L = load()
     p_rho, flag = _ptr(ct_density)
@@ -180,7 +198,7 @@ def dc_fspb_create(ct_density, grid, beams, beamlet_x, beamlet_y, comm, stream=N
     for q, b in enumerate(beams):
         arr[q] = dc_beam(b.gantry_deg, b.couch_deg, b.coll_deg, b.sad, (C.c_float * 3)(*b.iso),
                          b.field_x, b.field_y)
-    coeffs, keep = make_coeffs(comm)
+    coeffs, keep = make_coeffs(comm, lateral_mode)
     h = C.c_void_p()
     s = _current_stream() if stream is None else stream
     _check(L.dc_fspb_create(p_rho, C.byref(g), arr, len(beams), beamlet_x, beamlet_y,
@@ -191,12 +209,13 @@ def dc_fspb_create(ct_density, grid, beams, beamlet_x, beamlet_y, comm, stream=N
     return Plan(h, nb.value, nv.value, (grid.nz, grid.ny, grid.nx))
 
 
-def dc_fspb_create_from(plan_inputs, stream=None, device_density=None) -> Plan:
+def dc_fspb_create_from(plan_inputs, stream=None, device_density=None,
+                        lateral_mode=DC_LATERAL_ISO) -> Plan:
     """dc_fspb_create from a synth.Plan."""
     rho = plan_inputs.rho if device_density is None else device_density
     return dc_fspb_create(np.ascontiguousarray(rho, np.float32) if device_density is None else rho,
                           plan_inputs.grid, plan_inputs.beams, plan_inputs.beamlet_x,
-                          plan_inputs.beamlet_y, plan_inputs.comm, stream)
+                          plan_inputs.beamlet_y, plan_inputs.comm, stream, lateral_mode)
 
 
 def dc_fspb_set_density(plan: Plan, ct_density):
@@ -238,6 +257,86 @@ def dc_fspb_spmm(plan: Plan, F, Y=None):
 
 def dc_fspb_device_status(plan: Plan):
     _check(load().dc_fspb_device_status(plan.handle))
+
+
+def dc_fspb_set_surrogate(plan: Plan, params, rho_lo=0.05, rho_hi=2.0):
+    """Loads the surrogate network's 7491 parameters (host float32) and its training density range."""
+    p = np.ascontiguousarray(params, np.float32)
+    assert p.size == MLP_PARAMS
+    _check(load().dc_fspb_set_surrogate(plan.handle, p.ctypes.data_as(C.c_void_p), rho_lo, rho_hi))
+
+
+def dc_fspb_set_lateral_mode(plan: Plan, mode: int):
+    _check(load().dc_fspb_set_lateral_mode(plan.handle, int(mode)))
+
+
+def dc_fspb_lateral_fallbacks(plan: Plan) -> int:
+    n = C.c_int64()
+    _check(load().dc_fspb_lateral_fallbacks(plan.handle, C.byref(n)))
+    return n.value
+
+
+def dc_fspb_stencils(plan: Plan, voxels, beams):
+    """(X [n, 48] nearest-voxel taps, T [n, 3] axis-stencil densities) for (voxel, beam) pairs."""
+    v = np.ascontiguousarray(voxels, np.int32)
+    b = np.ascontiguousarray(beams, np.int32)
+    n = v.size
+    X = np.empty((n, 48), np.float32)
+    T = np.empty((n, 3), np.float32)
+    _check(load().dc_fspb_stencils(plan.handle, v.ctypes.data_as(C.c_void_p), b.ctypes.data_as(C.c_void_p), n,
+                                   X.ctypes.data_as(C.c_void_p), T.ctypes.data_as(C.c_void_p), 0))
+    return X, T
+
+
+class Mlp:
+    """Trainer of the surrogate network (dc_mlp_*), FP32 on the GPU."""
+
+    def __init__(self, params, stream=None):
+        p = np.ascontiguousarray(params, np.float32)
+        assert p.size == MLP_PARAMS
+        h = C.c_void_p()
+        s = _current_stream() if stream is None else stream
+        _check(load().dc_mlp_create(p.ctypes.data_as(C.c_void_p), C.c_void_p(s), C.byref(h)))
+        self.handle = h
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.dc_mlp_destroy(self.handle)
+            self.handle = None
+
+    def params(self):
+        out = np.empty(MLP_PARAMS, np.float32)
+        _check(load().dc_mlp_get_params(self.handle, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def gradient(self, X, T):
+        X = np.ascontiguousarray(X, np.float32)
+        T = np.ascontiguousarray(T, np.float32)
+        g = np.empty(MLP_PARAMS, np.float32)
+        loss = C.c_float()
+        _check(load().dc_mlp_gradient(self.handle, X.ctypes.data_as(C.c_void_p), T.ctypes.data_as(C.c_void_p),
+                                      X.shape[0], g.ctypes.data_as(C.c_void_p), C.byref(loss), 0))
+        return loss.value, g
+
+    def train(self, X, T, batch=4096, epochs=1, lr=1e-3):
+        """Minibatch Adam over X, T in the given order; returns the final loss on all of X."""
+        X = np.ascontiguousarray(X, np.float32)
+        T = np.ascontiguousarray(T, np.float32)
+        loss = C.c_float()
+        _check(load().dc_mlp_train(self.handle, X.ctypes.data_as(C.c_void_p), T.ctypes.data_as(C.c_void_p),
+                                   X.shape[0], batch, epochs, lr, C.byref(loss), 0))
+        return loss.value
+
+
+def dc_mlp_predict(params, X, stream=None):
+    """BF16 tensor-core inference of the network (the dose path's arithmetic): [n, 48] -> [n, 3]."""
+    p = np.ascontiguousarray(params, np.float32)
+    X = np.ascontiguousarray(X, np.float32)
+    Y = np.empty((X.shape[0], 3), np.float32)
+    s = _current_stream() if stream is None else stream
+    _check(load().dc_mlp_predict(p.ctypes.data_as(C.c_void_p), X.ctypes.data_as(C.c_void_p), X.shape[0],
+                                 Y.ctypes.data_as(C.c_void_p), 0, C.c_void_p(s)))
+    return Y
 
 
 def dc_fspb_launch_count() -> int:
