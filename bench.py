@@ -362,6 +362,7 @@ def run_ours(args, world, rank, local, pg):
               "nnz": pairs, "bytes": bytes_matrix}
 
     forms = run_forms(args, dc, torch, stream, peaks)
+    forms["surrogate"] = run_surrogate_form(args, dc, torch, stream)
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, dc, p, plan, pairs, torch)
@@ -450,6 +451,61 @@ def run_forms(args, dc, torch, stream, peaks, k=64):
                                        "bytes": bytes_alg},
                           "max_err_vs_fp32_over_colmax": err},
             "speedup_bf16_over_fp32": t_plain / t_spmm}
+
+
+def run_surrogate_form(args, dc, torch, stream, k=64):
+    """The learned lateral correction: 2M (nearest-tap stencil, plain axis
+    densities) samples from 200 random slab/sphere phantoms, trained with the
+    library's kernels, then the slab plan's 64-fluence dose with the network's
+    correction and the BF16 tensor-core SpMM, against the plain FP32 form (axis
+    stencils, direct evaluation), which is also the judge of its error."""
+    from paper_1103_1164_gb300 import surrogate, synth
+    t0 = time.perf_counter()
+    X, T = surrogate.generate_samples(n_phantoms=200, per_phantom=10000, seed=2024)
+    t_gen = time.perf_counter() - t0
+    n_tr = int(0.9 * X.shape[0])
+    t0 = time.perf_counter()
+    params, loss = surrogate.train(X[:n_tr], T[:n_tr], epochs=8, batch=4096, lr=2e-3, seed=17)
+    t_train = time.perf_counter() - t0
+    held = np.abs(dc.dc_mlp_predict(params, X[n_tr:]) - T[n_tr:]).max(1)
+
+    p1 = synth.config1()
+    rho = torch.from_numpy(p1.rho).cuda()
+    plan = dc.dc_fspb_create_from(p1, stream=stream.cuda_stream, device_density=rho,
+                                  lateral_mode=dc.DC_LATERAL_AXIS)
+    F = torch.from_numpy(np.random.default_rng(synth.FLUENCE_SEED).uniform(0, 1, (plan.n_beamlets, k))
+                         .astype(np.float32)).cuda()
+    Ft = F.t().contiguous()
+    dose = torch.empty((k, plan.n_voxels), device="cuda")
+    Y = torch.empty((plan.n_voxels, k), device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    dc.dc_fspb_autotune(plan, F[:, 0].contiguous())
+    reps = max(3, args.steps)
+    # plain FP32 form: axis-stencil factors (per density) + direct 64-fluence evaluation
+    t_set_axis = time_on_stream(torch, stream, lambda: dc.dc_fspb_set_density(plan, rho), reps, flush)
+    dc.dc_fspb_dose_batch(plan, Ft, dose)
+    t_plain = time_on_stream(torch, stream, lambda: dc.dc_fspb_dose_batch(plan, Ft, dose), reps, flush)
+    plain = dose.clone()
+    # surrogate + BF16 form: network factors (per density), BF16 matrix, tensor-core SpMM
+    dc.dc_fspb_set_surrogate(plan, params, surrogate.RHO_LO, surrogate.RHO_HI)
+    dc.dc_fspb_set_lateral_mode(plan, dc.DC_LATERAL_MLP)
+    t_set_mlp = time_on_stream(torch, stream, lambda: dc.dc_fspb_set_density(plan, rho), reps, flush)
+    t0 = time.perf_counter()
+    dc.dc_fspb_spmm_prepare(plan)
+    t_prep = time.perf_counter() - t0
+    dc.dc_fspb_spmm(plan, F, Y)
+    t_spmm = time_on_stream(torch, stream, lambda: dc.dc_fspb_spmm(plan, F, Y), reps, flush)
+    dc.dc_fspb_device_status(plan)
+    err = float(((Y.t() - plain).abs().max(1).values / plain.abs().max(1).values).max())
+    return {"workload": f"slab64 64^3 @0.25cm, 1 beam, {plan.n_beamlets} beamlets, {k} fluences U[0,1]; "
+                        f"network 48-64-64-3 SiLU trained on {n_tr} stencils from 200 random phantoms",
+            "samples_generate_s": t_gen, "train_s": t_train, "train_loss": loss,
+            "held_out_abs_err_density": {"p50": float(np.median(held)), "p99": float(np.percentile(held, 99))},
+            "plain_fp32_axis": {"set_density_ms": t_set_axis, "dose_64_ms": t_plain},
+            "surrogate_bf16": {"set_density_ms": t_set_mlp, "spmm_prepare_s": t_prep, "spmm_64_ms": t_spmm,
+                               "fallbacks": dc.dc_fspb_lateral_fallbacks(plan)},
+            "speedup_64_fluences": t_plain / t_spmm,
+            "max_err_vs_plain_over_colmax": err}
 
 
 def run_e2e(args, dc, p, plan, pairs, torch):
