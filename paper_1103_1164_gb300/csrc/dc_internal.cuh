@@ -82,6 +82,26 @@ struct PlanView {
     float f_rho0, inv_drho;
     float idx, idy, idz;          // 1 / voxel size
     float gw[16];                 // normalised Gaussian weights of the 16 stencil taps
+    int merged_rt;                // tabm is in use (runtime copy of the plan's choice)
+    int item_rt;                  // lfac is in use
+};
+
+// Arguments of the pair kernels (k_dose.cu) for one plan.
+struct DoseArgs {
+    PlanView P;
+    const float* fluence;   // [nf][ldf]
+    int nf, ldf;
+    float* dose;            // [nf][ldd]
+    int64_t ldd;
+    float* part;            // dose: per-beam partial dose [n_beams][NF][V]
+    int32_t* bcount;        // count: per-beam pair counts [n_beams][V]; fill reads them
+    const int64_t* rowptr;  // fill
+    int32_t* cols;
+    void* vals;
+    int value_dtype;
+    const int32_t* items;   // beam voxel lists (k_bin.cu)
+    const int64_t* base;    // [n_beams + 1]
+    int32_t* work;          // [0] work units, [1] counter
 };
 
 }  // namespace dc
@@ -228,6 +248,11 @@ constexpr int kMlpParams = 7491;
 constexpr int kMlpFragU2 = (3 * 8 + 4 * 8 + 4) * 32;
 constexpr int kMlpBias = 64 + 64 + 3;
 void mlp_pack(const float* theta, std::vector<uint2>& frag, std::vector<float>& bias);
+// multi-plan batch (k_dose.cu)
+DoseArgs dose_args(const dc_plan* p, const float* fluence, float* part);
+cudaError_t launch_batch(cudaStream_t s, const DoseArgs* d_args, int n, int64_t* d_prefix,
+                         unsigned long long* d_counter, int device);
+cudaError_t launch_sum_one(const dc_plan* p, cudaStream_t s, const float* part, float* dose);
 // block-sparse tensor-core SpMM (k_spmm.cu)
 dc_status spmm_prepare(dc_plan* p, const int64_t* rowptr, const int32_t* cols, const uint16_t* vals);
 cudaError_t spmm_run(dc_plan* p, const float* F, int k, float* Y);

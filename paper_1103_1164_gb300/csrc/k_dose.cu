@@ -30,23 +30,6 @@ constexpr int kStageLd = kStage + 1;
 
 enum Mode { kDose = 0, kCount = 1, kFill = 2 };
 
-struct DoseArgs {
-    PlanView P;
-    const float* fluence;   // [nf][ldf]
-    int nf, ldf;
-    float* dose;            // [nf][ldd]
-    int64_t ldd;
-    float* part;            // kDose: per-beam partial dose [n_beams][NF][V]
-    int32_t* bcount;        // kCount: per-beam pair counts [n_beams][V]; kFill reads them
-    const int64_t* rowptr;  // kFill
-    int32_t* cols;
-    void* vals;
-    int value_dtype;
-    const int32_t* items;   // beam voxel lists (k_bin.cu)
-    const int64_t* base;    // [n_beams + 1]
-    int32_t* work;          // [0] work units, [1] counter
-};
-
 __device__ __forceinline__ float ex2(float x)
 {
     float y;
@@ -184,6 +167,120 @@ __device__ __forceinline__ void flush_stage(const DoseArgs& a, const int* sc, co
     cnt = 0;
 }
 
+// Evaluates one warp work unit: the 32 list entries starting at e0 of beam b
+// (one voxel per lane) against the beamlets of the warp's union window.
+template <int MODE, int NF, bool MERGED, int LAT>
+__device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi, const int64_t e0, const int b,
+                                             const float4* __restrict__ sW, int* sc, float* sv, const int lane)
+{
+    const PlanView& P = a.P;
+    const int64_t V = (int64_t)P.nx * P.ny * P.nz;
+    Lane ln;
+    ln.valid = vi >= 0;
+    const int64_t v = ln.valid ? vi : 0;
+    const int ix = (int)(v % P.nx), iy = (int)((v / P.nx) % P.ny), iz = (int)(v / ((int64_t)P.nx * P.ny));
+    // explicit fma: the count and fill passes must round these identically
+    const float rx = fmaf((float)ix, P.dx, P.ox), ry = fmaf((float)iy, P.dy, P.oy),
+                rz = fmaf((float)iz, P.dz, P.oz);
+    const BeamDev& bm = P.beams[b];
+    if (MODE != kCount) {
+        const float4 fac = __ldg(P.fac + v);   // f_u1(rho), f_u2(rho_hat), f_w1(rho_hat), f_w2(rho_hat)
+        ln.cu1 = kLog2e * fac.x;
+        ln.cu2x = ln.cu2y = kLog2e * fac.y;
+        ln.cw1 = fac.z;
+        ln.cw2 = fac.w;
+        if (LAT == kItem) {
+            // (log2(e) f_u2 along x, along y, f_w1, f_w2) of this (voxel, beam)
+            const float4 lf = __ldg(P.lfac + e0 + lane);
+            ln.cu2x = lf.x;
+            ln.cu2y = lf.y;
+            ln.cw1 = lf.z;
+            ln.cw2 = lf.w;
+        }
+    }
+    float acc[NF];
+#pragma unroll
+    for (int q = 0; q < NF; ++q) acc[q] = 0.f;
+    int32_t cnt = 0;
+    int64_t pos = 0, pend = 0;
+    if (MODE == kFill && ln.valid) {
+        pos = a.rowptr[v];
+        for (int bb = 0; bb < b; ++bb) pos += a.bcount[(size_t)bb * V + v];
+        pend = pos + a.bcount[(size_t)b * V + v];   // this beam's segment of the row
+    }
+
+    const float sx = __ldg(&bm.src[0]), sy = __ldg(&bm.src[1]), sz = __ldg(&bm.src[2]);
+    const float sad = __ldg(&bm.sad);
+    ln.vx = rx - sx; ln.vy = ry - sy; ln.vz = rz - sz;
+    const float zz = ln.vx * __ldg(&bm.ez[0]) + ln.vy * __ldg(&bm.ez[1]) + ln.vz * __ldg(&bm.ez[2]);
+    const float pa = ln.vx * __ldg(&bm.ex[0]) + ln.vy * __ldg(&bm.ex[1]) + ln.vz * __ldg(&bm.ex[2]);
+    const float pc = ln.vx * __ldg(&bm.ey[0]) + ln.vy * __ldg(&bm.ey[1]) + ln.vz * __ldg(&bm.ey[2]);
+    const int M = __ldg(&bm.M), N = __ldg(&bm.N), first = __ldg(&bm.first);
+    const float hfx = __ldg(&bm.half_fx), hfy = __ldg(&bm.half_fy);
+    const bool live = ln.valid && zz > 1e-3f;
+    // isocentre-plane projection of the voxel and a conservative radius of
+    // the set of beamlet axes whose ROI cylinder can hold it
+    const float sz_ = sad / zz;
+    const float ca = pa * sz_, cc = pc * sz_;
+    const float rw = live ? (P.roi * sz_ * __ldg(&bm.inv_cos_max)) * 1.0005f + 1e-3f : 0.f;
+
+    int nlo = INT_MAX, nhi = INT_MIN;
+    if (live) {
+        nlo = max(0, (int)ceilf((cc - rw + hfy) / P.by - 0.5f));
+        nhi = min(N - 1, (int)floorf((cc + rw + hfy) / P.by - 0.5f));
+    }
+    const int wnlo = __reduce_min_sync(0xffffffffu, nlo);
+    const int wnhi = __reduce_max_sync(0xffffffffu, nhi);
+    for (int n = wnlo; n <= wnhi; ++n) {
+        const float dc_ = cc - (-hfy + (n + 0.5f) * P.by);
+        const float h2 = rw * rw - dc_ * dc_;
+        int mlo = INT_MAX, mhi = INT_MIN;
+        if (live && h2 >= 0.f) {
+            const float hx = sqrtf(h2);
+            mlo = max(0, (int)ceilf((ca - hx + hfx) / P.bx - 0.5f));
+            mhi = min(M - 1, (int)floorf((ca + hx + hfx) / P.bx - 0.5f));
+        }
+        const int wmlo = __reduce_min_sync(0xffffffffu, mlo);
+        const int wmhi = __reduce_max_sync(0xffffffffu, mhi);
+        const int row = first + n * M;
+        for (int m = wmlo; m <= wmhi; ++m) {
+            const int i = row + m;
+            if (MODE == kDose) {
+                float f[NF];
+#pragma unroll
+                for (int q = 0; q < NF; ++q) f[q] = q < a.nf ? __ldg(a.fluence + (size_t)q * a.ldf + i) : 0.f;
+                float D;
+                if (pair<true, MERGED, LAT>(P, ln, i, sad, sW, D)) {
+#pragma unroll
+                    for (int q = 0; q < NF; ++q) acc[q] = fmaf(f[q], D, acc[q]);
+                }
+            } else if (MODE == kCount) {
+                float D;
+                cnt += pair<false, false, kIso>(P, ln, i, sad, sW, D) ? 1 : 0;
+            } else {
+                float D;
+                if (pair<true, MERGED, LAT>(P, ln, i, sad, sW, D)) {
+                    sc[lane * kStageLd + cnt] = i;
+                    sv[lane * kStageLd + cnt] = D;
+                    ++cnt;
+                }
+                if (__any_sync(0xffffffffu, cnt == kStage)) flush_stage(a, sc, sv, lane, cnt, pos, pend);
+            }
+        }
+    }
+    if (MODE == kFill) {
+        flush_stage(a, sc, sv, lane, cnt, pos, pend);
+    } else if (ln.valid) {
+        if (MODE == kDose) {
+#pragma unroll
+            for (int q = 0; q < NF; ++q)
+                if (q < a.nf) a.part[((size_t)b * NF + q) * V + v] = acc[q];
+        } else {
+            a.bcount[(size_t)b * V + v] = cnt;
+        }
+    }
+}
+
 // One warp work unit = 32 consecutive entries of one beam's voxel list (voxels
 // of one or two neighbouring beam's-eye-view cells; -1 entries are padding).
 // Persistent CTAs take units from a global counter.
@@ -214,110 +311,7 @@ __global__ void __launch_bounds__(kThreads) k_pairs(const DoseArgs a)
         while (b + 1 < P.n_beams && s_base[b + 1] <= e0) ++b;
         const int32_t vi = __ldg(a.items + e0 + lane);
 
-        Lane ln;
-        ln.valid = vi >= 0;
-        const int64_t v = ln.valid ? vi : 0;
-        const int ix = (int)(v % P.nx), iy = (int)((v / P.nx) % P.ny), iz = (int)(v / ((int64_t)P.nx * P.ny));
-        // explicit fma: the count and fill passes must round these identically
-        const float rx = fmaf((float)ix, P.dx, P.ox), ry = fmaf((float)iy, P.dy, P.oy),
-                    rz = fmaf((float)iz, P.dz, P.oz);
-        const BeamDev& bm = P.beams[b];
-        if (MODE != kCount) {
-            const float4 fac = __ldg(P.fac + v);   // f_u1(rho), f_u2(rho_hat), f_w1(rho_hat), f_w2(rho_hat)
-            ln.cu1 = kLog2e * fac.x;
-            ln.cu2x = ln.cu2y = kLog2e * fac.y;
-            ln.cw1 = fac.z;
-            ln.cw2 = fac.w;
-            if (LAT == kItem) {
-                // (log2(e) f_u2 along x, along y, f_w1, f_w2) of this (voxel, beam)
-                const float4 lf = __ldg(P.lfac + e0 + lane);
-                ln.cu2x = lf.x;
-                ln.cu2y = lf.y;
-                ln.cw1 = lf.z;
-                ln.cw2 = lf.w;
-            }
-        }
-        float acc[NF];
-#pragma unroll
-        for (int q = 0; q < NF; ++q) acc[q] = 0.f;
-        int32_t cnt = 0;
-        int64_t pos = 0, pend = 0;
-        if (MODE == kFill && ln.valid) {
-            pos = a.rowptr[v];
-            for (int bb = 0; bb < b; ++bb) pos += a.bcount[(size_t)bb * V + v];
-            pend = pos + a.bcount[(size_t)b * V + v];   // this beam's segment of the row
-        }
-
-        const float sx = __ldg(&bm.src[0]), sy = __ldg(&bm.src[1]), sz = __ldg(&bm.src[2]);
-        const float sad = __ldg(&bm.sad);
-        ln.vx = rx - sx; ln.vy = ry - sy; ln.vz = rz - sz;
-        const float zz = ln.vx * __ldg(&bm.ez[0]) + ln.vy * __ldg(&bm.ez[1]) + ln.vz * __ldg(&bm.ez[2]);
-        const float pa = ln.vx * __ldg(&bm.ex[0]) + ln.vy * __ldg(&bm.ex[1]) + ln.vz * __ldg(&bm.ex[2]);
-        const float pc = ln.vx * __ldg(&bm.ey[0]) + ln.vy * __ldg(&bm.ey[1]) + ln.vz * __ldg(&bm.ey[2]);
-        const int M = __ldg(&bm.M), N = __ldg(&bm.N), first = __ldg(&bm.first);
-        const float hfx = __ldg(&bm.half_fx), hfy = __ldg(&bm.half_fy);
-        const bool live = ln.valid && zz > 1e-3f;
-        // isocentre-plane projection of the voxel and a conservative radius of
-        // the set of beamlet axes whose ROI cylinder can hold it
-        const float sz_ = sad / zz;
-        const float ca = pa * sz_, cc = pc * sz_;
-        const float rw = live ? (P.roi * sz_ * __ldg(&bm.inv_cos_max)) * 1.0005f + 1e-3f : 0.f;
-
-        int nlo = INT_MAX, nhi = INT_MIN;
-        if (live) {
-            nlo = max(0, (int)ceilf((cc - rw + hfy) / P.by - 0.5f));
-            nhi = min(N - 1, (int)floorf((cc + rw + hfy) / P.by - 0.5f));
-        }
-        const int wnlo = __reduce_min_sync(0xffffffffu, nlo);
-        const int wnhi = __reduce_max_sync(0xffffffffu, nhi);
-        for (int n = wnlo; n <= wnhi; ++n) {
-            const float dc_ = cc - (-hfy + (n + 0.5f) * P.by);
-            const float h2 = rw * rw - dc_ * dc_;
-            int mlo = INT_MAX, mhi = INT_MIN;
-            if (live && h2 >= 0.f) {
-                const float hx = sqrtf(h2);
-                mlo = max(0, (int)ceilf((ca - hx + hfx) / P.bx - 0.5f));
-                mhi = min(M - 1, (int)floorf((ca + hx + hfx) / P.bx - 0.5f));
-            }
-            const int wmlo = __reduce_min_sync(0xffffffffu, mlo);
-            const int wmhi = __reduce_max_sync(0xffffffffu, mhi);
-            const int row = first + n * M;
-            for (int m = wmlo; m <= wmhi; ++m) {
-                const int i = row + m;
-                if (MODE == kDose) {
-                    float f[NF];
-#pragma unroll
-                    for (int q = 0; q < NF; ++q) f[q] = q < a.nf ? __ldg(a.fluence + (size_t)q * a.ldf + i) : 0.f;
-                    float D;
-                    if (pair<true, MERGED, LAT>(P, ln, i, sad, sW, D)) {
-#pragma unroll
-                        for (int q = 0; q < NF; ++q) acc[q] = fmaf(f[q], D, acc[q]);
-                    }
-                } else if (MODE == kCount) {
-                    float D;
-                    cnt += pair<false, false, kIso>(P, ln, i, sad, sW, D) ? 1 : 0;
-                } else {
-                    float D;
-                    if (pair<true, MERGED, LAT>(P, ln, i, sad, sW, D)) {
-                        sc[lane * kStageLd + cnt] = i;
-                        sv[lane * kStageLd + cnt] = D;
-                        ++cnt;
-                    }
-                    if (__any_sync(0xffffffffu, cnt == kStage)) flush_stage(a, sc, sv, lane, cnt, pos, pend);
-                }
-            }
-        }
-        if (MODE == kFill) {
-            flush_stage(a, sc, sv, lane, cnt, pos, pend);
-        } else if (ln.valid) {
-            if (MODE == kDose) {
-#pragma unroll
-                for (int q = 0; q < NF; ++q)
-                    if (q < a.nf) a.part[((size_t)b * NF + q) * V + v] = acc[q];
-            } else {
-                a.bcount[(size_t)b * V + v] = cnt;
-            }
-        }
+        process_unit<MODE, NF, MERGED, LAT>(a, vi, e0, b, sW, sc, sv, lane);
     }
 }
 
