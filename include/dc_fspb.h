@@ -231,6 +231,36 @@ dc_status dc_fspb_spmm_info(const dc_plan* plan, int64_t* chunks, int64_t* row_b
  */
 dc_status dc_fspb_spmm(dc_plan* plan, const float* F, int32_t k, float* Y, uint32_t flags);
 
+/* Limits of dc_fspb_spmm_noalloc's static scratch (per device: 1.05 MiB of
+ * packed BF16 fluences and 16 MiB of per-beam partial rows). */
+#define DC_SPMM_STATIC_MAX_BEAMLETS 8192
+#define DC_SPMM_STATIC_MAX_PARTIALS 4194304
+
+/*
+ * dc_fspb_spmm for device buffers, allocating no device memory: the packed
+ * fluences and the per-beam partial rows live in file-scope device arrays of
+ * fixed size.  The paper has no counterpart; this entry point serves callers
+ * that cannot allocate during the call: an optimiser or serving loop that has
+ * handed the device's free memory to its own pool (a cudaMalloc would fail or
+ * evict), and latency-bound loops where a cudaFree would synchronise the whole
+ * device.  Same arithmetic and result as dc_fspb_spmm.
+ *   F [B][k] float32, Y [V][k] float32: device memory, caller-owned; the call
+ *   is asynchronous on the plan's stream.
+ * Limits: B <= DC_SPMM_STATIC_MAX_BEAMLETS and, for plans of more than one
+ * beam, (entries of all beam voxel lists) x k <= DC_SPMM_STATIC_MAX_PARTIALS;
+ * larger problems are rejected with DC_EINVAL (use dc_fspb_spmm).
+ * Set-up: the first call on a device looks up the arrays' device addresses
+ * (cudaGetSymbolAddress with that device current); make that first call
+ * before any stream capture.
+ * The arrays are shared by all plans on a device: calls whose executions
+ * overlap (other streams, other plans, other threads) race on them and give
+ * undefined results; serialise them.
+ * Errors: DC_EINVAL (not prepared, bad k, over the limits), DC_ECUDA;
+ * DC_ETIMEOUT of a bounded device-side wait is reported by the next
+ * dc_fspb_device_status.
+ */
+dc_status dc_fspb_spmm_noalloc(dc_plan* plan, const float* F, int32_t k, float* Y);
+
 /* Waits for the plan's stream and reports DC_ETIMEOUT if a bounded
  * device-side wait of an earlier call gave up, else DC_OK. */
 dc_status dc_fspb_device_status(dc_plan* plan);

@@ -712,6 +712,23 @@ dc_status dc_fspb_spmm(dc_plan* plan, const float* F, int32_t k, float* Y, uint3
     return check_device_status(plan);
 }
 
+dc_status dc_fspb_spmm_noalloc(dc_plan* plan, const float* F, int32_t k, float* Y)
+{
+    if (!plan || !F || !Y) return invalid("dc_fspb_spmm_noalloc: NULL argument");
+    if (k < 1 || k > 64) return invalid("dc_fspb_spmm_noalloc: k must be in [1, 64]");
+    if (!plan->sp_ready) return invalid("dc_fspb_spmm_noalloc: call dc_fspb_spmm_prepare first");
+    if (plan->B > DC_SPMM_STATIC_MAX_BEAMLETS)
+        return invalid("dc_fspb_spmm_noalloc: " + std::to_string(plan->B) +
+                       " beamlets exceed the static scratch limit of " +
+                       std::to_string(DC_SPMM_STATIC_MAX_BEAMLETS) + "; use dc_fspb_spmm");
+    if (plan->n_beams > 1 && plan->sp_items_total * (int64_t)k > (int64_t)DC_SPMM_STATIC_MAX_PARTIALS)
+        return invalid("dc_fspb_spmm_noalloc: " + std::to_string(plan->sp_items_total) + " beam-list entries x k = " +
+                       std::to_string(k) + " partial values exceed the static scratch limit of " +
+                       std::to_string(DC_SPMM_STATIC_MAX_PARTIALS) + "; use dc_fspb_spmm");
+    DC_CUDA(spmm_run_static(plan, F, k, Y));
+    return DC_OK;
+}
+
 dc_status dc_fspb_get_smoothed(const dc_plan* plan, float* out, uint32_t flags)
 {
     if (!plan || !out) return invalid("dc_fspb_get_smoothed: NULL argument");

@@ -256,5 +256,6 @@ cudaError_t launch_sum_one(const dc_plan* p, cudaStream_t s, const float* part, 
 // block-sparse tensor-core SpMM (k_spmm.cu)
 dc_status spmm_prepare(dc_plan* p, const int64_t* rowptr, const int32_t* cols, const uint16_t* vals);
 cudaError_t spmm_run(dc_plan* p, const float* F, int k, float* Y);
+cudaError_t spmm_run_static(dc_plan* p, const float* F, int k, float* Y);   // scratch in static device memory
 
 }  // namespace dc

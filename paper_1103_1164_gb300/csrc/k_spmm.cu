@@ -23,6 +23,7 @@
 // Per-beam partial results are combined with compensated (Neumaier) sums.
 #include <stdint.h>
 
+#include <mutex>
 #include <vector>
 
 #include "dc_internal.cuh"
@@ -606,6 +607,132 @@ cudaError_t spmm_run(dc_plan* p, const float* F, int k, float* Y)
     }
     if (!direct) {
         k_spmm_reduce<<<gsize(p->V * k), 256, 0, p->stream>>>(p->d_sp_p, p->d_sp_inv, p->n_beams, p->V, k, Y);
+        count_launches(1);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+// ---------------------------------------------------------------------------
+// SpMM with its scratch in static device memory (dc_fspb_spmm_noalloc).
+//
+// Callers that cannot allocate: an optimiser or serving loop that has handed
+// the device's free memory to its own pool (a cudaMalloc there fails or has
+// to evict), and a latency-bound loop where a cudaFree would synchronise the
+// whole device and stall the other streams.  For them the packed fluences and
+// the per-beam partial rows live in the file-scope arrays below, whose
+// addresses are looked up once per device; the call itself allocates nothing.
+// The arrays are shared by every plan on the device, so two such calls in
+// flight at once (two streams, two plans, two threads) race on them.
+namespace {
+
+constexpr int kStaticNkb = (DC_SPMM_STATIC_MAX_BEAMLETS + 7) / 8 + 2;
+constexpr size_t kStaticFp = (size_t)kStaticNkb * 8 * kN;   // BF16 elements
+
+// Packed fluence tiles are fully rewritten by k_pack_fluence and the partial
+// rows read back are exactly those k_spmm stores, so neither needs clearing.
+static __device__ __align__(256) uint16_t g_static_fp[kStaticFp];
+static __device__ __align__(256) float g_static_part[DC_SPMM_STATIC_MAX_PARTIALS];
+
+constexpr int kStaticDevices = 64;
+struct StaticScratch {
+    __nv_bfloat16* fp = nullptr;
+    float* part = nullptr;
+};
+StaticScratch g_scratch[kStaticDevices];
+std::mutex g_scratch_mu;
+
+// Device addresses of the static arrays on `device`, looked up on first use
+// with that device current (the caller's current device is restored).
+cudaError_t static_scratch(int device, StaticScratch* out)
+{
+    if (device < 0 || device >= kStaticDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    StaticScratch& s = g_scratch[device];
+    if (!s.fp || !s.part) {
+        int cur = -1;
+        cudaError_t e = cudaGetDevice(&cur);
+        if (e != cudaSuccess) return e;
+        if (cur != device) {
+            e = cudaSetDevice(device);
+            if (e != cudaSuccess) return e;
+        }
+        void* fp = nullptr;
+        void* part = nullptr;
+        e = cudaGetSymbolAddress(&fp, g_static_fp);
+        if (e == cudaSuccess) e = cudaGetSymbolAddress(&part, g_static_part);
+        if (cur != device) {
+            const cudaError_t e2 = cudaSetDevice(cur);
+            if (e == cudaSuccess) e = e2;
+        }
+        if (e != cudaSuccess) return e;
+        if (!fp || !part) return cudaErrorInvalidSymbol;
+        s.fp = reinterpret_cast<__nv_bfloat16*>(fp);
+        s.part = reinterpret_cast<float*>(part);
+    }
+    *out = s;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t spmm_run_static(dc_plan* p, const float* F, int k, float* Y)
+{
+    const int nkb = (p->B + 7) / 8 + 2;
+    const bool direct = p->n_beams == 1;
+    if (nkb > kStaticNkb) return cudaErrorInvalidValue;
+    if (!direct && (size_t)p->sp_items_total * k > (size_t)DC_SPMM_STATIC_MAX_PARTIALS) return cudaErrorInvalidValue;
+    StaticScratch sc;
+    cudaError_t e = static_scratch(p->device, &sc);
+    if (e != cudaSuccess) return e;
+    k_pack_fluence<<<gsize((int64_t)nkb * 8 * kN), 256, 0, p->stream>>>(F, p->B, k, nkb, sc.fp);
+    count_launches(1);
+    // the output rows of voxels outside every beam list are never written by
+    // k_spmm, and the bounded-wait status word is read after the call
+    if (direct) {
+        e = cudaMemsetAsync(Y, 0, (size_t)p->V * k * sizeof(float), p->stream);
+        if (e != cudaSuccess) return e;
+    }
+    e = cudaMemsetAsync(p->d_err, 0, sizeof(int32_t), p->stream);
+    if (e != cudaSuccess) return e;
+    SpmmArgs a{};
+    a.tiles = reinterpret_cast<const uint16_t*>(p->d_sp_tiles);
+    a.chunk_kb = p->d_sp_kb;
+    a.chunk_off = p->d_sp_off;
+    a.Fp = sc.fp;
+    a.items = p->d_items;
+    a.base = p->d_base;
+    a.n_items = p->d_nitems;
+    a.rb_first = p->d_sp_rbfirst;
+    a.n_beams = p->n_beams;
+    a.n_rb = p->sp_n_rb;
+    a.k = k;
+    a.Y = Y;
+    a.P = sc.part;
+    a.direct = direct ? 1 : 0;
+    float* out0 = direct ? Y : sc.part;
+    a.vec4 = (k % 4 == 0 && (reinterpret_cast<uintptr_t>(out0) & 15) == 0) ? 1 : 0;
+    a.err = p->d_err;
+    const size_t smem = (size_t)kStages * (kTileA + kTileB) + 1024 + 8192;
+    e = cudaFuncSetAttribute(k_spmm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int smem_sm = 0, sms = 0;
+    e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, p->device);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (e != cudaSuccess) return e;
+    int per_sm = smem_sm / (int)(smem + 2048);
+    per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
+    int grid = sms * per_sm;
+    if (grid > p->sp_n_rb) grid = p->sp_n_rb;
+    if (grid > 0) {
+        k_spmm<<<grid, kSpmmThreads, smem, p->stream>>>(a);
+        count_launches(1);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (!direct) {
+        k_spmm_reduce<<<gsize(p->V * k), 256, 0, p->stream>>>(sc.part, p->d_sp_inv, p->n_beams, p->V, k, Y);
         count_launches(1);
         e = cudaGetLastError();
     }

@@ -21,6 +21,7 @@ DC_DEVICE_PTRS = 1
 DC_F32, DC_BF16 = 0, 1
 DC_LATERAL_ISO, DC_LATERAL_AXIS, DC_LATERAL_MLP = 0, 1, 2
 MLP_PARAMS = 7491
+DC_SPMM_STATIC_MAX_BEAMLETS, DC_SPMM_STATIC_MAX_PARTIALS = 8192, 4194304
 
 _lib = None
 
@@ -62,7 +63,7 @@ EXPORTS = ["dc_last_error", "dc_status_str", "dc_fspb_create", "dc_fspb_destroy"
            "dc_fspb_pair_count", "dc_fspb_dose_matrix", "dc_fspb_get_smoothed",
            "dc_fspb_get_beamlets", "dc_fspb_get_tables", "dc_fspb_set_density",
            "dc_fspb_launch_count", "dc_fspb_autotune", "dc_fspb_spmm_prepare", "dc_fspb_spmm_info",
-           "dc_fspb_spmm", "dc_fspb_device_status", "dc_fspb_set_surrogate",
+           "dc_fspb_spmm", "dc_fspb_spmm_noalloc", "dc_fspb_device_status", "dc_fspb_set_surrogate",
            "dc_fspb_set_lateral_mode", "dc_fspb_lateral_fallbacks", "dc_fspb_stencils",
            "dc_mlp_create", "dc_mlp_destroy", "dc_mlp_get_params", "dc_mlp_gradient", "dc_mlp_train",
            "dc_mlp_predict"]
@@ -105,6 +106,7 @@ def load():
     L.dc_fspb_spmm_prepare.argtypes = [vp]
     L.dc_fspb_spmm_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
     L.dc_fspb_spmm.argtypes = [vp, vp, i32, vp, u32]
+    L.dc_fspb_spmm_noalloc.argtypes = [vp, vp, i32, vp]
     L.dc_fspb_device_status.argtypes = [vp]
     L.dc_fspb_set_surrogate.argtypes = [vp, vp, C.c_float, C.c_float]
     L.dc_fspb_set_lateral_mode.argtypes = [vp, i32]
@@ -252,6 +254,16 @@ def dc_fspb_spmm(plan: Plan, F, Y=None):
     pf, f1 = _ptr(F)
     py, f2 = _ptr(Y)
     _check(load().dc_fspb_spmm(plan.handle, pf, k, py, _same_kind(f1, f2)))
+    return Y
+
+
+def dc_fspb_spmm_noalloc(plan: Plan, F, Y):
+    """dc_fspb_spmm for device tensors F [B, k], Y [V, k] with static scratch (no device allocation)."""
+    pf, f1 = _ptr(F)
+    py, f2 = _ptr(Y)
+    if not (f1 & f2 & DC_DEVICE_PTRS):
+        raise ValueError("dc_fspb_spmm_noalloc takes device tensors")
+    _check(load().dc_fspb_spmm_noalloc(plan.handle, pf, int(F.shape[1]), py))
     return Y
 
 
