@@ -363,6 +363,7 @@ def run_ours(args, world, rank, local, pg):
 
     forms = run_forms(args, dc, torch, stream, peaks)
     forms["surrogate"] = run_surrogate_form(args, dc, torch, stream)
+    forms["batch"] = run_batch_form(args, dc, torch, stream, peak_pairs)
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, dc, p, plan, pairs, torch)
@@ -506,6 +507,79 @@ def run_surrogate_form(args, dc, torch, stream, k=64):
                                "fallbacks": dc.dc_fspb_lateral_fallbacks(plan)},
             "speedup_64_fluences": t_plain / t_spmm,
             "max_err_vs_plain_over_colmax": err}
+
+
+def run_batch_form(args, dc, torch, stream, peak_pairs):
+    """The 16 uneven head-and-neck plans (grids 112 x 112 x 64 to 256 x 256 x 192
+    at 0.2-0.3 cm, 5-9 beams, 0.25 cm beamlets, ROI 5 cm): one persistent
+    graph-replayed launch over all plans (dc_fspb_batch_run) against the plans'
+    own launches one after another, dose only and whole plans (density-dependent
+    steps + dose)."""
+    from paper_1103_1164_gb300 import synth
+    t0 = time.perf_counter()
+    inputs = synth.config5_plans()
+    t_gen = time.perf_counter() - t0
+    rhos = [torch.from_numpy(p.rho).cuda() for p in inputs]
+    flus = [torch.from_numpy(p.fluence).cuda() for p in inputs]
+    plans = [dc.dc_fspb_create_from(p, stream=stream.cuda_stream, device_density=r) for p, r in zip(inputs, rhos)]
+    doses = [torch.empty(pl.n_voxels, device="cuda") for pl in plans]
+    pairs = [dc.dc_fspb_pair_count(pl) for pl in plans]
+    batch = dc.dc_fspb_batch_create(plans, stream=stream.cuda_stream)
+    for j, pl in enumerate(plans):
+        fptr, _ = dc.dc_fspb_batch_buffers(batch, j)
+        dc_view(torch, fptr, pl.n_beamlets).copy_(flus[j])
+    variant, tune_ms = dc.dc_fspb_batch_autotune(batch)
+    reps = max(3, min(args.steps, 5))
+    dummy = torch.empty(1, device="cuda")   # inputs far exceed L2: no flush needed
+
+    def seq_dose():
+        for pl, f, d in zip(plans, flus, doses):
+            dc.dc_fspb_dose(pl, f, d)
+
+    def seq_full():
+        for pl, r, f, d in zip(plans, rhos, flus, doses):
+            dc.dc_fspb_set_density(pl, r)
+            dc.dc_fspb_dose(pl, f, d)
+
+    for _ in range(2):
+        dc.dc_fspb_batch_run(batch)
+        dc.dc_fspb_batch_run(batch, density=True)
+        seq_dose()
+    torch.cuda.synchronize()
+    l0 = dc.dc_fspb_launch_count()
+    t_batch = time_on_stream(torch, stream, lambda: dc.dc_fspb_batch_run(batch), reps, dummy)
+    launches = (dc.dc_fspb_launch_count() - l0) / reps
+    t_full = time_on_stream(torch, stream, lambda: dc.dc_fspb_batch_run(batch, density=True), reps, dummy)
+    t_seq = time_on_stream(torch, stream, seq_dose, reps, dummy)
+    t_seq_full = time_on_stream(torch, stream, seq_full, reps, dummy)
+    err = 0.0
+    for j, d in enumerate(doses):
+        _, dptr = dc.dc_fspb_batch_buffers(batch, j)
+        b = dc_view(torch, dptr, plans[j].n_voxels)
+        err = max(err, float((b - d).abs().max() / d.abs().max()))
+    total = int(sum(pairs))
+    ach = total / (t_batch * 1e-3)
+    return {"workload": f"{len(plans)} head-and-neck plans, {sum(pl.n_voxels for pl in plans)} voxels, "
+                        f"{sum(len(p.beams) for p in inputs)} beams, {sum(pl.n_beamlets for pl in plans)} "
+                        f"beamlets (0.25 cm), ROI 5 cm, density correction on",
+            "pairs": total, "generate_s": t_gen,
+            "batch_graph": {"dose_ms": t_batch, "full_plans_ms": t_full, "evals_per_s": ach,
+                            "kernels_per_replay": launches,
+                            "autotuned_ctas_per_sm": 4 + variant, "autotune_ms": tune_ms,
+                            "roofline": {"bound": "alu", "achieved": ach / 1e9, "peak": peak_pairs / 1e9,
+                                         "unit": "Gpair/s", "frac": ach / peak_pairs}},
+            "sequential_plans": {"dose_ms": t_seq, "full_plans_ms": t_seq_full,
+                                 "evals_per_s": total / (t_seq * 1e-3)},
+            "speedup_batch_over_sequential": {"dose": t_seq / t_batch, "full_plans": t_seq_full / t_full},
+            "max_diff_batch_vs_sequential_over_max": err}
+
+
+def dc_view(torch, ptr, n):
+    """torch view (no copy) of a float32 device buffer owned by the library."""
+    class _A:
+        __cuda_array_interface__ = {"shape": (n,), "typestr": "<f4", "data": (ptr, False), "version": 3,
+                                    "strides": None}
+    return torch.as_tensor(_A(), device="cuda")
 
 
 def run_e2e(args, dc, p, plan, pairs, torch):

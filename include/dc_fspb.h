@@ -56,6 +56,7 @@ typedef enum {
 } dc_status;
 
 #define DC_DEVICE_PTRS 1u  /* flags: pointer arguments are device memory */
+#define DC_BATCH_DENSITY 2u  /* batch flags: also recompute the density-dependent steps */
 
 /* Forms of the lateral density correction (Algorithm A1 step 11). */
 #define DC_LATERAL_ISO 0   /* the paper's: f(rho(r)), f(rho_hat(r)) at the dose voxel          */
@@ -120,6 +121,8 @@ typedef struct {
 } dc_kernel_coeffs;
 
 typedef struct dc_plan dc_plan;
+typedef struct dc_batch dc_batch;
+typedef struct dc_mlp dc_mlp;
 
 /* Message describing the calling thread's most recent failed call ("" if none). */
 const char* dc_last_error(void);
@@ -260,6 +263,144 @@ dc_status dc_fspb_spmm(dc_plan* plan, const float* F, int32_t k, float* Y, uint3
  * dc_fspb_device_status.
  */
 dc_status dc_fspb_spmm_noalloc(dc_plan* plan, const float* F, int32_t k, float* Y);
+
+/* ---- Lateral density correction forms (Algorithm A1 step 11) ----
+ *
+ * DC_LATERAL_ISO is the paper's reading: f_u1(rho(r)), f_u2/f_omega(rho_hat(r))
+ * at the dose voxel.  DC_LATERAL_AXIS samples, for each (voxel r, beam), 16
+ * trilinear density taps at (j - 7.5) d, j = 0..15, along each of the beam's
+ * axes e_x', e_y', e_z' through r, averages each axis with normalised Gaussian
+ * weights (sigma = smooth_sigma) and takes f_u2 at the x and y averages (the
+ * penumbra along x and along y) and f_omega at the mean of the three; f_u1
+ * stays at rho(r).  DC_LATERAL_MLP predicts the three averages from 48
+ * nearest-voxel taps with the surrogate network below, falling back to the
+ * AXIS computation for stencils with a density outside [rho_lo, rho_hi].  The
+ * factors are computed per density (dc_fspb_create, dc_fspb_set_density) for
+ * every (voxel, beam) entry of the beams' voxel lists.
+ */
+
+/*
+ * Loads the surrogate network into the plan: params [7491] host float32,
+ * packed W1[48][64], b1[64], W2[64][64], b2[64], W3[64][3], b3[3]; the network
+ * maps x = taps - 1 (48) through two SiLU layers of 64 to y (3) and predicts the
+ * effective densities 1 + y (mean, x, y).  Inference runs in BF16 with FP32
+ * accumulation.  [rho_lo, rho_hi] is the density range of its training data.
+ * Recomputes the factors when the plan is in the network form.  Synchronises.
+ * Errors: DC_EINVAL (NULL, non-finite parameter, rho_lo >= rho_hi), DC_ECUDA.
+ */
+dc_status dc_fspb_set_surrogate(dc_plan* plan, const float* params, float rho_lo, float rho_hi);
+
+/* Selects the lateral form (DC_LATERAL_*; DC_LATERAL_MLP needs
+ * dc_fspb_set_surrogate first) and recomputes the per-entry factors.
+ * Asynchronous on the plan's stream.  Errors: DC_EINVAL, DC_ECUDA. */
+dc_status dc_fspb_set_lateral_mode(dc_plan* plan, int32_t mode);
+
+/* Entries of the last network-form factor pass that fell back to the AXIS
+ * computation (0 in the other forms).  Synchronises. */
+dc_status dc_fspb_lateral_fallbacks(dc_plan* plan, int64_t* n);
+
+/*
+ * Network training and test samples for n (voxel, beam) pairs: X [n][48] the
+ * nearest-voxel densities at the 3 x 16 tap points (axis-major: e_x', e_y',
+ * e_z'), T [n][3] the AXIS effective densities (mean, x, y) of the pair.
+ * vox [n] voxel indices, beam [n] beam indices.  Host buffers, or all device
+ * buffers with DC_DEVICE_PTRS (then out-of-range indices give NaN rows instead
+ * of DC_EINVAL).  Errors: DC_EINVAL (NULL, n < 0, index out of range), DC_ECUDA.
+ */
+dc_status dc_fspb_stencils(dc_plan* plan, const int32_t* vox, const int32_t* beam, int32_t n, float* X, float* T,
+                           uint32_t flags);
+
+/* ---- The surrogate network's trainer (FP32 forward, backward and Adam) ---- */
+
+/* A trainer holding parameters (initial values params [7491], host) and Adam
+ * state on the device; its work runs on cuda_stream.  Errors: DC_EINVAL,
+ * DC_ENOMEM, DC_ECUDA. */
+dc_status dc_mlp_create(const float* params, void* cuda_stream, dc_mlp** out);
+dc_status dc_mlp_destroy(dc_mlp* m);
+/* Current parameters into out [7491] (host).  Synchronises. */
+dc_status dc_mlp_get_params(const dc_mlp* m, float* out);
+/*
+ * Gradient grad [7491] (host) and loss (host, may be NULL) of
+ * L = sum_s sum_o (1 + y_so - T_so)^2 / (3 n) over the n samples X [n][48],
+ * T [n][3] at the current parameters, in FP32 with per-CTA partial sums added
+ * in a fixed order (deterministic).  X, T host, or device with DC_DEVICE_PTRS.
+ */
+dc_status dc_mlp_gradient(dc_mlp* m, const float* X, const float* T, int32_t n, float* grad, float* loss,
+                          uint32_t flags);
+/*
+ * Adam (beta1 0.9, beta2 0.999, eps 1e-8, step size lr) over `epochs` passes
+ * of the samples in the given order, in whole mini-batches of `batch` (a
+ * remainder is skipped); *loss (if not NULL) receives L over all n samples
+ * after training.  Synchronises.  Errors: DC_EINVAL, DC_ENOMEM, DC_ECUDA.
+ */
+dc_status dc_mlp_train(dc_mlp* m, const float* X, const float* T, int32_t n, int32_t batch, int32_t epochs,
+                       float lr, float* loss, uint32_t flags);
+/* Effective densities Y [n][3] = 1 + network(X - 1) with the BF16 tensor-core
+ * inference of the dose path, for params [7491] (host).  X, Y host, or device
+ * with DC_DEVICE_PTRS.  Synchronises cuda_stream. */
+dc_status dc_mlp_predict(const float* params, const float* X, int32_t n, float* Y, uint32_t flags,
+                         void* cuda_stream);
+
+/* ---- Several plans in one launch ----
+ *
+ * Eq. (1) for n plans of uneven grids and beam counts (one fluence vector per
+ * plan) as ONE persistent launch of the pair kernel over the work units of all
+ * plans (units of the costliest plans first), followed by one launch of the
+ * per-plan beam sums, replayed from a CUDA graph built on the first run.  With
+ * DC_BATCH_DENSITY the graph also holds each plan's density-dependent work
+ * (Algorithm A1 steps 1-6, the beam's-eye-view binning, the lateral factors of
+ * step 11) from the plan's resident density, one graph branch per plan, so a
+ * run recomputes the whole plans.  Each plan gives the same dose as its own
+ * dc_fspb_dose (same per-pair arithmetic; the plans' table and lateral
+ * variants are chosen per work unit).
+ */
+
+/*
+ * plans [n] (1 <= n <= 64, distinct, all on the current device).  The batch
+ * owns one device fluence buffer [B_i] (zeroed) and one device dose buffer
+ * [V_i] per plan; runs are enqueued on cuda_stream (NULL: legacy default).
+ * The plans stay owned by the caller and must outlive the batch; a run is
+ * ordered after the work already enqueued on each plan's stream and before
+ * work enqueued there afterwards.  Changing a plan (dc_fspb_autotune,
+ * dc_fspb_set_lateral_mode, dc_fspb_set_surrogate, a larger
+ * dc_fspb_dose_batch) is detected at the next run, which rebuilds the graph.
+ * Errors: DC_EINVAL, DC_ENOMEM, DC_ECUDA.
+ */
+dc_status dc_fspb_batch_create(dc_plan* const* plans, int32_t n, void* cuda_stream, dc_batch** out);
+
+/* Frees the batch (waits for its stream first); NULL is a no-op. */
+dc_status dc_fspb_batch_destroy(dc_batch* batch);
+
+/* Device pointers of plan i's fluence [B_i] and dose [V_i] buffers (either out
+ * pointer may be NULL).  They stay valid for the batch's lifetime. */
+dc_status dc_fspb_batch_buffers(dc_batch* batch, int32_t i, float** fluence, float** dose);
+
+/* Replays the batch graph on the batch's stream (asynchronous): dose_i = D of
+ * plan i for the fluence in its batch buffer.  flags: 0 or DC_BATCH_DENSITY.
+ * A DC_BATCH_DENSITY run waits for each plan's stream on the host and drops
+ * the plans' matrix pattern and SpMM tiles (rebuilt on their next use). */
+dc_status dc_fspb_batch_run(dc_batch* batch, uint32_t flags);
+
+/* Copies fluence[i] [B_i] into the batch buffers, runs, copies the doses out
+ * to dose[i] [V_i], and waits.  All buffers host memory, or all device memory
+ * with DC_DEVICE_PTRS in flags; DC_BATCH_DENSITY as for dc_fspb_batch_run. */
+dc_status dc_fspb_batch_dose(dc_batch* batch, const float* const* fluence, float* const* dose, uint32_t flags);
+
+/*
+ * Autotuner of the batch's pair kernel: replays the dose graph (twice, after a
+ * warm-up) for each register budget of the persistent kernel (sized for 4 or
+ * for 5 CTAs per SM) and keeps the faster; *variant (0 or 1) and *ms (mean
+ * replay time) may be NULL.  Runs the batch (its dose buffers are written) and
+ * synchronises.  Errors: DC_EINVAL, DC_ECUDA.
+ */
+dc_status dc_fspb_batch_autotune(dc_batch* batch, int32_t* variant, float* ms);
+
+/* Waits for the batch's stream. */
+dc_status dc_fspb_batch_synchronize(dc_batch* batch);
+
+/* Kernel launches in one replay of the graph for `flags` (0 before the first
+ * run with those flags). */
+dc_status dc_fspb_batch_kernels(const dc_batch* batch, uint32_t flags, int32_t* kernels);
 
 /* Waits for the plan's stream and reports DC_ETIMEOUT if a bounded
  * device-side wait of an earlier call gave up, else DC_OK. */

@@ -74,6 +74,8 @@ dc::PlanView dc_plan::view() const
     v.idy = 1.0f / grid.dy;
     v.idz = 1.0f / grid.dz;
     for (int j = 0; j < 16; ++j) v.gw[j] = gw[j];
+    v.merged_rt = merged ? 1 : 0;
+    v.item_rt = (coeffs.density_correction && lateral_mode != DC_LATERAL_ISO) ? 1 : 0;
     return v;
 }
 
@@ -438,6 +440,7 @@ static dc_status rebin(dc_plan* p, float tile, float slab)
     if (p->coeffs.density_correction && p->lateral_mode != DC_LATERAL_ISO) DC_CUDA(launch_lateral(p));
     p->pairs = -1;
     if (p->sp_ready) p->spmm_free();
+    ++p->layout_gen;
     return DC_OK;
 }
 
@@ -560,6 +563,7 @@ dc_status dc_fspb_dose_batch(dc_plan* plan, const float* fluence, int32_t k, flo
         plan->part_cap = 0;
         DC_CUDA(dalloc(&plan->d_part, need));
         plan->part_cap = need;
+        ++plan->layout_gen;
     }
     if (flags & DC_DEVICE_PTRS) {
         DC_CUDA(launch_dose(plan, fluence, k, plan->B, dose, plan->V));

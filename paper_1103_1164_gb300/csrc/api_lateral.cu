@@ -101,6 +101,7 @@ dc_status dc_fspb_set_surrogate(dc_plan* plan, const float* params, float rho_lo
     plan->mlp_lo = rho_lo;
     plan->mlp_hi = rho_hi;
     plan->mlp_ready = true;
+    ++plan->layout_gen;
     if (plan->lateral_mode == DC_LATERAL_MLP && plan->coeffs.density_correction) DC_CUDA(launch_lateral(plan));
     if (plan->sp_ready) plan->spmm_free();
     DC_CUDA(cudaStreamSynchronize(plan->stream));
@@ -115,6 +116,7 @@ dc_status dc_fspb_set_lateral_mode(dc_plan* plan, int32_t mode)
     if (mode == DC_LATERAL_MLP && !plan->mlp_ready)
         return bad("dc_fspb_set_lateral_mode: the network form needs dc_fspb_set_surrogate first");
     plan->lateral_mode = mode;
+    ++plan->layout_gen;
     if (plan->coeffs.density_correction && mode != DC_LATERAL_ISO) DC_CUDA(launch_lateral(plan));
     if (plan->sp_ready) plan->spmm_free();   // matrix values depend on the form
     return DC_OK;

@@ -164,6 +164,9 @@ struct dc_plan {
     size_t part_cap = 0;
     int32_t* d_bcount = nullptr;     // per-beam pair counts [n_beams][V]
     int persist_ctas[4] = {0, 0, 0, 0};
+    // bumped whenever a buffer or a launch parameter that a captured batch
+    // graph holds changes (binning geometry, partial-dose buffer, lateral form)
+    uint64_t layout_gen = 0;
     // block-sparse BF16 dose-deposition matrix for the tensor-core SpMM (k_spmm.cu)
     bool sp_ready = false;
     int sp_n_rb = 0;
@@ -249,10 +252,16 @@ constexpr int kMlpFragU2 = (3 * 8 + 4 * 8 + 4) * 32;
 constexpr int kMlpBias = 64 + 64 + 3;
 void mlp_pack(const float* theta, std::vector<uint2>& frag, std::vector<float>& bias);
 // multi-plan batch (k_dose.cu)
-DoseArgs dose_args(const dc_plan* p, const float* fluence, float* part);
-cudaError_t launch_batch(cudaStream_t s, const DoseArgs* d_args, int n, int64_t* d_prefix,
-                         unsigned long long* d_counter, int device);
-cudaError_t launch_sum_one(const dc_plan* p, cudaStream_t s, const float* part, float* dose);
+// arguments of one plan for one fluence vector (partials in the plan's d_part)
+DoseArgs dose_args(const dc_plan* p, const float* fluence, float* dose);
+int batch_max_plans();
+constexpr int kBatchVariants = 2;   // register budgets of the batch pair kernel (4 or 5 CTAs per SM)
+// prefix of the plans' unit counts, the persistent pair kernel over all plans'
+// units (arguments h_args by value; d_args holds the same records on the
+// device), and the per-plan beam sums; the partials must be zero beforehand
+cudaError_t launch_batch(cudaStream_t s, const DoseArgs* h_args, const DoseArgs* d_args, int n,
+                         const int64_t* d_vpre, int64_t v_total, int64_t* d_prefix, unsigned int* d_counter,
+                         int device, int variant, bool shared_water);
 // block-sparse tensor-core SpMM (k_spmm.cu)
 dc_status spmm_prepare(dc_plan* p, const int64_t* rowptr, const int32_t* cols, const uint16_t* vals);
 cudaError_t spmm_run(dc_plan* p, const float* F, int k, float* Y);

@@ -16,6 +16,9 @@
 // exponentials); every table stores value + slope so an interpolation is one
 // load and one fma; eq. (4) is evaluated without branches.
 #include <math.h>
+#include <string.h>
+
+#include <mutex>
 
 #include "dc_internal.cuh"
 
@@ -315,6 +318,124 @@ __global__ void __launch_bounds__(kThreads) k_pairs(const DoseArgs a)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Several plans in one persistent launch.  The work units of all plans (one
+// fluence vector each) form one range, plans in the order of the argument
+// array; a warp takes the next unit from a global counter, finds its plan and
+// beam, and runs the same per-unit body as k_pairs with the plan's table and
+// lateral variants chosen at run time (warp-uniform branches).  The plans'
+// arguments travel as one grid-constant kernel parameter, so the hot loop
+// reads them from the constant bank as k_pairs does.  When every plan uses
+// the same water tables (one commissioned beam model), they are staged in
+// shared memory once per CTA; otherwise each plan's are read through L1.
+constexpr int kMaxBatch = 64;
+
+struct BatchParams {
+    DoseArgs a[kMaxBatch];
+};
+static_assert(sizeof(BatchParams) + 64 <= 32764, "kernel parameter space");
+
+// prefix[j] = units of plans 0..j-1 (the unit counts were written by each
+// plan's binning on the device); resets the work counter.
+__global__ void k_batch_prefix(const DoseArgs* __restrict__ args, int n, int64_t* __restrict__ prefix,
+                               unsigned int* __restrict__ counter)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int64_t s = 0;
+    for (int j = 0; j < n; ++j) {
+        prefix[j] = s;
+        s += *args[j].work;
+    }
+    prefix[n] = s;
+    *counter = 0u;
+}
+
+// MINB: CTAs per SM the register budget is set for (4: no spills; 5: 48
+// registers).  SHARED_W: all plans share the water tables of plan 0.
+template <int MINB, bool SHARED_W>
+__global__ void __launch_bounds__(kThreads, MINB) k_pairs_batch(const __grid_constant__ BatchParams bp, int n,
+                                                                const int64_t* __restrict__ prefix,
+                                                                unsigned int* __restrict__ counter)
+{
+    extern __shared__ float4 smem[];
+    __shared__ int64_t s_pre[kMaxBatch + 1];
+    for (int q = threadIdx.x; q <= n; q += blockDim.x) s_pre[q] = prefix[q];
+    if (SHARED_W)
+        for (int q = threadIdx.x; q < 2 * bp.a[0].P.w_n; q += blockDim.x) smem[q] = __ldg(bp.a[0].P.water + q);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t total = s_pre[n];
+    for (;;) {
+        unsigned int w = 0;
+        if (lane == 0) w = atomicAdd(counter, 1u);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if ((int64_t)w >= total) break;
+        int j = 0;
+        while (j + 1 < n && s_pre[j + 1] <= (int64_t)w) ++j;
+        const DoseArgs& a = bp.a[j];
+        const int64_t e0 = ((int64_t)w - s_pre[j]) * 32;
+        const int nb = a.P.n_beams;
+        int b = 0;
+        while (b + 1 < nb && __ldg(a.base + b + 1) <= e0) ++b;
+        const int32_t vi = __ldg(a.items + e0 + lane);
+        const float4* wt = SHARED_W ? smem : a.P.water;
+        if (a.P.merged_rt) {
+            if (a.P.item_rt)
+                process_unit<kDose, 1, true, kItem>(a, vi, e0, b, wt, nullptr, nullptr, lane);
+            else
+                process_unit<kDose, 1, true, kIso>(a, vi, e0, b, wt, nullptr, nullptr, lane);
+        } else {
+            if (a.P.item_rt)
+                process_unit<kDose, 1, false, kItem>(a, vi, e0, b, wt, nullptr, nullptr, lane);
+            else
+                process_unit<kDose, 1, false, kIso>(a, vi, e0, b, wt, nullptr, nullptr, lane);
+        }
+    }
+}
+
+template <int MINB, bool SHARED_W>
+cudaError_t batch_kernel(cudaStream_t s, const BatchParams& bp, int n, const int64_t* d_prefix,
+                         unsigned int* d_counter, int device, int w_n)
+{
+    auto kern = k_pairs_batch<MINB, SHARED_W>;
+    const size_t sm = SHARED_W ? 2 * sizeof(float4) * (size_t)w_n : 0;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, sm);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) return e;
+    kern<<<sms * (per_sm > 0 ? per_sm : 1), kThreads, sm, s>>>(bp, n, d_prefix, d_counter);
+    return cudaGetLastError();
+}
+
+// dose_j[v] = sum over plan j's beams of its partial doses (fixed beam order)
+// for every voxel of every plan; vpre[j] = voxels of plans 0..j-1.
+__global__ void __launch_bounds__(256) k_sum_batch(const DoseArgs* __restrict__ args, int n,
+                                                   const int64_t* __restrict__ vpre)
+{
+    __shared__ int64_t s_v[kMaxBatch + 1];
+    for (int q = threadIdx.x; q <= n; q += blockDim.x) s_v[q] = vpre[q];
+    __syncthreads();
+    const int64_t total = s_v[n];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = n - 1;   // last j with s_v[j] <= e
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_v[mid] <= e) lo = mid;
+            else hi = mid - 1;
+        }
+        const DoseArgs& a = args[lo];
+        const int64_t V = s_v[lo + 1] - s_v[lo];
+        const int64_t v = e - s_v[lo];
+        float sum = 0.f;
+        for (int b = 0; b < a.P.n_beams; ++b) sum += __ldg(a.part + (size_t)b * V + v);
+        a.dose[v] = sum;
+    }
+}
+
 // dose[q][v] = sum over beams of the partial doses (fixed beam order).
 __global__ void __launch_bounds__(256) k_sum_beams(const float* __restrict__ part, int n_beams, int nfs,
                                                    int nf, int64_t V, float* __restrict__ dose, int64_t ldd)
@@ -482,6 +603,46 @@ cudaError_t run(const dc_plan* p, const DoseArgs& a)
 }
 
 }  // namespace
+
+DoseArgs dose_args(const dc_plan* p, const float* fluence, float* dose)
+{
+    DoseArgs a = make_args(p);
+    a.fluence = fluence;
+    a.nf = 1;
+    a.ldf = p->B;
+    a.dose = dose;
+    a.ldd = p->V;
+    a.part = p->d_part;
+    return a;
+}
+
+int batch_max_plans() { return kMaxBatch; }
+
+cudaError_t launch_batch(cudaStream_t s, const DoseArgs* h_args, const DoseArgs* d_args, int n,
+                         const int64_t* d_vpre, int64_t v_total, int64_t* d_prefix, unsigned int* d_counter,
+                         int device, int variant, bool shared_water)
+{
+    if (n < 1 || n > kMaxBatch || variant < 0 || variant >= kBatchVariants) return cudaErrorInvalidValue;
+    static BatchParams bp;   // 24 KiB: kept off the stack; the launch copies it
+    static std::mutex bp_mu;
+    std::lock_guard<std::mutex> lock(bp_mu);
+    memset(&bp, 0, sizeof(bp));
+    memcpy(bp.a, h_args, sizeof(DoseArgs) * n);
+    const int w_n = h_args[0].P.w_n;
+    k_batch_prefix<<<1, 32, 0, s>>>(d_args, n, d_prefix, d_counter);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (variant == 0)
+        e = shared_water ? batch_kernel<4, true>(s, bp, n, d_prefix, d_counter, device, w_n)
+                         : batch_kernel<4, false>(s, bp, n, d_prefix, d_counter, device, w_n);
+    else
+        e = shared_water ? batch_kernel<5, true>(s, bp, n, d_prefix, d_counter, device, w_n)
+                         : batch_kernel<5, false>(s, bp, n, d_prefix, d_counter, device, w_n);
+    if (e != cudaSuccess) return e;
+    k_sum_batch<<<grid_for(v_total), 256, 0, s>>>(d_args, n, d_vpre);
+    count_launches(3);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_dose(const dc_plan* p, const float* fluence, int nf, int ldf, float* dose,
                         int64_t ldd)

@@ -18,6 +18,7 @@ from . import build as _build
 
 DC_OK, DC_EINVAL, DC_ENOMEM, DC_ECUDA, DC_ETIMEOUT, DC_EUNSUPPORTED = range(6)
 DC_DEVICE_PTRS = 1
+DC_BATCH_DENSITY = 2
 DC_F32, DC_BF16 = 0, 1
 DC_LATERAL_ISO, DC_LATERAL_AXIS, DC_LATERAL_MLP = 0, 1, 2
 MLP_PARAMS = 7491
@@ -66,7 +67,9 @@ EXPORTS = ["dc_last_error", "dc_status_str", "dc_fspb_create", "dc_fspb_destroy"
            "dc_fspb_spmm", "dc_fspb_spmm_noalloc", "dc_fspb_device_status", "dc_fspb_set_surrogate",
            "dc_fspb_set_lateral_mode", "dc_fspb_lateral_fallbacks", "dc_fspb_stencils",
            "dc_mlp_create", "dc_mlp_destroy", "dc_mlp_get_params", "dc_mlp_gradient", "dc_mlp_train",
-           "dc_mlp_predict"]
+           "dc_mlp_predict", "dc_fspb_batch_create", "dc_fspb_batch_destroy", "dc_fspb_batch_buffers",
+           "dc_fspb_batch_run", "dc_fspb_batch_dose", "dc_fspb_batch_synchronize", "dc_fspb_batch_kernels",
+           "dc_fspb_batch_autotune"]
 
 
 def library_path() -> str:
@@ -118,6 +121,14 @@ def load():
     L.dc_mlp_gradient.argtypes = [vp, vp, vp, i32, vp, C.POINTER(C.c_float), u32]
     L.dc_mlp_train.argtypes = [vp, vp, vp, i32, i32, i32, C.c_float, C.POINTER(C.c_float), u32]
     L.dc_mlp_predict.argtypes = [vp, vp, i32, vp, u32, vp]
+    L.dc_fspb_batch_create.argtypes = [vp, i32, vp, C.POINTER(vp)]
+    L.dc_fspb_batch_destroy.argtypes = [vp]
+    L.dc_fspb_batch_buffers.argtypes = [vp, i32, C.POINTER(vp), C.POINTER(vp)]
+    L.dc_fspb_batch_run.argtypes = [vp, u32]
+    L.dc_fspb_batch_dose.argtypes = [vp, vp, vp, u32]
+    L.dc_fspb_batch_synchronize.argtypes = [vp]
+    L.dc_fspb_batch_kernels.argtypes = [vp, u32, C.POINTER(i32)]
+    L.dc_fspb_batch_autotune.argtypes = [vp, C.POINTER(i32), C.POINTER(C.c_float)]
     for name in EXPORTS:
         if name not in ("dc_last_error", "dc_status_str"):
             getattr(L, name).restype = C.c_int
@@ -427,3 +438,72 @@ def dc_fspb_get_tables(plan: Plan, i: int, kmax: int = 1 << 16):
                                      kmax, C.byref(K)))
     k = min(K.value, kmax)
     return T[:k], W1[:k], W2[:k]
+
+
+class Batch:
+    """Owns a dc_batch*; holds its plans so they outlive it."""
+
+    def __init__(self, handle, plans):
+        self.handle = handle
+        self.plans = list(plans)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.dc_fspb_batch_destroy(self.handle)
+            self.handle = None
+
+
+def dc_fspb_batch_create(plans, stream=None) -> Batch:
+    """One persistent, graph-replayed launch for the doses of several plans."""
+    arr = (C.c_void_p * len(plans))(*[p.handle.value if isinstance(p.handle, C.c_void_p) else p.handle
+                                      for p in plans])
+    h = C.c_void_p()
+    s = _current_stream() if stream is None else stream
+    _check(load().dc_fspb_batch_create(arr, len(plans), C.c_void_p(s), C.byref(h)))
+    return Batch(h, plans)
+
+
+def dc_fspb_batch_buffers(batch: Batch, i: int):
+    """(fluence, dose) device addresses of plan i's batch buffers."""
+    f, d = C.c_void_p(), C.c_void_p()
+    _check(load().dc_fspb_batch_buffers(batch.handle, int(i), C.byref(f), C.byref(d)))
+    return f.value, d.value
+
+
+def dc_fspb_batch_run(batch: Batch, density=False):
+    _check(load().dc_fspb_batch_run(batch.handle, DC_BATCH_DENSITY if density else 0))
+
+
+def dc_fspb_batch_synchronize(batch: Batch):
+    _check(load().dc_fspb_batch_synchronize(batch.handle))
+
+
+def dc_fspb_batch_kernels(batch: Batch, density=False) -> int:
+    n = C.c_int32()
+    _check(load().dc_fspb_batch_kernels(batch.handle, DC_BATCH_DENSITY if density else 0, C.byref(n)))
+    return n.value
+
+
+def dc_fspb_batch_autotune(batch: Batch):
+    """Picks the batch kernel's register budget by timing; returns (variant, ms)."""
+    v, ms = C.c_int32(), C.c_float()
+    _check(load().dc_fspb_batch_autotune(batch.handle, C.byref(v), C.byref(ms)))
+    return v.value, ms.value
+
+
+def dc_fspb_batch_dose(batch: Batch, fluences, doses=None, density=False):
+    """dose_i of every plan for fluences[i] (host arrays, or CUDA tensors with doses given)."""
+    n = len(batch.plans)
+    assert len(fluences) == n
+    if doses is None:
+        doses = [np.empty(p.n_voxels, np.float32) for p in batch.plans]
+    fp, dp, flags = [], [], []
+    for f, d in zip(fluences, doses):
+        a, fa = _ptr(f)
+        b, fb = _ptr(d)
+        fp.append(a.value)
+        dp.append(b.value)
+        flags += [fa, fb]
+    flag = _same_kind(*flags) | (DC_BATCH_DENSITY if density else 0)
+    _check(load().dc_fspb_batch_dose(batch.handle, (C.c_void_p * n)(*fp), (C.c_void_p * n)(*dp), flag))
+    return doses
