@@ -75,6 +75,9 @@ dc::PlanView dc_plan::view() const
     v.idz = 1.0f / grid.dz;
     for (int j = 0; j < 16; ++j) v.gw[j] = gw[j];
     v.merged_rt = merged ? 1 : 0;
+    v.tstride = (uint32_t)((merged ? 3 : 2) * Kmax);
+    v.a_hi = (float)(coeffs.a_nt - 1);
+    v.w_hi = (float)(coeffs.w_n - 1);
     v.item_rt = (coeffs.density_correction && lateral_mode != DC_LATERAL_ISO) ? 1 : 0;
     return v;
 }
@@ -289,6 +292,11 @@ static dc_status create_impl(dc_plan* p, const float* ct, uint32_t flags)
     double diag = sqrt((double)g.nx * g.dx * g.nx * g.dx + (double)g.ny * g.dy * g.ny * g.dy +
                        (double)g.nz * g.dz * g.nz * g.dz);
     p->Kmax = (int)ceil(diag / p->d) + 3;
+    // the pair kernels address the per-beamlet tables with 32-bit offsets
+    if ((double)p->B * 3.0 * p->Kmax >= 2147483648.0 || (double)p->B * c.a_nt >= 2147483648.0) {
+        set_error("dc_fspb_create: beamlets x table samples exceed the 32-bit table offsets");
+        return DC_EUNSUPPORTED;
+    }
 
     DC_CUDA(dalloc(&p->d_rho, V));
     DC_CUDA(dalloc(&p->d_rhos, V));
@@ -756,12 +764,12 @@ dc_status dc_fspb_get_beamlets(const dc_plan* plan, float* rec)
         float* r = rec + 16 * (size_t)i;
         const BeamletDev& b = bl[i];
         r[0] = b.n_lin.x; r[1] = b.n_lin.y; r[2] = b.n_lin.z;
-        r[3] = b.ex_tout.x; r[4] = b.ex_tout.y; r[5] = b.ex_tout.z;
-        r[6] = b.ey_wth.x; r[7] = b.ey_wth.y; r[8] = b.ey_wth.z;
+        r[3] = b.exy_xy.x; r[4] = b.exy_xy.z; r[5] = b.exy_z.x;
+        r[6] = b.exy_xy.y; r[7] = b.exy_xy.w; r[8] = b.exy_z.y;
         r[9] = th[i];
         r[10] = (float)b.meta.z;
         r[11] = b.n_lin.w;
-        r[12] = b.ex_tout.w;
+        r[12] = b.exy_z.z;
         r[13] = (float)b.meta.x;
         r[14] = r[15] = 0.f;
     }

@@ -29,8 +29,10 @@ struct BeamDev {
 // Per-beamlet record (64 bytes, four 16-byte vectors).
 struct BeamletDev {
     float4 n_lin;     // unit direction n, L_in (source to body entry along the axis)
-    float4 ex_tout;   // lateral axis e_x'', L_out (-1 if the axis misses the body)
-    float4 ey_wth;    // lateral axis e_y'', weight of the theta row l+1 in A
+    float4 exy_xy;    // (e_x''.x, e_y''.x, e_x''.y, e_y''.y): the lateral axes interleaved, so that
+                      // (x', y') = v . (e_x'', e_y'') runs as packed FP32 pairs
+    float4 exy_z;     // (e_x''.z, e_y''.z, L_out (-1 if the axis misses the body),
+                      //  weight of the theta row l+1 in A)
     int4 meta;        // K (table samples), l (theta row of A), hit (0/1), beam
 };
 
@@ -84,6 +86,8 @@ struct PlanView {
     float gw[16];                 // normalised Gaussian weights of the 16 stencil taps
     int merged_rt;                // tabm is in use (runtime copy of the plan's choice)
     int item_rt;                  // lfac is in use
+    uint32_t tstride;             // float4 entries per beamlet in the table in use (3 or 2 Kmax)
+    float a_hi, w_hi;             // a_nt - 1, w_n - 1 as floats (clamps of the table coordinates)
 };
 
 // Arguments of the pair kernels (k_dose.cu) for one plan.

@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(256) k_bev_bounds(const BinGeom* __restrict__ 
                 const float da = ca - (-hfx + (m + 0.5f) * bx);
                 if (da * da + dc_ * dc_ > reach * reach) continue;
                 const BeamletDev& r = bl[first + n * M + m];
-                const float lout = __ldg(&r.ex_tout.w);
+                const float lout = __ldg(&r.exy_z.z);
                 if (lout < 0.f) continue;            // axis misses the body
                 lmin = fminf(lmin, __ldg(&r.n_lin.w));
                 lmax = fmaxf(lmax, lout);

@@ -40,14 +40,26 @@ __device__ __forceinline__ float ex2(float x)
     return y;
 }
 
+// 1/x to about one ulp (MUFU.RCP alone: no Newton step, no special-case path;
+// L is a positive, normal distance here).
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // For 0 <= x < 2^22: an integer n with n <= x and x - n <= 1 (floor(x), or
-// floor(x) - 1 when x is an exact integer), as int and as float, by rounding
-// x - 1/2 against 1.5 * 2^23.  No conversion instruction is issued.
-__device__ __forceinline__ int grid_index(float x, float& frac)
+// floor(x) - 1 when x is an exact integer) and frac = x - n, by rounding
+// x - 1/2 against 1.5 * 2^23; no conversion instruction is issued.  Returns
+// the bits of the rounded value, kGridBits + n: table offsets subtract
+// kGridBits in 32-bit arithmetic, which folds into one multiply-add.
+constexpr uint32_t kGridBits = 0x4B400000u;
+__device__ __forceinline__ uint32_t grid_bits(float x, float& frac)
 {
     const float f = __fadd_rn(__fadd_rn(x, -0.5f), 12582912.0f);
     frac = __fadd_rn(x, -__fadd_rn(f, -12582912.0f));
-    return __float_as_int(f) - 0x4B400000;
+    return __float_as_uint(f);
 }
 
 // Eq. (4) with k = u log2(e), kx0 = k x0: with e1 = exp(-u ||x| - x0|) and
@@ -76,34 +88,53 @@ struct Lane {
     bool valid;
 };
 
-// Decides whether the lane's voxel is in beamlet i's ROI and depth range and,
-// if EVAL, returns D_i(r) of eq. (2) for unit fluence.
-template <bool EVAL, bool MERGED, int LAT>
-__device__ __forceinline__ bool pair(const PlanView& P, const Lane& ln, int i, float sad,
-                                     const float4* __restrict__ sW, float& D)
-{
-    const BeamletDev* bl = P.bl + i;
-    const float4 q0 = __ldg(&bl->n_lin);
-    const float4 q1 = __ldg(&bl->ex_tout);
-    const float4 q2 = __ldg(&bl->ey_wth);
-    const float L = fmaf(ln.vx, q0.x, fmaf(ln.vy, q0.y, ln.vz * q0.z));
-    const float xp = fmaf(ln.vx, q1.x, fmaf(ln.vy, q1.y, ln.vz * q1.z));
-    const float yp = fmaf(ln.vx, q2.x, fmaf(ln.vy, q2.y, ln.vz * q2.z));
-    // in the ROI and between body entry and exit: L_in <= |r_a| <= L_out
-    const bool in = ln.valid && fmaf(xp, xp, yp * yp) <= P.R2 && L >= q0.w && L <= q1.w;
-    if (!EVAL || !in) return in;
+// The pair test of beamlet i for the lane's voxel: in the ROI and between
+// body entry and exit.  Padding lanes carry NaN coordinates, so every test
+// fails for them.  Record and table offsets are 32-bit (the plan checks
+// B * 3 Kmax < 2^31).
+struct PairTest {
+    float L;       // |r_a| along the beamlet axis
+    float2 pq;     // (x', y')
+    float L_in;
+    bool in;
+};
 
-    const float t = L - q0.w;                    // depth below the surface
-    const float s = sad * __frcp_rn(L);          // SAD / |r_a|
-    const float x = xp * s, y = yp * s;          // isocentre-plane coordinates
+__device__ __forceinline__ PairTest pair_test(const PlanView& P, const Lane& ln, const uint32_t i)
+{
+    const float4* bq = reinterpret_cast<const float4*>(P.bl) + 4u * i;
+    const float4 q0 = __ldg(bq);        // n, L_in
+    const float4 q1 = __ldg(bq + 1);    // (e_x''.x, e_y''.x, e_x''.y, e_y''.y)
+    const float4 q2 = __ldg(bq + 2);    // (e_x''.z, e_y''.z, L_out, theta weight)
+    PairTest r;
+    r.L = fmaf(ln.vx, q0.x, fmaf(ln.vy, q0.y, ln.vz * q0.z));
+    // (x', y') in one packed chain, each component rounded as the scalar fma chain
+    float2 pq = __fmul2_rn(make_float2(ln.vz, ln.vz), make_float2(q2.x, q2.y));
+    pq = __ffma2_rn(make_float2(ln.vy, ln.vy), make_float2(q1.z, q1.w), pq);
+    r.pq = __ffma2_rn(make_float2(ln.vx, ln.vx), make_float2(q1.x, q1.y), pq);
+    r.L_in = q0.w;
+    r.in = fmaf(r.pq.x, r.pq.x, r.pq.y * r.pq.y) <= P.R2 && r.L >= q0.w && r.L <= q2.z;
+    return r;
+}
+
+// D_i(r) of eq. (2) for unit fluence (called only where the pair is in).
+template <bool MERGED, int LAT>
+__device__ __forceinline__ float pair_eval(const PlanView& P, const Lane& ln, const uint32_t i, const float sad,
+                                           const float4* __restrict__ sW, const PairTest& pt)
+{
+    const float L = pt.L;
+    const float2 pq = pt.pq;
+    const float t = L - pt.L_in;                 // depth below the surface
+    const float s = sad * rcp_approx(L);         // SAD / |r_a|
+    const float2 xy = __fmul2_rn(pq, make_float2(s, s));   // isocentre-plane coordinates
+    const float x = xy.x, y = xy.y;
 
     // radiological depth and omega_corr tables (steps 5-6) and the water
     // parameters u_i^w(t), omega_i^w(t) (step 10), linear in t
     float fr;
-    const int k = grid_index(t * P.inv_d, fr);
+    const uint32_t kb = grid_bits(t * P.inv_d, fr);
     float teq, O1, O2, u1w, u2w;
     if (MERGED) {
-        const float4* tb = P.tabm + 3 * ((size_t)i * P.Kmax + k);
+        const float4* tb = P.tabm + (i * P.tstride + 3u * (kb - kGridBits));
         const float4 e0 = __ldg(tb), e1 = __ldg(tb + 1), e2 = __ldg(tb + 2);
         teq = fmaf(fr, e0.y, e0.x);
         O1 = fmaf(fr, e0.w, e0.z);
@@ -111,13 +142,13 @@ __device__ __forceinline__ bool pair(const PlanView& P, const Lane& ln, int i, f
         u1w = fmaf(fr, e1.w, e1.z);
         u2w = fmaf(fr, e2.y, e2.x);
     } else {
-        const float4* tb = P.tab + 2 * ((size_t)i * P.Kmax + k);
+        const float4* tb = P.tab + (i * P.tstride + 2u * (kb - kGridBits));
         const float4 e0 = __ldg(tb), e1 = __ldg(tb + 1);
         teq = fmaf(fr, e0.y, e0.x);
         const float c1 = fmaf(fr, e0.w, e0.z);
         const float c2 = fmaf(fr, e1.y, e1.x);
         float fw;
-        const int jw = grid_index(fminf(t * P.inv_wdt, (float)(P.w_n - 1)), fw);
+        const uint32_t jw = grid_bits(fminf(t * P.inv_wdt, P.w_hi), fw) - kGridBits;
         const float4 w0 = sW[2 * jw], w1 = sW[2 * jw + 1];
         u1w = fmaf(fw, w0.y, w0.x);
         u2w = fmaf(fw, w0.w, w0.z);
@@ -127,8 +158,8 @@ __device__ __forceinline__ bool pair(const PlanView& P, const Lane& ln, int i, f
 
     // A(t_eq, theta) (step 9): the beamlet's theta-interpolated row, linear in t_eq
     float fa;
-    const int j = grid_index(fminf(fmaxf(teq * P.inv_adt, 0.f), (float)(P.a_nt - 1)), fa);
-    const float2 ar = __ldg(P.arow + (size_t)i * P.a_nt + j);
+    const uint32_t jb = grid_bits(fminf(fmaxf(teq * P.inv_adt, 0.f), P.a_hi), fa);
+    const float2 ar = __ldg(P.arow + (i * (uint32_t)P.a_nt + (jb - kGridBits)));
     const float Av = fmaf(fa, ar.y, ar.x);
 
     // density correction (step 11)
@@ -140,8 +171,7 @@ __device__ __forceinline__ bool pair(const PlanView& P, const Lane& ln, int i, f
     // eqs. (3) and (2)
     const float F = fmaf(om1 * penumbra(x, k1, k1 * P.x0, P.x0), penumbra(y, k1, k1 * P.y0, P.y0),
                          om2 * penumbra(x, k2, k2 * P.x0, P.x0) * penumbra(y, k2y, k2y * P.y0, P.y0));
-    D = F * Av * (s * s);
-    return true;
+    return F * Av * (s * s);
 }
 
 // Writes the staged CSR entries of all 32 lanes of the warp: half-warps take
@@ -215,6 +245,7 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
     const float sx = __ldg(&bm.src[0]), sy = __ldg(&bm.src[1]), sz = __ldg(&bm.src[2]);
     const float sad = __ldg(&bm.sad);
     ln.vx = rx - sx; ln.vy = ry - sy; ln.vz = rz - sz;
+    if (!ln.valid) ln.vx = __int_as_float(0x7fffffff);   // NaN: no pair test passes
     const float zz = ln.vx * __ldg(&bm.ez[0]) + ln.vy * __ldg(&bm.ez[1]) + ln.vz * __ldg(&bm.ez[2]);
     const float pa = ln.vx * __ldg(&bm.ex[0]) + ln.vy * __ldg(&bm.ex[1]) + ln.vz * __ldg(&bm.ex[2]);
     const float pc = ln.vx * __ldg(&bm.ey[0]) + ln.vy * __ldg(&bm.ey[1]) + ln.vz * __ldg(&bm.ey[2]);
@@ -245,26 +276,25 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
         }
         const int wmlo = __reduce_min_sync(0xffffffffu, mlo);
         const int wmhi = __reduce_max_sync(0xffffffffu, mhi);
-        const int row = first + n * M;
+        const uint32_t row = (uint32_t)(first + n * M);
         for (int m = wmlo; m <= wmhi; ++m) {
-            const int i = row + m;
+            const uint32_t i = row + (uint32_t)m;
+            const PairTest pt = pair_test(P, ln, i);
+            if (MODE == kCount) {
+                cnt += pt.in ? 1 : 0;
+                continue;
+            }
             if (MODE == kDose) {
-                float f[NF];
+                if (pt.in) {
+                    const float D = pair_eval<MERGED, LAT>(P, ln, i, sad, sW, pt);
 #pragma unroll
-                for (int q = 0; q < NF; ++q) f[q] = q < a.nf ? __ldg(a.fluence + (size_t)q * a.ldf + i) : 0.f;
-                float D;
-                if (pair<true, MERGED, LAT>(P, ln, i, sad, sW, D)) {
-#pragma unroll
-                    for (int q = 0; q < NF; ++q) acc[q] = fmaf(f[q], D, acc[q]);
+                    for (int q = 0; q < NF; ++q)
+                        if (q < a.nf) acc[q] = fmaf(__ldg(a.fluence + (q * (uint32_t)a.ldf + i)), D, acc[q]);
                 }
-            } else if (MODE == kCount) {
-                float D;
-                cnt += pair<false, false, kIso>(P, ln, i, sad, sW, D) ? 1 : 0;
             } else {
-                float D;
-                if (pair<true, MERGED, LAT>(P, ln, i, sad, sW, D)) {
-                    sc[lane * kStageLd + cnt] = i;
-                    sv[lane * kStageLd + cnt] = D;
+                if (pt.in) {
+                    sc[lane * kStageLd + cnt] = (int)i;
+                    sv[lane * kStageLd + cnt] = pair_eval<MERGED, LAT>(P, ln, i, sad, sW, pt);
                     ++cnt;
                 }
                 if (__any_sync(0xffffffffu, cnt == kStage)) flush_stage(a, sc, sv, lane, cnt, pos, pend);
@@ -288,7 +318,7 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
 // of one or two neighbouring beam's-eye-view cells; -1 entries are padding).
 // Persistent CTAs take units from a global counter.
 template <int MODE, int NF, bool MERGED, int LAT>
-__global__ void __launch_bounds__(kThreads) k_pairs(const DoseArgs a)
+__global__ void __launch_bounds__(kThreads, MODE == kCount ? 4 : (NF == 1 ? 5 : 3)) k_pairs(const DoseArgs a)
 {
     extern __shared__ float4 smem[];
     __shared__ int64_t s_base[kMaxBeams + 1];
@@ -302,7 +332,6 @@ __global__ void __launch_bounds__(kThreads) k_pairs(const DoseArgs a)
     for (int q = threadIdx.x; q <= P.n_beams; q += blockDim.x) s_base[q] = a.base[q];
     __syncthreads();
     const int total = a.work[0];
-    const int64_t V = (int64_t)P.nx * P.ny * P.nz;
 
     for (;;) {
         int w = 0;
@@ -313,7 +342,6 @@ __global__ void __launch_bounds__(kThreads) k_pairs(const DoseArgs a)
         int b = 0;
         while (b + 1 < P.n_beams && s_base[b + 1] <= e0) ++b;
         const int32_t vi = __ldg(a.items + e0 + lane);
-
         process_unit<MODE, NF, MERGED, LAT>(a, vi, e0, b, sW, sc, sv, lane);
     }
 }

@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(256) k_arows(const float* __restrict__ A, int 
          e += (int64_t)gridDim.x * blockDim.x) {
         const int i = (int)(e / a_nt), j = (int)(e % a_nt);
         const int l = __ldg(&bl[i].meta.y);
-        const float w = __ldg(&bl[i].ey_wth.w);
+        const float w = __ldg(&bl[i].exy_z.w);
         const float* r0 = A + (size_t)l * a_nt;
         const float* r1 = r0 + a_nt;
         const float v = fmaf(w, __ldg(r1 + j) - __ldg(r0 + j), __ldg(r0 + j));
@@ -366,8 +366,8 @@ __global__ void __launch_bounds__(128) k_beamlets(const BeamletArgs A)
     }
     BeamletDev r;
     r.n_lin = make_float4((float)nv[0], (float)nv[1], (float)nv[2], (float)L_in);
-    r.ex_tout = make_float4((float)exx[0], (float)exx[1], (float)exx[2], hit ? (float)L_out : -1.0f);
-    r.ey_wth = make_float4((float)eyy[0], (float)eyy[1], (float)eyy[2], wl);
+    r.exy_xy = make_float4((float)exx[0], (float)eyy[0], (float)exx[1], (float)eyy[1]);
+    r.exy_z = make_float4((float)exx[2], (float)eyy[2], hit ? (float)L_out : -1.0f, wl);
     r.meta = make_int4(K, l, hit, b);
     A.out_bl[i] = r;
     A.out_theta[i] = (float)theta;
