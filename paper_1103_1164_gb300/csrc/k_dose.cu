@@ -30,6 +30,7 @@ constexpr int kThreads = 32 * kWarps;
 constexpr float kLog2e = 1.4426950408889634f;
 constexpr int kStage = 16;          // CSR entries staged per lane before a coalesced flush
 constexpr int kStageLd = kStage + 1;
+constexpr int kRowMax = 32;         // beamlet records of a row window staged per warp at a time
 
 enum Mode { kDose = 0, kCount = 1, kFill = 2 };
 
@@ -99,12 +100,11 @@ struct PairTest {
     bool in;
 };
 
-__device__ __forceinline__ PairTest pair_test(const PlanView& P, const Lane& ln, const uint32_t i)
+// q0 = (n, L_in), q1 = (e_x''.x, e_y''.x, e_x''.y, e_y''.y),
+// q2 = (e_x''.z, e_y''.z, L_out, theta weight): the beamlet's record.
+__device__ __forceinline__ PairTest pair_test(const PlanView& P, const Lane& ln, const float4 q0, const float4 q1,
+                                              const float4 q2)
 {
-    const float4* bq = reinterpret_cast<const float4*>(P.bl) + 4u * i;
-    const float4 q0 = __ldg(bq);        // n, L_in
-    const float4 q1 = __ldg(bq + 1);    // (e_x''.x, e_y''.x, e_x''.y, e_y''.y)
-    const float4 q2 = __ldg(bq + 2);    // (e_x''.z, e_y''.z, L_out, theta weight)
     PairTest r;
     r.L = fmaf(ln.vx, q0.x, fmaf(ln.vy, q0.y, ln.vz * q0.z));
     // (x', y') in one packed chain, each component rounded as the scalar fma chain
@@ -204,7 +204,8 @@ __device__ __forceinline__ void flush_stage(const DoseArgs& a, const int* sc, co
 // (one voxel per lane) against the beamlets of the warp's union window.
 template <int MODE, int NF, bool MERGED, int LAT>
 __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi, const int64_t e0, const int b,
-                                             const float4* __restrict__ sW, int* sc, float* sv, const int lane)
+                                             const float4* __restrict__ sW, int* sc, float* sv, float4* srow,
+                                             const int lane)
 {
     const PlanView& P = a.P;
     const int64_t V = (int64_t)P.nx * P.ny * P.nz;
@@ -277,9 +278,23 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
         const int wmlo = __reduce_min_sync(0xffffffffu, mlo);
         const int wmhi = __reduce_max_sync(0xffffffffu, mhi);
         const uint32_t row = (uint32_t)(first + n * M);
-        for (int m = wmlo; m <= wmhi; ++m) {
+        // the records of the row's window go to shared memory with one
+        // coalesced load per lane, so the traversal reads them without a
+        // global-memory round trip per beamlet
+        for (int m0 = wmlo; m0 <= wmhi; m0 += kRowMax) {
+        const int m1 = min(wmhi, m0 + kRowMax - 1);
+        __syncwarp();
+        if (m0 + lane <= m1) {
+            const float4* src = reinterpret_cast<const float4*>(P.bl) + 4u * (row + (uint32_t)(m0 + lane));
+            srow[3 * lane] = __ldg(src);
+            srow[3 * lane + 1] = __ldg(src + 1);
+            srow[3 * lane + 2] = __ldg(src + 2);
+        }
+        __syncwarp();
+        for (int m = m0; m <= m1; ++m) {
             const uint32_t i = row + (uint32_t)m;
-            const PairTest pt = pair_test(P, ln, i);
+            const float4* rq = srow + 3 * (m - m0);
+            const PairTest pt = pair_test(P, ln, rq[0], rq[1], rq[2]);
             if (MODE == kCount) {
                 cnt += pt.in ? 1 : 0;
                 continue;
@@ -299,6 +314,7 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
                 }
                 if (__any_sync(0xffffffffu, cnt == kStage)) flush_stage(a, sc, sv, lane, cnt, pos, pend);
             }
+        }
         }
     }
     if (MODE == kFill) {
@@ -327,6 +343,7 @@ __global__ void __launch_bounds__(kThreads, MODE == kCount ? 4 : (NF == 1 ? 5 : 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int* sc = reinterpret_cast<int*>(smem + 2 * P.w_n) + warp * (32 * kStageLd);
     float* sv = reinterpret_cast<float*>(smem + 2 * P.w_n) + kWarps * (32 * kStageLd) + warp * (32 * kStageLd);
+    __shared__ float4 s_row[kWarps][3 * kRowMax];
     if (MODE != kCount)
         for (int q = threadIdx.x; q < 2 * P.w_n; q += blockDim.x) sW[q] = __ldg(P.water + q);
     for (int q = threadIdx.x; q <= P.n_beams; q += blockDim.x) s_base[q] = a.base[q];
@@ -342,7 +359,7 @@ __global__ void __launch_bounds__(kThreads, MODE == kCount ? 4 : (NF == 1 ? 5 : 
         int b = 0;
         while (b + 1 < P.n_beams && s_base[b + 1] <= e0) ++b;
         const int32_t vi = __ldg(a.items + e0 + lane);
-        process_unit<MODE, NF, MERGED, LAT>(a, vi, e0, b, sW, sc, sv, lane);
+        process_unit<MODE, NF, MERGED, LAT>(a, vi, e0, b, sW, sc, sv, s_row[warp], lane);
     }
 }
 
@@ -387,6 +404,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_pairs_batch(const __grid_con
 {
     extern __shared__ float4 smem[];
     __shared__ int64_t s_pre[kMaxBatch + 1];
+    __shared__ float4 s_row[kWarps][3 * kRowMax];
     for (int q = threadIdx.x; q <= n; q += blockDim.x) s_pre[q] = prefix[q];
     if (SHARED_W)
         for (int q = threadIdx.x; q < 2 * bp.a[0].P.w_n; q += blockDim.x) smem[q] = __ldg(bp.a[0].P.water + q);
@@ -409,14 +427,14 @@ __global__ void __launch_bounds__(kThreads, MINB) k_pairs_batch(const __grid_con
         const float4* wt = SHARED_W ? smem : a.P.water;
         if (a.P.merged_rt) {
             if (a.P.item_rt)
-                process_unit<kDose, 1, true, kItem>(a, vi, e0, b, wt, nullptr, nullptr, lane);
+                process_unit<kDose, 1, true, kItem>(a, vi, e0, b, wt, nullptr, nullptr, s_row[threadIdx.x >> 5], lane);
             else
-                process_unit<kDose, 1, true, kIso>(a, vi, e0, b, wt, nullptr, nullptr, lane);
+                process_unit<kDose, 1, true, kIso>(a, vi, e0, b, wt, nullptr, nullptr, s_row[threadIdx.x >> 5], lane);
         } else {
             if (a.P.item_rt)
-                process_unit<kDose, 1, false, kItem>(a, vi, e0, b, wt, nullptr, nullptr, lane);
+                process_unit<kDose, 1, false, kItem>(a, vi, e0, b, wt, nullptr, nullptr, s_row[threadIdx.x >> 5], lane);
             else
-                process_unit<kDose, 1, false, kIso>(a, vi, e0, b, wt, nullptr, nullptr, lane);
+                process_unit<kDose, 1, false, kIso>(a, vi, e0, b, wt, nullptr, nullptr, s_row[threadIdx.x >> 5], lane);
         }
     }
 }
