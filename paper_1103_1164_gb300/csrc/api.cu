@@ -265,6 +265,7 @@ static dc_status compute_density_steps(dc_plan* p, const float* ct, uint32_t fla
     DC_CUDA(launch_binning(p));
     if (p->coeffs.density_correction && p->lateral_mode != DC_LATERAL_ISO) DC_CUDA(launch_lateral(p));
     p->pairs = -1;
+    p->counts_fresh = false;
     if (p->sp_ready) p->spmm_free();   // the SpMM tiles follow the voxel lists
     return DC_OK;
 }
@@ -447,6 +448,7 @@ static dc_status rebin(dc_plan* p, float tile, float slab)
     DC_CUDA(launch_binning(p));
     if (p->coeffs.density_correction && p->lateral_mode != DC_LATERAL_ISO) DC_CUDA(launch_lateral(p));
     p->pairs = -1;
+    p->counts_fresh = false;
     if (p->sp_ready) p->spmm_free();
     ++p->layout_gen;
     return DC_OK;
@@ -573,14 +575,19 @@ dc_status dc_fspb_dose_batch(dc_plan* plan, const float* fluence, int32_t k, flo
         plan->part_cap = need;
         ++plan->layout_gen;
     }
+    // a single-fluence pass records the pair counts of the matrix pattern
+    // while the pattern is unknown (every pair test is made there anyway)
+    const bool record = k == 1 && plan->pairs < 0 && !plan->counts_fresh;
     if (flags & DC_DEVICE_PTRS) {
-        DC_CUDA(launch_dose(plan, fluence, k, plan->B, dose, plan->V));
+        DC_CUDA(launch_dose(plan, fluence, k, plan->B, dose, plan->V, record));
+        if (record) plan->counts_fresh = true;
         return DC_OK;
     }
     dc_status s = ensure_staging(plan, nf, nd);
     if (s != DC_OK) return s;
     DC_CUDA(cudaMemcpyAsync(plan->d_fluence, fluence, nf * sizeof(float), cudaMemcpyHostToDevice, plan->stream));
-    DC_CUDA(launch_dose(plan, plan->d_fluence, k, plan->B, plan->d_dose, plan->V));
+    DC_CUDA(launch_dose(plan, plan->d_fluence, k, plan->B, plan->d_dose, plan->V, record));
+    if (record) plan->counts_fresh = true;
     DC_CUDA(cudaMemcpyAsync(dose, plan->d_dose, nd * sizeof(float), cudaMemcpyDeviceToHost, plan->stream));
     DC_CUDA(cudaStreamSynchronize(plan->stream));
     return DC_OK;
@@ -596,7 +603,11 @@ static dc_status ensure_pattern(dc_plan* p)
     if (p->pairs >= 0) return DC_OK;
     if (!p->d_rowcount) DC_CUDA(dalloc(&p->d_rowcount, p->V));
     if (!p->d_rowptr) DC_CUDA(dalloc(&p->d_rowptr, p->V + 1));
-    DC_CUDA(launch_count(p, p->d_rowcount));
+    if (p->counts_fresh)
+        DC_CUDA(launch_rowsum(p, p->d_rowcount));
+    else
+        DC_CUDA(launch_count(p, p->d_rowcount));
+    p->counts_fresh = true;
     int64_t* total = reinterpret_cast<int64_t*>(p->d_scan_tmp) + (p->scan_tmp_bytes / sizeof(int64_t) - 1);
     DC_CUDA(launch_scan_counts(p, p->d_rowcount, p->d_rowptr, total));
     int64_t h = 0;

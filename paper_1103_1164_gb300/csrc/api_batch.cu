@@ -187,6 +187,7 @@ dc_status run(dc_batch* bt, uint32_t flags)
             // the voxel lists are rebuilt: the matrix pattern and SpMM tiles follow them
             DC_CUDA(cudaStreamSynchronize(p->stream));
             p->pairs = -1;
+            p->counts_fresh = false;
             if (p->sp_ready) p->spmm_free();
         }
     for (int i = 0; i < bt->n; ++i) {

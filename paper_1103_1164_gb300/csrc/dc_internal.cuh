@@ -99,6 +99,7 @@ struct DoseArgs {
     int64_t ldd;
     float* part;            // dose: per-beam partial dose [n_beams][NF][V]
     int32_t* bcount;        // count: per-beam pair counts [n_beams][V]; fill reads them
+    int32_t* count_out;     // dose with one fluence vector: where to record the same counts (or null)
     const int64_t* rowptr;  // fill
     int32_t* cols;
     void* vals;
@@ -205,6 +206,7 @@ struct dc_plan {
     int32_t* d_rowcount = nullptr;
     int64_t* d_rowptr = nullptr;
     int64_t pairs = -1;
+    bool counts_fresh = false;       // d_bcount holds the pair counts of the current voxel lists
     void* d_scan_tmp = nullptr;
     // device staging of the matrix for calls with host buffers
     int32_t* d_mcols = nullptr;
@@ -235,9 +237,14 @@ cudaError_t launch_smooth(const dc_plan* p, float sigma);
 cudaError_t launch_factors(const dc_plan* p);
 cudaError_t launch_beamlets(const dc_plan* p);   // also builds the theta-blended A rows
 cudaError_t launch_binning(const dc_plan* p);
+// record_counts (one fluence vector only): the pass also writes the per-beam
+// pair counts that launch_count would (the matrix pattern then needs no
+// second traversal; see launch_rowsum)
 cudaError_t launch_dose(const dc_plan* p, const float* fluence, int nf, int ldf, float* dose,
-                        int64_t ldd);
+                        int64_t ldd, bool record_counts = false);
 cudaError_t launch_count(const dc_plan* p, int32_t* counts);
+// rowcount[v] = sum over beams of the per-beam pair counts already in d_bcount
+cudaError_t launch_rowsum(const dc_plan* p, int32_t* counts);
 cudaError_t launch_fill(const dc_plan* p, const int64_t* rowptr, int32_t* cols, void* vals,
                         int value_dtype);
 cudaError_t launch_scan_counts(const dc_plan* p, const int32_t* counts, int64_t* rowptr,

@@ -28,7 +28,7 @@ namespace {
 constexpr int kWarps = 8;           // warps per CTA
 constexpr int kThreads = 32 * kWarps;
 constexpr float kLog2e = 1.4426950408889634f;
-constexpr int kStage = 16;          // CSR entries staged per lane before a coalesced flush
+constexpr int kStage = 12;          // CSR entries staged per lane before a coalesced flush
 constexpr int kStageLd = kStage + 1;
 constexpr int kRowMax = 32;         // beamlet records of a row window staged per warp at a time
 
@@ -176,25 +176,37 @@ __device__ __forceinline__ float pair_eval(const PlanView& P, const Lane& ln, co
 
 // Writes the staged CSR entries of all 32 lanes of the warp: half-warps take
 // one lane's run each, so every store covers consecutive entries of one row.
+// A lane never writes past the end of its (voxel, beam) segment of the row.
+template <typename VT>
+__device__ __forceinline__ void flush_runs(int32_t* colsj, VT* valsj, const int* sc, const float* sv, int half,
+                                           int j, int lim, int64_t pos)
+{
+#pragma unroll 4
+    for (int l2 = 0; l2 < 32; l2 += 2) {
+        const int owner = l2 + half;
+        const int c = __shfl_sync(0xffffffffu, lim, owner);
+        const int64_t base = __shfl_sync(0xffffffffu, pos, owner);
+        if (j < c) {
+            colsj[base] = sc[owner * kStageLd + j];
+            const float v = sv[owner * kStageLd + j];
+            if (sizeof(VT) == 2)
+                valsj[base] = __float2bfloat16_rn(v);
+            else
+                valsj[base] = v;
+        }
+    }
+}
+
 __device__ __forceinline__ void flush_stage(const DoseArgs& a, const int* sc, const float* sv, int lane,
                                             int& cnt, int64_t& pos, int64_t pend)
 {
     const int half = lane >> 4, j = lane & 15;
+    const int lim = (int)min((int64_t)cnt, pend - pos);
     __syncwarp();
-    for (int l2 = 0; l2 < 32; l2 += 2) {
-        const int owner = l2 + half;
-        const int c = __shfl_sync(0xffffffffu, cnt, owner);
-        const int64_t base = __shfl_sync(0xffffffffu, pos, owner);
-        const int64_t end = __shfl_sync(0xffffffffu, pend, owner);
-        if (j < c && base + j < end) {
-            a.cols[base + j] = sc[owner * kStageLd + j];
-            const float v = sv[owner * kStageLd + j];
-            if (a.value_dtype == DC_BF16)
-                reinterpret_cast<__nv_bfloat16*>(a.vals)[base + j] = __float2bfloat16_rn(v);
-            else
-                reinterpret_cast<float*>(a.vals)[base + j] = v;
-        }
-    }
+    if (a.value_dtype == DC_BF16)
+        flush_runs(a.cols + j, reinterpret_cast<__nv_bfloat16*>(a.vals) + j, sc, sv, half, j, lim, pos);
+    else
+        flush_runs(a.cols + j, reinterpret_cast<float*>(a.vals) + j, sc, sv, half, j, lim, pos);
     __syncwarp();
     pos += cnt;
     cnt = 0;
@@ -288,7 +300,11 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
             const float4* src = reinterpret_cast<const float4*>(P.bl) + 4u * (row + (uint32_t)(m0 + lane));
             srow[3 * lane] = __ldg(src);
             srow[3 * lane + 1] = __ldg(src + 1);
-            srow[3 * lane + 2] = __ldg(src + 2);
+            float4 q2 = __ldg(src + 2);
+            // one fluence vector: the staged record carries f_i in place of the
+            // theta weight (which only the table set-up uses)
+            if (MODE == kDose && NF == 1) q2.w = __ldg(a.fluence + row + (uint32_t)(m0 + lane));
+            srow[3 * lane + 2] = q2;
         }
         __syncwarp();
         for (int m = m0; m <= m1; ++m) {
@@ -300,11 +316,16 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
                 continue;
             }
             if (MODE == kDose) {
+                if (NF == 1) cnt += pt.in ? 1 : 0;
                 if (pt.in) {
                     const float D = pair_eval<MERGED, LAT>(P, ln, i, sad, sW, pt);
+                    if (NF == 1) {
+                        acc[0] = fmaf(rq[2].w, D, acc[0]);
+                    } else {
 #pragma unroll
-                    for (int q = 0; q < NF; ++q)
-                        if (q < a.nf) acc[q] = fmaf(__ldg(a.fluence + (q * (uint32_t)a.ldf + i)), D, acc[q]);
+                        for (int q = 0; q < NF; ++q)
+                            if (q < a.nf) acc[q] = fmaf(__ldg(a.fluence + (q * (uint32_t)a.ldf + i)), D, acc[q]);
+                    }
                 }
             } else {
                 if (pt.in) {
@@ -324,6 +345,7 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
 #pragma unroll
             for (int q = 0; q < NF; ++q)
                 if (q < a.nf) a.part[((size_t)b * NF + q) * V + v] = acc[q];
+            if (NF == 1 && a.count_out) a.count_out[(size_t)b * V + v] = cnt;
         } else {
             a.bcount[(size_t)b * V + v] = cnt;
         }
@@ -341,10 +363,12 @@ __global__ void __launch_bounds__(kThreads, MODE == kCount ? 4 : (NF == 1 ? 5 : 
     const PlanView& P = a.P;
     float4* sW = smem;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int* sc = reinterpret_cast<int*>(smem + 2 * P.w_n) + warp * (32 * kStageLd);
-    float* sv = reinterpret_cast<float*>(smem + 2 * P.w_n) + kWarps * (32 * kStageLd) + warp * (32 * kStageLd);
+    float4* sstage = smem + (MERGED ? 0 : 2 * P.w_n);
+    int* sc = reinterpret_cast<int*>(sstage) + warp * (32 * kStageLd);
+    float* sv = reinterpret_cast<float*>(sstage) + kWarps * (32 * kStageLd) + warp * (32 * kStageLd);
     __shared__ float4 s_row[kWarps][3 * kRowMax];
-    if (MODE != kCount)
+    // the water tables are read from shared memory unless merged into the depth tables
+    if (MODE != kCount && !MERGED)
         for (int q = threadIdx.x; q < 2 * P.w_n; q += blockDim.x) sW[q] = __ldg(P.water + q);
     for (int q = threadIdx.x; q <= P.n_beams; q += blockDim.x) s_base[q] = a.base[q];
     __syncthreads();
@@ -607,7 +631,7 @@ DoseArgs make_args(const dc_plan* p)
 size_t smem_bytes(const dc_plan* p, int mode)
 {
     if (mode == kCount) return 0;
-    size_t s = 2 * sizeof(float4) * p->coeffs.w_n;
+    size_t s = p->merged ? 0 : 2 * sizeof(float4) * p->coeffs.w_n;
     if (mode == kFill) s += 2 * sizeof(int) * kWarps * 32 * kStageLd;
     return s;
 }
@@ -691,11 +715,16 @@ cudaError_t launch_batch(cudaStream_t s, const DoseArgs* h_args, const DoseArgs*
 }
 
 cudaError_t launch_dose(const dc_plan* p, const float* fluence, int nf, int ldf, float* dose,
-                        int64_t ldd)
+                        int64_t ldd, bool record_counts)
 {
     DoseArgs a = make_args(p);
     a.ldf = ldf;
     a.part = p->d_part;
+    if (record_counts && nf == 1) {
+        cudaError_t e = cudaMemsetAsync(p->d_bcount, 0, sizeof(int32_t) * (size_t)p->n_beams * p->V, p->stream);
+        if (e != cudaSuccess) return e;
+        a.count_out = p->d_bcount;
+    }
     for (int q0 = 0; q0 < nf; q0 += 16) {
         a.fluence = fluence + (size_t)q0 * ldf;
         a.nf = nf - q0 < 16 ? nf - q0 : 16;
@@ -719,6 +748,13 @@ cudaError_t launch_count(const dc_plan* p, int32_t* counts)
     if (e != cudaSuccess) return e;
     e = run<kCount, 1>(p, a);
     if (e != cudaSuccess) return e;
+    k_rowsum<<<grid_for(p->V), 256, 0, p->stream>>>(p->d_bcount, p->n_beams, p->V, counts);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rowsum(const dc_plan* p, int32_t* counts)
+{
     k_rowsum<<<grid_for(p->V), 256, 0, p->stream>>>(p->d_bcount, p->n_beams, p->V, counts);
     count_launches(1);
     return cudaGetLastError();
