@@ -28,9 +28,14 @@ namespace {
 constexpr int kWarps = 8;           // warps per CTA
 constexpr int kThreads = 32 * kWarps;
 constexpr float kLog2e = 1.4426950408889634f;
-constexpr int kStage = 12;          // CSR entries staged per lane before a coalesced flush
-constexpr int kStageLd = kStage + 1;
-constexpr int kRowMax = 32;         // beamlet records of a row window staged per warp at a time
+// CSR entries staged per lane: a ring in which the entry at position g of the
+// column array sits in slot g mod kRing, so a run of pending entries never
+// needs moving when only its head is written out
+constexpr int kRing = 16;
+constexpr int kRingLd = kRing + 1;
+// beamlet records of a row window staged per warp at a time (fewer in the
+// fill, whose CSR staging shares the CTA's shared memory)
+constexpr int row_max(int mode) { return mode == 2 ? 16 : 32; }
 
 enum Mode { kDose = 0, kCount = 1, kFill = 2 };
 
@@ -174,49 +179,83 @@ __device__ __forceinline__ float pair_eval(const PlanView& P, const Lane& ln, co
     return F * Av * (s * s);
 }
 
-// Writes the staged CSR entries of all 32 lanes of the warp: half-warps take
-// one lane's run each, so every store covers consecutive entries of one row.
-// A lane never writes past the end of its (voxel, beam) segment of the row.
+// Writes nw staged CSR entries of every lane (nw <= kRing).  A quarter-warp
+// takes one lane's run at a time, 8 entries (one 32-byte sector of the column
+// array once the run is aligned) per pass: first the leading 8 entries of all
+// 32 runs, then entries 8..15 of the runs that are longer, four runs per pass.
+// Streaming stores: the matrix is written once and should not evict the depth
+// tables from L2.  Each staged entry is (column, value bits).
 template <typename VT>
-__device__ __forceinline__ void flush_runs(int32_t* colsj, VT* valsj, const int* sc, const float* sv, int half,
-                                           int j, int lim, int64_t pos)
+__device__ __forceinline__ void store_entry(int32_t* cols, VT* vals, int64_t g, int2 e)
 {
-#pragma unroll 4
-    for (int l2 = 0; l2 < 32; l2 += 2) {
-        const int owner = l2 + half;
-        const int c = __shfl_sync(0xffffffffu, lim, owner);
+    __stcs(cols + g, e.x);
+    if (sizeof(VT) == 2)
+        __stcs(reinterpret_cast<__nv_bfloat16*>(vals) + g, __float2bfloat16_rn(__int_as_float(e.y)));
+    else
+        __stcs(reinterpret_cast<float*>(vals) + g, __int_as_float(e.y));
+}
+
+template <typename VT>
+__device__ __forceinline__ void flush_runs(int32_t* cols, VT* vals, const int2* st, int lane, int nw, int64_t pos)
+{
+    const int q = lane >> 3, j = lane & 7;
+#pragma unroll 2
+    for (int o4 = 0; o4 < 32; o4 += 4) {
+        const int owner = o4 + q;
+        const int c = __shfl_sync(0xffffffffu, nw, owner);
         const int64_t base = __shfl_sync(0xffffffffu, pos, owner);
-        if (j < c) {
-            colsj[base] = sc[owner * kStageLd + j];
-            const float v = sv[owner * kStageLd + j];
-            if (sizeof(VT) == 2)
-                valsj[base] = __float2bfloat16_rn(v);
-            else
-                valsj[base] = v;
-        }
+        if (j < c)
+            store_entry(cols, vals, base + j,
+                        st[owner * kRingLd + (int)(((uint32_t)base + (uint32_t)j) & (kRing - 1))]);
+    }
+    uint32_t longer = __ballot_sync(0xffffffffu, nw > 8);
+    while (longer) {
+        uint32_t mq = longer;   // quarter q takes the q-th lowest set bit
+#pragma unroll
+        for (int t = 0; t < 3; ++t)
+            if (t < q) mq &= mq - 1u;
+        const int src = mq ? __ffs((int)mq) - 1 : 0;
+        int c = __shfl_sync(0xffffffffu, nw, src);
+        const int64_t base = __shfl_sync(0xffffffffu, pos, src);
+        if (!mq) c = 0;
+        if (j + 8 < c)
+            store_entry(cols, vals, base + 8 + j,
+                        st[src * kRingLd + (int)(((uint32_t)base + 8u + (uint32_t)j) & (kRing - 1))]);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) longer &= longer - 1u;
     }
 }
 
-__device__ __forceinline__ void flush_stage(const DoseArgs& a, const int* sc, const float* sv, int lane,
-                                            int& cnt, int64_t& pos, int64_t pend)
+// Writes out the lanes' pending entries.  Except at the end of a work unit
+// (`last`), a lane stops at the last 32-byte boundary of the column array
+// inside its run and keeps the rest staged, so that DRAM sees whole sectors
+// (a partly written sector evicted from L2 costs a read-modify-write); mis is
+// the column array's offset from a 32-byte boundary, in entries.  A lane never
+// writes past the end of its (voxel, beam) segment of the row.
+__device__ __forceinline__ void flush_stage(const DoseArgs& a, const int2* st, int lane, int& cnt, int64_t& pos,
+                                            int64_t pend, int mis, bool last)
 {
-    const int half = lane >> 4, j = lane & 15;
-    const int lim = (int)min((int64_t)cnt, pend - pos);
+    int nw = cnt;
+    if (!last) {
+        const int64_t end = ((pos + cnt + mis) & ~(int64_t)7) - mis;
+        nw = end > pos ? (int)(end - pos) : 0;
+    }
+    nw = (int)min((int64_t)nw, pend - pos);
     __syncwarp();
     if (a.value_dtype == DC_BF16)
-        flush_runs(a.cols + j, reinterpret_cast<__nv_bfloat16*>(a.vals) + j, sc, sv, half, j, lim, pos);
+        flush_runs(a.cols, reinterpret_cast<__nv_bfloat16*>(a.vals), st, lane, nw, pos);
     else
-        flush_runs(a.cols + j, reinterpret_cast<float*>(a.vals) + j, sc, sv, half, j, lim, pos);
+        flush_runs(a.cols, reinterpret_cast<float*>(a.vals), st, lane, nw, pos);
     __syncwarp();
-    pos += cnt;
-    cnt = 0;
+    pos += nw;
+    cnt -= nw;
 }
 
 // Evaluates one warp work unit: the 32 list entries starting at e0 of beam b
 // (one voxel per lane) against the beamlets of the warp's union window.
 template <int MODE, int NF, bool MERGED, int LAT>
 __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi, const int64_t e0, const int b,
-                                             const float4* __restrict__ sW, int* sc, float* sv, float4* srow,
+                                             const float4* __restrict__ sW, int2* sst, float4* srow,
                                              const int lane)
 {
     const PlanView& P = a.P;
@@ -249,6 +288,7 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
     for (int q = 0; q < NF; ++q) acc[q] = 0.f;
     int32_t cnt = 0;
     int64_t pos = 0, pend = 0;
+    const int mis = MODE == kFill ? (int)((reinterpret_cast<uintptr_t>(a.cols) >> 2) & 7) : 0;
     if (MODE == kFill && ln.valid) {
         pos = a.rowptr[v];
         for (int bb = 0; bb < b; ++bb) pos += a.bcount[(size_t)bb * V + v];
@@ -293,8 +333,8 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
         // the records of the row's window go to shared memory with one
         // coalesced load per lane, so the traversal reads them without a
         // global-memory round trip per beamlet
-        for (int m0 = wmlo; m0 <= wmhi; m0 += kRowMax) {
-        const int m1 = min(wmhi, m0 + kRowMax - 1);
+        for (int m0 = wmlo; m0 <= wmhi; m0 += row_max(MODE)) {
+        const int m1 = min(wmhi, m0 + row_max(MODE) - 1);
         __syncwarp();
         if (m0 + lane <= m1) {
             const float4* src = reinterpret_cast<const float4*>(P.bl) + 4u * (row + (uint32_t)(m0 + lane));
@@ -329,17 +369,18 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
                 }
             } else {
                 if (pt.in) {
-                    sc[lane * kStageLd + cnt] = (int)i;
-                    sv[lane * kStageLd + cnt] = pair_eval<MERGED, LAT>(P, ln, i, sad, sW, pt);
+                    const float D = pair_eval<MERGED, LAT>(P, ln, i, sad, sW, pt);
+                    sst[lane * kRingLd + (int)(((uint32_t)pos + (uint32_t)cnt) & (kRing - 1))] =
+                        make_int2((int)i, __float_as_int(D));
                     ++cnt;
                 }
-                if (__any_sync(0xffffffffu, cnt == kStage)) flush_stage(a, sc, sv, lane, cnt, pos, pend);
+                if (__any_sync(0xffffffffu, cnt >= kRing)) flush_stage(a, sst, lane, cnt, pos, pend, mis, false);
             }
         }
         }
     }
     if (MODE == kFill) {
-        flush_stage(a, sc, sv, lane, cnt, pos, pend);
+        flush_stage(a, sst, lane, cnt, pos, pend, mis, true);
     } else if (ln.valid) {
         if (MODE == kDose) {
 #pragma unroll
@@ -364,9 +405,8 @@ __global__ void __launch_bounds__(kThreads, MODE == kCount ? 4 : (NF == 1 ? 5 : 
     float4* sW = smem;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float4* sstage = smem + (MERGED ? 0 : 2 * P.w_n);
-    int* sc = reinterpret_cast<int*>(sstage) + warp * (32 * kStageLd);
-    float* sv = reinterpret_cast<float*>(sstage) + kWarps * (32 * kStageLd) + warp * (32 * kStageLd);
-    __shared__ float4 s_row[kWarps][3 * kRowMax];
+    int2* sst = reinterpret_cast<int2*>(sstage) + warp * (32 * kRingLd);
+    __shared__ float4 s_row[kWarps][3 * row_max(MODE)];
     // the water tables are read from shared memory unless merged into the depth tables
     if (MODE != kCount && !MERGED)
         for (int q = threadIdx.x; q < 2 * P.w_n; q += blockDim.x) sW[q] = __ldg(P.water + q);
@@ -383,7 +423,7 @@ __global__ void __launch_bounds__(kThreads, MODE == kCount ? 4 : (NF == 1 ? 5 : 
         int b = 0;
         while (b + 1 < P.n_beams && s_base[b + 1] <= e0) ++b;
         const int32_t vi = __ldg(a.items + e0 + lane);
-        process_unit<MODE, NF, MERGED, LAT>(a, vi, e0, b, sW, sc, sv, s_row[warp], lane);
+        process_unit<MODE, NF, MERGED, LAT>(a, vi, e0, b, sW, sst, s_row[warp], lane);
     }
 }
 
@@ -428,7 +468,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_pairs_batch(const __grid_con
 {
     extern __shared__ float4 smem[];
     __shared__ int64_t s_pre[kMaxBatch + 1];
-    __shared__ float4 s_row[kWarps][3 * kRowMax];
+    __shared__ float4 s_row[kWarps][3 * row_max(kDose)];
     for (int q = threadIdx.x; q <= n; q += blockDim.x) s_pre[q] = prefix[q];
     if (SHARED_W)
         for (int q = threadIdx.x; q < 2 * bp.a[0].P.w_n; q += blockDim.x) smem[q] = __ldg(bp.a[0].P.water + q);
@@ -451,14 +491,14 @@ __global__ void __launch_bounds__(kThreads, MINB) k_pairs_batch(const __grid_con
         const float4* wt = SHARED_W ? smem : a.P.water;
         if (a.P.merged_rt) {
             if (a.P.item_rt)
-                process_unit<kDose, 1, true, kItem>(a, vi, e0, b, wt, nullptr, nullptr, s_row[threadIdx.x >> 5], lane);
+                process_unit<kDose, 1, true, kItem>(a, vi, e0, b, wt, nullptr, s_row[threadIdx.x >> 5], lane);
             else
-                process_unit<kDose, 1, true, kIso>(a, vi, e0, b, wt, nullptr, nullptr, s_row[threadIdx.x >> 5], lane);
+                process_unit<kDose, 1, true, kIso>(a, vi, e0, b, wt, nullptr, s_row[threadIdx.x >> 5], lane);
         } else {
             if (a.P.item_rt)
-                process_unit<kDose, 1, false, kItem>(a, vi, e0, b, wt, nullptr, nullptr, s_row[threadIdx.x >> 5], lane);
+                process_unit<kDose, 1, false, kItem>(a, vi, e0, b, wt, nullptr, s_row[threadIdx.x >> 5], lane);
             else
-                process_unit<kDose, 1, false, kIso>(a, vi, e0, b, wt, nullptr, nullptr, s_row[threadIdx.x >> 5], lane);
+                process_unit<kDose, 1, false, kIso>(a, vi, e0, b, wt, nullptr, s_row[threadIdx.x >> 5], lane);
         }
     }
 }
@@ -632,7 +672,7 @@ size_t smem_bytes(const dc_plan* p, int mode)
 {
     if (mode == kCount) return 0;
     size_t s = p->merged ? 0 : 2 * sizeof(float4) * p->coeffs.w_n;
-    if (mode == kFill) s += 2 * sizeof(int) * kWarps * 32 * kStageLd;
+    if (mode == kFill) s += sizeof(int2) * kWarps * 32 * kRingLd;
     return s;
 }
 

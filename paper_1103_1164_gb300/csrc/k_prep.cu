@@ -186,18 +186,25 @@ __device__ __forceinline__ float lut_dens(const BeamletArgs& A, int q, float r)
     return lut1(A.dens + (size_t)q * A.f_n, A.f_n, A.f_rho0, A.inv_drho, r);
 }
 
-// Cumulative integrals of rho, b_1(rho), b_2(rho) from L_in, sampled at
-// L_in + k d for k < K, stored as value + slope to the next sample:
+// Steps 4-6 in one FP64 walk of the beamlet's central axis.  The body entry
+// L_in is the start of the first segment whose density exceeds the surface
+// threshold and L_out the end of the last one.  From L_in on, the cumulative
+// integrals of rho, b_1(rho), b_2(rho) are sampled at L_in + k d and stored as
+// value + slope to the next sample:
 //   tab[2k] = (T_k, T_k+1 - T_k, W1_k, W1_k+1 - W1_k), tab[2k+1] = (W2_k, W2_k+1 - W2_k, 0, 0)
-// (zero slope at k = K - 1).  Acc is float for rays up to 40 cm in the grid
-// and double beyond.
+// with zero slope at k = K - 1, K = ceil((L_out - L_in) / d) + 1 (at least 2,
+// at most Kmax).  K is known only at the end of the walk, so samples are
+// emitted up to the end of the ray (or Kmax) and the table is closed at K - 1
+// afterwards.  Acc is float for rays up to 40 cm in the grid and double beyond.
 template <typename Acc>
-__device__ void fill_tables(const BeamletArgs& A, const Walk& w0, double L_in, int K,
-                            float4* __restrict__ tab)
+__device__ void trace_beamlet(const BeamletArgs& A, const Walk& w0, float4* __restrict__ tab, double& L_in,
+                              double& L_out, int& K)
 {
     Acc cT = 0, c1 = 0, c2 = 0;
     float pT = 0.f, p1 = 0.f, p2 = 0.f;
     int k = 0;
+    const int kcap = A.Kmax;
+    double first_a = -1, last_a = -1;
     auto emit = [&](float T, float a, float b) {
         if (k > 0) {
             tab[2 * (k - 1)] = make_float4(pT, T - pT, p1, a - p1);
@@ -206,13 +213,18 @@ __device__ void fill_tables(const BeamletArgs& A, const Walk& w0, double L_in, i
         pT = T; p1 = a; p2 = b;
         ++k;
     };
+    const float surf = A.rho_surf;
     walk_run(A, w0, [&](double a0, double a1, int64_t vox) {
-        if (a1 <= L_in || k >= K) return;
-        double lo = fmax(a0, L_in);
-        float r = __ldg(A.rho + vox);
+        const float r = __ldg(A.rho + vox);
+        if (r > surf) {
+            if (first_a < 0) first_a = a0;
+            last_a = a1;
+        }
+        if (first_a < 0 || k >= kcap) return;
+        const double lo = fmax(a0, first_a);
         Acc vr = (Acc)r, v1 = (Acc)lut_dens(A, 4, r), v2 = (Acc)lut_dens(A, 5, r);
-        while (k < K) {
-            double sk = L_in + k * A.d;
+        while (k < kcap) {
+            double sk = first_a + k * A.d;
             if (sk > a1) break;
             Acc len = (Acc)(sk - lo);
             emit((float)(cT + vr * len), (float)(c1 + v1 * len), (float)(c2 + v2 * len));
@@ -222,9 +234,23 @@ __device__ void fill_tables(const BeamletArgs& A, const Walk& w0, double L_in, i
         c1 += v1 * len;
         c2 += v2 * len;
     });
+    K = 0;
+    if (first_a < 0) return;
+    L_in = first_a;
+    L_out = last_a;
+    K = max(2, (int)ceil((L_out - L_in) / A.d) + 1);
+    K = min(K, kcap);
     while (k < K) emit((float)cT, (float)c1, (float)c2);
-    tab[2 * (K - 1)] = make_float4(pT, 0.f, p1, 0.f);
-    tab[2 * (K - 1) + 1] = make_float4(p2, 0.f, 0.f, 0.f);
+    if (k == K) {
+        // sample K - 1 is still pending
+        tab[2 * (K - 1)] = make_float4(pT, 0.f, p1, 0.f);
+        tab[2 * (K - 1) + 1] = make_float4(p2, 0.f, 0.f, 0.f);
+    } else {
+        // samples past K - 1 were emitted: only the slopes of K - 1 change
+        tab[2 * (K - 1)].y = 0.f;
+        tab[2 * (K - 1)].w = 0.f;
+        tab[2 * (K - 1) + 1].y = 0.f;
+    }
 }
 
 // Merged per-beamlet tables for plans whose water tables are sampled on the
@@ -273,7 +299,10 @@ __global__ void __launch_bounds__(256) k_arows(const float* __restrict__ A, int 
     }
 }
 
-__global__ void __launch_bounds__(128) k_beamlets(const BeamletArgs A)
+// One thread per beamlet, one warp per CTA: the walk is FP64-bound, so the
+// beamlets are spread over every SM.
+constexpr int kBeamletThreads = 32;
+__global__ void __launch_bounds__(kBeamletThreads) k_beamlets(const BeamletArgs A)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= A.B) return;
@@ -343,26 +372,12 @@ __global__ void __launch_bounds__(128) k_beamlets(const BeamletArgs A)
     int hit = 0, K = 0;
     double L_in = 0, L_out = 0;
     if (walk_init(A, src, nv, w)) {
-        double first_a = -1, last_a = -1;
-        const float surf = A.rho_surf;
-        walk_run(A, w, [&](double a0, double a1, int64_t vox) {
-            if (__ldg(A.rho + vox) > surf) {
-                if (first_a < 0) first_a = a0;
-                last_a = a1;
-            }
-        });
-        if (first_a >= 0) {
-            hit = 1;
-            L_in = first_a;
-            L_out = last_a;
-            K = max(2, (int)ceil((L_out - L_in) / A.d) + 1);
-            K = min(K, A.Kmax);
-            float4* tb = A.tab + 2 * (size_t)i * A.Kmax;
-            if (w.amax - w.acur > 40.0)
-                fill_tables<double>(A, w, L_in, K, tb);
-            else
-                fill_tables<float>(A, w, L_in, K, tb);
-        }
+        float4* tb = A.tab + 2 * (size_t)i * A.Kmax;
+        if (w.amax - w.acur > 40.0)
+            trace_beamlet<double>(A, w, tb, L_in, L_out, K);
+        else
+            trace_beamlet<float>(A, w, tb, L_in, L_out, K);
+        hit = K > 0 ? 1 : 0;
     }
     BeamletDev r;
     r.n_lin = make_float4((float)nv[0], (float)nv[1], (float)nv[2], (float)L_in);
@@ -461,7 +476,7 @@ cudaError_t launch_beamlets(const dc_plan* p)
         A.M[b] = p->M[b];
     }
     A.first[p->n_beams] = p->B;
-    k_beamlets<<<(p->B + 127) / 128, 128, 0, p->stream>>>(A);
+    k_beamlets<<<(p->B + kBeamletThreads - 1) / kBeamletThreads, kBeamletThreads, 0, p->stream>>>(A);
     count_launches(1);
     k_arows<<<grid_for((int64_t)p->B * p->coeffs.a_nt, 256), 256, 0, p->stream>>>(
         p->d_A, p->coeffs.a_nt, p->d_bl, p->B, p->d_arow);
