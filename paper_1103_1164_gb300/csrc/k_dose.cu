@@ -55,16 +55,26 @@ __device__ __forceinline__ float rcp_approx(float x)
     return y;
 }
 
-// For 0 <= x < 2^22: an integer n with n <= x and x - n <= 1 (floor(x), or
-// floor(x) - 1 when x is an exact integer) and frac = x - n, by rounding
-// x - 1/2 against 1.5 * 2^23; no conversion instruction is issued.  Returns
-// the bits of the rounded value, kGridBits + n: table offsets subtract
-// kGridBits in 32-bit arithmetic, which folds into one multiply-add.
+// Table coordinates without a conversion instruction (conversions share the
+// quarter-rate pipe with the exponentials).  For 0 <= x < 2^22, adding
+// 1.5 * 2^23 with rounding toward -infinity leaves floor(x) in the low
+// mantissa bits: the result's bits are kGridBits + floor(x), and table
+// offsets subtract kGridBits in 32-bit arithmetic, which folds into one
+// multiply-add.  frac = x - floor(x).
 constexpr uint32_t kGridBits = 0x4B400000u;
 __device__ __forceinline__ uint32_t grid_bits(float x, float& frac)
 {
-    const float f = __fadd_rn(__fadd_rn(x, -0.5f), 12582912.0f);
+    const float f = __fadd_rd(x, 12582912.0f);
     frac = __fadd_rn(x, -__fadd_rn(f, -12582912.0f));
+    return __float_as_uint(f);
+}
+
+// The same for x = a b without rounding the product: floor(a b) and
+// frac = a b - floor(a b) from two multiply-adds of the exact product.
+__device__ __forceinline__ uint32_t grid_bits_mul(float a, float b, float& frac)
+{
+    const float f = __fmaf_rd(a, b, 12582912.0f);
+    frac = __fmaf_rn(a, b, -__fadd_rn(f, -12582912.0f));
     return __float_as_uint(f);
 }
 
@@ -136,7 +146,7 @@ __device__ __forceinline__ float pair_eval(const PlanView& P, const Lane& ln, co
     // radiological depth and omega_corr tables (steps 5-6) and the water
     // parameters u_i^w(t), omega_i^w(t) (step 10), linear in t
     float fr;
-    const uint32_t kb = grid_bits(t * P.inv_d, fr);
+    const uint32_t kb = grid_bits_mul(t, P.inv_d, fr);
     float teq, O1, O2, u1w, u2w;
     if (MERGED) {
         const float4* tb = P.tabm + (i * P.tstride + 3u * (kb - kGridBits));
@@ -396,8 +406,14 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
 // One warp work unit = 32 consecutive entries of one beam's voxel list (voxels
 // of one or two neighbouring beam's-eye-view cells; -1 entries are padding).
 // Persistent CTAs take units from a global counter.
+// Register budgets: 48 per thread for the single-fluence dose (5 CTAs per
+// SM), 64 for the pair count and the CSR fill (4 CTAs; the fill's extra state
+// would otherwise be recomputed in the hot loop), 80 for 16 fluence vectors.
+template <int MODE, int NF>
+constexpr int min_ctas() { return MODE == kCount ? 4 : (MODE == kFill ? 4 : (NF == 1 ? 5 : 3)); }
+
 template <int MODE, int NF, bool MERGED, int LAT>
-__global__ void __launch_bounds__(kThreads, MODE == kCount ? 4 : (NF == 1 ? 5 : 3)) k_pairs(const DoseArgs a)
+__global__ void __launch_bounds__(kThreads, min_ctas<MODE, NF>()) k_pairs(const DoseArgs a)
 {
     extern __shared__ float4 smem[];
     __shared__ int64_t s_base[kMaxBeams + 1];
