@@ -36,8 +36,9 @@ constexpr int kKC = 16;              // beamlets per K-chunk
 constexpr int kN = 64;               // fluence columns of the MMA
 constexpr int kTileA = kRB * kKC * 2;     // 4096 bytes
 constexpr int kTileB = kKC * kN * 2;      // 2048 bytes
-constexpr int kStages = 6;
-constexpr int kSpmmThreads = 128;
+constexpr int kStages = 8;
+constexpr int kEpiWarps = 4;                  // epilogue warps (one per 32 accumulator rows)
+constexpr int kSpmmThreads = 32 * (kEpiWarps + 2);
 constexpr long long kSpinLimit = 1ll << 26;   // bounded mbarrier waits ...
 constexpr uint64_t kWaitNs = 2000000000ull;   // ... of at most 2 s
 
@@ -260,13 +261,51 @@ struct SpmmArgs {
     int32_t* err;
 };
 
+// Reads 32 FP32 columns of this warp's 32 accumulator rows from tensor memory.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r)
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Writes 32 columns [q0, q0 + 32) of an output row.
+__device__ __forceinline__ void store_cols(float* out, int q0, int k, bool vec4, const uint32_t* r)
+{
+    if (vec4) {
+#pragma unroll
+        for (int q = 0; q < 32; q += 4)
+            if (q0 + q < k)
+                *reinterpret_cast<float4*>(out + q0 + q) = make_float4(
+                    __uint_as_float(r[q]), __uint_as_float(r[q + 1]), __uint_as_float(r[q + 2]), __uint_as_float(r[q + 3]));
+    } else {
+#pragma unroll
+        for (int q = 0; q < 32; ++q)
+            if (q0 + q < k) out[q0 + q] = __uint_as_float(r[q]);
+    }
+}
+
+// Warp roles: warps 0-3 drain the accumulator of a finished row-block (warp w
+// owns tensor-memory lanes 32w..32w+31, i.e. rows 32w.. of the row-block),
+// warp 4 (one lane) streams the A and F tiles of all the CTA's row-blocks
+// through the stage ring, warp 5 (one lane) issues the MMAs.  The accumulator
+// is double-buffered in tensor memory (2 x 64 columns), so the loads and MMAs
+// of row-block j + 1 overlap the epilogue of row-block j and the ring never
+// drains between row-blocks.
 __global__ void __launch_bounds__(kSpmmThreads) k_spmm(const SpmmArgs a)
 {
     extern __shared__ __align__(1024) uint8_t sm[];
-    __shared__ uint64_t full[kStages], empty[kStages], done;
+    __shared__ uint64_t full[kStages], empty[kStages], acc_full[2], acc_empty[2];
     __shared__ uint32_t tmem_base;
-    __shared__ int s_abort;
-    const int t = threadIdx.x, warp = t >> 5;
+    __shared__ volatile int s_abort;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
 
     // stage buffers, 1 KB aligned
     uint8_t* buf = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(sm) + 1023) & ~(uintptr_t)1023);
@@ -275,13 +314,16 @@ __global__ void __launch_bounds__(kSpmmThreads) k_spmm(const SpmmArgs a)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(&done, 1);
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&acc_full[q], 1);
+            mbar_init(&acc_empty[q], kEpiWarps);
+        }
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                     "r"(kN));
+                     "r"(2 * kN));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -289,120 +331,132 @@ __global__ void __launch_bounds__(kSpmmThreads) k_spmm(const SpmmArgs a)
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_base;
 
-    uint32_t g_load = 0, g_mma = 0, n_done = 0;   // chunks issued / consumed so far, row-blocks done
-    for (int rb = blockIdx.x; rb < a.n_rb; rb += gridDim.x) {
-        const int64_t ch0 = a.chunk_off[rb], nch = a.chunk_off[rb + 1] - ch0;
-        if (t == 0 && !s_abort) {
+    if (warp == kEpiWarps) {
+        // ---- producer: every chunk of every row-block of this CTA, in order
+        if (lane == 0) {
+            uint32_t g = 0;
             bool ok = true;
-            // prologue: fill up to kStages stages
-            int64_t issued = 0;
-            auto issue = [&](int64_t c) {
-                const uint32_t s = g_load % kStages;
-                if (g_load >= kStages && !mbar_wait(&empty[s], ((g_load / kStages) - 1) & 1)) {
-                    ok = false;
-                    return;
-                }
-                uint8_t* sa = buf + s * (kTileA + kTileB);
-                mbar_expect_tx(&full[s], kTileA + kTileB);
-                bulk_g2s(sa, a.tiles + (size_t)(ch0 + c) * (kRB * kKC), kTileA, &full[s]);
-                bulk_g2s(sa + kTileA, a.Fp + (size_t)a.chunk_kb[ch0 + c] * (8 * kN), kTileB, &full[s]);
-                ++g_load;
-            };
-            for (; issued < nch && issued < kStages && ok; ++issued) issue(issued);
-            for (int64_t c = 0; c < nch && ok; ++c) {
-                const uint32_t s = g_mma % kStages;
-                ok = mbar_wait(&full[s], (g_mma / kStages) & 1);
-                if (!ok) break;
-                asm volatile("tcgen05.fence::after_thread_sync;");
-                uint8_t* sa = buf + s * (kTileA + kTileB);
-                const uint64_t da = smem_desc(sa, 128, 256);            // A: LBO along K, SBO along M
-                const uint64_t db = smem_desc(sa + kTileA, 1024, 128);  // B: LBO along K, SBO along N
-                umma_bf16(tmem, da, db, c > 0 ? 1u : 0u);
-                umma_commit(&empty[s]);
-                ++g_mma;
-                if (issued < nch) {
-                    issue(issued);
-                    ++issued;
+            for (int rb = blockIdx.x; rb < a.n_rb && ok; rb += gridDim.x) {
+                const int64_t ch0 = a.chunk_off[rb], nch = a.chunk_off[rb + 1] - ch0;
+                for (int64_t c = 0; c < nch; ++c, ++g) {
+                    const uint32_t s = g % kStages;
+                    if (g >= kStages && !mbar_wait(&empty[s], ((g / kStages) - 1) & 1)) {
+                        ok = false;
+                        break;
+                    }
+                    if (s_abort) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* sa = buf + s * (kTileA + kTileB);
+                    mbar_expect_tx(&full[s], kTileA + kTileB);
+                    bulk_g2s(sa, a.tiles + (size_t)(ch0 + c) * (kRB * kKC), kTileA, &full[s]);
+                    bulk_g2s(sa + kTileA, a.Fp + (size_t)a.chunk_kb[ch0 + c] * (8 * kN), kTileB, &full[s]);
                 }
             }
             if (!ok) {
-                // give up: let the copies already issued land (bounded) so that
-                // nothing is in flight when the CTA releases its memory
-                for (; g_mma < g_load; ++g_mma) mbar_wait(&full[g_mma % kStages], (g_mma / kStages) & 1);
                 s_abort = 1;
                 atomicExch(a.err, 1);
             }
-            umma_commit(&done);
+            // nothing may be in flight when the CTA releases its shared memory:
+            // wait (bounded) until the MMA warp has consumed, or the copies
+            // have landed in, every issued stage
+            for (uint32_t q = g > kStages ? g - kStages : 0; q < g; ++q)
+                if (!mbar_wait(&full[q % kStages], (q / kStages) & 1)) break;
         }
-        // epilogue: wait for the accumulator (all MMAs of this row-block), read this warp's 32 rows
-        bool ok = mbar_wait(&done, n_done & 1);
-        ++n_done;
-        if (!ok) {
-            atomicExch(a.err, 1);
-            s_abort = 1;
+    } else if (warp == kEpiWarps + 1) {
+        // ---- MMA issuer
+        if (lane == 0) {
+            uint32_t g = 0, j = 0;
+            bool ok = true;
+            for (int rb = blockIdx.x; rb < a.n_rb && ok; rb += gridDim.x, ++j) {
+                const int64_t nch = a.chunk_off[rb + 1] - a.chunk_off[rb];
+                const uint32_t ab = j & 1;
+                // the epilogue of row-block j - 2 has read this accumulator
+                if (j >= 2 && !mbar_wait(&acc_empty[ab], ((j >> 1) - 1) & 1)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                for (int64_t c = 0; c < nch; ++c, ++g) {
+                    const uint32_t s = g % kStages;
+                    if (!mbar_wait(&full[s], (g / kStages) & 1) || s_abort) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    uint8_t* sa = buf + s * (kTileA + kTileB);
+                    const uint64_t da = smem_desc(sa, 128, 256);            // A: LBO along K, SBO along M
+                    const uint64_t db = smem_desc(sa + kTileA, 1024, 128);  // B: LBO along K, SBO along N
+                    umma_bf16(tmem + ab * kN, da, db, c > 0 ? 1u : 0u);
+                    umma_commit(&empty[s]);
+                }
+                if (!ok) break;
+                umma_commit(&acc_full[ab]);   // arrives when this row-block's MMAs are complete
+            }
+            if (!ok) {
+                s_abort = 1;
+                atomicExch(a.err, 1);
+            }
         }
-        __syncthreads();
-        if (s_abort) break;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        if (ok) {
+    } else {
+        // ---- epilogue (warps 0-3)
+        uint32_t j = 0;
+        for (int rb = blockIdx.x; rb < a.n_rb; rb += gridDim.x, ++j) {
+            const int64_t nch = a.chunk_off[rb + 1] - a.chunk_off[rb];
+            const uint32_t ab = j & 1;
+            bool ok = true;
+            if (lane == 0) ok = mbar_wait(&acc_full[ab], (j >> 1) & 1) && !s_abort;
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            if (!ok) {
+                if (lane == 0) {
+                    s_abort = 1;
+                    atomicExch(a.err, 1);
+                }
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
             int b = 0;
             while (b + 1 < a.n_beams && a.rb_first[b + 1] <= rb) ++b;
             const int e = (rb - a.rb_first[b]) * kRB + t;
-            const bool valid = nch > 0 && e < a.n_items[b];
-            uint32_t r[kN];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-            if (nch > 0) {
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                      "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                      "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                      "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                    : "r"(taddr));
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                    : "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]),
-                      "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]),
-                      "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]),
-                      "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]),
-                      "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
-                    : "r"(taddr + 32));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            } else {
-#pragma unroll
-                for (int q = 0; q < kN; ++q) r[q] = 0u;
-            }
-            if (valid) {
-                float* out;
+            // every listed row is written (zeros for a row-block without
+            // chunks), so the per-beam partial rows never hold stale values
+            float* out = nullptr;
+            if (e < a.n_items[b]) {
                 if (a.direct) {
                     const int v = a.items[a.base[b] + e];
                     out = a.Y + (size_t)v * a.k;
                 } else {
                     out = a.P + (size_t)(a.base[b] + e) * a.k;
                 }
-                if (a.vec4) {
-#pragma unroll
-                    for (int q = 0; q < kN; q += 4)
-                        if (q < a.k)
-                            *reinterpret_cast<float4*>(out + q) =
-                                make_float4(__uint_as_float(r[q]), __uint_as_float(r[q + 1]),
-                                            __uint_as_float(r[q + 2]), __uint_as_float(r[q + 3]));
+            }
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + ab * kN;
+#pragma unroll 1
+            for (int h = 0; h < kN; h += 32) {
+                uint32_t r[32];
+                if (nch > 0) {
+                    tmem_ld32(taddr + h, r);
                 } else {
 #pragma unroll
-                    for (int q = 0; q < kN; ++q)
-                        if (q < a.k) out[q] = __uint_as_float(r[q]);
+                    for (int q = 0; q < 32; ++q) r[q] = 0u;
                 }
+                if (h + 32 == kN) {
+                    // the accumulator is free once the last columns are in registers
+                    asm volatile("tcgen05.fence::before_thread_sync;");
+                    __syncwarp();
+                    if (lane == 0)
+                        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[ab]))
+                                     : "memory");
+                }
+                if (out) store_cols(out, h, a.k, a.vec4 != 0, r);
             }
         }
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-        if (s_abort) break;
     }
+    asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kN));
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kN));
 }
 
 // Y[v][q] = sum over beams of the partial rows, in beam order, with
@@ -436,6 +490,43 @@ __global__ void __launch_bounds__(256) k_inverse(const int32_t* __restrict__ ite
         const int v = items[base[b] + e];
         if (v >= 0) inv[(size_t)b * V + v] = (int32_t)(base[b] + e);
     }
+}
+
+// Grid and dynamic shared memory of k_spmm.  Each CTA holds 2 x 64 columns of
+// tensor memory, so at most 4 CTAs may be resident on an SM (512 columns): the
+// shared-memory request is raised, if needed, so that a fifth cannot fit (an
+// allocation beyond the SM's columns would wait for a resident CTA to finish).
+cudaError_t spmm_launch_shape(int device, size_t smem, int n_rb, int* grid, size_t* smem_req)
+{
+    int smem_sm = 0, sms = 0, reserved = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, device);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa{};
+    e = cudaFuncGetAttributes(&fa, k_spmm);
+    if (e != cudaSuccess) return e;
+    const size_t static_smem = fa.sharedSizeBytes;
+    size_t req = smem;
+    const size_t min_per_cta = (size_t)smem_sm / 5 + 1;   // five CTAs must not fit
+    if (req + static_smem + (size_t)reserved < min_per_cta) req = min_per_cta - static_smem - (size_t)reserved;
+    e = cudaFuncSetAttribute(k_spmm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)req);
+    if (e != cudaSuccess) return e;
+    // resident CTAs per SM from the shared-memory and register budgets
+    int regs_sm = 0;
+    e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, device);
+    if (e != cudaSuccess) return e;
+    const int by_smem = smem_sm / (int)(req + static_smem + (size_t)reserved);
+    const int regs_cta = ((fa.numRegs + 7) / 8 * 8) * kSpmmThreads;
+    const int by_regs = regs_cta > 0 ? regs_sm / regs_cta : 4;
+    int per_sm = by_smem < by_regs ? by_smem : by_regs;
+    per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
+    int g = sms * per_sm;
+    *grid = g > n_rb ? n_rb : g;
+    *smem_req = req;
+    return cudaSuccess;
 }
 
 int gsize(int64_t n)
@@ -585,22 +676,13 @@ cudaError_t spmm_run(dc_plan* p, const float* F, int k, float* Y)
     float* out0 = direct ? Y : p->d_sp_p;
     a.vec4 = (k % 4 == 0 && (reinterpret_cast<uintptr_t>(out0) & 15) == 0) ? 1 : 0;
     a.err = p->d_err;
-    const size_t smem = (size_t)kStages * (kTileA + kTileB) + 1024 + 8192;
-    e = cudaFuncSetAttribute(k_spmm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = (size_t)kStages * (kTileA + kTileB) + 1024;
+    int grid = 0;
+    size_t smem_req = 0;
+    e = spmm_launch_shape(p->device, smem, p->sp_n_rb, &grid, &smem_req);
     if (e != cudaSuccess) return e;
-    // CTAs per SM from the shared-memory budget (each holds kStages tiles in
-    // flight and 64 TMEM columns; at most 4 per SM keeps TMEM at 256 of 512 columns)
-    int smem_sm = 0, sms = 0;
-    e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, p->device);
-    if (e != cudaSuccess) return e;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
-    if (e != cudaSuccess) return e;
-    int per_sm = smem_sm / (int)(smem + 2048);
-    per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
-    int grid = sms * per_sm;
-    if (grid > p->sp_n_rb) grid = p->sp_n_rb;
     if (grid > 0) {
-        k_spmm<<<grid, kSpmmThreads, smem, p->stream>>>(a);
+        k_spmm<<<grid, kSpmmThreads, smem_req, p->stream>>>(a);
         count_launches(1);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -713,20 +795,13 @@ cudaError_t spmm_run_static(dc_plan* p, const float* F, int k, float* Y)
     float* out0 = direct ? Y : sc.part;
     a.vec4 = (k % 4 == 0 && (reinterpret_cast<uintptr_t>(out0) & 15) == 0) ? 1 : 0;
     a.err = p->d_err;
-    const size_t smem = (size_t)kStages * (kTileA + kTileB) + 1024 + 8192;
-    e = cudaFuncSetAttribute(k_spmm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = (size_t)kStages * (kTileA + kTileB) + 1024;
+    int grid = 0;
+    size_t smem_req = 0;
+    e = spmm_launch_shape(p->device, smem, p->sp_n_rb, &grid, &smem_req);
     if (e != cudaSuccess) return e;
-    int smem_sm = 0, sms = 0;
-    e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, p->device);
-    if (e != cudaSuccess) return e;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
-    if (e != cudaSuccess) return e;
-    int per_sm = smem_sm / (int)(smem + 2048);
-    per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
-    int grid = sms * per_sm;
-    if (grid > p->sp_n_rb) grid = p->sp_n_rb;
     if (grid > 0) {
-        k_spmm<<<grid, kSpmmThreads, smem, p->stream>>>(a);
+        k_spmm<<<grid, kSpmmThreads, smem_req, p->stream>>>(a);
         count_launches(1);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
