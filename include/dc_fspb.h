@@ -249,9 +249,11 @@ dc_status dc_fspb_spmm(dc_plan* plan, const float* F, int32_t k, float* Y, uint3
  * device.  Same arithmetic and result as dc_fspb_spmm.
  *   F [B][k] float32, Y [V][k] float32: device memory, caller-owned; the call
  *   is asynchronous on the plan's stream.
- * Limits: B <= DC_SPMM_STATIC_MAX_BEAMLETS and, for plans of more than one
- * beam, (entries of all beam voxel lists) x k <= DC_SPMM_STATIC_MAX_PARTIALS;
- * larger problems are rejected with DC_EINVAL (use dc_fspb_spmm).
+ * Limits: the beamlets, counted per beam in whole 4 x 4 patches of its M x N
+ * beamlet grid (4 ceil(M/4) x 4 ceil(N/4)), <= DC_SPMM_STATIC_MAX_BEAMLETS
+ * and, for plans of more than one beam, (entries of all beam voxel lists) x k
+ * <= DC_SPMM_STATIC_MAX_PARTIALS; larger problems are rejected with DC_EINVAL
+ * (use dc_fspb_spmm).
  * Set-up: the first call on a device looks up the arrays' device addresses
  * (cudaGetSymbolAddress with that device current); make that first call
  * before any stream capture.

@@ -740,9 +740,9 @@ dc_status dc_fspb_spmm_noalloc(dc_plan* plan, const float* F, int32_t k, float* 
     if (!plan || !F || !Y) return invalid("dc_fspb_spmm_noalloc: NULL argument");
     if (k < 1 || k > 64) return invalid("dc_fspb_spmm_noalloc: k must be in [1, 64]");
     if (!plan->sp_ready) return invalid("dc_fspb_spmm_noalloc: call dc_fspb_spmm_prepare first");
-    if (plan->B > DC_SPMM_STATIC_MAX_BEAMLETS)
-        return invalid("dc_fspb_spmm_noalloc: " + std::to_string(plan->B) +
-                       " beamlets exceed the static scratch limit of " +
+    if (plan->sp_cols > DC_SPMM_STATIC_MAX_BEAMLETS)
+        return invalid("dc_fspb_spmm_noalloc: " + std::to_string(plan->sp_cols) +
+                       " beamlets (in whole 4 x 4 patches per beam) exceed the static scratch limit of " +
                        std::to_string(DC_SPMM_STATIC_MAX_BEAMLETS) + "; use dc_fspb_spmm");
     if (plan->n_beams > 1 && plan->sp_items_total * (int64_t)k > (int64_t)DC_SPMM_STATIC_MAX_PARTIALS)
         return invalid("dc_fspb_spmm_noalloc: " + std::to_string(plan->sp_items_total) + " beam-list entries x k = " +

@@ -177,12 +177,15 @@ struct dc_plan {
     int sp_n_rb = 0;
     int64_t sp_chunks = 0, sp_items_total = 0;
     int32_t* d_sp_rbfirst = nullptr;
-    int32_t* d_sp_first = nullptr;
+    int4* d_sp_first = nullptr;      // per beam (first beamlet, M, N, first tile column), [n_beams + 1]
+    int sp_cols = 0;                 // tile columns of all beams (4 x 4 beamlet patches)
     int32_t* d_sp_nchunk = nullptr;
     int64_t* d_sp_off = nullptr;
     int32_t* d_sp_kb = nullptr;
     void* d_sp_tiles = nullptr;
     int32_t* d_sp_inv = nullptr;
+    int32_t* d_sp_zero = nullptr;    // one-beam plans: voxels in no list (their output rows are zero)
+    int64_t sp_n_zero = 0;
     void* d_sp_fp = nullptr;
     size_t sp_fp_cap = 0;
     float* d_sp_p = nullptr;
@@ -190,14 +193,18 @@ struct dc_plan {
     int32_t* d_err = nullptr;        // device status word of bounded waits
     void spmm_free()
     {
-        void* bufs[] = {d_sp_rbfirst, d_sp_first, d_sp_nchunk, d_sp_off, d_sp_kb, d_sp_tiles, d_sp_inv};
+        void* bufs[] = {d_sp_rbfirst, d_sp_first, d_sp_nchunk, d_sp_off, d_sp_kb, d_sp_tiles, d_sp_inv, d_sp_zero};
         for (void* b : bufs)
             if (b) cudaFree(b);
-        d_sp_rbfirst = d_sp_first = d_sp_nchunk = nullptr;
+        d_sp_rbfirst = d_sp_nchunk = nullptr;
+        d_sp_first = nullptr;
+        sp_cols = 0;
         d_sp_off = nullptr;
         d_sp_kb = nullptr;
         d_sp_tiles = nullptr;
         d_sp_inv = nullptr;
+        d_sp_zero = nullptr;
+        sp_n_zero = 0;
         sp_ready = false;
         sp_n_rb = 0;
         sp_chunks = 0;

@@ -143,7 +143,7 @@ struct TileArgs {
     const int64_t* base;         // start of each beam's list
     const int32_t* n_items;
     const int32_t* rb_first;     // [n_beams + 1] first row-block of each beam (host-computed)
-    const int32_t* first;        // [n_beams + 1] first beamlet of each beam
+    const int4* beam;            // [n_beams + 1] (first beamlet, M, N, first tile column) of each beam
     int n_beams;
     int32_t* nchunk;             // count pass output [n_rb]
     const int64_t* chunk_off;    // fill pass: first chunk of each row-block
@@ -151,7 +151,20 @@ struct TileArgs {
     uint16_t* tiles;             // fill pass: [chunks][128 * 16]
 };
 
-constexpr int kMaxKB = 4096;   // k-blocks of one beam (32768 beamlets)
+constexpr int kMaxKB = 4096;   // k-blocks of one beam (32768 tile columns)
+
+// Tile column order: each beam's beamlets in 4 x 4 patches of its M x N
+// beamlet grid (patches row by row, then the patch's rows, then its columns);
+// patch cells past the grid's edge are padding columns.  The beamlets of one
+// voxel form a disc in the grid (the ROI), which these patches cover with
+// fewer 16-column chunks than the grid's rows do.  The CSR matrix and the
+// fluence vectors keep the beamlet order of the ABI; only the tiles and the
+// packed fluences use this one.
+__host__ __device__ __forceinline__ int patch_col(int n, int m, int M)
+{
+    return ((n >> 2) * ((M + 3) >> 2) + (m >> 2)) * 16 + ((n & 3) << 2) + (m & 3);
+}
+__host__ __device__ __forceinline__ int patch_cols(int M, int N) { return ((M + 3) >> 2) * ((N + 3) >> 2) * 16; }
 
 template <bool FILL>
 __global__ void __launch_bounds__(kRB) k_tiles(const TileArgs a)
@@ -165,8 +178,14 @@ __global__ void __launch_bounds__(kRB) k_tiles(const TileArgs a)
     const int j = rb - a.rb_first[b];
     const int nit = a.n_items[b];
     const int t = threadIdx.x;
-    const int c0 = a.first[b], c1 = a.first[b + 1];
-    const int kb0 = c0 / 8, nkb = (c1 + 7) / 8 - kb0;
+    const int4 bm = a.beam[b];
+    const int c0 = bm.x, c1 = bm.x + bm.y * bm.z, M = bm.y;
+    const int kb0 = bm.w / 8, nkb = (a.beam[b + 1].w - bm.w) / 8;
+    // tile column of beamlet c of this beam
+    auto col_of = [&](int c) {
+        const int l = c - c0, n = l / M;
+        return bm.w + patch_col(n, l - n * M, M);
+    };
     for (int q = t; q < kMaxKB / 32; q += blockDim.x) mark[q] = 0;
     __syncthreads();
     const int e = j * kRB + t;
@@ -178,7 +197,7 @@ __global__ void __launch_bounds__(kRB) k_tiles(const TileArgs a)
         for (int64_t q = r0; q < r1; ++q) {
             const int c = a.cols[q];
             if (c >= c0 && c < c1) {
-                const int kb = c / 8 - kb0;
+                const int kb = col_of(c) / 8 - kb0;
                 atomicOr(&mark[kb >> 5], 1u << (kb & 31));
             }
         }
@@ -216,8 +235,9 @@ __global__ void __launch_bounds__(kRB) k_tiles(const TileArgs a)
         for (int64_t q = r0; q < r1; ++q) {
             const int c = a.cols[q];
             if (c < c0 || c >= c1) continue;
-            const int ch = chunk_of[c / 8 - kb0];
-            const int k = c - 8 * a.chunk_kb[a.chunk_off[rb] + ch];   // column within the chunk, 0..15
+            const int pc = col_of(c);
+            const int ch = chunk_of[pc / 8 - kb0];
+            const int k = pc - 8 * a.chunk_kb[a.chunk_off[rb] + ch];   // column within the chunk, 0..15
             // element (m = t, k) of the K-major core-matrix layout
             const int off = ((t >> 3) * 2 + (k >> 3)) * 64 + (t & 7) * 8 + (k & 7);
             tiles[(size_t)ch * (kRB * kKC) + off] = a.vals[q];
@@ -226,10 +246,12 @@ __global__ void __launch_bounds__(kRB) k_tiles(const TileArgs a)
 }
 
 // ---------------------------------------------------------------------------
-// F [B][k] (FP32, row-major) -> BF16 K-major core tiles: element (beamlet c,
-// fluence n) at ((c / 8) * 8 + n / 8) * 64 + (n % 8) * 8 + c % 8; fluence
-// columns n >= k and beamlets c >= B are zero.
-__global__ void __launch_bounds__(256) k_pack_fluence(const float* __restrict__ F, int B, int k, int nkb,
+// F [B][k] (FP32, row-major) -> BF16 K-major core tiles in tile column order:
+// element (tile column p, fluence n) at ((p / 8) * 8 + n / 8) * 64 + (n % 8) * 8
+// + p % 8; fluence columns n >= k, padding columns and columns past the last
+// beam are zero.
+__global__ void __launch_bounds__(256) k_pack_fluence(const float* __restrict__ F, int k, int nkb,
+                                                      const int4* __restrict__ beam, int n_beams,
                                                       __nv_bfloat16* __restrict__ Fp)
 {
     const int64_t n_el = (int64_t)nkb * 8 * kN;
@@ -237,8 +259,16 @@ __global__ void __launch_bounds__(256) k_pack_fluence(const float* __restrict__ 
         const int kb = (int)(e / (8 * kN));
         const int r = (int)(e % (8 * kN));
         const int nb = r / 64, n_in = (r % 64) / 8, c_in = r % 8;
-        const int c = kb * 8 + c_in, n = nb * 8 + n_in;
-        const float x = (c < B && n < k) ? __ldg(F + (size_t)c * k + n) : 0.f;
+        const int pc = kb * 8 + c_in, n = nb * 8 + n_in;
+        float x = 0.f;
+        if (n < k && pc < __ldg(&beam[n_beams].w)) {
+            int b = 0;
+            while (b + 1 < n_beams && __ldg(&beam[b + 1].w) <= pc) ++b;
+            const int4 bm = beam[b];
+            const int l = pc - bm.w, patch = l >> 4, q = l & 15, MB = (bm.y + 3) >> 2;
+            const int row = (patch / MB) * 4 + (q >> 2), col = (patch % MB) * 4 + (q & 3);
+            if (row < bm.z && col < bm.y) x = __ldg(F + (size_t)(bm.x + row * bm.y + col) * k + n);
+        }
         Fp[e] = __float2bfloat16_rn(x);
     }
 }
@@ -529,6 +559,22 @@ cudaError_t spmm_launch_shape(int device, size_t smem, int n_rb, int* grid, size
     return cudaSuccess;
 }
 
+// zero[] = the voxels that no beam list holds (inv[v] < 0), in any order.
+__global__ void __launch_bounds__(256) k_unlisted(const int32_t* __restrict__ inv, int64_t V,
+                                                  int32_t* __restrict__ zero, unsigned long long* __restrict__ n)
+{
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x)
+        if (inv[v] < 0) zero[atomicAdd(n, 1ull)] = (int32_t)v;
+}
+
+// Y[v][0..k) = 0 for the voxels v of zero[] (in no beam list: k_spmm does not write their rows).
+__global__ void __launch_bounds__(256) k_zero_rows(const int32_t* __restrict__ zero, int64_t n, int k,
+                                                   float* __restrict__ Y)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * k; e += (int64_t)gridDim.x * blockDim.x)
+        Y[(size_t)zero[e / k] * k + e % k] = 0.f;
+}
+
 int gsize(int64_t n)
 {
     int64_t g = (n + 255) / 256;
@@ -546,29 +592,32 @@ dc_status spmm_prepare(dc_plan* p, const int64_t* rowptr, const int32_t* cols, c
     std::vector<int32_t> n_items(nb);
     DC_CUDA(cudaMemcpyAsync(n_items.data(), p->d_nitems, nb * sizeof(int32_t), cudaMemcpyDeviceToHost, p->stream));
     DC_CUDA(cudaStreamSynchronize(p->stream));
-    std::vector<int32_t> rb_first(nb + 1), first(nb + 1);
-    int n_rb = 0;
+    std::vector<int32_t> rb_first(nb + 1);
+    std::vector<int4> beam(nb + 1);
+    int n_rb = 0, cols_total = 0;
     for (int b = 0; b < nb; ++b) {
         rb_first[b] = n_rb;
         n_rb += (n_items[b] + kRB - 1) / kRB;
-        first[b] = p->first[b];
-    }
-    rb_first[nb] = n_rb;
-    first[nb] = p->B;
-    for (int b = 0; b < nb; ++b)
-        if ((first[b + 1] + 7) / 8 - first[b] / 8 > kMaxKB) {
-            set_error("spmm: a beam has more than 32768 beamlets");
+        const int M = p->M[b], N = p->N[b];
+        if (patch_cols(M, N) / 8 > kMaxKB) {
+            set_error("spmm: a beam has more than 32768 beamlets (4 x 4 patches included)");
             return DC_EUNSUPPORTED;
         }
+        beam[b] = make_int4(p->first[b], M, N, cols_total);
+        cols_total += patch_cols(M, N);
+    }
+    rb_first[nb] = n_rb;
+    beam[nb] = make_int4(p->B, 0, 0, cols_total);
     p->spmm_free();
     p->sp_n_rb = n_rb;
     DC_CUDA(cudaMalloc(&p->d_sp_rbfirst, (nb + 1) * sizeof(int32_t)));
-    DC_CUDA(cudaMalloc(&p->d_sp_first, (nb + 1) * sizeof(int32_t)));
+    DC_CUDA(cudaMalloc(&p->d_sp_first, (nb + 1) * sizeof(int4)));
+    p->sp_cols = cols_total;
     DC_CUDA(cudaMalloc(&p->d_sp_nchunk, (size_t)(n_rb + 1) * sizeof(int32_t)));
     DC_CUDA(cudaMalloc(&p->d_sp_off, (size_t)(n_rb + 1) * sizeof(int64_t)));
     DC_CUDA(cudaMemcpyAsync(p->d_sp_rbfirst, rb_first.data(), (nb + 1) * sizeof(int32_t), cudaMemcpyHostToDevice,
                             p->stream));
-    DC_CUDA(cudaMemcpyAsync(p->d_sp_first, first.data(), (nb + 1) * sizeof(int32_t), cudaMemcpyHostToDevice,
+    DC_CUDA(cudaMemcpyAsync(p->d_sp_first, beam.data(), (nb + 1) * sizeof(int4), cudaMemcpyHostToDevice,
                             p->stream));
     TileArgs ta{};
     ta.rowptr = rowptr;
@@ -578,7 +627,7 @@ dc_status spmm_prepare(dc_plan* p, const int64_t* rowptr, const int32_t* cols, c
     ta.base = p->d_base;
     ta.n_items = p->d_nitems;
     ta.rb_first = p->d_sp_rbfirst;
-    ta.first = p->d_sp_first;
+    ta.beam = p->d_sp_first;
     ta.n_beams = nb;
     ta.nchunk = p->d_sp_nchunk;
     if (n_rb > 0) {
@@ -606,7 +655,9 @@ dc_status spmm_prepare(dc_plan* p, const int64_t* rowptr, const int32_t* cols, c
         count_launches(1);
         DC_CUDA(cudaGetLastError());
     }
-    if (nb > 1) {
+    {
+        // inverse of the beam lists (the reduction of several beams' partial
+        // rows reads it; one-beam plans keep only the voxels in no list)
         DC_CUDA(cudaMalloc(&p->d_sp_inv, (size_t)nb * p->V * sizeof(int32_t)));
         DC_CUDA(cudaMemsetAsync(p->d_sp_inv, 0xff, (size_t)nb * p->V * sizeof(int32_t), p->stream));
         int maxn = 0;
@@ -618,6 +669,20 @@ dc_status spmm_prepare(dc_plan* p, const int64_t* rowptr, const int32_t* cols, c
         int64_t items_total = 0;
         for (int b = 0; b < nb; ++b) items_total += ((int64_t)n_items[b] + 31) / 32 * 32;
         p->sp_items_total = items_total;
+        if (nb == 1) {
+            DC_CUDA(cudaMalloc(&p->d_sp_zero, (size_t)p->V * sizeof(int32_t) + sizeof(unsigned long long)));
+            unsigned long long* cnt = reinterpret_cast<unsigned long long*>(p->d_sp_zero + p->V);
+            DC_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), p->stream));
+            k_unlisted<<<gsize(p->V), 256, 0, p->stream>>>(p->d_sp_inv, p->V, p->d_sp_zero, cnt);
+            count_launches(1);
+            DC_CUDA(cudaGetLastError());
+            unsigned long long h = 0;
+            DC_CUDA(cudaMemcpyAsync(&h, cnt, sizeof(h), cudaMemcpyDeviceToHost, p->stream));
+            DC_CUDA(cudaStreamSynchronize(p->stream));
+            p->sp_n_zero = (int64_t)h;
+            cudaFree(p->d_sp_inv);
+            p->d_sp_inv = nullptr;
+        }
     }
     if (!p->d_err) DC_CUDA(cudaMalloc(&p->d_err, sizeof(int32_t)));
     DC_CUDA(cudaStreamSynchronize(p->stream));
@@ -627,7 +692,7 @@ dc_status spmm_prepare(dc_plan* p, const int64_t* rowptr, const int32_t* cols, c
 
 cudaError_t spmm_run(dc_plan* p, const float* F, int k, float* Y)
 {
-    const int nkb = (p->B + 7) / 8 + 2;
+    const int nkb = (p->sp_cols + 7) / 8 + 2;
     cudaError_t e = cudaSuccess;
     if (p->sp_fp_cap < (size_t)nkb * 8 * kN) {
         if (p->d_sp_fp) cudaFree(p->d_sp_fp);
@@ -649,12 +714,12 @@ cudaError_t spmm_run(dc_plan* p, const float* F, int k, float* Y)
             p->sp_p_cap = need;
         }
     }
-    k_pack_fluence<<<gsize((int64_t)nkb * 8 * kN), 256, 0, p->stream>>>(F, p->B, k, nkb,
-                                                                       reinterpret_cast<__nv_bfloat16*>(p->d_sp_fp));
+    k_pack_fluence<<<gsize((int64_t)nkb * 8 * kN), 256, 0, p->stream>>>(
+        F, k, nkb, p->d_sp_first, p->n_beams, reinterpret_cast<__nv_bfloat16*>(p->d_sp_fp));
     count_launches(1);
-    if (direct) {
-        e = cudaMemsetAsync(Y, 0, (size_t)p->V * k * sizeof(float), p->stream);
-        if (e != cudaSuccess) return e;
+    if (direct && p->sp_n_zero > 0) {
+        k_zero_rows<<<gsize(p->sp_n_zero * k), 256, 0, p->stream>>>(p->d_sp_zero, p->sp_n_zero, k, Y);
+        count_launches(1);
     }
     e = cudaMemsetAsync(p->d_err, 0, sizeof(int32_t), p->stream);
     if (e != cudaSuccess) return e;
@@ -760,20 +825,21 @@ cudaError_t static_scratch(int device, StaticScratch* out)
 
 cudaError_t spmm_run_static(dc_plan* p, const float* F, int k, float* Y)
 {
-    const int nkb = (p->B + 7) / 8 + 2;
+    const int nkb = (p->sp_cols + 7) / 8 + 2;
     const bool direct = p->n_beams == 1;
     if (nkb > kStaticNkb) return cudaErrorInvalidValue;
     if (!direct && (size_t)p->sp_items_total * k > (size_t)DC_SPMM_STATIC_MAX_PARTIALS) return cudaErrorInvalidValue;
     StaticScratch sc;
     cudaError_t e = static_scratch(p->device, &sc);
     if (e != cudaSuccess) return e;
-    k_pack_fluence<<<gsize((int64_t)nkb * 8 * kN), 256, 0, p->stream>>>(F, p->B, k, nkb, sc.fp);
+    k_pack_fluence<<<gsize((int64_t)nkb * 8 * kN), 256, 0, p->stream>>>(F, k, nkb, p->d_sp_first, p->n_beams,
+                                                                       sc.fp);
     count_launches(1);
     // the output rows of voxels outside every beam list are never written by
     // k_spmm, and the bounded-wait status word is read after the call
-    if (direct) {
-        e = cudaMemsetAsync(Y, 0, (size_t)p->V * k * sizeof(float), p->stream);
-        if (e != cudaSuccess) return e;
+    if (direct && p->sp_n_zero > 0) {
+        k_zero_rows<<<gsize(p->sp_n_zero * k), 256, 0, p->stream>>>(p->d_sp_zero, p->sp_n_zero, k, Y);
+        count_launches(1);
     }
     e = cudaMemsetAsync(p->d_err, 0, sizeof(int32_t), p->stream);
     if (e != cudaSuccess) return e;
