@@ -88,6 +88,7 @@ struct BeamletArgs {
     BeamDev* out_beams;
     BeamletDev* out_bl;
     float* out_theta;
+    double* ray;             // [B][8] FP64 axis source and direction (k_beamlets -> k_trace)
     float4* tab;
     int first[kMaxBeams + 1];
     int M[kMaxBeams];
@@ -157,6 +158,40 @@ __device__ bool walk_init(const BeamletArgs& A, const double* s, const double* n
     w.acur = amin;
     w.amax = amax;
     return true;
+}
+
+// The walk state at a_start on the ray s + a n, to run up to a_end (both
+// inside [amin, amax] of walk_init): the voxel holding the ray just past
+// a_start and the next plane crossing along each axis.
+__device__ void walk_from(const BeamletArgs& A, const double* s, const double* n, double a_start, double a_end,
+                          Walk& w)
+{
+    const int dims[3] = {A.nx, A.ny, A.nz};
+    const double del[3] = {A.dx, A.dy, A.dz};
+    const double org[3] = {A.ox, A.oy, A.oz};
+    for (int a = 0; a < 3; ++a) {
+        const double p0 = org[a] - 0.5 * del[a];
+        const double f = (s[a] + a_start * n[a] - p0) / del[a];
+        int id = (int)floor(f);
+        if (n[a] < 0 && f == floor(f)) id -= 1;
+        id = min(max(id, 0), dims[a] - 1);
+        w.idx[a] = id;
+        if (fabs(n[a]) < 1e-15) {
+            w.step[a] = 0;
+            w.anext[a] = 1e300;
+            w.adelta[a] = 1e300;
+        } else if (n[a] > 0) {
+            w.step[a] = 1;
+            w.anext[a] = (p0 + (id + 1) * del[a] - s[a]) / n[a];
+            w.adelta[a] = del[a] / n[a];
+        } else {
+            w.step[a] = -1;
+            w.anext[a] = (p0 + id * del[a] - s[a]) / n[a];
+            w.adelta[a] = -del[a] / n[a];
+        }
+    }
+    w.acur = a_start;
+    w.amax = a_end;
 }
 
 template <typename F>
@@ -299,9 +334,8 @@ __global__ void __launch_bounds__(256) k_arows(const float* __restrict__ A, int 
     }
 }
 
-// One thread per beamlet, one warp per CTA: the walk is FP64-bound, so the
-// beamlets are spread over every SM.
-constexpr int kBeamletThreads = 32;
+// Steps 2-3: beam frame, beamlet axis and frame, theta; one thread per beamlet.
+constexpr int kBeamletThreads = 64;
 __global__ void __launch_bounds__(kBeamletThreads) k_beamlets(const BeamletArgs A)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -367,25 +401,213 @@ __global__ void __launch_bounds__(kBeamletThreads) k_beamlets(const BeamletArgs 
     int l = min((int)rl, A.a_nth - 2);
     float wl = rl - (float)l;
 
-    // steps 4-6: Siddon walk in FP64
-    Walk w;
-    int hit = 0, K = 0;
-    double L_in = 0, L_out = 0;
-    if (walk_init(A, src, nv, w)) {
-        float4* tb = A.tab + 2 * (size_t)i * A.Kmax;
-        if (w.amax - w.acur > 40.0)
-            trace_beamlet<double>(A, w, tb, L_in, L_out, K);
-        else
-            trace_beamlet<float>(A, w, tb, L_in, L_out, K);
-        hit = K > 0 ? 1 : 0;
+    // the axis in FP64 for the trace (k_trace), which also fills in L_in,
+    // L_out, K and hit
+    double* ray = A.ray + 8 * (size_t)i;
+    for (int q = 0; q < 3; ++q) {
+        ray[q] = src[q];
+        ray[4 + q] = nv[q];
     }
+    ray[3] = ray[7] = 0.0;
     BeamletDev r;
-    r.n_lin = make_float4((float)nv[0], (float)nv[1], (float)nv[2], (float)L_in);
+    r.n_lin = make_float4((float)nv[0], (float)nv[1], (float)nv[2], 0.f);
     r.exy_xy = make_float4((float)exx[0], (float)eyy[0], (float)exx[1], (float)eyy[1]);
-    r.exy_z = make_float4((float)exx[2], (float)eyy[2], hit ? (float)L_out : -1.0f, wl);
-    r.meta = make_int4(K, l, hit, b);
+    r.exy_z = make_float4((float)exx[2], (float)eyy[2], -1.0f, wl);
+    r.meta = make_int4(0, l, 0, b);
     A.out_bl[i] = r;
     A.out_theta[i] = (float)theta;
+}
+
+// ---------------------------------------------------------------------------
+// Steps 4-6 with one warp per beamlet.  The FP64 walk is latency-bound, so
+// the ray [amin, amax] inside the grid is cut into 32 pieces of equal length
+// and lane j walks piece j, keeping its segments (end parameter, density) in
+// shared memory.  Warp reductions give the body entry L_in (start of the first
+// segment denser than the surface threshold) and exit L_out (end of the last),
+// an exclusive warp scan of the pieces' integrals of rho, b_1(rho), b_2(rho)
+// from L_in gives each piece its starting values, and each lane then emits the
+// depth samples L_in + k d that fall in its piece, with the same per-segment
+// arithmetic as a single walk (only the order of the sums differs).  A ray
+// with more segments in a piece than the buffer holds is traced by one lane
+// with the single walk (trace_beamlet).
+constexpr int kTraceWarps = 4;
+constexpr int kSegCap = 24;     // segments per piece (rays of up to ~700 voxel crossings)
+
+template <typename Acc>
+__device__ __forceinline__ Acc warp_exclusive_sum(Acc x, int lane)
+{
+    Acc incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const Acc y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    return incl - x;
+}
+
+// Returns false if a piece overflowed its segment buffer (nothing written).
+template <typename Acc>
+__device__ bool trace_warp(const BeamletArgs& A, const double* s, const double* n, const Walk& w0, int lane,
+                           double* __restrict__ sa1, float* __restrict__ sr, float4* __restrict__ tab, double& L_in,
+                           double& L_out, int& K)
+{
+    const double amin = w0.acur, amax = w0.amax;
+    const double span = (amax - amin) / 32.0;
+    const double a_start = amin + lane * span;
+    const double a_end = lane == 31 ? amax : amin + (lane + 1) * span;
+    const float surf = A.rho_surf;
+
+    // 1. walk the piece
+    int ns = 0;
+    double first_a = 1e300, last_a = -1.0;
+    Walk w;
+    walk_from(A, s, n, a_start, a_end, w);
+    walk_run(A, w, [&](double a0, double a1, int64_t vox) {
+        const float r = __ldg(A.rho + vox);
+        if (ns < kSegCap) {
+            sa1[ns] = a1;
+            sr[ns] = r;
+        }
+        ++ns;
+        if (r > surf) {
+            first_a = fmin(first_a, a0);
+            last_a = a1;
+        }
+    });
+    if (__any_sync(0xffffffffu, ns > kSegCap)) return false;
+
+    // 2. body entry and exit of the whole ray
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        first_a = fmin(first_a, __shfl_xor_sync(0xffffffffu, first_a, o));
+        last_a = fmax(last_a, __shfl_xor_sync(0xffffffffu, last_a, o));
+    }
+    K = 0;
+    if (first_a >= 1e299) return true;   // the axis misses the body
+    L_in = first_a;
+    L_out = last_a;
+    const double d = A.d;
+    K = max(2, (int)ceil((L_out - L_in) / d) + 1);
+    K = min(K, A.Kmax);
+
+    // 3. this piece's integrals from L_in, and the piece's starting values
+    Acc pT = 0, p1 = 0, p2 = 0;
+    double a0 = a_start;
+    for (int q = 0; q < ns; ++q) {
+        const double a1 = sa1[q];
+        if (a1 > L_in) {
+            const float r = sr[q];
+            const Acc len = (Acc)(a1 - fmax(a0, L_in));
+            pT += (Acc)r * len;
+            p1 += (Acc)lut_dens(A, 4, r) * len;
+            p2 += (Acc)lut_dens(A, 5, r) * len;
+        }
+        a0 = a1;
+    }
+    Acc cT = warp_exclusive_sum(pT, lane), c1 = warp_exclusive_sum(p1, lane), c2 = warp_exclusive_sum(p2, lane);
+
+    // 4. the samples L_in + k d in [max(a_start, L_in), a_end) (the last piece
+    // also takes those past the end of the ray)
+    const double lo0 = fmax(a_start, L_in);
+    int k = max(0, (int)ceil((lo0 - L_in) / d));
+    while (k > 0 && L_in + (k - 1) * d >= lo0) --k;
+    while (L_in + k * d < lo0) ++k;
+    a0 = a_start;
+    for (int q = 0; q < ns && k < K; ++q) {
+        const double a1 = sa1[q];
+        if (a1 > L_in) {
+            const double lo = fmax(a0, L_in);
+            const float r = sr[q];
+            const Acc vr = (Acc)r, v1 = (Acc)lut_dens(A, 4, r), v2 = (Acc)lut_dens(A, 5, r);
+            while (k < K) {
+                const double sk = L_in + k * d;
+                if (sk > a1 || (lane < 31 && sk >= a_end)) break;
+                const Acc len = (Acc)(sk - lo);
+                tab[2 * k] = make_float4((float)(cT + vr * len), 0.f, (float)(c1 + v1 * len), 0.f);
+                tab[2 * k + 1] = make_float4((float)(c2 + v2 * len), 0.f, 0.f, 0.f);
+                ++k;
+            }
+            const Acc len = (Acc)(a1 - lo);
+            cT += vr * len;
+            c1 += v1 * len;
+            c2 += v2 * len;
+        }
+        a0 = a1;
+    }
+    if (lane == 31)
+        for (; k < K; ++k) {
+            tab[2 * k] = make_float4((float)cT, 0.f, (float)c1, 0.f);
+            tab[2 * k + 1] = make_float4((float)c2, 0.f, 0.f, 0.f);
+        }
+    __syncwarp();
+
+    // 5. slopes to the next sample (zero at K - 1): read, then write
+    for (int k0 = 0; k0 < K; k0 += 32) {
+        const int kk = k0 + lane;
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+        float nT = 0.f, n1 = 0.f, n2 = 0.f;
+        if (kk < K) {
+            a = tab[2 * kk];
+            b = tab[2 * kk + 1];
+            nT = a.x;
+            n1 = a.z;
+            n2 = b.x;
+            if (kk + 1 < K) {
+                const float4 an = tab[2 * kk + 2], bn = tab[2 * kk + 3];
+                nT = an.x;
+                n1 = an.z;
+                n2 = bn.x;
+            }
+        }
+        __syncwarp();
+        if (kk < K) {
+            tab[2 * kk] = make_float4(a.x, nT - a.x, a.z, n1 - a.z);
+            tab[2 * kk + 1] = make_float4(b.x, n2 - b.x, 0.f, 0.f);
+        }
+        __syncwarp();
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(32 * kTraceWarps) k_trace(const BeamletArgs A)
+{
+    __shared__ double s_a1[kTraceWarps][32][kSegCap];
+    __shared__ float s_r[kTraceWarps][32][kSegCap];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * kTraceWarps + warp;
+    if (i >= A.B) return;   // whole warps
+    const double* ray = A.ray + 8 * (size_t)i;
+    const double s[3] = {ray[0], ray[1], ray[2]}, n[3] = {ray[4], ray[5], ray[6]};
+    Walk w;
+    int K = 0;
+    double L_in = 0, L_out = 0;
+    if (walk_init(A, s, n, w)) {
+        float4* tb = A.tab + 2 * (size_t)i * A.Kmax;
+        const bool dbl = w.amax - w.acur > 40.0;
+        const bool ok = dbl ? trace_warp<double>(A, s, n, w, lane, s_a1[warp][lane], s_r[warp][lane], tb, L_in,
+                                                 L_out, K)
+                            : trace_warp<float>(A, s, n, w, lane, s_a1[warp][lane], s_r[warp][lane], tb, L_in,
+                                                L_out, K);
+        if (!ok && lane == 0) {
+            if (dbl)
+                trace_beamlet<double>(A, w, tb, L_in, L_out, K);
+            else
+                trace_beamlet<float>(A, w, tb, L_in, L_out, K);
+        }
+        if (!ok) {
+            K = __shfl_sync(0xffffffffu, K, 0);
+            L_in = __shfl_sync(0xffffffffu, L_in, 0);
+            L_out = __shfl_sync(0xffffffffu, L_out, 0);
+        }
+    }
+    if (lane == 0) {
+        BeamletDev& r = A.out_bl[i];
+        const int hit = K > 0 ? 1 : 0;
+        r.n_lin.w = (float)L_in;
+        r.exy_z.z = hit ? (float)L_out : -1.0f;
+        r.meta.x = K;
+        r.meta.z = hit;
+    }
 }
 
 int grid_for(int64_t n, int threads)
@@ -471,13 +693,15 @@ cudaError_t launch_beamlets(const dc_plan* p)
     A.out_bl = p->d_bl;
     A.out_theta = p->d_theta;
     A.tab = p->d_tab;
+    A.ray = p->d_ray;
     for (int b = 0; b < p->n_beams; ++b) {
         A.first[b] = p->first[b];
         A.M[b] = p->M[b];
     }
     A.first[p->n_beams] = p->B;
     k_beamlets<<<(p->B + kBeamletThreads - 1) / kBeamletThreads, kBeamletThreads, 0, p->stream>>>(A);
-    count_launches(1);
+    k_trace<<<(p->B + kTraceWarps - 1) / kTraceWarps, 32 * kTraceWarps, 0, p->stream>>>(A);
+    count_launches(2);
     k_arows<<<grid_for((int64_t)p->B * p->coeffs.a_nt, 256), 256, 0, p->stream>>>(
         p->d_A, p->coeffs.a_nt, p->d_bl, p->B, p->d_arow);
     count_launches(1);
