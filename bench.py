@@ -42,6 +42,31 @@ ALG_MUFU_PER_PAIR = 9      # 8 exponentials (four p() of eq. 4) + 1 reciprocal (
 FP32_LANES_PER_SM = 128
 MUFU_LANES_PER_SM = 16
 L2_FLUSH_BYTES = 256 << 20
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the dose kernel on the thorax9 plan, from an ncu capture of the kernel built
+# from the sources with these SHA-256 digests (profiles/k_pairs_dose_thorax9.md);
+# reported only while the sources are unchanged.
+DOSE_TRAFFIC_BYTES = 110298368 + 21456640
+DOSE_TRAFFIC_SOURCES = {
+    "paper_1103_1164_gb300/csrc/k_dose.cu": "5a1c060da362e95195becba5159b99ba5bbc0c65eb8bcacad07961f5903bc2e6",
+    "paper_1103_1164_gb300/csrc/dc_internal.cuh": "285ff9782a2e610a848767b7764bf6014d0010df71d493bafc964423f199c67d",
+}
+
+
+def dose_traffic(scale):
+    """The captured per-launch DRAM traffic, or None if the kernel's sources
+    changed since the capture or the workload is not the captured one."""
+    import hashlib
+    if scale != 1.0:
+        return None
+    for rel, digest in DOSE_TRAFFIC_SOURCES.items():
+        try:
+            with open(os.path.join(ROOT, rel), "rb") as f:
+                if hashlib.sha256(f.read()).hexdigest() != digest:
+                    return None
+        except OSError:
+            return None
+    return DOSE_TRAFFIC_BYTES
 
 
 def parse():
@@ -351,10 +376,13 @@ def run_ours(args, world, rank, local, pg):
     achieved = pairs / t_dose
     roofline = {"kernel": "k_dose<dose,1> (eqs. 1-4)", "bound": "alu",
                 "achieved": achieved / 1e9, "peak": peak_pairs / 1e9, "unit": "Gpair/s",
-                "frac": achieved / peak_pairs, "traffic": None,
+                "frac": achieved / peak_pairs, "traffic": dose_traffic(args.scale),
+                "traffic_unit": "bytes per launch (ncu dram read + write)",
                 "peak_basis": f"{props.multi_processor_count} SMs x {sm_max:.0f} MHz x "
                               f"min(128/{ALG_FP32_PER_PAIR} FP32, 16/{ALG_MUFU_PER_PAIR} MUFU) per pair",
-                "dose_kernel_ms": t_dose * 1e3}
+                "dose_kernel_ms": t_dose * 1e3,
+                "timing": "CUDA events around dc_fspb_dose on the plan's stream: the pair kernel plus "
+                          "the per-beam sum and two small memsets (the pair kernel alone is ~2 % shorter)"}
     fill_ms = float(stage[:, 3].mean())
     bytes_matrix = pairs * 8 + (V + 1) * 8
     matrix = {"fill_ms": fill_ms, "fill_GBps": bytes_matrix / (fill_ms * 1e-3) / 1e9,
