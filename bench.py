@@ -196,7 +196,9 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def dist_setup(args):
+def dist_setup(args, backend=None):
+    """One process per GPU (torchrun): ranks from the environment; NCCL for
+    our arm on GPUs, gloo for the CPU reference arm (and CPU tests)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -204,34 +206,47 @@ def dist_setup(args):
     if world > 1:
         import torch.distributed as dist
         import torch
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+        if backend is None:
+            backend = "nccl" if (args.impl == "ours" and torch.cuda.is_available()) else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
         pg = dist
     return world, rank, local, pg
 
 
+def _on_gpu(pg):
+    return pg.get_backend() == "nccl"
+
+
 def barrier(pg, torch):
     if pg is not None:
-        if torch.cuda.is_available():
+        if _on_gpu(pg):
             pg.barrier(device_ids=[torch.cuda.current_device()])
         else:
             pg.barrier()
 
 
-def max_over_ranks(pg, torch, x):
-    if pg is None:
-        return x
-    t = torch.tensor([float(x)], device="cuda")
-    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+def _all_reduce(pg, torch, x, op):
+    t = torch.tensor([float(x)], dtype=torch.float64, device="cuda" if _on_gpu(pg) else "cpu")
+    pg.all_reduce(t, op=op)
     return float(t.item())
+
+
+def max_over_ranks(pg, torch, x):
+    return x if pg is None else _all_reduce(pg, torch, x, pg.ReduceOp.MAX)
 
 
 def sum_over_ranks(pg, torch, x):
-    if pg is None:
-        return x
-    t = torch.tensor([float(x)], device="cuda")
-    pg.all_reduce(t, op=pg.ReduceOp.SUM)
-    return float(t.item())
+    return x if pg is None else _all_reduce(pg, torch, x, pg.ReduceOp.SUM)
+
+
+def aggregate_throughput(pg, torch, evals_rank, t_rank_ms):
+    """Weak scaling over independent plans: every rank's evaluations over the
+    slowest rank's time.  Returns (evaluations/s of the whole job, that time in ms)."""
+    t_ms = max_over_ranks(pg, torch, t_rank_ms)
+    total = sum_over_ranks(pg, torch, evals_rank)
+    return total / (t_ms * 1e-3), t_ms
 
 
 # ---------------------------------------------------------------------------
@@ -362,10 +377,8 @@ def run_ours(args, world, rank, local, pg):
     launches = dc.dc_fspb_launch_count() - launches0
     stage = np.array([[evs[k][j].elapsed_time(evs[k][j + 1]) for j in range(4)] for k in range(args.steps)])
     step_ms = stage.sum(1)
-    t_total_ms = max_over_ranks(pg, torch, float(step_ms.sum()))
     evals_step = 2 * pairs
-    total_evals = sum_over_ranks(pg, torch, evals_step * args.steps)
-    value = total_evals / (t_total_ms * 1e-3)
+    value, t_total_ms = aggregate_throughput(pg, torch, evals_step * args.steps, float(step_ms.sum()))
     ms_per_step = t_total_ms / args.steps
 
     # roofline of the dominant kernel: the direct dose kernel (ALU bound)
