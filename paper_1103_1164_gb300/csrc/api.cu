@@ -75,7 +75,6 @@ dc::PlanView dc_plan::view() const
     v.idz = 1.0f / grid.dz;
     for (int j = 0; j < 16; ++j) v.gw[j] = gw[j];
     v.merged_rt = merged ? 1 : 0;
-    v.tstride = (uint32_t)((merged ? 3 : 2) * Kmax);
     v.a_hi = (float)(coeffs.a_nt - 1);
     v.w_hi = (float)(coeffs.w_n - 1);
     v.item_rt = (coeffs.density_correction && lateral_mode != DC_LATERAL_ISO) ? 1 : 0;

@@ -29,7 +29,7 @@ struct dc_batch {
     std::vector<cudaEvent_t> pre;       // plans' pending work, before a replay
     std::vector<DoseArgs> h_args;       // [n], in unit-range order
     DoseArgs* d_args = nullptr;         // device copy
-    int64_t* d_prefix = nullptr;        // [n + 1] unit prefix (device-computed)
+    int64_t* d_prefix = nullptr;        // [groups][n + 1] unit prefix per plan group (device-computed)
     int64_t* d_vpre = nullptr;          // [n + 1] voxel prefix
     unsigned int* d_counter = nullptr;
     std::vector<float*> d_fluence, d_dose;   // caller order, owned by the batch
@@ -271,9 +271,9 @@ dc_status dc_fspb_batch_create(dc_plan* const* plans, int32_t n, void* cuda_stre
         if (e != cudaSuccess) return fail(cuda_fail(e, "batch buffers"));
     }
     e = cudaMalloc(&bt->d_args, sizeof(DoseArgs) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&bt->d_prefix, sizeof(int64_t) * (n + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&bt->d_prefix, sizeof(int64_t) * batch_groups() * (n + 1));
     if (e == cudaSuccess) e = cudaMalloc(&bt->d_vpre, sizeof(int64_t) * (n + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&bt->d_counter, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMalloc(&bt->d_counter, sizeof(unsigned int) * batch_groups());
     if (e == cudaSuccess) e = cudaMemcpy(bt->d_vpre, vpre.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return fail(cuda_fail(e, "batch set-up"));
     // one set of water tables for all plans (the usual case: one beam model)?

@@ -86,7 +86,6 @@ struct PlanView {
     float gw[16];                 // normalised Gaussian weights of the 16 stencil taps
     int merged_rt;                // tabm is in use (runtime copy of the plan's choice)
     int item_rt;                  // lfac is in use
-    uint32_t tstride;             // float4 entries per beamlet in the table in use (3 or 2 Kmax)
     float a_hi, w_hi;             // a_nt - 1, w_n - 1 as floats (clamps of the table coordinates)
 };
 
@@ -275,9 +274,14 @@ void mlp_pack(const float* theta, std::vector<uint2>& frag, std::vector<float>& 
 DoseArgs dose_args(const dc_plan* p, const float* fluence, float* dose);
 int batch_max_plans();
 constexpr int kBatchVariants = 2;   // register budgets of the batch pair kernel (4 or 5 CTAs per SM)
-// prefix of the plans' unit counts, the persistent pair kernel over all plans'
-// units (arguments h_args by value; d_args holds the same records on the
-// device), and the per-plan beam sums; the partials must be zero beforehand
+// The plans are grouped by lateral form (at most batch_groups() groups); per
+// group, the prefix of its plans' unit counts and one persistent pair kernel
+// over all their units (one launch in all when the plans share the lateral
+// form, the usual case); then the per-plan beam sums.  Arguments
+// h_args by value, d_args the same records on the device; d_prefix holds
+// batch_groups() x (n + 1) entries and d_counter batch_groups(); the partials
+// must be zero beforehand.
+int batch_groups();
 cudaError_t launch_batch(cudaStream_t s, const DoseArgs* h_args, const DoseArgs* d_args, int n,
                          const int64_t* d_vpre, int64_t v_total, int64_t* d_prefix, unsigned int* d_counter,
                          int device, int variant, bool shared_water);

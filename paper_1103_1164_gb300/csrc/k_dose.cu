@@ -149,7 +149,7 @@ __device__ __forceinline__ float pair_eval(const PlanView& P, const Lane& ln, co
     const uint32_t kb = grid_bits_mul(t, P.inv_d, fr);
     float teq, O1, O2, u1w, u2w;
     if (MERGED) {
-        const float4* tb = P.tabm + (i * P.tstride + 3u * (kb - kGridBits));
+        const float4* tb = P.tabm + (i * (3u * (uint32_t)P.Kmax) + 3u * (kb - kGridBits));
         const float4 e0 = __ldg(tb), e1 = __ldg(tb + 1), e2 = __ldg(tb + 2);
         teq = fmaf(fr, e0.y, e0.x);
         O1 = fmaf(fr, e0.w, e0.z);
@@ -157,7 +157,7 @@ __device__ __forceinline__ float pair_eval(const PlanView& P, const Lane& ln, co
         u1w = fmaf(fr, e1.w, e1.z);
         u2w = fmaf(fr, e2.y, e2.x);
     } else {
-        const float4* tb = P.tab + (i * P.tstride + 2u * (kb - kGridBits));
+        const float4* tb = P.tab + (i * (2u * (uint32_t)P.Kmax) + 2u * (kb - kGridBits));
         const float4 e0 = __ldg(tb), e1 = __ldg(tb + 1);
         teq = fmaf(fr, e0.y, e0.x);
         const float c1 = fmaf(fr, e0.w, e0.z);
@@ -444,49 +444,61 @@ __global__ void __launch_bounds__(kThreads, min_ctas<MODE, NF>()) k_pairs(const 
 }
 
 // ---------------------------------------------------------------------------
-// Several plans in one persistent launch.  The work units of all plans (one
-// fluence vector each) form one range, plans in the order of the argument
-// array; a warp takes the next unit from a global counter, finds its plan and
-// beam, and runs the same per-unit body as k_pairs with the plan's table and
-// lateral variants chosen at run time (warp-uniform branches).  The plans'
-// arguments travel as one grid-constant kernel parameter, so the hot loop
-// reads them from the constant bank as k_pairs does.  When every plan uses
-// the same water tables (one commissioned beam model), they are staged in
-// shared memory once per CTA; otherwise each plan's are read through L1.
+// Several plans in one persistent launch.  The plans are grouped by lateral
+// form (per-voxel or per-item factors); a group runs on the merged depth tables
+// when all its plans have them, else on the general tables (which every plan
+// keeps).  The work units of a group's plans (one fluence vector each) form
+// one range, and
+// a warp takes the next unit from the group's counter, finds its plan and
+// beam, and runs the same per-unit body as k_pairs, specialised for the group
+// (no run-time choice of variant in the hot loop).  The plans' arguments travel
+// as one grid-constant kernel parameter, so the hot loop reads them from the
+// constant bank as k_pairs does.  When every plan uses the same water tables
+// (one commissioned beam model), they are staged in shared memory once per
+// CTA; otherwise each plan's are read through L1.
 constexpr int kMaxBatch = 64;
+constexpr int kBatchGroups = 2;   // per-voxel or per-item lateral factors
 
 struct BatchParams {
     DoseArgs a[kMaxBatch];
 };
-static_assert(sizeof(BatchParams) + 64 <= 32764, "kernel parameter space");
+static_assert(sizeof(BatchParams) + 64 + 72 <= 32764, "kernel parameter space");
 
-// prefix[j] = units of plans 0..j-1 (the unit counts were written by each
-// plan's binning on the device); resets the work counter.
-__global__ void k_batch_prefix(const DoseArgs* __restrict__ args, int n, int64_t* __restrict__ prefix,
+// The plans of one group: indices into BatchParams::a.
+struct BatchGroup {
+    int8_t j[kMaxBatch];
+    int n;
+};
+
+// prefix[q] = units of the group's plans 0..q-1 (the unit counts were written
+// by each plan's binning on the device); resets the group's work counter.
+__global__ void k_batch_prefix(const DoseArgs* __restrict__ args, const BatchGroup g, int64_t* __restrict__ prefix,
                                unsigned int* __restrict__ counter)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     int64_t s = 0;
-    for (int j = 0; j < n; ++j) {
-        prefix[j] = s;
-        s += *args[j].work;
+    for (int q = 0; q < g.n; ++q) {
+        prefix[q] = s;
+        s += *args[g.j[q]].work;
     }
-    prefix[n] = s;
+    prefix[g.n] = s;
     *counter = 0u;
 }
 
-// MINB: CTAs per SM the register budget is set for (4: no spills; 5: 48
-// registers).  SHARED_W: all plans share the water tables of plan 0.
-template <int MINB, bool SHARED_W>
-__global__ void __launch_bounds__(kThreads, MINB) k_pairs_batch(const __grid_constant__ BatchParams bp, int n,
+// MINB: CTAs per SM the register budget is set for (4: 64 registers; 5: 48).
+// SHARED_W: all plans share the water tables of plan 0.
+template <int MINB, bool SHARED_W, bool MERGED, int LAT>
+__global__ void __launch_bounds__(kThreads, MINB) k_pairs_batch(const __grid_constant__ BatchParams bp,
+                                                                const __grid_constant__ BatchGroup g,
                                                                 const int64_t* __restrict__ prefix,
                                                                 unsigned int* __restrict__ counter)
 {
     extern __shared__ float4 smem[];
     __shared__ int64_t s_pre[kMaxBatch + 1];
     __shared__ float4 s_row[kWarps][3 * row_max(kDose)];
+    const int n = g.n;
     for (int q = threadIdx.x; q <= n; q += blockDim.x) s_pre[q] = prefix[q];
-    if (SHARED_W)
+    if (SHARED_W && !MERGED)
         for (int q = threadIdx.x; q < 2 * bp.a[0].P.w_n; q += blockDim.x) smem[q] = __ldg(bp.a[0].P.water + q);
     __syncthreads();
     const int lane = threadIdx.x & 31;
@@ -496,35 +508,25 @@ __global__ void __launch_bounds__(kThreads, MINB) k_pairs_batch(const __grid_con
         if (lane == 0) w = atomicAdd(counter, 1u);
         w = __shfl_sync(0xffffffffu, w, 0);
         if ((int64_t)w >= total) break;
-        int j = 0;
-        while (j + 1 < n && s_pre[j + 1] <= (int64_t)w) ++j;
-        const DoseArgs& a = bp.a[j];
-        const int64_t e0 = ((int64_t)w - s_pre[j]) * 32;
+        int q = 0;
+        while (q + 1 < n && s_pre[q + 1] <= (int64_t)w) ++q;
+        const DoseArgs& a = bp.a[g.j[q]];
+        const int64_t e0 = ((int64_t)w - s_pre[q]) * 32;
         const int nb = a.P.n_beams;
         int b = 0;
         while (b + 1 < nb && __ldg(a.base + b + 1) <= e0) ++b;
         const int32_t vi = __ldg(a.items + e0 + lane);
         const float4* wt = SHARED_W ? smem : a.P.water;
-        if (a.P.merged_rt) {
-            if (a.P.item_rt)
-                process_unit<kDose, 1, true, kItem>(a, vi, e0, b, wt, nullptr, s_row[threadIdx.x >> 5], lane);
-            else
-                process_unit<kDose, 1, true, kIso>(a, vi, e0, b, wt, nullptr, s_row[threadIdx.x >> 5], lane);
-        } else {
-            if (a.P.item_rt)
-                process_unit<kDose, 1, false, kItem>(a, vi, e0, b, wt, nullptr, s_row[threadIdx.x >> 5], lane);
-            else
-                process_unit<kDose, 1, false, kIso>(a, vi, e0, b, wt, nullptr, s_row[threadIdx.x >> 5], lane);
-        }
+        process_unit<kDose, 1, MERGED, LAT>(a, vi, e0, b, wt, nullptr, s_row[threadIdx.x >> 5], lane);
     }
 }
 
-template <int MINB, bool SHARED_W>
-cudaError_t batch_kernel(cudaStream_t s, const BatchParams& bp, int n, const int64_t* d_prefix,
+template <int MINB, bool SHARED_W, bool MERGED, int LAT>
+cudaError_t batch_kernel(cudaStream_t s, const BatchParams& bp, const BatchGroup& g, const int64_t* d_prefix,
                          unsigned int* d_counter, int device, int w_n)
 {
-    auto kern = k_pairs_batch<MINB, SHARED_W>;
-    const size_t sm = SHARED_W ? 2 * sizeof(float4) * (size_t)w_n : 0;
+    auto kern = k_pairs_batch<MINB, SHARED_W, MERGED, LAT>;
+    const size_t sm = (SHARED_W && !MERGED) ? 2 * sizeof(float4) * (size_t)w_n : 0;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     int per_sm = 0, sms = 0;
@@ -532,8 +534,19 @@ cudaError_t batch_kernel(cudaStream_t s, const BatchParams& bp, int n, const int
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) return e;
-    kern<<<sms * (per_sm > 0 ? per_sm : 1), kThreads, sm, s>>>(bp, n, d_prefix, d_counter);
+    kern<<<sms * (per_sm > 0 ? per_sm : 1), kThreads, sm, s>>>(bp, g, d_prefix, d_counter);
     return cudaGetLastError();
+}
+
+template <bool MERGED, int LAT>
+cudaError_t batch_group(cudaStream_t s, const BatchParams& bp, const BatchGroup& g, const int64_t* d_prefix,
+                        unsigned int* d_counter, int device, int w_n, int variant, bool shared_water)
+{
+    if (variant == 0)
+        return shared_water ? batch_kernel<4, true, MERGED, LAT>(s, bp, g, d_prefix, d_counter, device, w_n)
+                            : batch_kernel<4, false, MERGED, LAT>(s, bp, g, d_prefix, d_counter, device, w_n);
+    return shared_water ? batch_kernel<5, true, MERGED, LAT>(s, bp, g, d_prefix, d_counter, device, w_n)
+                        : batch_kernel<5, false, MERGED, LAT>(s, bp, g, d_prefix, d_counter, device, w_n);
 }
 
 // dose_j[v] = sum over plan j's beams of its partial doses (fixed beam order)
@@ -743,6 +756,7 @@ DoseArgs dose_args(const dc_plan* p, const float* fluence, float* dose)
 }
 
 int batch_max_plans() { return kMaxBatch; }
+int batch_groups() { return kBatchGroups; }
 
 cudaError_t launch_batch(cudaStream_t s, const DoseArgs* h_args, const DoseArgs* d_args, int n,
                          const int64_t* d_vpre, int64_t v_total, int64_t* d_prefix, unsigned int* d_counter,
@@ -755,18 +769,32 @@ cudaError_t launch_batch(cudaStream_t s, const DoseArgs* h_args, const DoseArgs*
     memset(&bp, 0, sizeof(bp));
     memcpy(bp.a, h_args, sizeof(DoseArgs) * n);
     const int w_n = h_args[0].P.w_n;
-    k_batch_prefix<<<1, 32, 0, s>>>(d_args, n, d_prefix, d_counter);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    if (variant == 0)
-        e = shared_water ? batch_kernel<4, true>(s, bp, n, d_prefix, d_counter, device, w_n)
-                         : batch_kernel<4, false>(s, bp, n, d_prefix, d_counter, device, w_n);
-    else
-        e = shared_water ? batch_kernel<5, true>(s, bp, n, d_prefix, d_counter, device, w_n)
-                         : batch_kernel<5, false>(s, bp, n, d_prefix, d_counter, device, w_n);
-    if (e != cudaSuccess) return e;
+    for (int gi = 0; gi < kBatchGroups; ++gi) {
+        const bool item = gi == 1;
+        BatchGroup g{};
+        bool merged = true;
+        for (int j = 0; j < n; ++j)
+            if ((h_args[j].P.item_rt != 0) == item) {
+                g.j[g.n++] = (int8_t)j;
+                merged = merged && h_args[j].P.merged_rt != 0;
+            }
+        if (g.n == 0) continue;
+        int64_t* pre = d_prefix + (size_t)gi * (n + 1);
+        unsigned int* cnt = d_counter + gi;
+        k_batch_prefix<<<1, 32, 0, s>>>(d_args, g, pre, cnt);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        if (merged)
+            e = item ? batch_group<true, kItem>(s, bp, g, pre, cnt, device, w_n, variant, shared_water)
+                     : batch_group<true, kIso>(s, bp, g, pre, cnt, device, w_n, variant, shared_water);
+        else
+            e = item ? batch_group<false, kItem>(s, bp, g, pre, cnt, device, w_n, variant, shared_water)
+                     : batch_group<false, kIso>(s, bp, g, pre, cnt, device, w_n, variant, shared_water);
+        if (e != cudaSuccess) return e;
+        count_launches(2);
+    }
     k_sum_batch<<<grid_for(v_total), 256, 0, s>>>(d_args, n, d_vpre);
-    count_launches(3);
+    count_launches(1);
     return cudaGetLastError();
 }
 

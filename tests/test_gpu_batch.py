@@ -46,6 +46,11 @@ def _uneven(dc):
     return inputs, plans
 
 
+def _groups(inputs, modes, dc):
+    """Plan groups of the batch: per-voxel or per-item lateral factors."""
+    return len({bool(p.comm.density_correction) and m != dc.DC_LATERAL_ISO for p, m in zip(inputs, modes)})
+
+
 def _close(a, b, label):
     a = np.asarray(a, np.float64).reshape(-1)
     b = np.asarray(b, np.float64).reshape(-1)
@@ -77,7 +82,10 @@ def test_batch_matches_single_plans_and_oracle(dc, oracle_mod):
         got = dc.dc_fspb_batch_dose(batch, flu)
         for j in range(len(plans)):
             _close(got[j], single[j], f"plan {j} run {rep}")
-    assert dc.dc_fspb_batch_kernels(batch) == 3
+    # one prefix and one persistent pair kernel per plan group, one beam sum
+    modes = [dc.DC_LATERAL_ISO, dc.DC_LATERAL_AXIS, dc.DC_LATERAL_ISO, dc.DC_LATERAL_AXIS]
+    assert _groups(inputs, modes, dc) == 2
+    assert dc.dc_fspb_batch_kernels(batch) == 1 + 2 * 2
     for j, p in enumerate(inputs):
         want, amb = oracle_mod.OraclePlan(p, lateral_mode=1 if j in (1, 3) else 0).dose(with_amb=True)
         assert_dose_close(got[j], want, amb, label=f"batch plan {j}")
@@ -151,6 +159,9 @@ def test_head_neck_batch_full_size_sampled(dc, oracle_mod):
     plans = [dc.dc_fspb_create_from(p) for p in inputs]
     batch = dc.dc_fspb_batch_create(plans)
     got = dc.dc_fspb_batch_dose(batch, [np.ascontiguousarray(p.fluence, np.float32) for p in inputs])
+    # one lateral form: one persistent pair launch for all 16 plans (one of
+    # them has merged tables, the others not)
+    assert dc.dc_fspb_batch_kernels(batch) == 3
     for j, (p, pl) in enumerate(zip(inputs, plans)):
         _close(got[j], dc.dc_fspb_dose(pl, p.fluence), f"hn{j}")
     sizes = [pl.n_voxels for pl in plans]
