@@ -87,7 +87,8 @@ static void free_plan(dc_plan* p)
     void* bufs[] = {p->d_rho, p->d_rhos, p->d_tmp, p->d_fac, p->d_beams, p->d_bl, p->d_theta, p->d_ray,
                     p->d_tab, p->d_arow, p->d_tabm, p->d_A, p->d_water, p->d_dens, p->d_beamin, p->d_fluence,
                     p->d_dose, p->d_rowcount, p->d_rowptr, p->d_scan_tmp, p->d_mcols, p->d_mvals,
-                    p->d_bin, p->d_bounds, p->d_cellof, p->d_hist, p->d_nitems, p->d_base, p->d_work,
+                    p->d_bin, p->d_bounds, p->d_cellof, p->d_hist, p->d_nitems, p->d_bstart, p->d_bscan,
+                    p->d_base, p->d_work,
                     p->d_items, p->d_part, p->d_bcount, p->d_sp_fp, p->d_sp_p, p->d_err,
                     p->d_lfac, p->d_mlp_frag, p->d_mlp_bias, p->d_nfall};
     for (void* b : bufs)
@@ -330,6 +331,8 @@ static dc_status create_impl(dc_plan* p, const float* ct, uint32_t flags)
     DC_CUDA(dalloc(&p->d_bin, nb));
     DC_CUDA(dalloc(&p->d_cellof, nb * V));
     DC_CUDA(dalloc(&p->d_nitems, nb));
+    DC_CUDA(dalloc(&p->d_bstart, nb + 1));
+    DC_CUDA(dalloc(&p->d_bscan, (nb * (size_t)p->cells_cap + 4095) / 4096 + 2));
     DC_CUDA(dalloc(&p->d_base, nb + 1));
     DC_CUDA(dalloc(&p->d_work, 2));
     DC_CUDA(dalloc(&p->d_items, nb * (V + 32)));

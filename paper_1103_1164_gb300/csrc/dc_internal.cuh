@@ -162,6 +162,8 @@ struct dc_plan {
     int32_t* d_cellof = nullptr;     // [n_beams][V]
     int32_t* d_hist = nullptr;       // [n_beams][cells_max]
     int32_t* d_nitems = nullptr;     // [n_beams]
+    int32_t* d_bstart = nullptr;     // [n_beams + 1] start of each beam's cells in the device-wide cell scan
+    int32_t* d_bscan = nullptr;      // chunk sums of that scan
     int64_t* d_base = nullptr;       // [n_beams + 1] start of each beam's list (whole warps)
     int32_t* d_work = nullptr;       // [0] warp work units, [1] work counter
     int32_t* d_items = nullptr;      // [n_beams][V + 32]

@@ -97,55 +97,109 @@ __global__ void __launch_bounds__(256) k_bin_hist(const PlanView P, const BinGeo
     }
 }
 
-// Pass 2 (one CTA per beam): exclusive scan of the beam's cell histogram in
-// place (the histogram becomes the cell cursors), and the beam's item count.
-__global__ void __launch_bounds__(1024) k_bin_scan(const BinGeom* __restrict__ G, int cells_max,
-                                                   int32_t* __restrict__ hist, int32_t* __restrict__ n_items)
+// Pass 2: exclusive scan of all beams' cell histograms, [n_beams][cells_max]
+// in one range, in place (the histogram becomes the cell cursors); beam b's
+// cells start at bstart[b] in that range and bstart[n_beams] is the total.
+// Three kernels: chunk sums, a scan of the chunk sums, and the scan inside
+// each chunk plus its chunk's offset.
+constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 4;
+constexpr int kScanChunk = kScanThreads * kScanPer;
+
+__device__ __forceinline__ int32_t block_exclusive_scan32(int32_t x, int32_t* s_warp, int32_t* total)
 {
-    __shared__ int32_t sw[33];
-    const int b = blockIdx.x;
-    const int cells = G[b].cells;
-    int32_t* h = hist + (size_t)b * cells_max;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int32_t carry = 0;
-    for (int base = 0; base < cells; base += blockDim.x) {
-        const int q = base + threadIdx.x;
-        const int32_t x = q < cells ? h[q] : 0;
-        int32_t incl = x;
-        for (int o = 1; o < 32; o <<= 1) {
-            int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        if (lane == 31) sw[warp] = incl;
-        __syncthreads();
-        if (warp == 0) {
-            int32_t w = lane < (int)(blockDim.x >> 5) ? sw[lane] : 0;
-            int32_t wi = w;
-            for (int o = 1; o < 32; o <<= 1) {
-                int32_t y = __shfl_up_sync(0xffffffffu, wi, o);
-                if (lane >= o) wi += y;
-            }
-            sw[lane] = wi - w;
-            if (lane == 31) sw[32] = wi;
-        }
-        __syncthreads();
-        if (q < cells) h[q] = carry + incl - x + sw[warp];
-        carry += sw[32];
-        __syncthreads();
+    int32_t incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
     }
-    if (threadIdx.x == 0) n_items[b] = carry;
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int32_t w = lane < (int)(blockDim.x >> 5) ? s_warp[lane] : 0;
+        int32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        s_warp[lane] = wi - w;
+        if (lane == 31) s_warp[32] = wi;
+    }
+    __syncthreads();
+    const int32_t r = incl - x + s_warp[warp];
+    *total = s_warp[32];
+    __syncthreads();
+    return r;
 }
 
-// Pass 3 (one thread): start of each beam's item list, padded to whole warps,
-// and the total number of warp work units.
-__global__ void k_bin_bases(int n_beams, const int32_t* __restrict__ n_items, int64_t* __restrict__ base,
-                            int32_t* __restrict__ work)
+__global__ void __launch_bounds__(kScanThreads) k_cell_scan_sums(const int32_t* __restrict__ h, int64_t n,
+                                                                 int32_t* __restrict__ sums)
+{
+    __shared__ int32_t sw[33];
+    const int64_t base = (int64_t)blockIdx.x * kScanChunk + threadIdx.x * kScanPer;
+    int32_t s = 0;
+    for (int q = 0; q < kScanPer; ++q)
+        if (base + q < n) s += h[base + q];
+    int32_t tot;
+    block_exclusive_scan32(s, sw, &tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_cell_scan_top(int32_t* __restrict__ sums, int nb,
+                                                                int32_t* __restrict__ bstart, int n_beams)
+{
+    __shared__ int32_t sw[33];
+    int32_t carry = 0;
+    for (int base = 0; base < nb; base += kScanThreads) {
+        const int q = base + threadIdx.x;
+        const int32_t x = q < nb ? sums[q] : 0;
+        int32_t tot;
+        const int32_t e = block_exclusive_scan32(x, sw, &tot);
+        if (q < nb) sums[q] = e + carry;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) bstart[n_beams] = carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_cell_scan_apply(int32_t* __restrict__ h, int64_t n,
+                                                                  const int32_t* __restrict__ sums, int cells_max,
+                                                                  int32_t* __restrict__ bstart)
+{
+    __shared__ int32_t sw[33];
+    const int64_t base = (int64_t)blockIdx.x * kScanChunk + threadIdx.x * kScanPer;
+    int32_t x[kScanPer];
+    int32_t s = 0;
+    for (int q = 0; q < kScanPer; ++q) {
+        x[q] = base + q < n ? h[base + q] : 0;
+        s += x[q];
+    }
+    int32_t tot;
+    int32_t e = block_exclusive_scan32(s, sw, &tot) + sums[blockIdx.x];
+    for (int q = 0; q < kScanPer; ++q) {
+        const int64_t i = base + q;
+        if (i < n) {
+            h[i] = e;
+            if (i % cells_max == 0) bstart[i / cells_max] = e;
+        }
+        e += x[q];
+    }
+}
+
+// Pass 3 (one thread): each beam's item count, the start of its item list
+// (padded to whole warps) and the total number of warp work units.
+__global__ void k_bin_bases(int n_beams, const int32_t* __restrict__ bstart, int32_t* __restrict__ n_items,
+                            int64_t* __restrict__ base, int32_t* __restrict__ work)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     int64_t s = 0;
     for (int b = 0; b < n_beams; ++b) {
+        const int32_t nb = bstart[b + 1] - bstart[b];
+        n_items[b] = nb;
         base[b] = s;
-        s += ((int64_t)n_items[b] + 31) / 32 * 32;
+        s += ((int64_t)nb + 31) / 32 * 32;
     }
     base[n_beams] = s;
     work[0] = (int32_t)(s / 32);
@@ -157,6 +211,7 @@ __global__ void __launch_bounds__(256) k_bin_scatter(int64_t V, int n_beams, int
                                                      const int32_t* __restrict__ cellof,
                                                      int32_t* __restrict__ cursor,
                                                      const int32_t* __restrict__ n_items,
+                                                     const int32_t* __restrict__ bstart,
                                                      const int64_t* __restrict__ base,
                                                      int32_t* __restrict__ items)
 {
@@ -166,7 +221,7 @@ __global__ void __launch_bounds__(256) k_bin_scatter(int64_t V, int n_beams, int
          v += (int64_t)gridDim.x * blockDim.x) {
         const int cell = cellof[(size_t)b * V + v];
         if (cell >= 0) {
-            const int pos = atomicAdd(cursor + (size_t)b * cells_max + cell, 1);
+            const int pos = atomicAdd(cursor + (size_t)b * cells_max + cell, 1) - bstart[b];
             items[b0 + pos] = (int32_t)v;
         }
     }
@@ -189,11 +244,16 @@ cudaError_t launch_binning(const dc_plan* p)
     dim3 gv(gx, p->n_beams);
     k_bin_hist<<<gv, 256, 0, p->stream>>>(P, p->d_bin, p->d_bounds, p->tiles_max, p->cells_max, p->d_cellof,
                                           p->d_hist);
-    k_bin_scan<<<p->n_beams, 1024, 0, p->stream>>>(p->d_bin, p->cells_max, p->d_hist, p->d_nitems);
-    k_bin_bases<<<1, 32, 0, p->stream>>>(p->n_beams, p->d_nitems, p->d_base, p->d_work);
+    const int64_t ncell = (int64_t)p->n_beams * p->cells_max;
+    const int nchunk = (int)((ncell + kScanChunk - 1) / kScanChunk);
+    k_cell_scan_sums<<<nchunk, kScanThreads, 0, p->stream>>>(p->d_hist, ncell, p->d_bscan);
+    k_cell_scan_top<<<1, kScanThreads, 0, p->stream>>>(p->d_bscan, nchunk, p->d_bstart, p->n_beams);
+    k_cell_scan_apply<<<nchunk, kScanThreads, 0, p->stream>>>(p->d_hist, ncell, p->d_bscan, p->cells_max,
+                                                              p->d_bstart);
+    k_bin_bases<<<1, 32, 0, p->stream>>>(p->n_beams, p->d_bstart, p->d_nitems, p->d_base, p->d_work);
     k_bin_scatter<<<gv, 256, 0, p->stream>>>(p->V, p->n_beams, p->cells_max, p->d_cellof, p->d_hist,
-                                             p->d_nitems, p->d_base, p->d_items);
-    count_launches(5);
+                                             p->d_nitems, p->d_bstart, p->d_base, p->d_items);
+    count_launches(7);
     return cudaGetLastError();
 }
 
