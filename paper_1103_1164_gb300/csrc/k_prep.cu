@@ -81,6 +81,8 @@ struct BeamletArgs {
     float f_rho0, inv_drho;
     int nx, ny, nz, B, n_beams, Kmax;
     double dx, dy, dz, ox, oy, oz, d;
+    double idx, idy, idz;    // 1 / voxel size
+    double inv_d;            // 1 / d
     double bx, by;
     float rho_surf;
     int a_nth;
@@ -116,10 +118,19 @@ struct Walk {
     double acur, amax;
 };
 
-__device__ bool walk_init(const BeamletArgs& A, const double* s, const double* n, Walk& w)
+// 1 / n[a] per axis (0 where the axis is parallel to the ray): the walk
+// multiplies by these instead of dividing (FP64 division is a long sequence
+// on this GPU, whose FP64 rate is a small fraction of its FP32 rate).
+__device__ __forceinline__ void ray_inverse(const double* n, double* inv_n)
+{
+    for (int a = 0; a < 3; ++a) inv_n[a] = fabs(n[a]) < 1e-15 ? 0.0 : 1.0 / n[a];
+}
+
+__device__ bool walk_init(const BeamletArgs& A, const double* s, const double* n, const double* inv_n, Walk& w)
 {
     const int dims[3] = {A.nx, A.ny, A.nz};
     const double del[3] = {A.dx, A.dy, A.dz};
+    const double idel[3] = {A.idx, A.idy, A.idz};
     const double org[3] = {A.ox, A.oy, A.oz};
     double amin = 0.0, amax = 1e300;
     for (int a = 0; a < 3; ++a) {
@@ -128,7 +139,7 @@ __device__ bool walk_init(const BeamletArgs& A, const double* s, const double* n
             if (s[a] <= p0 || s[a] >= p1) return false;
             continue;
         }
-        double t0 = (p0 - s[a]) / n[a], t1 = (p1 - s[a]) / n[a];
+        double t0 = (p0 - s[a]) * inv_n[a], t1 = (p1 - s[a]) * inv_n[a];
         amin = fmax(amin, fmin(t0, t1));
         amax = fmin(amax, fmax(t0, t1));
     }
@@ -136,7 +147,7 @@ __device__ bool walk_init(const BeamletArgs& A, const double* s, const double* n
     for (int a = 0; a < 3; ++a) {
         double p0 = org[a] - 0.5 * del[a];
         double pos = s[a] + amin * n[a];
-        double f = (pos - p0) / del[a];
+        double f = (pos - p0) * idel[a];
         int id = (int)floor(f);
         if (n[a] < 0 && f == floor(f)) id -= 1;
         id = min(max(id, 0), dims[a] - 1);
@@ -147,12 +158,12 @@ __device__ bool walk_init(const BeamletArgs& A, const double* s, const double* n
             w.adelta[a] = 1e300;
         } else if (n[a] > 0) {
             w.step[a] = 1;
-            w.anext[a] = (p0 + (id + 1) * del[a] - s[a]) / n[a];
-            w.adelta[a] = del[a] / n[a];
+            w.anext[a] = (p0 + (id + 1) * del[a] - s[a]) * inv_n[a];
+            w.adelta[a] = del[a] * inv_n[a];
         } else {
             w.step[a] = -1;
-            w.anext[a] = (p0 + id * del[a] - s[a]) / n[a];
-            w.adelta[a] = -del[a] / n[a];
+            w.anext[a] = (p0 + id * del[a] - s[a]) * inv_n[a];
+            w.adelta[a] = -del[a] * inv_n[a];
         }
     }
     w.acur = amin;
@@ -163,15 +174,16 @@ __device__ bool walk_init(const BeamletArgs& A, const double* s, const double* n
 // The walk state at a_start on the ray s + a n, to run up to a_end (both
 // inside [amin, amax] of walk_init): the voxel holding the ray just past
 // a_start and the next plane crossing along each axis.
-__device__ void walk_from(const BeamletArgs& A, const double* s, const double* n, double a_start, double a_end,
-                          Walk& w)
+__device__ void walk_from(const BeamletArgs& A, const double* s, const double* n, const double* inv_n,
+                          double a_start, double a_end, Walk& w)
 {
     const int dims[3] = {A.nx, A.ny, A.nz};
     const double del[3] = {A.dx, A.dy, A.dz};
+    const double idel[3] = {A.idx, A.idy, A.idz};
     const double org[3] = {A.ox, A.oy, A.oz};
     for (int a = 0; a < 3; ++a) {
         const double p0 = org[a] - 0.5 * del[a];
-        const double f = (s[a] + a_start * n[a] - p0) / del[a];
+        const double f = (s[a] + a_start * n[a] - p0) * idel[a];
         int id = (int)floor(f);
         if (n[a] < 0 && f == floor(f)) id -= 1;
         id = min(max(id, 0), dims[a] - 1);
@@ -182,12 +194,12 @@ __device__ void walk_from(const BeamletArgs& A, const double* s, const double* n
             w.adelta[a] = 1e300;
         } else if (n[a] > 0) {
             w.step[a] = 1;
-            w.anext[a] = (p0 + (id + 1) * del[a] - s[a]) / n[a];
-            w.adelta[a] = del[a] / n[a];
+            w.anext[a] = (p0 + (id + 1) * del[a] - s[a]) * inv_n[a];
+            w.adelta[a] = del[a] * inv_n[a];
         } else {
             w.step[a] = -1;
-            w.anext[a] = (p0 + id * del[a] - s[a]) / n[a];
-            w.adelta[a] = -del[a] / n[a];
+            w.anext[a] = (p0 + id * del[a] - s[a]) * inv_n[a];
+            w.adelta[a] = -del[a] * inv_n[a];
         }
     }
     w.acur = a_start;
@@ -447,7 +459,8 @@ __device__ __forceinline__ Acc warp_exclusive_sum(Acc x, int lane)
 
 // Returns false if a piece overflowed its segment buffer (nothing written).
 template <typename Acc>
-__device__ bool trace_warp(const BeamletArgs& A, const double* s, const double* n, const Walk& w0, int lane,
+__device__ bool trace_warp(const BeamletArgs& A, const double* s, const double* n, const double* inv_n,
+                           const Walk& w0, int lane,
                            double* __restrict__ sa1, float* __restrict__ sr, float4* __restrict__ tab, double& L_in,
                            double& L_out, int& K)
 {
@@ -461,7 +474,7 @@ __device__ bool trace_warp(const BeamletArgs& A, const double* s, const double* 
     int ns = 0;
     double first_a = 1e300, last_a = -1.0;
     Walk w;
-    walk_from(A, s, n, a_start, a_end, w);
+    walk_from(A, s, n, inv_n, a_start, a_end, w);
     walk_run(A, w, [&](double a0, double a1, int64_t vox) {
         const float r = __ldg(A.rho + vox);
         if (ns < kSegCap) {
@@ -509,7 +522,7 @@ __device__ bool trace_warp(const BeamletArgs& A, const double* s, const double* 
     // 4. the samples L_in + k d in [max(a_start, L_in), a_end) (the last piece
     // also takes those past the end of the ray)
     const double lo0 = fmax(a_start, L_in);
-    int k = max(0, (int)ceil((lo0 - L_in) / d));
+    int k = max(0, (int)ceil((lo0 - L_in) * A.inv_d));   // then made exact:
     while (k > 0 && L_in + (k - 1) * d >= lo0) --k;
     while (L_in + k * d < lo0) ++k;
     a0 = a_start;
@@ -578,16 +591,18 @@ __global__ void __launch_bounds__(32 * kTraceWarps) k_trace(const BeamletArgs A)
     if (i >= A.B) return;   // whole warps
     const double* ray = A.ray + 8 * (size_t)i;
     const double s[3] = {ray[0], ray[1], ray[2]}, n[3] = {ray[4], ray[5], ray[6]};
+    double inv_n[3];
+    ray_inverse(n, inv_n);
     Walk w;
     int K = 0;
     double L_in = 0, L_out = 0;
-    if (walk_init(A, s, n, w)) {
+    if (walk_init(A, s, n, inv_n, w)) {
         float4* tb = A.tab + 2 * (size_t)i * A.Kmax;
         const bool dbl = w.amax - w.acur > 40.0;
-        const bool ok = dbl ? trace_warp<double>(A, s, n, w, lane, s_a1[warp][lane], s_r[warp][lane], tb, L_in,
-                                                 L_out, K)
-                            : trace_warp<float>(A, s, n, w, lane, s_a1[warp][lane], s_r[warp][lane], tb, L_in,
-                                                L_out, K);
+        const bool ok = dbl ? trace_warp<double>(A, s, n, inv_n, w, lane, s_a1[warp][lane], s_r[warp][lane], tb,
+                                                 L_in, L_out, K)
+                            : trace_warp<float>(A, s, n, inv_n, w, lane, s_a1[warp][lane], s_r[warp][lane], tb,
+                                                L_in, L_out, K);
         if (!ok && lane == 0) {
             if (dbl)
                 trace_beamlet<double>(A, w, tb, L_in, L_out, K);
@@ -682,8 +697,10 @@ cudaError_t launch_beamlets(const dc_plan* p)
     A.n_beams = p->n_beams;
     A.Kmax = p->Kmax;
     A.dx = g.dx; A.dy = g.dy; A.dz = g.dz;
+    A.idx = 1.0 / (double)g.dx; A.idy = 1.0 / (double)g.dy; A.idz = 1.0 / (double)g.dz;
     A.ox = g.ox; A.oy = g.oy; A.oz = g.oz;
     A.d = 0.5 * fmin((double)g.dx, fmin((double)g.dy, (double)g.dz));
+    A.inv_d = 1.0 / A.d;
     A.bx = p->bx;
     A.by = p->by;
     A.rho_surf = c.rho_surface;
