@@ -250,9 +250,9 @@ __global__ void __launch_bounds__(kRB) k_tiles(const TileArgs a)
 // element (tile column p, fluence n) at ((p / 8) * 8 + n / 8) * 64 + (n % 8) * 8
 // + p % 8; fluence columns n >= k, padding columns and columns past the last
 // beam are zero.
-__global__ void __launch_bounds__(256) k_pack_fluence(const float* __restrict__ F, int k, int nkb,
-                                                      const int4* __restrict__ beam, int n_beams,
-                                                      __nv_bfloat16* __restrict__ Fp)
+__device__ __forceinline__ void pack_fluence(const float* __restrict__ F, int k, int nkb,
+                                             const int4* __restrict__ beam, int n_beams,
+                                             __nv_bfloat16* __restrict__ Fp)
 {
     const int64_t n_el = (int64_t)nkb * 8 * kN;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_el; e += (int64_t)gridDim.x * blockDim.x) {
@@ -567,11 +567,18 @@ __global__ void __launch_bounds__(256) k_unlisted(const int32_t* __restrict__ in
         if (inv[v] < 0) zero[atomicAdd(n, 1ull)] = (int32_t)v;
 }
 
-// Y[v][0..k) = 0 for the voxels v of zero[] (in no beam list: k_spmm does not write their rows).
-__global__ void __launch_bounds__(256) k_zero_rows(const int32_t* __restrict__ zero, int64_t n, int k,
-                                                   float* __restrict__ Y)
+// The work of one call before k_spmm, in one launch: the packed fluences; for
+// one-beam plans Y[v][0..k) = 0 for the voxels v of zero[] (in no beam list:
+// k_spmm does not write their rows); and the bounded-wait status word cleared.
+__global__ void __launch_bounds__(256) k_spmm_pre(const float* __restrict__ F, int k, int nkb,
+                                                  const int4* __restrict__ beam, int n_beams,
+                                                  __nv_bfloat16* __restrict__ Fp, const int32_t* __restrict__ zero,
+                                                  int64_t n_zero, float* __restrict__ Y, int32_t* __restrict__ err)
 {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * k; e += (int64_t)gridDim.x * blockDim.x)
+    if (blockIdx.x == 0 && threadIdx.x == 0) *err = 0;
+    pack_fluence(F, k, nkb, beam, n_beams, Fp);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_zero * k;
+         e += (int64_t)gridDim.x * blockDim.x)
         Y[(size_t)zero[e / k] * k + e % k] = 0.f;
 }
 
@@ -714,15 +721,13 @@ cudaError_t spmm_run(dc_plan* p, const float* F, int k, float* Y)
             p->sp_p_cap = need;
         }
     }
-    k_pack_fluence<<<gsize((int64_t)nkb * 8 * kN), 256, 0, p->stream>>>(
-        F, k, nkb, p->d_sp_first, p->n_beams, reinterpret_cast<__nv_bfloat16*>(p->d_sp_fp));
-    count_launches(1);
-    if (direct && p->sp_n_zero > 0) {
-        k_zero_rows<<<gsize(p->sp_n_zero * k), 256, 0, p->stream>>>(p->d_sp_zero, p->sp_n_zero, k, Y);
+    {
+        const int64_t nz = direct ? p->sp_n_zero : 0;
+        k_spmm_pre<<<gsize((int64_t)nkb * 8 * kN + nz * k), 256, 0, p->stream>>>(
+            F, k, nkb, p->d_sp_first, p->n_beams, reinterpret_cast<__nv_bfloat16*>(p->d_sp_fp), p->d_sp_zero, nz,
+            Y, p->d_err);
         count_launches(1);
     }
-    e = cudaMemsetAsync(p->d_err, 0, sizeof(int32_t), p->stream);
-    if (e != cudaSuccess) return e;
     SpmmArgs a{};
     a.tiles = reinterpret_cast<const uint16_t*>(p->d_sp_tiles);
     a.chunk_kb = p->d_sp_kb;
@@ -776,7 +781,7 @@ namespace {
 constexpr int kStaticNkb = (DC_SPMM_STATIC_MAX_BEAMLETS + 7) / 8 + 2;
 constexpr size_t kStaticFp = (size_t)kStaticNkb * 8 * kN;   // BF16 elements
 
-// Packed fluence tiles are fully rewritten by k_pack_fluence and the partial
+// Packed fluence tiles are fully rewritten by k_spmm_pre and the partial
 // rows read back are exactly those k_spmm stores, so neither needs clearing.
 static __device__ __align__(256) uint16_t g_static_fp[kStaticFp];
 static __device__ __align__(256) float g_static_part[DC_SPMM_STATIC_MAX_PARTIALS];
@@ -832,17 +837,14 @@ cudaError_t spmm_run_static(dc_plan* p, const float* F, int k, float* Y)
     StaticScratch sc;
     cudaError_t e = static_scratch(p->device, &sc);
     if (e != cudaSuccess) return e;
-    k_pack_fluence<<<gsize((int64_t)nkb * 8 * kN), 256, 0, p->stream>>>(F, k, nkb, p->d_sp_first, p->n_beams,
-                                                                       sc.fp);
-    count_launches(1);
-    // the output rows of voxels outside every beam list are never written by
-    // k_spmm, and the bounded-wait status word is read after the call
-    if (direct && p->sp_n_zero > 0) {
-        k_zero_rows<<<gsize(p->sp_n_zero * k), 256, 0, p->stream>>>(p->d_sp_zero, p->sp_n_zero, k, Y);
+    // the packed fluences, the output rows of voxels outside every beam list
+    // (never written by k_spmm) and the bounded-wait status word read after the call
+    {
+        const int64_t nz = direct ? p->sp_n_zero : 0;
+        k_spmm_pre<<<gsize((int64_t)nkb * 8 * kN + nz * k), 256, 0, p->stream>>>(
+            F, k, nkb, p->d_sp_first, p->n_beams, sc.fp, p->d_sp_zero, nz, Y, p->d_err);
         count_launches(1);
     }
-    e = cudaMemsetAsync(p->d_err, 0, sizeof(int32_t), p->stream);
-    if (e != cudaSuccess) return e;
     SpmmArgs a{};
     a.tiles = reinterpret_cast<const uint16_t*>(p->d_sp_tiles);
     a.chunk_kb = p->d_sp_kb;
