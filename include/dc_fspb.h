@@ -447,6 +447,42 @@ dc_status dc_fspb_autotune(dc_plan* plan, const float* fluence, uint32_t flags, 
  * (all plans, all threads), for accounting of GPU work. */
 dc_status dc_fspb_launch_count(uint64_t* n);
 
+/* ---- Gamma-index comparison of two dose distributions ----
+ *
+ * Section 3 (accuracy evaluation) compares each computed dose with a reference
+ * dose by the 3-D gamma index at 3 %-3 mm, the percentage taken of the
+ * reference's maximum dose, and reports gamma_max over the whole distribution,
+ * the mean gamma inside the reference's 50 % isodose line and the percentage
+ * of voxels there with gamma < 1 (Tables 2-3).  The paper does not say how the
+ * evaluated dose is searched; here, for each reference voxel centre r:
+ *   gamma(r) = min(R / dta, min over whole-voxel offsets o, |o| <= R, r + o in
+ *              the grid, of sqrt(|o|^2 / dta^2 + (D_eval(r + o) - D_ref(r))^2 / dD^2))
+ * with dD = dose_pct / 100 * max D_ref and R = search_cm (gamma is capped at
+ * R / dta: any point farther away has a larger distance term alone).
+ */
+typedef struct {
+    double gamma_max;      /* over all voxels                              */
+    double gamma_avg50;    /* mean over voxels with D_ref >= 0.5 max D_ref */
+    double pass50_pct;     /* % of those voxels with gamma < 1              */
+    int64_t n50;           /* number of those voxels                       */
+    float dose_max;        /* max D_ref                                    */
+} dc_gamma_stats;
+
+/*
+ * ref, eval: dose [nz][ny][nx] on `grid` (x fastest); gamma: output of the
+ * same size, or NULL for the statistics only; all three host memory, or
+ * device memory of the current device with DC_DEVICE_PTRS in `flags`
+ * (caller-owned).  dose_pct > 0, dta_cm > 0, search_cm >= dta_cm (<= 64
+ * voxels along each axis).  The work runs on `cuda_stream` (NULL: the legacy
+ * default stream); the call synchronises it and returns the statistics in
+ * *stats (may be NULL).  Results are deterministic.
+ * Errors: DC_EINVAL (NULL arguments, bad sizes or criteria, a reference dose
+ * that is zero everywhere), DC_ENOMEM, DC_ECUDA.
+ */
+dc_status dc_gamma_index(const float* ref, const float* eval, const dc_grid* grid, float dose_pct, float dta_cm,
+                         float search_cm, float* gamma, dc_gamma_stats* stats, void* cuda_stream,
+                         uint32_t flags);
+
 #ifdef __cplusplus
 }
 #endif

@@ -64,3 +64,21 @@ def gamma_stats(gamma, ref):
     r = np.asarray(ref, np.float64).ravel()
     m = r >= 0.5 * r.max()
     return float(g.max()), float(g[m].mean()), float(100.0 * (g[m] < 1.0).mean()), int(m.sum())
+
+
+def gamma_at(ref, ev, spacing, voxels, pct=3.0, dta=0.3, radius=None):
+    """gamma_index at the flat voxel indices `voxels` only (for large grids)."""
+    ref = np.asarray(ref, np.float64)
+    ev = np.asarray(ev, np.float64)
+    radius = 5.0 * dta if radius is None else float(radius)
+    dD = pct / 100.0 * float(ref.max())
+    nz, ny, nx = ref.shape
+    offs, d2 = offsets(spacing, radius)
+    out = np.empty(len(voxels))
+    for n, v in enumerate(np.asarray(voxels, np.int64)):
+        z, y, x = v // (nx * ny), (v // nx) % ny, v % nx
+        xx, yy, zz = x + offs[:, 0], y + offs[:, 1], z + offs[:, 2]
+        inside = (xx >= 0) & (xx < nx) & (yy >= 0) & (yy < ny) & (zz >= 0) & (zz < nz)
+        g2 = d2[inside] / dta ** 2 + (ev[zz[inside], yy[inside], xx[inside]] - ref.flat[v]) ** 2 / dD ** 2
+        out[n] = np.sqrt(min((radius / dta) ** 2, g2.min() if g2.size else np.inf))
+    return out

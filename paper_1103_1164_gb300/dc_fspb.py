@@ -43,6 +43,11 @@ class dc_grid(C.Structure):
                 ("ox", C.c_float), ("oy", C.c_float), ("oz", C.c_float)]
 
 
+class dc_gamma_stats(C.Structure):
+    _fields_ = [("gamma_max", C.c_double), ("gamma_avg50", C.c_double), ("pass50_pct", C.c_double),
+                ("n50", C.c_int64), ("dose_max", C.c_float)]
+
+
 class dc_beam(C.Structure):
     _fields_ = [("gantry_deg", C.c_float), ("couch_deg", C.c_float), ("coll_deg", C.c_float),
                 ("sad", C.c_float), ("iso", C.c_float * 3), ("field_x", C.c_float),
@@ -69,7 +74,7 @@ EXPORTS = ["dc_last_error", "dc_status_str", "dc_fspb_create", "dc_fspb_destroy"
            "dc_mlp_create", "dc_mlp_destroy", "dc_mlp_get_params", "dc_mlp_gradient", "dc_mlp_train",
            "dc_mlp_predict", "dc_fspb_batch_create", "dc_fspb_batch_destroy", "dc_fspb_batch_buffers",
            "dc_fspb_batch_run", "dc_fspb_batch_dose", "dc_fspb_batch_synchronize", "dc_fspb_batch_kernels",
-           "dc_fspb_batch_autotune"]
+           "dc_fspb_batch_autotune", "dc_gamma_index"]
 
 
 def library_path() -> str:
@@ -129,6 +134,8 @@ def load():
     L.dc_fspb_batch_synchronize.argtypes = [vp]
     L.dc_fspb_batch_kernels.argtypes = [vp, u32, C.POINTER(i32)]
     L.dc_fspb_batch_autotune.argtypes = [vp, C.POINTER(i32), C.POINTER(C.c_float)]
+    L.dc_gamma_index.argtypes = [vp, vp, C.POINTER(dc_grid), C.c_float, C.c_float, C.c_float, vp,
+                                 C.POINTER(dc_gamma_stats), vp, u32]
     for name in EXPORTS:
         if name not in ("dc_last_error", "dc_status_str"):
             getattr(L, name).restype = C.c_int
@@ -507,3 +514,26 @@ def dc_fspb_batch_dose(batch: Batch, fluences, doses=None, density=False):
     flag = _same_kind(*flags) | (DC_BATCH_DENSITY if density else 0)
     _check(load().dc_fspb_batch_dose(batch.handle, (C.c_void_p * n)(*fp), (C.c_void_p * n)(*dp), flag))
     return doses
+
+
+def dc_gamma_index(ref, ev, grid, pct=3.0, dta=0.3, search=None, gamma=None, stream=None):
+    """3-D gamma index of the dose ev against the reference dose ref on `grid`
+    (pct % of max ref, dta cm, search radius cm, default 5 dta).  Host arrays
+    or CUDA tensors [nz, ny, nx]; returns (gamma, statistics dict)."""
+    search = 5.0 * dta if search is None else search
+    g = dc_grid(grid.nx, grid.ny, grid.nz, grid.dx, grid.dy, grid.dz, grid.ox, grid.oy, grid.oz)
+    if gamma is None:
+        if _is_torch(ref):
+            import torch
+            gamma = torch.empty_like(ref)
+        else:
+            gamma = np.empty(np.shape(ref), np.float32)
+    pr, f1 = _ptr(ref)
+    pe, f2 = _ptr(ev)
+    pg, f3 = _ptr(gamma)
+    st = dc_gamma_stats()
+    sp = stream if stream is not None else (_current_stream() if f1 else 0)
+    _check(load().dc_gamma_index(pr, pe, C.byref(g), pct, dta, search, pg, C.byref(st), C.c_void_p(sp),
+                                 _same_kind(f1, f2, f3)))
+    return gamma, dict(gamma_max=st.gamma_max, gamma_avg50=st.gamma_avg50, pass50_pct=st.pass50_pct,
+                       n50=int(st.n50), dose_max=st.dose_max)

@@ -74,3 +74,13 @@ def test_stats_definitions():
     assert gmax == 2.0 and n50 == 5
     assert gavg == pytest.approx((0.5 + 1.5 + 0.7 + 2.0 + 0.9) / 5)
     assert p50 == pytest.approx(60.0)
+
+
+def test_gamma_at_matches_full_grid():
+    rng = np.random.default_rng(4)
+    ref = rng.uniform(0, 1, (5, 6, 7))
+    ev = ref + rng.normal(0, 0.05, ref.shape)
+    full = og.gamma_index(ref, ev, (0.2, 0.25, 0.3), pct=2.0, dta=0.25, radius=0.8)
+    vox = rng.choice(ref.size, 40, replace=False)
+    got = og.gamma_at(ref, ev, (0.2, 0.25, 0.3), vox, pct=2.0, dta=0.25, radius=0.8)
+    assert np.allclose(got, full.ravel()[vox], rtol=1e-13)
