@@ -405,6 +405,7 @@ def run_ours(args, world, rank, local, pg):
     forms = run_forms(args, dc, torch, stream, peaks)
     forms["surrogate"] = run_surrogate_form(args, dc, torch, stream)
     forms["batch"] = run_batch_form(args, dc, torch, stream, peak_pairs)
+    forms["gamma"] = run_gamma_form(args, dc, torch, stream, p, rho_d, flu_d)
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, dc, p, plan, pairs, torch)
@@ -548,6 +549,47 @@ def run_surrogate_form(args, dc, torch, stream, k=64):
                                "fallbacks": dc.dc_fspb_lateral_fallbacks(plan)},
             "speedup_64_fluences": t_plain / t_spmm,
             "max_err_vs_plain_over_colmax": err}
+
+
+def run_gamma_form(args, dc, torch, stream, p, rho_d, flu_d):
+    """The 3 %-3 mm gamma index of plain FSPB (no density correction) against
+    DC-FSPB on the thorax plan (dc_gamma_index, device buffers), the paper's
+    accuracy statistics of the density correction's effect; the FP64 oracle
+    on seeded voxels gives its CPU rate."""
+    import dataclasses
+    from oracle import gamma as og
+    ref = torch.empty(p.grid.shape, device="cuda")
+    ev = torch.empty(p.grid.shape, device="cuda")
+    pq = dataclasses.replace(p, comm=dataclasses.replace(p.comm, density_correction=0))
+    for inp, out in ((p, ref), (pq, ev)):
+        plan = dc.dc_fspb_create_from(inp, stream=stream.cuda_stream, device_density=rho_d)
+        dc.dc_fspb_dose(plan, flu_d, out)
+        del plan
+    gamma = torch.empty_like(ref)
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            dc.dc_gamma_index(ref, ev, p.grid, gamma=gamma, stream=stream.cuda_stream)
+        ts = []
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, st = dc.dc_gamma_index(ref, ev, p.grid, gamma=gamma, stream=stream.cuda_stream)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+    ms = float(np.median(ts))
+    V = p.grid.n_voxels
+    out = {"workload": f"FSPB vs DC-FSPB doses of thorax9 ({V} voxels), 3 %-3 mm, search 1.5 cm",
+           "ms": ms, "voxels_per_s": V / (ms * 1e-3), **st}
+    if not args.no_cpu:
+        r, e = ref.cpu().numpy(), ev.cpu().numpy()
+        vox = np.random.default_rng(4).choice(V, 4000, replace=False)
+        t0 = time.perf_counter()
+        want = og.gamma_at(r, e, (p.grid.dx, p.grid.dy, p.grid.dz), vox)
+        dt = time.perf_counter() - t0
+        out["oracle_voxels_per_s"] = vox.size / dt
+        out["max_abs_diff_vs_oracle"] = float(np.abs(gamma.cpu().numpy().ravel()[vox] - want).max())
+    return out
 
 
 def run_batch_form(args, dc, torch, stream, peak_pairs):
