@@ -46,10 +46,10 @@ L2_FLUSH_BYTES = 256 << 20
 # the dose kernel on the thorax9 plan, from an ncu capture of the kernel built
 # from the sources with these SHA-256 digests (profiles/k_pairs_dose_thorax9.md);
 # reported only while the sources are unchanged.
-DOSE_TRAFFIC_BYTES = 110172160 + 20577280
+DOSE_TRAFFIC_BYTES = 110455552 + 20622336
 DOSE_TRAFFIC_SOURCES = {
     "paper_1103_1164_gb300/csrc/k_dose.cu": "43573a455c81c178255291b940ab56b63e2e1be6db51f215a36045d2c295364a",
-    "paper_1103_1164_gb300/csrc/dc_internal.cuh": "a2fa443c5d3f8ce0fc42bb7f49cd38f02ad98089ceacbcc6db221c7b56ced19b",
+    "paper_1103_1164_gb300/csrc/dc_internal.cuh": "2ead58576c533758c30753bf1f63cba61149cf1b82cbc79058f50f4568c86f64",
 }
 
 
@@ -78,7 +78,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--scale", type=float, default=1.0, help="grid scale of the thorax plan")
-    ap.add_argument("--profile", default=None, choices=["dose", "fill", "prep", "spmm", "step"],
+    ap.add_argument("--profile", default=None, choices=["dose", "fill", "prep", "spmm", "step", "table1"],
                     help="small fixed run of one stage for profiler captures (prints no bench line)")
     return ap.parse_args()
 
@@ -100,7 +100,7 @@ def run_profile(args):
         dc.dc_fspb_device_status(plan)
         print(f"profile run done: spmm, {plan.n_voxels} voxels, {plan.n_beamlets} beamlets")
         return
-    p = synth.config2(args.scale)
+    p = synth.table1_case("H5") if args.profile == "table1" else synth.config2(args.scale)
     rho_d = torch.from_numpy(p.rho).cuda()
     flu_d = torch.from_numpy(p.fluence).cuda()
     plan = dc.dc_fspb_create_from(p, device_density=rho_d)
@@ -129,6 +129,10 @@ def run_profile(args):
         vals = torch.empty(pairs, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup + args.steps):
         if args.profile == "dose":
+            dc.dc_fspb_dose(plan, flu_d, dose_d)
+        elif args.profile == "table1":
+            # the largest Table 1 case: density-dependent steps + dose
+            dc.dc_fspb_set_density(plan, rho_d)
             dc.dc_fspb_dose(plan, flu_d, dose_d)
         elif args.profile == "fill":
             dc.dc_fspb_dose_matrix(plan, dc.DC_F32, rowptr, cols, vals)
@@ -406,6 +410,7 @@ def run_ours(args, world, rank, local, pg):
     forms["surrogate"] = run_surrogate_form(args, dc, torch, stream)
     forms["batch"] = run_batch_form(args, dc, torch, stream, peak_pairs)
     forms["gamma"] = run_gamma_form(args, dc, torch, stream, p, rho_d, flu_d)
+    forms["table1"] = run_table1_form(args, dc, torch, stream, flush)
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, dc, p, plan, pairs, torch)
@@ -590,6 +595,91 @@ def run_gamma_form(args, dc, torch, stream, p, rho_d, flu_d):
         out["oracle_voxels_per_s"] = vox.size / dt
         out["max_abs_diff_vs_oracle"] = float(np.abs(gamma.cpu().numpy().ravel()[vox] - want).max())
     return out
+
+
+# Table 4: g-DC-FSPB GPU computation time T_gpu (s) per case on a Tesla C1060
+# (the paper's hardware; context for the synthetic stand-ins, not a target).
+TABLE4_TGPU_S = {"H1": 0.64, "H2": 0.40, "H3": 0.38, "H4": 0.35, "H5": 1.31,
+                 "L1": 0.22, "L2": 0.40, "L3": 0.30, "L4": 0.25, "L5": 0.33}
+
+
+def run_table1_form(args, dc, torch, stream, flush):
+    """The ten synthetic Table 1 cases (128 x 128 x 72-103 at 0.4 x 0.4 x 0.25 cm,
+    5-8 coplanar or non-coplanar beams, 637-10,369 beamlets of 0.2 x 0.5 cm):
+    per case the GPU time of the density-dependent steps plus the dose (the
+    paper's T_gpu: smoothing, beamlet geometry, ray tracing, tables, binning,
+    eq. 1) with the default binning cell and again after dc_fspb_autotune; then,
+    on the tuned plan, the same through pinned host buffers (density and
+    fluence in, dose out: T_gpu + T_tr, host wall clock) and all ten cases as
+    one batch graph."""
+    from paper_1103_1164_gb300 import synth
+    inputs = synth.table1_plans()
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    cases, plans, flus = [], [], []
+    reps = max(3, min(args.steps, 5))
+    for p in inputs:
+        rho_d = torch.from_numpy(p.rho).cuda()
+        flu_d = torch.from_numpy(p.fluence).cuda()
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        plan = dc.dc_fspb_create_from(p, stream=stream.cuda_stream, device_density=rho_d)
+        torch.cuda.synchronize()
+        t_create = (time.perf_counter() - w0) * 1e3
+        dose_d = torch.empty(plan.shape, device="cuda")
+
+        def gpu_step():
+            dc.dc_fspb_set_density(plan, rho_d)
+            dc.dc_fspb_dose(plan, flu_d, dose_d)
+
+        gpu_step()
+        t_gpu = time_on_stream(torch, stream, gpu_step, reps, flush)
+        t_dose = time_on_stream(torch, stream, lambda: dc.dc_fspb_dose(plan, flu_d, dose_d), reps, flush)
+        tuned = dc.dc_fspb_autotune(plan, flu_d)
+        t_gpu_tuned = time_on_stream(torch, stream, gpu_step, reps, flush)
+        t_dose_tuned = time_on_stream(torch, stream, lambda: dc.dc_fspb_dose(plan, flu_d, dose_d), reps, flush)
+        pairs = dc.dc_fspb_pair_count(plan)
+        rho_h, flu_h = pin(p.rho), pin(p.fluence)
+        dose_h = torch.empty(plan.shape, dtype=torch.float32).pin_memory()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            w0 = time.perf_counter()
+            dc.dc_fspb_set_density(plan, rho_h.numpy())
+            dc.dc_fspb_dose(plan, flu_h.numpy(), dose_h.numpy())
+            ts.append((time.perf_counter() - w0) * 1e3)
+        diff = float((dose_h.cuda() - dose_d).abs().max() / dose_d.abs().max())
+        cases.append({"case": p.name, "beams": len(p.beams),
+                      "non_coplanar": any(b.couch_deg != 0.0 for b in p.beams),
+                      "beamlets": plan.n_beamlets, "voxels": plan.n_voxels, "pairs": pairs,
+                      "create_ms": t_create, "t_gpu_ms": t_gpu, "dose_ms": t_dose,
+                      "autotuned": {"tile_cm": tuned[0], "slab_cm": tuned[1], "t_gpu_ms": t_gpu_tuned,
+                                    "dose_ms": t_dose_tuned},
+                      "t_tot_host_buffers_ms": float(np.median(ts)),
+                      "evals_per_s": 2 * pairs / (t_gpu * 1e-3),
+                      "paper_t_gpu_ms_c1060": 1e3 * TABLE4_TGPU_S[p.name],
+                      "host_vs_device_max_diff_over_max": diff})
+        plans.append(plan)
+        flus.append(flu_d)
+    batch = dc.dc_fspb_batch_create(plans, stream=stream.cuda_stream)
+    for j, pl in enumerate(plans):
+        fptr, _ = dc.dc_fspb_batch_buffers(batch, j)
+        dc_view(torch, fptr, pl.n_beamlets).copy_(flus[j])
+    for _ in range(2):
+        dc.dc_fspb_batch_run(batch, density=True)
+    t_batch = time_on_stream(torch, stream, lambda: dc.dc_fspb_batch_run(batch, density=True), reps, flush)
+    t_batch_dose = time_on_stream(torch, stream, lambda: dc.dc_fspb_batch_run(batch), reps, flush)
+    tg = [c["t_gpu_ms"] for c in cases]
+    pairs = sum(c["pairs"] for c in cases)
+    return {"workload": "10 synthetic Table 1 cases (H1-H5 head-and-neck, L1-L5 lung), "
+                        "128x128x72-103 @0.4x0.4x0.25 cm, 0.2x0.5 cm beamlets, ROI 5 cm, "
+                        "density correction on",
+            "cases": cases, "pairs": pairs,
+            "sum_t_gpu_ms": float(sum(tg)), "median_t_gpu_ms": float(np.median(tg)),
+            "paper_median_t_gpu_ms_c1060": 1e3 * float(np.median(list(TABLE4_TGPU_S.values()))),
+            "batch_graph": {"full_plans_ms": t_batch, "dose_ms": t_batch_dose,
+                            "evals_per_s": 2 * pairs / (t_batch * 1e-3),
+                            "kernels_per_replay": dc.dc_fspb_batch_kernels(batch)}}
 
 
 def run_batch_form(args, dc, torch, stream, peak_pairs):

@@ -84,7 +84,7 @@ dc::PlanView dc_plan::view() const
 static void free_plan(dc_plan* p)
 {
     if (!p) return;
-    void* bufs[] = {p->d_rho, p->d_rhos, p->d_tmp, p->d_fac, p->d_beams, p->d_bl, p->d_theta, p->d_ray,
+    void* bufs[] = {p->d_rho, p->d_rhos, p->d_tmp, p->d_fac, p->d_beams, p->d_bl, p->d_theta, p->d_ray, p->d_lio,
                     p->d_tab, p->d_arow, p->d_tabm, p->d_A, p->d_water, p->d_dens, p->d_beamin, p->d_fluence,
                     p->d_dose, p->d_rowcount, p->d_rowptr, p->d_scan_tmp, p->d_mcols, p->d_mvals,
                     p->d_bin, p->d_bounds, p->d_cellof, p->d_hist, p->d_nitems, p->d_bstart, p->d_bscan,
@@ -308,6 +308,7 @@ static dc_status create_impl(dc_plan* p, const float* ct, uint32_t flags)
     DC_CUDA(dalloc(&p->d_bl, p->B));
     DC_CUDA(dalloc(&p->d_theta, p->B));
     DC_CUDA(dalloc(&p->d_ray, 8 * (size_t)p->B));
+    DC_CUDA(dalloc(&p->d_lio, p->B));
     DC_CUDA(dalloc(&p->d_tab, 2 * (size_t)p->B * p->Kmax));
     DC_CUDA(dalloc(&p->d_arow, (size_t)p->B * c.a_nt));
     p->merged = c.w_dt == p->d;

@@ -130,6 +130,7 @@ struct dc_plan {
     dc::BeamletDev* d_bl = nullptr;
     float* d_theta = nullptr;
     double* d_ray = nullptr;         // [B][8]: FP64 source (3) and direction (3) of each beamlet axis
+    float2* d_lio = nullptr;         // [B]: (L_in, L_out) of each axis, L_out < 0 if it misses the body
     float4* d_tab = nullptr;
     float2* d_arow = nullptr;
     float4* d_tabm = nullptr;        // merged depth + water tables (only when w_dt == d)

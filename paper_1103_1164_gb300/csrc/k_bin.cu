@@ -20,40 +20,54 @@ namespace {
 
 constexpr float kBig = 3.0e38f;
 
-// Per (beam, tile): min L_in and max L_out of the hit beamlets near the tile.
-__global__ void __launch_bounds__(256) k_bev_bounds(const BinGeom* __restrict__ G, int n_beams,
-                                                    const BeamDev* __restrict__ beams,
-                                                    const BeamletDev* __restrict__ bl, float bx, float by,
-                                                    float2* __restrict__ bounds, int tiles_max)
+// Per (beam, tile): min L_in and max L_out of the hit beamlets whose centre
+// lies within rw_max + half the tile diagonal of the tile's centre (in the
+// isocentre plane).  One warp per tile: the lanes run along each row of
+// beamlets inside that disc, then a warp reduction.
+constexpr int kBoundsWarps = 8;
+__global__ void __launch_bounds__(32 * kBoundsWarps) k_bev_bounds(const BinGeom* __restrict__ G, int n_beams,
+                                                                  const BeamDev* __restrict__ beams,
+                                                                  const float2* __restrict__ lio, float bx,
+                                                                  float by, float2* __restrict__ bounds,
+                                                                  int tiles_max)
 {
     const int b = blockIdx.y;
     if (b >= n_beams) return;
+    const int lane = threadIdx.x & 31;
     const BinGeom g = G[b];
     const int ntile = g.nta * g.ntc;
     const int M = beams[b].M, N = beams[b].N, first = beams[b].first;
     const float hfx = beams[b].half_fx, hfy = beams[b].half_fy;
     const float reach = g.rw_max + 0.7072f * g.tile;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntile; t += gridDim.x * blockDim.x) {
+    const int nwarps = gridDim.x * kBoundsWarps;
+    for (int t = blockIdx.x * kBoundsWarps + (threadIdx.x >> 5); t < ntile; t += nwarps) {
         const int ta = t % g.nta, tc = t / g.nta;
         const float ca = g.a0 + (ta + 0.5f) * g.tile, cc = g.c0 + (tc + 0.5f) * g.tile;
         const int n0 = max(0, (int)floorf((cc - reach + hfy) / by - 0.5f));
         const int n1 = min(N - 1, (int)ceilf((cc + reach + hfy) / by - 0.5f));
-        const int m0 = max(0, (int)floorf((ca - reach + hfx) / bx - 0.5f));
-        const int m1 = min(M - 1, (int)ceilf((ca + reach + hfx) / bx - 0.5f));
         float lmin = kBig, lmax = -kBig;
         for (int n = n0; n <= n1; ++n) {
             const float dc_ = cc - (-hfy + (n + 0.5f) * by);
-            for (int m = m0; m <= m1; ++m) {
+            // the row's beamlets within the disc's chord, one beamlet of slack
+            // each side (the exact test below decides)
+            const float h = sqrtf(fmaxf(reach * reach - dc_ * dc_, 0.f));
+            const int m0 = max(0, (int)floorf((ca - h + hfx) / bx - 1.5f));
+            const int m1 = min(M - 1, (int)ceilf((ca + h + hfx) / bx + 0.5f));
+            for (int m = m0 + lane; m <= m1; m += 32) {
                 const float da = ca - (-hfx + (m + 0.5f) * bx);
                 if (da * da + dc_ * dc_ > reach * reach) continue;
-                const BeamletDev& r = bl[first + n * M + m];
-                const float lout = __ldg(&r.exy_z.z);
-                if (lout < 0.f) continue;            // axis misses the body
-                lmin = fminf(lmin, __ldg(&r.n_lin.w));
-                lmax = fmaxf(lmax, lout);
+                const float2 r = __ldg(lio + first + n * M + m);
+                if (r.y < 0.f) continue;             // axis misses the body
+                lmin = fminf(lmin, r.x);
+                lmax = fmaxf(lmax, r.y);
             }
         }
-        bounds[(size_t)b * tiles_max + t] = make_float2(lmin, lmax);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lmin = fminf(lmin, __shfl_xor_sync(0xffffffffu, lmin, o));
+            lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+        }
+        if (lane == 0) bounds[(size_t)b * tiles_max + t] = make_float2(lmin, lmax);
     }
 }
 
@@ -237,9 +251,9 @@ cudaError_t launch_binning(const dc_plan* p)
     const PlanView P = p->view();
     cudaError_t e = cudaMemsetAsync(p->d_hist, 0, sizeof(int32_t) * (size_t)p->n_beams * p->cells_max, p->stream);
     if (e != cudaSuccess) return e;
-    dim3 gb((p->tiles_max + 255) / 256, p->n_beams);
-    k_bev_bounds<<<gb, 256, 0, p->stream>>>(p->d_bin, p->n_beams, p->d_beams, p->d_bl, p->bx, p->by,
-                                            p->d_bounds, p->tiles_max);
+    dim3 gb((p->tiles_max + kBoundsWarps - 1) / kBoundsWarps, p->n_beams);
+    k_bev_bounds<<<gb, 32 * kBoundsWarps, 0, p->stream>>>(p->d_bin, p->n_beams, p->d_beams, p->d_lio, p->bx,
+                                                          p->by, p->d_bounds, p->tiles_max);
     int gx = (int)std::min<int64_t>((p->V + 255) / 256, 2048);
     dim3 gv(gx, p->n_beams);
     k_bin_hist<<<gv, 256, 0, p->stream>>>(P, p->d_bin, p->d_bounds, p->tiles_max, p->cells_max, p->d_cellof,

@@ -91,6 +91,7 @@ struct BeamletArgs {
     BeamletDev* out_bl;
     float* out_theta;
     double* ray;             // [B][8] FP64 axis source and direction (k_beamlets -> k_trace)
+    float2* lio;             // [B] (L_in, L_out) for the binning bounds (k_trace)
     float4* tab;
     int first[kMaxBeams + 1];
     int M[kMaxBeams];
@@ -431,127 +432,195 @@ __global__ void __launch_bounds__(kBeamletThreads) k_beamlets(const BeamletArgs 
 }
 
 // ---------------------------------------------------------------------------
-// Steps 4-6 with one warp per beamlet.  The FP64 walk is latency-bound, so
-// the ray [amin, amax] inside the grid is cut into 32 pieces of equal length
-// and lane j walks piece j, keeping its segments (end parameter, density) in
-// shared memory.  Warp reductions give the body entry L_in (start of the first
-// segment denser than the surface threshold) and exit L_out (end of the last),
-// an exclusive warp scan of the pieces' integrals of rho, b_1(rho), b_2(rho)
-// from L_in gives each piece its starting values, and each lane then emits the
-// depth samples L_in + k d that fall in its piece, with the same per-segment
-// arithmetic as a single walk (only the order of the sums differs).  A ray
-// with more segments in a piece than the buffer holds is traced by one lane
-// with the single walk (trace_beamlet).
+// Steps 4-6 with one warp per beamlet.  The ray [amin, amax] inside the grid
+// is cut into 32 pieces of equal length and lane j walks piece j, keeping its
+// segments (end, density) in shared memory.  FP64 only places each piece on
+// the ray (its first voxel and first plane crossings); the walk itself runs
+// in FP32 offsets from the piece's start, which stay below the piece length,
+// so their rounding is far below that of the absolute FP64 walk's results
+// once stored in FP32 (this GPU's FP64 pipe runs at a small fraction of its
+// FP32 rate and would otherwise bound the kernel).  Ballots give the body
+// entry L_in (start of the first segment denser than the surface threshold)
+// and exit L_out (end of the last), an exclusive warp scan of the pieces'
+// integrals of rho, b_1(rho), b_2(rho) from L_in gives each piece its starting
+// values, and each lane then emits the depth samples L_in + k d of its piece.
+// The sample indices are split between the lanes exactly (in FP64), so every
+// sample is written once.  A ray with more segments in a piece than the buffer
+// holds is traced by one lane with the single FP64 walk (trace_beamlet).
 constexpr int kTraceWarps = 4;
 constexpr int kSegCap = 24;     // segments per piece (rays of up to ~700 voxel crossings)
 
-template <typename Acc>
-__device__ __forceinline__ Acc warp_exclusive_sum(Acc x, int lane)
+__device__ __forceinline__ float warp_exclusive_sum(float x, int lane)
 {
-    Acc incl = x;
+    float incl = x;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const Acc y = __shfl_up_sync(0xffffffffu, incl, o);
+        const float y = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += y;
     }
     return incl - x;
 }
 
+// Walk state of one piece: plane crossings as FP32 offsets from its start.
+struct PieceWalk {
+    int idx[3], step[3];
+    float next[3], delta[3];
+    float len;
+};
+
+__device__ void piece_init(const BeamletArgs& A, const double* s, const double* n, const double* inv_n,
+                           double a_start, double a_end, PieceWalk& w)
+{
+    Walk f;
+    walk_from(A, s, n, inv_n, a_start, a_end, f);
+    for (int a = 0; a < 3; ++a) {
+        w.idx[a] = f.idx[a];
+        w.step[a] = f.step[a];
+        const bool par = f.step[a] == 0;
+        w.next[a] = par ? 3.0e38f : (float)(f.anext[a] - a_start);
+        w.delta[a] = par ? 0.f : (float)f.adelta[a];
+    }
+    w.len = (float)(a_end - a_start);
+}
+
+template <typename F>
+__device__ void piece_run(const BeamletArgs& A, const PieceWalk& w, F&& visit)
+{
+    // the state in scalars (no dynamically indexed arrays: registers only)
+    int i0 = w.idx[0], i1 = w.idx[1], i2 = w.idx[2];
+    float n0 = w.next[0], n1 = w.next[1], n2 = w.next[2];
+    const int maxit = A.nx + A.ny + A.nz + 8;
+    float cur = 0.f;
+    for (int it = 0; it < maxit; ++it) {
+        float an = n0;
+        int ax = 0;
+        if (n1 < an) { an = n1; ax = 1; }
+        if (n2 < an) { an = n2; ax = 2; }
+        const bool last = an >= w.len;
+        if (last) an = w.len;
+        if (an > cur) visit(cur, an, ((int64_t)i2 * A.ny + i1) * A.nx + i0);
+        if (last) return;
+        if (ax == 0) {
+            i0 += w.step[0];
+            if (i0 < 0 || i0 >= A.nx) return;
+            n0 += w.delta[0];
+        } else if (ax == 1) {
+            i1 += w.step[1];
+            if (i1 < 0 || i1 >= A.ny) return;
+            n1 += w.delta[1];
+        } else {
+            i2 += w.step[2];
+            if (i2 < 0 || i2 >= A.nz) return;
+            n2 += w.delta[2];
+        }
+        cur = an;
+    }
+}
+
 // Returns false if a piece overflowed its segment buffer (nothing written).
-template <typename Acc>
 __device__ bool trace_warp(const BeamletArgs& A, const double* s, const double* n, const double* inv_n,
-                           const Walk& w0, int lane,
-                           double* __restrict__ sa1, float* __restrict__ sr, float4* __restrict__ tab, double& L_in,
-                           double& L_out, int& K)
+                           const Walk& w0, int lane, float2* __restrict__ seg, float4* __restrict__ tab,
+                           double& L_in, double& L_out, int& K)
 {
     const double amin = w0.acur, amax = w0.amax;
     const double span = (amax - amin) / 32.0;
+    // piece j starts at amin + j span; the end of piece j is the start of
+    // piece j + 1 (the same expression, so the same value)
     const double a_start = amin + lane * span;
     const double a_end = lane == 31 ? amax : amin + (lane + 1) * span;
     const float surf = A.rho_surf;
 
     // 1. walk the piece
     int ns = 0;
-    double first_a = 1e300, last_a = -1.0;
-    Walk w;
-    walk_from(A, s, n, inv_n, a_start, a_end, w);
-    walk_run(A, w, [&](double a0, double a1, int64_t vox) {
+    bool dense = false;
+    float first_r = 0.f, last_r = 0.f;
+    PieceWalk w;
+    piece_init(A, s, n, inv_n, a_start, a_end, w);
+    piece_run(A, w, [&](float a0, float a1, int64_t vox) {
         const float r = __ldg(A.rho + vox);
-        if (ns < kSegCap) {
-            sa1[ns] = a1;
-            sr[ns] = r;
-        }
+        if (ns < kSegCap) seg[ns] = make_float2(a1, r);
         ++ns;
         if (r > surf) {
-            first_a = fmin(first_a, a0);
-            last_a = a1;
+            if (!dense) first_r = a0;
+            dense = true;
+            last_r = a1;
         }
     });
     if (__any_sync(0xffffffffu, ns > kSegCap)) return false;
 
-    // 2. body entry and exit of the whole ray
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        first_a = fmin(first_a, __shfl_xor_sync(0xffffffffu, first_a, o));
-        last_a = fmax(last_a, __shfl_xor_sync(0xffffffffu, last_a, o));
-    }
+    // 2. body entry and exit of the whole ray: the first dense segment of the
+    // first lane that has one, the last dense segment of the last
+    const unsigned dm = __ballot_sync(0xffffffffu, dense);
     K = 0;
-    if (first_a >= 1e299) return true;   // the axis misses the body
-    L_in = first_a;
-    L_out = last_a;
+    if (dm == 0) return true;   // the axis misses the body
+    const int lf = __ffs(dm) - 1, ll = 31 - __clz(dm);
+    const float fr = __shfl_sync(0xffffffffu, first_r, lf);
+    const float lr = __shfl_sync(0xffffffffu, last_r, ll);
+    L_in = (amin + lf * span) + (double)fr;
+    L_out = (amin + ll * span) + (double)lr;
     const double d = A.d;
     K = max(2, (int)ceil((L_out - L_in) / d) + 1);
     K = min(K, A.Kmax);
 
     // 3. this piece's integrals from L_in, and the piece's starting values
-    Acc pT = 0, p1 = 0, p2 = 0;
-    double a0 = a_start;
+    const float Lrel = (float)(L_in - a_start);
+    float pT = 0.f, p1 = 0.f, p2 = 0.f;
+    float a0 = 0.f;
     for (int q = 0; q < ns; ++q) {
-        const double a1 = sa1[q];
-        if (a1 > L_in) {
-            const float r = sr[q];
-            const Acc len = (Acc)(a1 - fmax(a0, L_in));
-            pT += (Acc)r * len;
-            p1 += (Acc)lut_dens(A, 4, r) * len;
-            p2 += (Acc)lut_dens(A, 5, r) * len;
+        const float2 sg = seg[q];
+        if (sg.x > Lrel) {
+            const float len = sg.x - fmaxf(a0, Lrel);
+            pT = fmaf(sg.y, len, pT);
+            p1 = fmaf(lut_dens(A, 4, sg.y), len, p1);
+            p2 = fmaf(lut_dens(A, 5, sg.y), len, p2);
         }
-        a0 = a1;
+        a0 = sg.x;
     }
-    Acc cT = warp_exclusive_sum(pT, lane), c1 = warp_exclusive_sum(p1, lane), c2 = warp_exclusive_sum(p2, lane);
+    float cT = warp_exclusive_sum(pT, lane), c1 = warp_exclusive_sum(p1, lane), c2 = warp_exclusive_sum(p2, lane);
 
-    // 4. the samples L_in + k d in [max(a_start, L_in), a_end) (the last piece
-    // also takes those past the end of the ray)
-    const double lo0 = fmax(a_start, L_in);
-    int k = max(0, (int)ceil((lo0 - L_in) * A.inv_d));   // then made exact:
-    while (k > 0 && L_in + (k - 1) * d >= lo0) --k;
-    while (L_in + k * d < lo0) ++k;
-    a0 = a_start;
-    for (int q = 0; q < ns && k < K; ++q) {
-        const double a1 = sa1[q];
-        if (a1 > L_in) {
-            const double lo = fmax(a0, L_in);
-            const float r = sr[q];
-            const Acc vr = (Acc)r, v1 = (Acc)lut_dens(A, 4, r), v2 = (Acc)lut_dens(A, 5, r);
-            while (k < K) {
-                const double sk = L_in + k * d;
-                if (sk > a1 || (lane < 31 && sk >= a_end)) break;
-                const Acc len = (Acc)(sk - lo);
-                tab[2 * k] = make_float4((float)(cT + vr * len), 0.f, (float)(c1 + v1 * len), 0.f);
-                tab[2 * k + 1] = make_float4((float)(c2 + v2 * len), 0.f, 0.f, 0.f);
+    // 4. the samples of this piece: k in [k_lo, k_hi), k_lo the least k >= 0
+    // with L_in + k d >= a_start, k_hi the next lane's k_lo (lane 31: K, the
+    // samples past the end of the ray included); positions as FP32 offsets
+    // from a_start
+    int k_lo = 0;
+    if (a_start > L_in) {
+        k_lo = (int)ceil((a_start - L_in) * A.inv_d);
+        while (k_lo > 0 && L_in + (k_lo - 1) * d >= a_start) --k_lo;
+        while (L_in + k_lo * d < a_start) ++k_lo;
+    }
+    int k_hi = __shfl_down_sync(0xffffffffu, k_lo, 1);
+    if (lane == 31) k_hi = K;
+    k_hi = min(k_hi, K);
+    const float base = (float)((L_in + k_lo * d) - a_start);
+    const float df = (float)d;
+    int k = k_lo;
+    a0 = 0.f;
+    for (int q = 0; q < ns && k < k_hi; ++q) {
+        const float2 sg = seg[q];
+        if (sg.x > Lrel) {
+            const float lo = fmaxf(a0, Lrel);
+            const float v1 = lut_dens(A, 4, sg.y), v2 = lut_dens(A, 5, sg.y);
+            while (k < k_hi) {
+                const float sk = fmaf((float)(k - k_lo), df, base);
+                if (sk > sg.x) break;
+                const float len = sk - lo;
+                tab[2 * k] = make_float4(fmaf(sg.y, len, cT), 0.f, fmaf(v1, len, c1), 0.f);
+                tab[2 * k + 1] = make_float4(fmaf(v2, len, c2), 0.f, 0.f, 0.f);
                 ++k;
             }
-            const Acc len = (Acc)(a1 - lo);
-            cT += vr * len;
-            c1 += v1 * len;
-            c2 += v2 * len;
+            const float len = sg.x - lo;
+            cT = fmaf(sg.y, len, cT);
+            c1 = fmaf(v1, len, c1);
+            c2 = fmaf(v2, len, c2);
         }
-        a0 = a1;
+        a0 = sg.x;
     }
-    if (lane == 31)
-        for (; k < K; ++k) {
-            tab[2 * k] = make_float4((float)cT, 0.f, (float)c1, 0.f);
-            tab[2 * k + 1] = make_float4((float)c2, 0.f, 0.f, 0.f);
-        }
+    // past the last segment: the samples beyond the end of the ray (lane 31),
+    // or within rounding of the piece's end
+    for (; k < k_hi; ++k) {
+        tab[2 * k] = make_float4(cT, 0.f, c1, 0.f);
+        tab[2 * k + 1] = make_float4(c2, 0.f, 0.f, 0.f);
+    }
     __syncwarp();
 
     // 5. slopes to the next sample (zero at K - 1): read, then write
@@ -584,8 +653,7 @@ __device__ bool trace_warp(const BeamletArgs& A, const double* s, const double* 
 
 __global__ void __launch_bounds__(32 * kTraceWarps) k_trace(const BeamletArgs A)
 {
-    __shared__ double s_a1[kTraceWarps][32][kSegCap];
-    __shared__ float s_r[kTraceWarps][32][kSegCap];
+    __shared__ float2 s_seg[kTraceWarps][32][kSegCap];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int i = blockIdx.x * kTraceWarps + warp;
     if (i >= A.B) return;   // whole warps
@@ -598,13 +666,9 @@ __global__ void __launch_bounds__(32 * kTraceWarps) k_trace(const BeamletArgs A)
     double L_in = 0, L_out = 0;
     if (walk_init(A, s, n, inv_n, w)) {
         float4* tb = A.tab + 2 * (size_t)i * A.Kmax;
-        const bool dbl = w.amax - w.acur > 40.0;
-        const bool ok = dbl ? trace_warp<double>(A, s, n, inv_n, w, lane, s_a1[warp][lane], s_r[warp][lane], tb,
-                                                 L_in, L_out, K)
-                            : trace_warp<float>(A, s, n, inv_n, w, lane, s_a1[warp][lane], s_r[warp][lane], tb,
-                                                L_in, L_out, K);
+        const bool ok = trace_warp(A, s, n, inv_n, w, lane, s_seg[warp][lane], tb, L_in, L_out, K);
         if (!ok && lane == 0) {
-            if (dbl)
+            if (w.amax - w.acur > 40.0)
                 trace_beamlet<double>(A, w, tb, L_in, L_out, K);
             else
                 trace_beamlet<float>(A, w, tb, L_in, L_out, K);
@@ -622,6 +686,7 @@ __global__ void __launch_bounds__(32 * kTraceWarps) k_trace(const BeamletArgs A)
         r.exy_z.z = hit ? (float)L_out : -1.0f;
         r.meta.x = K;
         r.meta.z = hit;
+        A.lio[i] = make_float2((float)L_in, hit ? (float)L_out : -1.0f);
     }
 }
 
@@ -711,6 +776,7 @@ cudaError_t launch_beamlets(const dc_plan* p)
     A.out_theta = p->d_theta;
     A.tab = p->d_tab;
     A.ray = p->d_ray;
+    A.lio = p->d_lio;
     for (int b = 0; b < p->n_beams; ++b) {
         A.first[b] = p->first[b];
         A.M[b] = p->M[b];

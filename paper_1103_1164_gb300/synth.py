@@ -205,12 +205,15 @@ def thorax_phantom(g: Grid, seed: int) -> np.ndarray:
     return _to_zyx(rho)
 
 
-def head_neck_phantom(g: Grid, seed: int) -> np.ndarray:
-    """Water cylinder with air cavities, bone and a lung base (head-and-neck-like)."""
+def head_neck_phantom(g: Grid, seed: int, radius: float = None) -> np.ndarray:
+    """Water cylinder with air cavities, bone and a lung base (head-and-neck-like).
+
+    The cylinder's radius is ``radius`` cm, else 0.42 of the grid's smaller
+    transverse extent."""
     rng = np.random.default_rng(seed)
     X, Y, Z = _mesh(g)
     ext = np.array([g.nx * g.dx, g.ny * g.dy, g.nz * g.dz])
-    rad = 0.42 * min(ext[0], ext[1])
+    rad = 0.42 * min(ext[0], ext[1]) if radius is None else float(radius)
     rho = np.full_like(X, 0.001)
     body = X ** 2 + Y ** 2 <= rad ** 2
     rho[body] = 1.0
@@ -334,3 +337,93 @@ def small_plan(seed: int, n=(12, 10, 8), vox=0.5, n_beams=2, field=2.0, beamlet=
     p = Plan(f"small{seed}", g, rho, beams, beamlet, by, comm, np.zeros(0, np.float32))
     p.fluence = uniform_fluence(p.n_beamlets, seed + 1)
     return p
+
+
+# ---------------------------------------------------------------------------
+# The ten evaluation cases of Table 1, synthetic
+# ---------------------------------------------------------------------------
+
+# Table 1 (Section 2.3): case, site, number of beams, non-coplanar, number of
+# beamlets, number of voxels (all 128 x 128 in x, y).  The tumour position
+# (x, y, z in cm, patient frame) is this module's choice, placed by the site
+# the table names; lung tumours are water-density spheres inside a lung.
+TABLE1 = (
+    ("H1", "parotid", 8, True, 7264, 72, (4.0, -1.0, 0.0)),
+    ("H2", "hypopharynx", 7, True, 4429, 72, (0.0, 1.0, -2.0)),
+    ("H3", "nasal cavity", 8, True, 3381, 72, (0.0, -4.0, 3.0)),
+    ("H4", "parotid", 5, False, 4179, 72, (-4.0, -1.0, 0.0)),
+    ("H5", "larynx", 7, True, 10369, 72, (0.0, -2.0, -1.0)),
+    ("L1", "left lung, lower lobe, near the pleura", 6, False, 637, 80, (9.0, 0.0, -4.0)),
+    ("L2", "right lung, lower lobe, paravertebral", 6, False, 1720, 103, (-3.5, 4.0, -4.0)),
+    ("L3", "left lung, upper lobe, near the pleura", 5, False, 921, 80, (9.0, -1.0, 4.0)),
+    ("L4", "right lung, upper lobe, near the heart", 7, False, 841, 80, (-3.0, -1.0, 3.0)),
+    ("L5", "left lung, middle", 5, False, 686, 80, (6.5, 0.0, 0.0)),
+)
+TABLE1_VOXEL = (0.4, 0.4, 0.25)       # cm, the CT resolution of Section 2.3
+TABLE1_BEAMLET = (0.2, 0.5)           # cm, 0.2 cm along the leaf motion (x)
+
+
+def _table1_fields(rng, n_beamlets, n_beams, bx, by):
+    """Per-beam (field_x, field_y) whose beamlet counts sum to about n_beamlets:
+    near-square fields, per-beam targets jittered by +-20 %, the last beam's
+    shape (aspect 0.7-1.4) chosen to close the gap best."""
+    share = rng.uniform(0.8, 1.2, size=n_beams)
+    share *= n_beamlets / share.sum()
+    fields, done = [], 0
+    for b in range(n_beams):
+        t = share[b] if b < n_beams - 1 else max(n_beamlets - done, 1)
+        ny0 = max(1, int(round(math.sqrt(t * bx / by))))
+        shapes = [(max(1, int(round(t / ny))), ny) for ny in
+                  (range(max(1, ny0 - 3), ny0 + 4) if b == n_beams - 1 else (ny0,))]
+        square = [s for s in shapes if 0.7 <= (s[0] * bx) / (s[1] * by) <= 1.4] or shapes
+        nx, ny = min(square, key=lambda s: abs(s[0] * s[1] - t))
+        fields.append((nx * bx, ny * by))
+        done += nx * ny
+    return fields
+
+
+def table1_case(name: str) -> Plan:
+    """A synthetic stand-in for one of the ten clinical cases of Table 1.
+
+    Grid 128 x 128 x nz at 0.4 x 0.4 x 0.25 cm; head-and-neck cases use a
+    9 cm-radius neck phantom, lung cases the thorax phantom with a 1.5 cm
+    water-density tumour at the case's site.  Beams: SAD 100 cm, isocentre at
+    the tumour, gantry angles evenly spread from a random start (coplanar) or,
+    for the non-coplanar cases, every other beam with a couch rotation of
+    15-45 degrees and a collimator rotation within +-15 degrees.  Beamlets are
+    0.2 x 0.5 cm and the rectangular fields give about the case's beamlet
+    count; fluence U[0, 1] per beamlet.  Commissioning as for the other
+    workloads (ROI radius 5 cm, density correction on).
+    """
+    idx = [c[0] for c in TABLE1].index(name)
+    case, _, nb, noncop, n_bl, nz, tumour = TABLE1[idx]
+    seed = 1100 + idx
+    rng = np.random.default_rng(seed)
+    g = centred_grid(128, 128, nz, *TABLE1_VOXEL)
+    if case.startswith("H"):
+        rho = head_neck_phantom(g, seed, radius=9.0)
+    else:
+        rho = thorax_phantom(g, seed)
+        X, Y, Z = _mesh(g)
+        ball = (X - tumour[0]) ** 2 + (Y - tumour[1]) ** 2 + (Z - tumour[2]) ** 2 <= 1.5 ** 2
+        rho[_to_zyx(ball.astype(np.float32)) > 0.5] = 1.0
+    bx, by = TABLE1_BEAMLET
+    fields = _table1_fields(rng, n_bl, nb, bx, by)
+    start = float(rng.uniform(0.0, 360.0 / nb))
+    beams = []
+    for b in range(nb):
+        gantry = (start + 360.0 * b / nb + float(rng.uniform(-10.0, 10.0))) % 360.0
+        couch = coll = 0.0
+        if noncop and b % 2 == 1:
+            couch = float(rng.choice([-1.0, 1.0]) * rng.uniform(15.0, 45.0))
+            coll = float(rng.uniform(-15.0, 15.0))
+        beams.append(Beam(gantry, 100.0, tumour, fields[b][0], fields[b][1], couch, coll))
+    comm = make_commissioning(COEFF_SEED, roi_radius=5.0)
+    p = Plan(case, g, rho, beams, bx, by, comm, np.zeros(0, np.float32))
+    p.fluence = uniform_fluence(p.n_beamlets, FLUENCE_SEED + seed)
+    return p
+
+
+def table1_plans() -> List[Plan]:
+    """All ten synthetic Table 1 cases, H1-H5 then L1-L5."""
+    return [table1_case(c[0]) for c in TABLE1]
