@@ -22,15 +22,15 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c with gcc (-O2, OpenMP, IEEE double: no fast-math)."""
-    src = os.path.join(_HERE, "oracle.c")
+    """Compile oracle.c and fluence.c with gcc (-O2, OpenMP, IEEE double: no fast-math)."""
+    srcs = [os.path.join(_HERE, n) for n in ("oracle.c", "fluence.c")]
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(src)):
+            and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(s) for s in srcs)):
         return _LIB_PATH
     os.makedirs(_BUILD, exist_ok=True)
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
-                           "-D_DEFAULT_SOURCE", "-o", tmp, src, "-lm"])
+                           "-D_DEFAULT_SOURCE", "-o", tmp, *srcs, "-lm"])
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 

@@ -427,3 +427,100 @@ def table1_case(name: str) -> Plan:
 def table1_plans() -> List[Plan]:
     """All ten synthetic Table 1 cases, H1-H5 then L1-L5."""
     return [table1_case(c[0]) for c in TABLE1]
+
+
+# ---------------------------------------------------------------------------
+# MLC leaf sequences (the input from which Section 2.3 makes the fluence maps)
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class LeafSequence:
+    """One beam's leaf sequence in the collimator frame of the isocentre plane.
+
+    edges [n_leaves + 1]       leaf-pair boundaries along y (cm, increasing)
+    mu    [n_cp]               cumulative meterset at each control point
+    left, right [n_cp][n_leaves]  leaf tip positions along x (cm), left <= right;
+                               tips move linearly in meterset between control
+                               points (a step-and-shoot segment is two control
+                               points with the same positions, the moves between
+                               segments happen at a repeated meterset)
+    jaws  (x1, x2, y1, y2)     collimator jaws (cm)
+    transmission               fraction of the fluence through closed leaves
+    """
+    edges: np.ndarray
+    mu: np.ndarray
+    left: np.ndarray
+    right: np.ndarray
+    jaws: tuple
+    transmission: float = 0.0
+
+    @property
+    def n_leaves(self) -> int:
+        return int(len(self.edges) - 1)
+
+    @property
+    def n_cp(self) -> int:
+        return int(len(self.mu))
+
+
+def leaf_edges(field_y: float, width: float = 0.5, extra: int = 2, offset: float = 0.0) -> np.ndarray:
+    """Leaf-pair boundaries of equal width covering [-field_y/2, field_y/2] plus
+    ``extra`` leaves on each side, shifted by ``offset`` cm."""
+    n = int(math.ceil(field_y / width)) + 2 * extra
+    return (offset - 0.5 * n * width + width * np.arange(n + 1)).astype(np.float32)
+
+
+def sliding_window(rng, field_x, field_y, n_cp=64, mu_total=100.0, width=0.5, min_gap=0.1,
+                   offset=0.0, transmission=0.0, jaw_margin=0.0) -> LeafSequence:
+    """Unidirectional sliding-window sequence: each leaf pair starts closed at
+    the field's -x side and ends closed past its +x side; between control
+    points (equal meterset steps) each tip advances by a random non-negative
+    amount, the right tip first, with the gap kept >= min_gap."""
+    edges = leaf_edges(field_y, width, offset=offset)
+    nl = len(edges) - 1
+    x0, x1 = -0.5 * field_x - 0.5, 0.5 * field_x + 0.5
+    inc_r = rng.gamma(0.7, 1.0, size=(n_cp - 1, nl))
+    inc_l = rng.gamma(0.7, 1.0, size=(n_cp - 1, nl))
+    r = np.vstack([np.zeros((1, nl)), np.cumsum(inc_r, 0)])
+    l = np.vstack([np.zeros((1, nl)), np.cumsum(inc_l, 0)])
+    r = x0 + min_gap + (x1 - x0 - min_gap) * r / r[-1]
+    l = x0 + (x1 - x0 - min_gap) * l / l[-1]
+    l = np.minimum(l, r - min_gap)
+    mu = np.linspace(0.0, mu_total, n_cp)
+    jaws = (-0.5 * field_x - jaw_margin, 0.5 * field_x + jaw_margin,
+            -0.5 * field_y - jaw_margin, 0.5 * field_y + jaw_margin)
+    return LeafSequence(edges, mu.astype(np.float32), l.astype(np.float32), r.astype(np.float32),
+                        tuple(float(v) for v in jaws), float(transmission))
+
+
+def step_and_shoot(rng, field_x, field_y, n_seg=5, mu_total=100.0, width=0.5, offset=0.0,
+                   transmission=0.0, jaw_margin=0.0) -> LeafSequence:
+    """Step-and-shoot sequence: n_seg random apertures (per leaf pair a random
+    open interval inside the field, some pairs closed), each delivered with a
+    random share of the meterset; leaves move between segments at a repeated
+    meterset value."""
+    edges = leaf_edges(field_y, width, offset=offset)
+    nl = len(edges) - 1
+    w = rng.uniform(0.2, 1.0, size=n_seg)
+    cum = np.concatenate([[0.0], np.cumsum(w / w.sum() * mu_total)])
+    mu, L, R = [], [], []
+    for s in range(n_seg):
+        a = rng.uniform(-0.6, 0.5, size=nl) * field_x
+        b = a + rng.uniform(0.0, 0.8, size=nl) * field_x
+        closed = rng.uniform(size=nl) < 0.2
+        b[closed] = a[closed]
+        for k in (0, 1):
+            mu.append(cum[s + k])
+            L.append(a)
+            R.append(b)
+    jaws = (-0.5 * field_x - jaw_margin, 0.5 * field_x + jaw_margin,
+            -0.5 * field_y - jaw_margin, 0.5 * field_y + jaw_margin)
+    return LeafSequence(edges, np.asarray(mu, np.float32), np.asarray(L, np.float32),
+                        np.asarray(R, np.float32), tuple(float(v) for v in jaws), float(transmission))
+
+
+def plan_sequences(plan: Plan, seed: int, kind: str = "sliding", **kw) -> List[LeafSequence]:
+    """One sequence per beam of the plan (sliding window or step and shoot)."""
+    rng = np.random.default_rng(seed)
+    make = sliding_window if kind == "sliding" else step_and_shoot
+    return [make(rng, b.field_x, b.field_y, **kw) for b in plan.beams]
