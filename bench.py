@@ -44,12 +44,12 @@ MUFU_LANES_PER_SM = 16
 L2_FLUSH_BYTES = 256 << 20
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the dose kernel on the thorax9 plan, from an ncu capture of the kernel built
-# from the sources with these SHA-256 digests (profiles/k_pairs_dose_thorax9.md);
-# reported only while the sources are unchanged.
-DOSE_TRAFFIC_BYTES = 110455552 + 20622336
+# from the sources with these SHA-256 digests (the kernel and the structures it
+# reads; profiles/k_pairs_dose_thorax9.md); reported only while they are unchanged.
+DOSE_TRAFFIC_BYTES = 110287872 + 20627456
 DOSE_TRAFFIC_SOURCES = {
     "paper_1103_1164_gb300/csrc/k_dose.cu": "43573a455c81c178255291b940ab56b63e2e1be6db51f215a36045d2c295364a",
-    "paper_1103_1164_gb300/csrc/dc_internal.cuh": "2ead58576c533758c30753bf1f63cba61149cf1b82cbc79058f50f4568c86f64",
+    "paper_1103_1164_gb300/csrc/dc_views.cuh": "876c93613262887f8c1924a9fd07ca736db19493e19ef78261ec02b35c671d3a",
 }
 
 
@@ -411,6 +411,7 @@ def run_ours(args, world, rank, local, pg):
     forms["batch"] = run_batch_form(args, dc, torch, stream, peak_pairs)
     forms["gamma"] = run_gamma_form(args, dc, torch, stream, p, rho_d, flu_d)
     forms["table1"] = run_table1_form(args, dc, torch, stream, flush)
+    forms["leaf_sequences"] = run_leaf_form(args, dc, torch, stream, flush)
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, dc, p, plan, pairs, torch)
@@ -680,6 +681,59 @@ def run_table1_form(args, dc, torch, stream, flush):
             "batch_graph": {"full_plans_ms": t_batch, "dose_ms": t_batch_dose,
                             "evals_per_s": 2 * pairs / (t_batch * 1e-3),
                             "kernels_per_replay": dc.dc_fspb_batch_kernels(batch)}}
+
+
+def run_leaf_form(args, dc, torch, stream, flush, n_cp=128):
+    """Replanning loop on the largest Table 1 case (H5, 7 non-coplanar beams,
+    10,369 beamlets of 0.2 x 0.5 cm): each iteration turns new sliding-window
+    leaf sequences (n_cp control points per beam, host memory) into the
+    fluence (dc_fluence_from_leaves) and the dose of the cached plan.  Device
+    time of the fluence step and of fluence + dose; host wall time of an
+    iteration through host buffers (sequences in, dose out)."""
+    from paper_1103_1164_gb300 import synth
+    p = synth.table1_case("H5")
+    seqs = [synth.plan_sequences(p, 2000 + k, "sliding", n_cp=n_cp, transmission=0.015) for k in range(4)]
+    rho_d = torch.from_numpy(p.rho).cuda()
+    plan = dc.dc_fspb_create_from(p, stream=stream.cuda_stream, device_density=rho_d)
+    flu_d = torch.empty(plan.n_beamlets, device="cuda")
+    dose_d = torch.empty(plan.shape, device="cuda")
+    dc.dc_fspb_autotune(plan, torch.from_numpy(p.fluence).cuda())
+    reps = max(3, min(args.steps, 5))
+    it = iter(range(1 << 30))
+    nxt = lambda: seqs[next(it) % len(seqs)]
+    for _ in range(2):
+        dc.dc_fluence_from_leaves(plan, nxt(), flu_d)
+        dc.dc_fspb_dose(plan, flu_d, dose_d)
+    torch.cuda.synchronize()
+    t_flu = time_on_stream(torch, stream, lambda: dc.dc_fluence_from_leaves(plan, nxt(), flu_d), reps, flush)
+
+    def flu_dose():
+        dc.dc_fluence_from_leaves(plan, nxt(), flu_d)
+        dc.dc_fspb_dose(plan, flu_d, dose_d)
+
+    t_both = time_on_stream(torch, stream, flu_dose, reps, flush)
+    dose_h = torch.empty(plan.shape, dtype=torch.float32).pin_memory().numpy()
+    flu_h = np.empty(plan.n_beamlets, np.float32)
+    ts = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        dc.dc_fluence_from_leaves(plan, nxt(), flu_h)
+        dc.dc_fspb_dose(plan, flu_h, dose_h)
+        ts.append((time.perf_counter() - w0) * 1e3)
+    out = {"workload": f"H5 ({plan.n_beamlets} beamlets, 7 non-coplanar beams), sliding-window sequences "
+                       f"of {n_cp} control points per beam, 0.5 cm leaves, 1.5 % transmission",
+           "fluence_ms": t_flu, "fluence_plus_dose_ms": t_both,
+           "iteration_host_buffers_ms": float(np.median(ts)),
+           "beamlet_intervals_per_s": plan.n_beamlets * (n_cp - 1) / (t_flu * 1e-3)}
+    if not args.no_cpu:
+        from oracle import fluence as ofl
+        t0 = time.perf_counter()
+        fo = ofl.plan_fluence(p, seqs[0])
+        out["oracle_fluence_ms"] = (time.perf_counter() - t0) * 1e3
+        dc.dc_fluence_from_leaves(plan, seqs[0], flu_h)
+        out["max_diff_vs_oracle_over_mu"] = float(np.abs(flu_h - fo).max() / 100.0)
+    return out
 
 
 def run_batch_form(args, dc, torch, stream, peak_pairs):

@@ -447,6 +447,51 @@ dc_status dc_fspb_autotune(dc_plan* plan, const float* fluence, uint32_t flags, 
  * (all plans, all threads), for accounting of GPU work. */
 dc_status dc_fspb_launch_count(uint64_t* n);
 
+/* ---- Fluence maps from MLC leaf sequences ----
+ *
+ * Section 2.3: each plan's leaf sequences and monitor units are converted
+ * into a fluence map on the beamlet grid (0.2 x 0.5 cm, 0.2 cm along the leaf
+ * motion), which is the fluence eq. (1) weights the beamlets with.  The paper
+ * gives no formula; the reading here is the delivered fluence: for beamlet
+ * i of a beam, with its rectangle [xa, xb] x [ya, yb] in the isocentre plane of
+ * the collimator frame first clipped to the jaws,
+ *   f_i = 1/(bx by) * sum over leaf pairs j, control-point intervals c of
+ *         h_ij * [ (1 - tau) * (area of the (x, meterset) region that pair j
+ *                  leaves open between control points c and c+1, within
+ *                  [xa, xb]) + tau * (xb - xa) * (mu_c+1 - mu_c) ]
+ * where h_ij is the length of [ya, yb] inside the pair's band and the leaf
+ * tips move linearly in meterset between control points.  A step-and-shoot
+ * segment is two control points with equal positions; leaf moves between
+ * segments sit at a repeated meterset value and deliver nothing.  Outside the
+ * leaf bank and the jaws the fluence is zero.  f_i is in meterset units.
+ */
+typedef struct {
+    int32_t n_leaves;     /* leaf pairs, >= 1                                      */
+    int32_t n_cp;         /* control points, >= 1 (one control point: no fluence)  */
+    const float* edges;   /* [n_leaves + 1] pair boundaries along y (cm), increasing */
+    const float* mu;      /* [n_cp] cumulative meterset, non-decreasing             */
+    const float* left;    /* [n_cp][n_leaves] tip of the -x bank (cm)               */
+    const float* right;   /* [n_cp][n_leaves] tip of the +x bank (cm), >= left      */
+    float jaw_x1, jaw_x2; /* jaws along x (cm), x1 <= x2                            */
+    float jaw_y1, jaw_y2; /* jaws along y (cm), y1 <= y2                            */
+    float transmission;   /* fraction passing closed leaves, in [0, 1]              */
+} dc_leaf_sequence;
+
+/*
+ * fluence [B] (beamlet order of the plan: beam by beam, row n of a beam at
+ * n M + m) from seqs [n_beams], one sequence per beam in the plan's beam
+ * order.  The sequences are host memory (read during the call); fluence is
+ * host memory, or device memory with DC_DEVICE_PTRS in flags.  The work runs
+ * on the plan's stream: with a host fluence the call waits for it; with a
+ * device fluence it returns once the kernel is enqueued, so a following
+ * dc_fspb_dose on the same plan is ordered after it.  At most 2^28 sequence
+ * values in all.
+ * Errors: DC_EINVAL (NULL arguments, sizes, non-increasing edges, decreasing
+ * or non-finite meterset, left > right, non-finite positions, bad jaws or
+ * transmission), DC_ENOMEM, DC_ECUDA.
+ */
+dc_status dc_fluence_from_leaves(dc_plan* plan, const dc_leaf_sequence* seqs, float* fluence, uint32_t flags);
+
 /* ---- Gamma-index comparison of two dose distributions ----
  *
  * Section 3 (accuracy evaluation) compares each computed dose with a reference

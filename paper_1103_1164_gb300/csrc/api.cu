@@ -90,7 +90,7 @@ static void free_plan(dc_plan* p)
                     p->d_bin, p->d_bounds, p->d_cellof, p->d_hist, p->d_nitems, p->d_bstart, p->d_bscan,
                     p->d_base, p->d_work,
                     p->d_items, p->d_part, p->d_bcount, p->d_sp_fp, p->d_sp_p, p->d_err,
-                    p->d_lfac, p->d_mlp_frag, p->d_mlp_bias, p->d_nfall};
+                    p->d_lfac, p->d_mlp_frag, p->d_mlp_bias, p->d_nfall, p->d_leaf};
     for (void* b : bufs)
         if (b) cudaFree(b);
     p->spmm_free();

@@ -48,6 +48,12 @@ class dc_gamma_stats(C.Structure):
                 ("n50", C.c_int64), ("dose_max", C.c_float)]
 
 
+class dc_leaf_sequence(C.Structure):
+    _fields_ = [("n_leaves", C.c_int32), ("n_cp", C.c_int32), ("edges", C.c_void_p), ("mu", C.c_void_p),
+                ("left", C.c_void_p), ("right", C.c_void_p), ("jaw_x1", C.c_float), ("jaw_x2", C.c_float),
+                ("jaw_y1", C.c_float), ("jaw_y2", C.c_float), ("transmission", C.c_float)]
+
+
 class dc_beam(C.Structure):
     _fields_ = [("gantry_deg", C.c_float), ("couch_deg", C.c_float), ("coll_deg", C.c_float),
                 ("sad", C.c_float), ("iso", C.c_float * 3), ("field_x", C.c_float),
@@ -74,7 +80,7 @@ EXPORTS = ["dc_last_error", "dc_status_str", "dc_fspb_create", "dc_fspb_destroy"
            "dc_mlp_create", "dc_mlp_destroy", "dc_mlp_get_params", "dc_mlp_gradient", "dc_mlp_train",
            "dc_mlp_predict", "dc_fspb_batch_create", "dc_fspb_batch_destroy", "dc_fspb_batch_buffers",
            "dc_fspb_batch_run", "dc_fspb_batch_dose", "dc_fspb_batch_synchronize", "dc_fspb_batch_kernels",
-           "dc_fspb_batch_autotune", "dc_gamma_index"]
+           "dc_fspb_batch_autotune", "dc_gamma_index", "dc_fluence_from_leaves"]
 
 
 def library_path() -> str:
@@ -136,6 +142,7 @@ def load():
     L.dc_fspb_batch_autotune.argtypes = [vp, C.POINTER(i32), C.POINTER(C.c_float)]
     L.dc_gamma_index.argtypes = [vp, vp, C.POINTER(dc_grid), C.c_float, C.c_float, C.c_float, vp,
                                  C.POINTER(dc_gamma_stats), vp, u32]
+    L.dc_fluence_from_leaves.argtypes = [vp, C.POINTER(dc_leaf_sequence), vp, u32]
     for name in EXPORTS:
         if name not in ("dc_last_error", "dc_status_str"):
             getattr(L, name).restype = C.c_int
@@ -182,8 +189,9 @@ def _current_stream():
 class Plan:
     """Owns a dc_plan*; freed by dc_fspb_destroy (or when garbage-collected)."""
 
-    def __init__(self, handle, n_beamlets, n_voxels, grid_shape, keep=()):
+    def __init__(self, handle, n_beamlets, n_voxels, grid_shape, keep=(), n_beams=0):
         self.handle = handle
+        self.n_beams = n_beams
         self.n_beamlets = n_beamlets
         self.n_voxels = n_voxels
         self.shape = grid_shape
@@ -226,7 +234,7 @@ def dc_fspb_create(ct_density, grid, beams, beamlet_x, beamlet_y, comm, stream=N
     nb, nv = C.c_int32(), C.c_int64()
     _check(L.dc_fspb_n_beamlets(h, C.byref(nb)))
     _check(L.dc_fspb_n_voxels(h, C.byref(nv)))
-    return Plan(h, nb.value, nv.value, (grid.nz, grid.ny, grid.nx))
+    return Plan(h, nb.value, nv.value, (grid.nz, grid.ny, grid.nx), n_beams=len(beams))
 
 
 def dc_fspb_create_from(plan_inputs, stream=None, device_density=None,
@@ -537,3 +545,27 @@ def dc_gamma_index(ref, ev, grid, pct=3.0, dta=0.3, search=None, gamma=None, str
                                  _same_kind(f1, f2, f3)))
     return gamma, dict(gamma_max=st.gamma_max, gamma_avg50=st.gamma_avg50, pass50_pct=st.pass50_pct,
                        n50=int(st.n50), dose_max=st.dose_max)
+
+
+def dc_fluence_from_leaves(plan: Plan, seqs, out=None):
+    """The plan's beamlet fluence [B] from one leaf sequence per beam
+    (synth.LeafSequence-like objects: edges, mu, left, right, jaws,
+    transmission).  out: a host array or a CUDA tensor of B float32 (default:
+    a new host array)."""
+    if len(seqs) != plan.n_beams:
+        raise ValueError("one leaf sequence per beam")
+    keep, arr = [], (dc_leaf_sequence * len(seqs))()
+    for k, s in enumerate(seqs):
+        ed, mu, le, ri = (np.ascontiguousarray(a, np.float32) for a in (s.edges, s.mu, s.left, s.right))
+        nl, ncp = ed.size - 1, mu.size
+        if le.size != nl * ncp or ri.size != nl * ncp:
+            raise ValueError("left/right must be [n_cp][n_leaves]")
+        keep += [ed, mu, le, ri]
+        x1, x2, y1, y2 = (float(v) for v in s.jaws)
+        arr[k] = dc_leaf_sequence(nl, ncp, ed.ctypes.data, mu.ctypes.data, le.ctypes.data, ri.ctypes.data,
+                                  x1, x2, y1, y2, float(s.transmission))
+    if out is None:
+        out = np.empty(plan.n_beamlets, np.float32)
+    p, flag = _ptr(out)
+    _check(load().dc_fluence_from_leaves(plan.handle, arr, p, flag))
+    return out
