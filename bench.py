@@ -407,6 +407,8 @@ def run_ours(args, world, rank, local, pg):
               "nnz": pairs, "bytes": bytes_matrix}
 
     forms = run_forms(args, dc, torch, stream, peaks)
+    forms["fused_plan"] = run_fused_form(args, dc, torch, stream, plan, rho_d, flu_d, dose_d, rowptr_d, cols_d,
+                                         vals_d, flush, float(step_ms.mean()), pairs)
     forms["surrogate"] = run_surrogate_form(args, dc, torch, stream)
     forms["batch"] = run_batch_form(args, dc, torch, stream, peak_pairs)
     forms["gamma"] = run_gamma_form(args, dc, torch, stream, p, rho_d, flu_d)
@@ -441,6 +443,27 @@ def run_ours(args, world, rank, local, pg):
             "roofline": roofline, "peaks": peak_kind, "dose_matrix": matrix, "forms": forms,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
+
+
+def run_fused_form(args, dc, torch, stream, plan, rho_d, flu_d, dose_d, rowptr_d, cols_d, vals_d, flush,
+                   step_ms, pairs):
+    """The same plan (thorax9: steps 1-6, dose and FP32 matrix) with the dose
+    accumulated by the matrix fill (dc_fspb_dose_and_matrix): one evaluation
+    of each pair instead of two, after a pair-count pass for the row pattern.
+    Full-plan device time against the benchmark step's."""
+    def fused():
+        dc.dc_fspb_set_density(plan, rho_d)
+        dc.dc_fspb_dose_and_matrix(plan, flu_d, dose_d, dc.DC_F32, rowptr_d, cols_d, vals_d)
+
+    ref = dose_d.clone()
+    fused()
+    torch.cuda.synchronize()
+    same = bool(torch.equal(ref, dose_d))
+    reps = max(3, min(args.steps, 5))
+    t = time_on_stream(torch, stream, fused, reps, flush)
+    return {"workload": "thorax9 plan, dose + FP32 matrix from one pass (after a pair-count pass)",
+            "full_plan_ms": t, "benchmark_step_ms": step_ms, "speedup": step_ms / t,
+            "pairs_per_s": pairs / (t * 1e-3), "dose_identical_to_step": same}
 
 
 def time_on_stream(torch, stream, fn, reps, flush):

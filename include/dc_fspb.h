@@ -206,6 +206,18 @@ dc_status dc_fspb_dose_matrix(dc_plan* plan, int32_t value_dtype, int64_t* rowpt
                               void* vals, uint32_t flags);
 
 /*
+ * dc_fspb_dose and dc_fspb_dose_matrix from ONE evaluation of each pair: the
+ * CSR fill pass also accumulates eq. (1) for `fluence` [B] into `dose` [V].
+ * Results are identical to the two separate calls (same pairs, same order of
+ * the sums).  rowptr, cols, vals as for dc_fspb_dose_matrix; fluence and dose
+ * host memory, or all five device memory with DC_DEVICE_PTRS.  When the row
+ * pattern is not yet known a pair-count pass runs first.
+ * Errors: as dc_fspb_dose_matrix.
+ */
+dc_status dc_fspb_dose_and_matrix(dc_plan* plan, const float* fluence, float* dose, int32_t value_dtype,
+                                  int64_t* rowptr, int32_t* cols, void* vals, uint32_t flags);
+
+/*
  * Builds, inside the plan, the dose-deposition matrix of dc_fspb_dose_matrix
  * (M[v][i] = D_i(r_v) over the pairs of eq. 1) with BF16 values, stored
  * block-sparse for the tensor cores: per beam, the voxels of the beam's

@@ -544,6 +544,20 @@ dc_status dc_fspb_n_voxels(const dc_plan* plan, int64_t* n)
     return DC_OK;
 }
 
+// Per-beam partial dose buffer of at least `need` floats.
+static dc_status ensure_part(dc_plan* p, size_t need)
+{
+    if (need <= p->part_cap) return DC_OK;
+    DC_CUDA(cudaStreamSynchronize(p->stream));
+    cudaFree(p->d_part);
+    p->d_part = nullptr;
+    p->part_cap = 0;
+    DC_CUDA(dalloc(&p->d_part, need));
+    p->part_cap = need;
+    ++p->layout_gen;
+    return DC_OK;
+}
+
 static dc_status ensure_staging(dc_plan* p, size_t nflu, size_t ndose)
 {
     if (nflu > p->fluence_cap) {
@@ -569,16 +583,8 @@ dc_status dc_fspb_dose_batch(dc_plan* plan, const float* fluence, int32_t k, flo
     if (k < 1 || k > 64) return invalid("dc_fspb_dose_batch: k must be in [1, 64]");
     const size_t nf = (size_t)k * plan->B, nd = (size_t)k * plan->V;
     // per-beam partial doses: 16 fluence vectors per pass when k > 1
-    const size_t need = (size_t)plan->n_beams * (k > 1 ? 16 : 1) * plan->V;
-    if (need > plan->part_cap) {
-        DC_CUDA(cudaStreamSynchronize(plan->stream));
-        cudaFree(plan->d_part);
-        plan->d_part = nullptr;
-        plan->part_cap = 0;
-        DC_CUDA(dalloc(&plan->d_part, need));
-        plan->part_cap = need;
-        ++plan->layout_gen;
-    }
+    dc_status ps = ensure_part(plan, (size_t)plan->n_beams * (k > 1 ? 16 : 1) * plan->V);
+    if (ps != DC_OK) return ps;
     // a single-fluence pass records the pair counts of the matrix pattern
     // while the pattern is unknown (every pair test is made there anyway)
     const bool record = k == 1 && plan->pairs < 0 && !plan->counts_fresh;
@@ -630,19 +636,24 @@ dc_status dc_fspb_pair_count(dc_plan* plan, int64_t* pairs)
     return DC_OK;
 }
 
-dc_status dc_fspb_dose_matrix(dc_plan* plan, int32_t value_dtype, int64_t* rowptr, int32_t* cols,
-                              void* vals, uint32_t flags)
+// The CSR matrix, and with a fluence also eq. (1), from one fill pass.
+static dc_status matrix_impl(dc_plan* plan, int32_t value_dtype, int64_t* rowptr, int32_t* cols, void* vals,
+                             const float* fluence, float* dose, uint32_t flags, const char* who)
 {
-    if (!plan || !rowptr || !cols || !vals) return invalid("dc_fspb_dose_matrix: NULL argument");
+    if (!plan || !rowptr || !cols || !vals) return invalid(std::string(who) + ": NULL argument");
     if (value_dtype != DC_F32 && value_dtype != DC_BF16)
-        return invalid("dc_fspb_dose_matrix: value_dtype must be DC_F32 or DC_BF16");
+        return invalid(std::string(who) + ": value_dtype must be DC_F32 or DC_BF16");
+    if (fluence) {
+        dc_status s = ensure_part(plan, (size_t)plan->n_beams * plan->V);
+        if (s != DC_OK) return s;
+    }
     dc_status s = ensure_pattern(plan);
     if (s != DC_OK) return s;
     const size_t nnz = (size_t)plan->pairs, vsz = value_dtype == DC_BF16 ? 2 : 4;
     if (flags & DC_DEVICE_PTRS) {
         DC_CUDA(cudaMemcpyAsync(rowptr, plan->d_rowptr, (plan->V + 1) * sizeof(int64_t),
                                 cudaMemcpyDeviceToDevice, plan->stream));
-        DC_CUDA(launch_fill(plan, plan->d_rowptr, cols, vals, value_dtype));
+        DC_CUDA(launch_fill(plan, plan->d_rowptr, cols, vals, value_dtype, fluence, dose));
         return DC_OK;
     }
     const size_t need = nnz * sizeof(int32_t) + 16;
@@ -656,18 +667,40 @@ dc_status dc_fspb_dose_matrix(dc_plan* plan, int32_t value_dtype, int64_t* rowpt
         DC_CUDA(cudaMalloc(&plan->d_mvals, need));
         plan->mstage_bytes = need;
     }
+    if (fluence) {
+        s = ensure_staging(plan, plan->B, plan->V);
+        if (s != DC_OK) return s;
+        DC_CUDA(cudaMemcpyAsync(plan->d_fluence, fluence, plan->B * sizeof(float), cudaMemcpyHostToDevice,
+                                plan->stream));
+    }
     int32_t* dcols = plan->d_mcols;
     void* dvals = plan->d_mvals;
-    cudaError_t e = launch_fill(plan, plan->d_rowptr, dcols, dvals, value_dtype);
+    cudaError_t e = launch_fill(plan, plan->d_rowptr, dcols, dvals, value_dtype, fluence ? plan->d_fluence : nullptr,
+                                fluence ? plan->d_dose : nullptr);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(rowptr, plan->d_rowptr, (plan->V + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost,
                             plan->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(cols, dcols, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, plan->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(vals, dvals, nnz * vsz, cudaMemcpyDeviceToHost, plan->stream);
+    if (e == cudaSuccess && fluence)
+        e = cudaMemcpyAsync(dose, plan->d_dose, plan->V * sizeof(float), cudaMemcpyDeviceToHost, plan->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(plan->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "dc_fspb_dose_matrix");
+    if (e != cudaSuccess) return cuda_fail(e, who);
     return DC_OK;
+}
+
+dc_status dc_fspb_dose_matrix(dc_plan* plan, int32_t value_dtype, int64_t* rowptr, int32_t* cols,
+                              void* vals, uint32_t flags)
+{
+    return matrix_impl(plan, value_dtype, rowptr, cols, vals, nullptr, nullptr, flags, "dc_fspb_dose_matrix");
+}
+
+dc_status dc_fspb_dose_and_matrix(dc_plan* plan, const float* fluence, float* dose, int32_t value_dtype,
+                                  int64_t* rowptr, int32_t* cols, void* vals, uint32_t flags)
+{
+    if (!fluence || !dose) return invalid("dc_fspb_dose_and_matrix: NULL argument");
+    return matrix_impl(plan, value_dtype, rowptr, cols, vals, fluence, dose, flags, "dc_fspb_dose_and_matrix");
 }
 
 static dc_status check_device_status(dc_plan* p)

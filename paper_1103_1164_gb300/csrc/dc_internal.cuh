@@ -159,8 +159,9 @@ cudaError_t launch_dose(const dc_plan* p, const float* fluence, int nf, int ldf,
 cudaError_t launch_count(const dc_plan* p, int32_t* counts);
 // rowcount[v] = sum over beams of the per-beam pair counts already in d_bcount
 cudaError_t launch_rowsum(const dc_plan* p, int32_t* counts);
+// with a fluence (device), the same pass also accumulates eq. (1) into dose [V]
 cudaError_t launch_fill(const dc_plan* p, const int64_t* rowptr, int32_t* cols, void* vals,
-                        int value_dtype);
+                        int value_dtype, const float* fluence = nullptr, float* dose = nullptr);
 cudaError_t launch_scan_counts(const dc_plan* p, const int32_t* counts, int64_t* rowptr,
                                int64_t* total_dev);
 // lateral factors, stencil samples and the surrogate network (k_lateral.cu)

@@ -293,9 +293,9 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
             ln.cw2 = lf.w;
         }
     }
-    float acc[NF];
+    float acc[NF > 0 ? NF : 1];
 #pragma unroll
-    for (int q = 0; q < NF; ++q) acc[q] = 0.f;
+    for (int q = 0; q < (NF > 0 ? NF : 1); ++q) acc[q] = 0.f;
     int32_t cnt = 0;
     int64_t pos = 0, pend = 0;
     const int mis = MODE == kFill ? (int)((reinterpret_cast<uintptr_t>(a.cols) >> 2) & 7) : 0;
@@ -353,7 +353,7 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
             float4 q2 = __ldg(src + 2);
             // one fluence vector: the staged record carries f_i in place of the
             // theta weight (which only the table set-up uses)
-            if (MODE == kDose && NF == 1) q2.w = __ldg(a.fluence + row + (uint32_t)(m0 + lane));
+            if (MODE != kCount && NF == 1) q2.w = __ldg(a.fluence + row + (uint32_t)(m0 + lane));
             srow[3 * lane + 2] = q2;
         }
         __syncwarp();
@@ -383,6 +383,7 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
                     sst[lane * kRingLd + (int)(((uint32_t)pos + (uint32_t)cnt) & (kRing - 1))] =
                         make_int2((int)i, __float_as_int(D));
                     ++cnt;
+                    if (NF == 1) acc[0] = fmaf(rq[2].w, D, acc[0]);   // eq. (1) from the same evaluation
                 }
                 if (__any_sync(0xffffffffu, cnt >= kRing)) flush_stage(a, sst, lane, cnt, pos, pend, mis, false);
             }
@@ -391,6 +392,7 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
     }
     if (MODE == kFill) {
         flush_stage(a, sst, lane, cnt, pos, pend, mis, true);
+        if (NF == 1 && ln.valid) a.part[(size_t)b * V + v] = acc[0];
     } else if (ln.valid) {
         if (MODE == kDose) {
 #pragma unroll
@@ -845,14 +847,28 @@ cudaError_t launch_rowsum(const dc_plan* p, int32_t* counts)
 }
 
 cudaError_t launch_fill(const dc_plan* p, const int64_t* rowptr, int32_t* cols, void* vals,
-                        int value_dtype)
+                        int value_dtype, const float* fluence, float* dose)
 {
     DoseArgs a = make_args(p);
     a.rowptr = rowptr;
     a.cols = cols;
     a.vals = vals;
     a.value_dtype = value_dtype;
-    return run<kFill, 1>(p, a);
+    if (!fluence) return run<kFill, 0>(p, a);
+    // the matrix and eq. (1) from one evaluation of each pair: per-beam
+    // partial doses as in launch_dose, summed in beam order
+    if (p->part_cap < (size_t)p->n_beams * p->V) return cudaErrorInvalidValue;
+    a.fluence = fluence;
+    a.nf = 1;
+    a.ldf = p->B;
+    a.part = p->d_part;
+    cudaError_t e = cudaMemsetAsync(p->d_part, 0, sizeof(float) * (size_t)p->n_beams * p->V, p->stream);
+    if (e != cudaSuccess) return e;
+    e = run<kFill, 1>(p, a);
+    if (e != cudaSuccess) return e;
+    k_sum_beams<<<grid_for((int64_t)p->V), 256, 0, p->stream>>>(p->d_part, p->n_beams, 1, 1, p->V, dose, p->V);
+    count_launches(1);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_scan_counts(const dc_plan* p, const int32_t* counts, int64_t* rowptr,

@@ -72,7 +72,7 @@ class dc_kernel_coeffs(C.Structure):
 
 EXPORTS = ["dc_last_error", "dc_status_str", "dc_fspb_create", "dc_fspb_destroy",
            "dc_fspb_n_beamlets", "dc_fspb_n_voxels", "dc_fspb_dose", "dc_fspb_dose_batch",
-           "dc_fspb_pair_count", "dc_fspb_dose_matrix", "dc_fspb_get_smoothed",
+           "dc_fspb_pair_count", "dc_fspb_dose_matrix", "dc_fspb_dose_and_matrix", "dc_fspb_get_smoothed",
            "dc_fspb_get_beamlets", "dc_fspb_get_tables", "dc_fspb_set_density",
            "dc_fspb_launch_count", "dc_fspb_autotune", "dc_fspb_spmm_prepare", "dc_fspb_spmm_info",
            "dc_fspb_spmm", "dc_fspb_spmm_noalloc", "dc_fspb_device_status", "dc_fspb_set_surrogate",
@@ -110,6 +110,7 @@ def load():
     L.dc_fspb_dose_batch.argtypes = [vp, vp, i32, vp, u32]
     L.dc_fspb_pair_count.argtypes = [vp, C.POINTER(i64)]
     L.dc_fspb_dose_matrix.argtypes = [vp, i32, vp, vp, vp, u32]
+    L.dc_fspb_dose_and_matrix.argtypes = [vp, vp, vp, i32, vp, vp, vp, u32]
     L.dc_fspb_get_smoothed.argtypes = [vp, vp, u32]
     L.dc_fspb_get_beamlets.argtypes = [vp, vp]
     L.dc_fspb_get_tables.argtypes = [vp, i32, vp, vp, vp, i32, C.POINTER(i32)]
@@ -430,6 +431,27 @@ def dc_fspb_dose_matrix(plan: Plan, value_dtype=DC_F32, rowptr=None, cols=None, 
     pv, f3 = _ptr(vals, vals.dtype if not _is_torch(vals) else None)
     _check(load().dc_fspb_dose_matrix(plan.handle, value_dtype, pr, pc, pv, _same_kind(f1, f2, f3)))
     return rowptr, cols[:nnz] if not _is_torch(cols) else cols, vals[:nnz] if not _is_torch(vals) else vals
+
+
+def dc_fspb_dose_and_matrix(plan: Plan, fluence, dose=None, value_dtype=DC_F32, rowptr=None, cols=None,
+                            vals=None):
+    """Dose for `fluence` and the CSR matrix from one pass; returns (dose, rowptr, cols, vals)."""
+    nnz = dc_fspb_pair_count(plan)
+    if rowptr is None:
+        rowptr = np.empty(plan.n_voxels + 1, np.int64)
+        cols = np.empty(max(nnz, 1), np.int32)
+        vals = np.empty(max(nnz, 1), np.float32 if value_dtype == DC_F32 else np.uint16)
+    if dose is None:
+        dose = np.empty(plan.shape, np.float32)
+    pf, f0 = _ptr(fluence)
+    pd, f4 = _ptr(dose)
+    pr, f1 = _ptr(rowptr, np.int64)
+    pc, f2 = _ptr(cols, np.int32)
+    pv, f3 = _ptr(vals, vals.dtype if not _is_torch(vals) else None)
+    _check(load().dc_fspb_dose_and_matrix(plan.handle, pf, pd, value_dtype, pr, pc, pv,
+                                          _same_kind(f0, f1, f2, f3, f4)))
+    trim = lambda a: a[:nnz] if not _is_torch(a) else a
+    return dose, rowptr, trim(cols), trim(vals)
 
 
 def dc_fspb_get_smoothed(plan: Plan):

@@ -6,6 +6,8 @@
 * the Siddon trace splits each ray over the 32 lanes of a warp and falls back
   to one lane for rays with more segments per piece than its buffer holds
   (rays of ~1000 voxel crossings here, FP64 sums: rays > 40 cm);
+* dc_fspb_dose_and_matrix fills the matrix and accumulates eq. (1) in one
+  pass: both results bit-identical to the separate calls;
 * the SpMM numbers its tile columns in 4 x 4 beamlet patches, including
   beamlet grids whose sides are not multiples of 4, and a one-beam plan zeroes
   the output rows of voxels that are in no beam list.
@@ -50,6 +52,38 @@ def test_dose_pass_counts_give_the_same_matrix(dc):
     dc.dc_fspb_set_density(c, rho2)
     assert dc.dc_fspb_pair_count(b) == dc.dc_fspb_pair_count(c)
     assert np.array_equal(dc.dc_fspb_dose_matrix(b)[1], dc.dc_fspb_dose_matrix(c)[1])
+
+
+@pytest.mark.parametrize("value_dtype", [0, 1])
+def test_dose_and_matrix_in_one_pass(dc, value_dtype):
+    import torch
+    p = synth.config2(0.375)
+    a = dc.dc_fspb_create_from(p)
+    b = dc.dc_fspb_create_from(p)
+    # b: fresh plan, the pattern comes from a count pass inside the call
+    dose_b, rb, cb, vb = dc.dc_fspb_dose_and_matrix(b, p.fluence, value_dtype=value_dtype)
+    dose_a = dc.dc_fspb_dose(a, p.fluence)
+    ra, ca, va = dc.dc_fspb_dose_matrix(a, value_dtype)
+    assert np.array_equal(dose_a, dose_b)
+    assert np.array_equal(ra, rb) and np.array_equal(ca, cb) and np.array_equal(va, vb)
+    # device buffers, a second fluence, after a new density
+    rho2 = np.ascontiguousarray(p.rho * np.float32(0.97))
+    for pl in (a, b):
+        dc.dc_fspb_set_density(pl, rho2)
+    f2 = np.ascontiguousarray(p.fluence[::-1], np.float32)
+    nnz = dc.dc_fspb_pair_count(b)
+    vt = torch.float32 if value_dtype == 0 else torch.int16
+    d_dev = torch.full(p.grid.shape, float("nan"), device="cuda")
+    r_dev = torch.empty(p.grid.n_voxels + 1, dtype=torch.int64, device="cuda")
+    c_dev = torch.empty(nnz, dtype=torch.int32, device="cuda")
+    v_dev = torch.empty(nnz, dtype=vt, device="cuda")
+    dc.dc_fspb_dose_and_matrix(b, torch.from_numpy(f2).cuda(), d_dev, value_dtype, r_dev, c_dev, v_dev)
+    torch.cuda.synchronize()
+    dose_a = dc.dc_fspb_dose(a, f2)
+    ra, ca, va = dc.dc_fspb_dose_matrix(a, value_dtype)
+    assert np.array_equal(d_dev.cpu().numpy(), dose_a)
+    assert np.array_equal(r_dev.cpu().numpy(), ra) and np.array_equal(c_dev.cpu().numpy(), ca)
+    assert np.array_equal(v_dev.cpu().numpy().view(va.dtype), va)
 
 
 def test_long_rays_take_the_single_lane_trace(dc, oracle_mod):
