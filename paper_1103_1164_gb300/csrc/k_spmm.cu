@@ -362,28 +362,48 @@ __global__ void __launch_bounds__(kSpmmThreads) k_spmm(const SpmmArgs a)
     const uint32_t tmem = tmem_base;
 
     if (warp == kEpiWarps) {
-        // ---- producer: every chunk of every row-block of this CTA, in order
-        if (lane == 0) {
-            uint32_t g = 0;
-            bool ok = true;
-            for (int rb = blockIdx.x; rb < a.n_rb && ok; rb += gridDim.x) {
-                const int64_t ch0 = a.chunk_off[rb], nch = a.chunk_off[rb + 1] - ch0;
-                for (int64_t c = 0; c < nch; ++c, ++g) {
-                    const uint32_t s = g % kStages;
-                    if (g >= kStages && !mbar_wait(&empty[s], ((g / kStages) - 1) & 1)) {
-                        ok = false;
-                        break;
+        // ---- producer: every chunk of every row-block of this CTA, in order.
+        // The whole warp loads the chunks' k-block indices 32 at a time (and
+        // the row-blocks' chunk ranges 32 row-blocks at a time), so the copies
+        // are not serialised behind one dependent load each; lane 0 issues
+        // the copies.
+        uint32_t g = 0;
+        bool ok = true;
+        for (int rb0 = blockIdx.x; rb0 < a.n_rb && ok; rb0 += 32 * gridDim.x) {
+            const int rbl = rb0 + lane * gridDim.x;
+            const int64_t my_c0 = rbl < a.n_rb ? a.chunk_off[rbl] : 0;
+            const int64_t my_c1 = rbl < a.n_rb ? a.chunk_off[rbl + 1] : 0;
+            for (int j = 0; j < 32 && ok; ++j) {
+                const int rb = rb0 + j * gridDim.x;
+                if (rb >= a.n_rb) break;
+                const int64_t ch0 = __shfl_sync(0xffffffffu, my_c0, j);
+                const int64_t nch = __shfl_sync(0xffffffffu, my_c1, j) - ch0;
+                for (int64_t cb = 0; cb < nch && ok; cb += 32) {
+                    const int my_kb = cb + lane < nch ? a.chunk_kb[ch0 + cb + lane] : 0;
+                    const int n_in = (int)(nch - cb < 32 ? nch - cb : 32);
+                    for (int c = 0; c < n_in; ++c, ++g) {
+                        const int kb = __shfl_sync(0xffffffffu, my_kb, c);
+                        int lok = 1;
+                        if (lane == 0) {
+                            const uint32_t s = g % kStages;
+                            if (g >= kStages && !mbar_wait(&empty[s], ((g / kStages) - 1) & 1)) lok = 0;
+                            else if (s_abort) lok = 0;
+                            if (lok) {
+                                uint8_t* sa = buf + s * (kTileA + kTileB);
+                                mbar_expect_tx(&full[s], kTileA + kTileB);
+                                bulk_g2s(sa, a.tiles + (size_t)(ch0 + cb + c) * (kRB * kKC), kTileA, &full[s]);
+                                bulk_g2s(sa + kTileA, a.Fp + (size_t)kb * (8 * kN), kTileB, &full[s]);
+                            }
+                        }
+                        if (__shfl_sync(0xffffffffu, lok, 0) == 0) {
+                            ok = false;
+                            break;
+                        }
                     }
-                    if (s_abort) {
-                        ok = false;
-                        break;
-                    }
-                    uint8_t* sa = buf + s * (kTileA + kTileB);
-                    mbar_expect_tx(&full[s], kTileA + kTileB);
-                    bulk_g2s(sa, a.tiles + (size_t)(ch0 + c) * (kRB * kKC), kTileA, &full[s]);
-                    bulk_g2s(sa + kTileA, a.Fp + (size_t)a.chunk_kb[ch0 + c] * (8 * kN), kTileB, &full[s]);
                 }
             }
+        }
+        if (lane == 0) {
             if (!ok) {
                 s_abort = 1;
                 atomicExch(a.err, 1);
@@ -433,19 +453,9 @@ __global__ void __launch_bounds__(kSpmmThreads) k_spmm(const SpmmArgs a)
         // ---- epilogue (warps 0-3)
         uint32_t j = 0;
         for (int rb = blockIdx.x; rb < a.n_rb; rb += gridDim.x, ++j) {
+            // the row-block's metadata and output row are looked up before
+            // waiting for its accumulator, so the loads overlap the MMAs
             const int64_t nch = a.chunk_off[rb + 1] - a.chunk_off[rb];
-            const uint32_t ab = j & 1;
-            bool ok = true;
-            if (lane == 0) ok = mbar_wait(&acc_full[ab], (j >> 1) & 1) && !s_abort;
-            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-            if (!ok) {
-                if (lane == 0) {
-                    s_abort = 1;
-                    atomicExch(a.err, 1);
-                }
-                break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;");
             int b = 0;
             while (b + 1 < a.n_beams && a.rb_first[b + 1] <= rb) ++b;
             const int e = (rb - a.rb_first[b]) * kRB + t;
@@ -460,6 +470,18 @@ __global__ void __launch_bounds__(kSpmmThreads) k_spmm(const SpmmArgs a)
                     out = a.P + (size_t)(a.base[b] + e) * a.k;
                 }
             }
+            const uint32_t ab = j & 1;
+            bool ok = true;
+            if (lane == 0) ok = mbar_wait(&acc_full[ab], (j >> 1) & 1) && !s_abort;
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            if (!ok) {
+                if (lane == 0) {
+                    s_abort = 1;
+                    atomicExch(a.err, 1);
+                }
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + ab * kN;
 #pragma unroll 1
             for (int h = 0; h < kN; h += 32) {
