@@ -101,13 +101,21 @@ __global__ void __launch_bounds__(256) k_bin_hist(const PlanView P, const BinGeo
     const BinGeom g = G[b];
     const BeamDev bm = P.beams[b];
     const int64_t V = (int64_t)P.nx * P.ny * P.nz;
-    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V;
-         v += (int64_t)gridDim.x * blockDim.x) {
-        const int ix = (int)(v % P.nx), iy = (int)((v / P.nx) % P.ny), iz = (int)(v / ((int64_t)P.nx * P.ny));
-        const int cell = voxel_cell(g, bm, bounds + (size_t)b * tiles_max, P.R2, fmaf((float)ix, P.dx, P.ox),
-                                    fmaf((float)iy, P.dy, P.oy), fmaf((float)iz, P.dz, P.oz));
-        cellof[(size_t)b * V + v] = cell;
-        if (cell >= 0) atomicAdd(hist + (size_t)b * cells_max + cell, 1);
+    const int lane = threadIdx.x & 31;
+    // whole warps iterate together: the lanes of a warp that fall into the
+    // same cell add to its count with one atomic
+    const int64_t step = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); v0 < V; v0 += step) {
+        const int64_t v = v0 + lane;
+        int cell = -1;
+        if (v < V) {
+            const int ix = (int)(v % P.nx), iy = (int)((v / P.nx) % P.ny), iz = (int)(v / ((int64_t)P.nx * P.ny));
+            cell = voxel_cell(g, bm, bounds + (size_t)b * tiles_max, P.R2, fmaf((float)ix, P.dx, P.ox),
+                              fmaf((float)iy, P.dy, P.oy), fmaf((float)iz, P.dz, P.oz));
+            cellof[(size_t)b * V + v] = cell;
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, cell);
+        if (cell >= 0 && lane == __ffs(peers) - 1) atomicAdd(hist + (size_t)b * cells_max + cell, __popc(peers));
     }
 }
 
@@ -231,11 +239,20 @@ __global__ void __launch_bounds__(256) k_bin_scatter(int64_t V, int n_beams, int
 {
     const int b = blockIdx.y;
     const int64_t b0 = base[b];
-    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V;
-         v += (int64_t)gridDim.x * blockDim.x) {
-        const int cell = cellof[(size_t)b * V + v];
+    const int lane = threadIdx.x & 31;
+    // one atomic per cell and warp; the warp's voxels of a cell keep their
+    // order (lane order) inside the cell's list
+    const int64_t step = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); v0 < V; v0 += step) {
+        const int64_t v = v0 + lane;
+        const int cell = v < V ? cellof[(size_t)b * V + v] : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, cell);
+        const int leader = __ffs(peers) - 1;
+        int first = 0;
+        if (cell >= 0 && lane == leader) first = atomicAdd(cursor + (size_t)b * cells_max + cell, __popc(peers));
+        first = __shfl_sync(0xffffffffu, first, leader);
         if (cell >= 0) {
-            const int pos = atomicAdd(cursor + (size_t)b * cells_max + cell, 1) - bstart[b];
+            const int pos = first + __popc(peers & ((1u << lane) - 1u)) - bstart[b];
             items[b0 + pos] = (int32_t)v;
         }
     }
