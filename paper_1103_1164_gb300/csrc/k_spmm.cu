@@ -23,6 +23,7 @@
 // Per-beam partial results are combined with compensated (Neumaier) sums.
 #include <stdint.h>
 
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -287,8 +288,9 @@ struct SpmmArgs {
     float* Y;                    // single beam: [V][k]
     float* P;                    // several beams: partial rows [item][k] per beam list position
     int direct;
-    int vec4;                    // rows may be written as float4 (k % 4 == 0, 16-byte aligned output)
     int32_t* err;
+    const int32_t* zero;         // single beam: voxels in no list, whose rows are written as zeros
+    int64_t n_zero;
 };
 
 // Reads 32 FP32 columns of this warp's 32 accumulator rows from tensor memory.
@@ -306,22 +308,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r)
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Writes 32 columns [q0, q0 + 32) of an output row.
-__device__ __forceinline__ void store_cols(float* out, int q0, int k, bool vec4, const uint32_t* r)
-{
-    if (vec4) {
-#pragma unroll
-        for (int q = 0; q < 32; q += 4)
-            if (q0 + q < k)
-                *reinterpret_cast<float4*>(out + q0 + q) = make_float4(
-                    __uint_as_float(r[q]), __uint_as_float(r[q + 1]), __uint_as_float(r[q + 2]), __uint_as_float(r[q + 3]));
-    } else {
-#pragma unroll
-        for (int q = 0; q < 32; ++q)
-            if (q0 + q < k) out[q0 + q] = __uint_as_float(r[q]);
-    }
-}
-
 // Warp roles: warps 0-3 drain the accumulator of a finished row-block (warp w
 // owns tensor-memory lanes 32w..32w+31, i.e. rows 32w.. of the row-block),
 // warp 4 (one lane) streams the A and F tiles of all the CTA's row-blocks
@@ -335,6 +321,7 @@ __global__ void __launch_bounds__(kSpmmThreads) k_spmm(const SpmmArgs a)
     __shared__ uint64_t full[kStages], empty[kStages], acc_full[2], acc_empty[2];
     __shared__ uint32_t tmem_base;
     __shared__ volatile int s_abort;
+    __shared__ float s_epi[kEpiWarps][32 * 33];   // epilogue transpose, one 32 x 32 block per warp
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
 
     // stage buffers, 1 KB aligned
@@ -360,6 +347,9 @@ __global__ void __launch_bounds__(kSpmmThreads) k_spmm(const SpmmArgs a)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_base;
+    // the launch may overlap the pre-pass (programmatic dependent launch):
+    // from here on its packed fluences and status word are needed
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 
     if (warp == kEpiWarps) {
         // ---- producer: every chunk of every row-block of this CTA, in order.
@@ -451,6 +441,13 @@ __global__ void __launch_bounds__(kSpmmThreads) k_spmm(const SpmmArgs a)
         }
     } else {
         // ---- epilogue (warps 0-3)
+        // first, while the first accumulator fills: the rows of voxels in no
+        // beam list (one-beam plans), which no row-block writes
+        // (a warp per row: consecutive lanes write consecutive columns)
+        for (int64_t z = blockIdx.x * (int64_t)kEpiWarps + warp; z < a.n_zero; z += (int64_t)gridDim.x * kEpiWarps) {
+            float* out = a.Y + (size_t)__ldg(a.zero + z) * a.k;
+            for (int q = lane; q < a.k; q += 32) out[q] = 0.f;
+        }
         uint32_t j = 0;
         for (int rb = blockIdx.x; rb < a.n_rb; rb += gridDim.x, ++j) {
             // the row-block's metadata and output row are looked up before
@@ -500,7 +497,21 @@ __global__ void __launch_bounds__(kSpmmThreads) k_spmm(const SpmmArgs a)
                         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[ab]))
                                      : "memory");
                 }
-                if (out) store_cols(out, h, a.k, a.vec4 != 0, r);
+                // through shared memory, so that each store writes one row's 32
+                // consecutive columns (128 contiguous bytes) instead of 16 bytes
+                // of 32 different rows: lane l holds row l; row stride 33 words
+                // keeps both the writes and the reads free of bank conflicts
+                float* sw = s_epi[warp];
+#pragma unroll
+                for (int q = 0; q < 32; ++q) sw[lane * 33 + q] = __uint_as_float(r[q]);
+                __syncwarp();
+                const bool col_ok = h + lane < a.k;
+#pragma unroll 4
+                for (int row = 0; row < 32; ++row) {
+                    float* o = reinterpret_cast<float*>(__shfl_sync(0xffffffffu, reinterpret_cast<uintptr_t>(out), row));
+                    if (o && col_ok) o[h + lane] = sw[row * 33 + lane];
+                }
+                __syncwarp();
             }
         }
     }
@@ -548,7 +559,7 @@ __global__ void __launch_bounds__(256) k_inverse(const int32_t* __restrict__ ite
 // tensor memory, so at most 4 CTAs may be resident on an SM (512 columns): the
 // shared-memory request is raised, if needed, so that a fifth cannot fit (an
 // allocation beyond the SM's columns would wait for a resident CTA to finish).
-cudaError_t spmm_launch_shape(int device, size_t smem, int n_rb, int* grid, size_t* smem_req)
+cudaError_t spmm_launch_shape(int device, size_t smem, int n_rb, int64_t n_zero, int* grid, size_t* smem_req)
 {
     int smem_sm = 0, sms = 0, reserved = 0;
     cudaError_t e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device);
@@ -575,8 +586,10 @@ cudaError_t spmm_launch_shape(int device, size_t smem, int n_rb, int* grid, size
     const int by_regs = regs_cta > 0 ? regs_sm / regs_cta : 4;
     int per_sm = by_smem < by_regs ? by_smem : by_regs;
     per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
-    int g = sms * per_sm;
-    *grid = g > n_rb ? n_rb : g;
+    // enough CTAs for the row-blocks, and for the zero rows (one per epilogue warp and pass)
+    const int64_t need = std::max<int64_t>(n_rb, (n_zero + kEpiWarps - 1) / kEpiWarps);
+    const int g = sms * per_sm;
+    *grid = (int)(g > need ? need : g);
     *smem_req = req;
     return cudaSuccess;
 }
@@ -589,19 +602,34 @@ __global__ void __launch_bounds__(256) k_unlisted(const int32_t* __restrict__ in
         if (inv[v] < 0) zero[atomicAdd(n, 1ull)] = (int32_t)v;
 }
 
-// The work of one call before k_spmm, in one launch: the packed fluences; for
-// one-beam plans Y[v][0..k) = 0 for the voxels v of zero[] (in no beam list:
-// k_spmm does not write their rows); and the bounded-wait status word cleared.
+// The work of one call before k_spmm: the packed fluences and the
+// bounded-wait status word cleared.  k_spmm may start (its set-up) as soon as
+// every CTA of this grid has begun; it waits for this grid's completion before
+// it reads the packed fluences.
 __global__ void __launch_bounds__(256) k_spmm_pre(const float* __restrict__ F, int k, int nkb,
                                                   const int4* __restrict__ beam, int n_beams,
-                                                  __nv_bfloat16* __restrict__ Fp, const int32_t* __restrict__ zero,
-                                                  int64_t n_zero, float* __restrict__ Y, int32_t* __restrict__ err)
+                                                  __nv_bfloat16* __restrict__ Fp, int32_t* __restrict__ err)
 {
+    asm volatile("griddepcontrol.launch_dependents;");
     if (blockIdx.x == 0 && threadIdx.x == 0) *err = 0;
     pack_fluence(F, k, nkb, beam, n_beams, Fp);
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_zero * k;
-         e += (int64_t)gridDim.x * blockDim.x)
-        Y[(size_t)zero[e / k] * k + e % k] = 0.f;
+}
+
+// k_spmm on `stream`, allowed to overlap the tail of the preceding kernel
+// (k_spmm_pre) through programmatic dependent launch.
+cudaError_t launch_spmm(const SpmmArgs& a, int grid, size_t smem, cudaStream_t stream)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kSpmmThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_spmm, a);
 }
 
 int gsize(int64_t n)
@@ -743,13 +771,9 @@ cudaError_t spmm_run(dc_plan* p, const float* F, int k, float* Y)
             p->sp_p_cap = need;
         }
     }
-    {
-        const int64_t nz = direct ? p->sp_n_zero : 0;
-        k_spmm_pre<<<gsize((int64_t)nkb * 8 * kN + nz * k), 256, 0, p->stream>>>(
-            F, k, nkb, p->d_sp_first, p->n_beams, reinterpret_cast<__nv_bfloat16*>(p->d_sp_fp), p->d_sp_zero, nz,
-            Y, p->d_err);
-        count_launches(1);
-    }
+    k_spmm_pre<<<gsize((int64_t)nkb * 8 * kN), 256, 0, p->stream>>>(
+        F, k, nkb, p->d_sp_first, p->n_beams, reinterpret_cast<__nv_bfloat16*>(p->d_sp_fp), p->d_err);
+    count_launches(1);
     SpmmArgs a{};
     a.tiles = reinterpret_cast<const uint16_t*>(p->d_sp_tiles);
     a.chunk_kb = p->d_sp_kb;
@@ -765,18 +789,17 @@ cudaError_t spmm_run(dc_plan* p, const float* F, int k, float* Y)
     a.Y = Y;
     a.P = p->d_sp_p;
     a.direct = direct ? 1 : 0;
-    float* out0 = direct ? Y : p->d_sp_p;
-    a.vec4 = (k % 4 == 0 && (reinterpret_cast<uintptr_t>(out0) & 15) == 0) ? 1 : 0;
     a.err = p->d_err;
+    a.zero = p->d_sp_zero;
+    a.n_zero = direct ? p->sp_n_zero : 0;
     const size_t smem = (size_t)kStages * (kTileA + kTileB) + 1024;
     int grid = 0;
     size_t smem_req = 0;
-    e = spmm_launch_shape(p->device, smem, p->sp_n_rb, &grid, &smem_req);
+    e = spmm_launch_shape(p->device, smem, p->sp_n_rb, a.n_zero, &grid, &smem_req);
     if (e != cudaSuccess) return e;
     if (grid > 0) {
-        k_spmm<<<grid, kSpmmThreads, smem_req, p->stream>>>(a);
+        e = launch_spmm(a, grid, smem_req, p->stream);
         count_launches(1);
-        e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     if (!direct) {
@@ -859,14 +882,11 @@ cudaError_t spmm_run_static(dc_plan* p, const float* F, int k, float* Y)
     StaticScratch sc;
     cudaError_t e = static_scratch(p->device, &sc);
     if (e != cudaSuccess) return e;
-    // the packed fluences, the output rows of voxels outside every beam list
-    // (never written by k_spmm) and the bounded-wait status word read after the call
-    {
-        const int64_t nz = direct ? p->sp_n_zero : 0;
-        k_spmm_pre<<<gsize((int64_t)nkb * 8 * kN + nz * k), 256, 0, p->stream>>>(
-            F, k, nkb, p->d_sp_first, p->n_beams, sc.fp, p->d_sp_zero, nz, Y, p->d_err);
-        count_launches(1);
-    }
+    // the packed fluences and the bounded-wait status word read after the call
+    // (k_spmm itself writes the zero rows of voxels outside every beam list)
+    k_spmm_pre<<<gsize((int64_t)nkb * 8 * kN), 256, 0, p->stream>>>(F, k, nkb, p->d_sp_first, p->n_beams, sc.fp,
+                                                                    p->d_err);
+    count_launches(1);
     SpmmArgs a{};
     a.tiles = reinterpret_cast<const uint16_t*>(p->d_sp_tiles);
     a.chunk_kb = p->d_sp_kb;
@@ -882,18 +902,17 @@ cudaError_t spmm_run_static(dc_plan* p, const float* F, int k, float* Y)
     a.Y = Y;
     a.P = sc.part;
     a.direct = direct ? 1 : 0;
-    float* out0 = direct ? Y : sc.part;
-    a.vec4 = (k % 4 == 0 && (reinterpret_cast<uintptr_t>(out0) & 15) == 0) ? 1 : 0;
     a.err = p->d_err;
+    a.zero = p->d_sp_zero;
+    a.n_zero = direct ? p->sp_n_zero : 0;
     const size_t smem = (size_t)kStages * (kTileA + kTileB) + 1024;
     int grid = 0;
     size_t smem_req = 0;
-    e = spmm_launch_shape(p->device, smem, p->sp_n_rb, &grid, &smem_req);
+    e = spmm_launch_shape(p->device, smem, p->sp_n_rb, a.n_zero, &grid, &smem_req);
     if (e != cudaSuccess) return e;
     if (grid > 0) {
-        k_spmm<<<grid, kSpmmThreads, smem_req, p->stream>>>(a);
+        e = launch_spmm(a, grid, smem_req, p->stream);
         count_launches(1);
-        e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     if (!direct) {
