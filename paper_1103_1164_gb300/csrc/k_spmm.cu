@@ -37,7 +37,9 @@ constexpr int kKC = 16;              // beamlets per K-chunk
 constexpr int kN = 64;               // fluence columns of the MMA
 constexpr int kTileA = kRB * kKC * 2;     // 4096 bytes
 constexpr int kTileB = kKC * kN * 2;      // 2048 bytes
-constexpr int kStages = 8;
+constexpr int kStages = 3;
+constexpr int kAcc = 1;                       // accumulators in tensor memory (kN columns each)
+constexpr int kMaxCtasPerSm = 512 / (kAcc * kN);   // tensor memory holds 512 columns per SM
 constexpr int kEpiWarps = 4;                  // epilogue warps (one per 32 accumulator rows)
 constexpr int kSpmmThreads = 32 * (kEpiWarps + 2);
 constexpr long long kSpinLimit = 1ll << 26;   // bounded mbarrier waits ...
@@ -311,14 +313,15 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r)
 // Warp roles: warps 0-3 drain the accumulator of a finished row-block (warp w
 // owns tensor-memory lanes 32w..32w+31, i.e. rows 32w.. of the row-block),
 // warp 4 (one lane) streams the A and F tiles of all the CTA's row-blocks
-// through the stage ring, warp 5 (one lane) issues the MMAs.  The accumulator
-// is double-buffered in tensor memory (2 x 64 columns), so the loads and MMAs
-// of row-block j + 1 overlap the epilogue of row-block j and the ring never
-// drains between row-blocks.
+// through the stage ring, warp 5 (one lane) issues the MMAs.  With kAcc
+// accumulators in tensor memory, the MMAs of row-block j + kAcc wait for the
+// epilogue of row-block j; the loads run ahead through the ring.  One
+// accumulator and a 3-stage ring per CTA let 6 CTAs share an SM (measured:
+// more resident CTAs per SM shorten the call, deeper rings per CTA do not).
 __global__ void __launch_bounds__(kSpmmThreads) k_spmm(const SpmmArgs a)
 {
     extern __shared__ __align__(1024) uint8_t sm[];
-    __shared__ uint64_t full[kStages], empty[kStages], acc_full[2], acc_empty[2];
+    __shared__ uint64_t full[kStages], empty[kStages], acc_full[kAcc], acc_empty[kAcc];
     __shared__ uint32_t tmem_base;
     __shared__ volatile int s_abort;
     __shared__ float s_epi[kEpiWarps][32 * 33];   // epilogue transpose, one 32 x 32 block per warp
@@ -331,7 +334,7 @@ __global__ void __launch_bounds__(kSpmmThreads) k_spmm(const SpmmArgs a)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < kAcc; ++q) {
             mbar_init(&acc_full[q], 1);
             mbar_init(&acc_empty[q], kEpiWarps);
         }
@@ -340,7 +343,7 @@ __global__ void __launch_bounds__(kSpmmThreads) k_spmm(const SpmmArgs a)
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                     "r"(2 * kN));
+                     "r"(kAcc * kN));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -411,9 +414,9 @@ __global__ void __launch_bounds__(kSpmmThreads) k_spmm(const SpmmArgs a)
             bool ok = true;
             for (int rb = blockIdx.x; rb < a.n_rb && ok; rb += gridDim.x, ++j) {
                 const int64_t nch = a.chunk_off[rb + 1] - a.chunk_off[rb];
-                const uint32_t ab = j & 1;
-                // the epilogue of row-block j - 2 has read this accumulator
-                if (j >= 2 && !mbar_wait(&acc_empty[ab], ((j >> 1) - 1) & 1)) {
+                const uint32_t ab = j % kAcc;
+                // the epilogue of row-block j - kAcc has read this accumulator
+                if (j >= kAcc && !mbar_wait(&acc_empty[ab], ((j / kAcc) - 1) & 1)) {
                     ok = false;
                     break;
                 }
@@ -467,9 +470,9 @@ __global__ void __launch_bounds__(kSpmmThreads) k_spmm(const SpmmArgs a)
                     out = a.P + (size_t)(a.base[b] + e) * a.k;
                 }
             }
-            const uint32_t ab = j & 1;
+            const uint32_t ab = j % kAcc;
             bool ok = true;
-            if (lane == 0) ok = mbar_wait(&acc_full[ab], (j >> 1) & 1) && !s_abort;
+            if (lane == 0) ok = mbar_wait(&acc_full[ab], (j / kAcc) & 1) && !s_abort;
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             if (!ok) {
                 if (lane == 0) {
@@ -519,7 +522,7 @@ __global__ void __launch_bounds__(kSpmmThreads) k_spmm(const SpmmArgs a)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kN));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kAcc * kN));
 }
 
 // Y[v][q] = sum over beams of the partial rows, in beam order, with
@@ -573,7 +576,7 @@ cudaError_t spmm_launch_shape(int device, size_t smem, int n_rb, int64_t n_zero,
     if (e != cudaSuccess) return e;
     const size_t static_smem = fa.sharedSizeBytes;
     size_t req = smem;
-    const size_t min_per_cta = (size_t)smem_sm / 5 + 1;   // five CTAs must not fit
+    const size_t min_per_cta = (size_t)smem_sm / (kMaxCtasPerSm + 1) + 1;   // one more CTA than tensor memory holds must not fit
     if (req + static_smem + (size_t)reserved < min_per_cta) req = min_per_cta - static_smem - (size_t)reserved;
     e = cudaFuncSetAttribute(k_spmm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)req);
     if (e != cudaSuccess) return e;
@@ -585,7 +588,7 @@ cudaError_t spmm_launch_shape(int device, size_t smem, int n_rb, int64_t n_zero,
     const int regs_cta = ((fa.numRegs + 7) / 8 * 8) * kSpmmThreads;
     const int by_regs = regs_cta > 0 ? regs_sm / regs_cta : 4;
     int per_sm = by_smem < by_regs ? by_smem : by_regs;
-    per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
+    per_sm = per_sm < 1 ? 1 : (per_sm > kMaxCtasPerSm ? kMaxCtasPerSm : per_sm);
     // enough CTAs for the row-blocks, and for the zero rows (one per epilogue warp and pass)
     const int64_t need = std::max<int64_t>(n_rb, (n_zero + kEpiWarps - 1) / kEpiWarps);
     const int g = sms * per_sm;
