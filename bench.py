@@ -411,14 +411,23 @@ def run_ours(args, world, rank, local, pg):
               "hbm_peak_GBps": peaks.get("hbm_gbs"), "count_scan_ms": float(stage[:, 2].mean()),
               "nnz": pairs, "bytes": bytes_matrix}
 
-    forms = run_forms(args, dc, torch, stream, peaks)
-    forms["fused_plan"] = run_fused_form(args, dc, torch, stream, plan, rho_d, flu_d, dose_d, rowptr_d, cols_d,
-                                         vals_d, flush, float(step_ms.mean()), pairs)
-    forms["surrogate"] = run_surrogate_form(args, dc, torch, stream)
-    forms["batch"] = run_batch_form(args, dc, torch, stream, peak_pairs)
-    forms["gamma"] = run_gamma_form(args, dc, torch, stream, p, rho_d, flu_d)
-    forms["table1"] = run_table1_form(args, dc, torch, stream, flush)
-    forms["leaf_sequences"] = run_leaf_form(args, dc, torch, stream, flush)
+    # the other forms of the path; one that fails is reported as such and does
+    # not take the benchmark line with it
+    def form(fn, *fa):
+        try:
+            return fn(*fa)
+        except Exception as exc:                      # noqa: BLE001 (reported in the line)
+            torch.cuda.synchronize()
+            return {"error": f"{type(exc).__name__}: {exc}"[:300]}
+
+    forms = form(run_forms, args, dc, torch, stream, peaks)
+    forms["fused_plan"] = form(run_fused_form, args, dc, torch, stream, plan, rho_d, flu_d, dose_d, rowptr_d,
+                               cols_d, vals_d, flush, float(step_ms.mean()), pairs)
+    forms["surrogate"] = form(run_surrogate_form, args, dc, torch, stream)
+    forms["batch"] = form(run_batch_form, args, dc, torch, stream, peak_pairs)
+    forms["gamma"] = form(run_gamma_form, args, dc, torch, stream, p, rho_d, flu_d)
+    forms["table1"] = form(run_table1_form, args, dc, torch, stream, flush)
+    forms["leaf_sequences"] = form(run_leaf_form, args, dc, torch, stream, flush)
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, dc, p, plan, pairs, torch)
