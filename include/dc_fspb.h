@@ -445,7 +445,7 @@ dc_status dc_fspb_get_tables(const dc_plan* plan, int32_t i, float* teq, float* 
  * projection into the isocentre plane (tiles of `tile` cm) and their depth
  * along the beam axis (slabs of `slab` cm), 32 voxels per warp.  This call
  * times dc_fspb_dose for each candidate (tile in {0.35, 0.5, 0.75} cm, slab in
- * {1, 2, 4} cm) with `fluence` [B] (host, or device with DC_DEVICE_PTRS), keeps
+ * {0.5, 1, 2, 4} cm) with `fluence` [B] (host, or device with DC_DEVICE_PTRS), keeps
  * the fastest for the plan, and returns it in *tile, *slab and its time in
  * *best_ms (each output may be NULL).  Results do not depend on the choice
  * (every voxel sums the same pairs in the same order).

@@ -146,7 +146,7 @@ static void beam_frame_host(const dc_beam& bm, double* ex, double* ey, double* e
 // (finest first: the plan's buffers are sized for the first pair).
 static const float kDefaultTile = 0.5f, kDefaultSlab = 2.0f;
 static const float kTuneTiles[] = {0.35f, 0.5f, 0.75f};
-static const float kTuneSlabs[] = {1.0f, 2.0f, 4.0f};
+static const float kTuneSlabs[] = {0.5f, 1.0f, 2.0f, 4.0f};
 
 // Beam's-eye-view binning grid of each beam (see k_bin.cu).
 static void bin_geometry(dc_plan* p, float tile, float slab)
