@@ -562,7 +562,18 @@ __global__ void __launch_bounds__(256) k_inverse(const int32_t* __restrict__ ite
 // tensor memory, so at most 4 CTAs may be resident on an SM (512 columns): the
 // shared-memory request is raised, if needed, so that a fifth cannot fit (an
 // allocation beyond the SM's columns would wait for a resident CTA to finish).
-cudaError_t spmm_launch_shape(int device, size_t smem, int n_rb, int64_t n_zero, int* grid, size_t* smem_req)
+// Resident CTAs per SM and the dynamic shared memory to request, per device
+// (looked up on the first call on a device: the attribute queries cost more
+// than the launch itself on small problems).
+struct SpmmShape {
+    int per_sm = 0, sms = 0;
+    size_t req = 0;
+};
+constexpr int kShapeDevices = 64;
+SpmmShape g_shape[kShapeDevices];
+std::mutex g_shape_mu;
+
+cudaError_t spmm_device_shape(int device, size_t smem, SpmmShape* out)
 {
     int smem_sm = 0, sms = 0, reserved = 0;
     cudaError_t e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device);
@@ -589,11 +600,31 @@ cudaError_t spmm_launch_shape(int device, size_t smem, int n_rb, int64_t n_zero,
     const int by_regs = regs_cta > 0 ? regs_sm / regs_cta : 4;
     int per_sm = by_smem < by_regs ? by_smem : by_regs;
     per_sm = per_sm < 1 ? 1 : (per_sm > kMaxCtasPerSm ? kMaxCtasPerSm : per_sm);
+    out->per_sm = per_sm;
+    out->sms = sms;
+    out->req = req;
+    return cudaSuccess;
+}
+
+cudaError_t spmm_launch_shape(int device, size_t smem, int n_rb, int64_t n_zero, int* grid, size_t* smem_req)
+{
+    if (device < 0 || device >= kShapeDevices) return cudaErrorInvalidDevice;
+    SpmmShape sh;
+    {
+        std::lock_guard<std::mutex> lock(g_shape_mu);
+        sh = g_shape[device];
+    }
+    if (sh.per_sm == 0) {
+        cudaError_t e = spmm_device_shape(device, smem, &sh);
+        if (e != cudaSuccess) return e;
+        std::lock_guard<std::mutex> lock(g_shape_mu);
+        g_shape[device] = sh;
+    }
     // enough CTAs for the row-blocks, and for the zero rows (one per epilogue warp and pass)
     const int64_t need = std::max<int64_t>(n_rb, (n_zero + kEpiWarps - 1) / kEpiWarps);
-    const int g = sms * per_sm;
+    const int g = sh.sms * sh.per_sm;
     *grid = (int)(g > need ? need : g);
-    *smem_req = req;
+    *smem_req = sh.req;
     return cudaSuccess;
 }
 
