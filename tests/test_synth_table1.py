@@ -1,8 +1,38 @@
 """The synthetic Table 1 cases follow the table's case dimensions (host only)."""
+import os
+
 import numpy as np
 import pytest
 
 from paper_1103_1164_gb300 import synth
+
+TESTS = os.path.dirname(os.path.abspath(__file__))
+GOLDEN = os.path.join(TESTS, "golden")
+
+
+def _tsv(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+def test_table1_constants_match_the_printed_table():
+    printed = {r[0]: (int(r[1]), bool(int(r[2])), int(r[3]), (int(r[4]), int(r[5]), int(r[6])))
+               for r in _tsv("table1_cases.tsv")}
+    assert set(printed) == {c[0] for c in synth.TABLE1}
+    for name, _, nb, noncop, n_bl, nz, _ in synth.TABLE1:
+        assert printed[name] == (nb, noncop, n_bl, (128, 128, nz)), name
+
+
+def test_table4_times_in_the_bench_match_the_printed_table():
+    import sys
+    sys.path.insert(0, os.path.dirname(TESTS))
+    import bench
+    printed = {r[0]: float(r[1]) for r in _tsv("table4_tgpu.tsv")}
+    assert bench.TABLE4_TGPU_S == printed
 
 
 @pytest.mark.parametrize("row", synth.TABLE1, ids=[r[0] for r in synth.TABLE1])
