@@ -41,16 +41,15 @@ ALG_FP32_PER_PAIR = 98     # FP32 add/mul/fma/compare/round operations (itemised
 ALG_MUFU_PER_PAIR = 9      # 8 exponentials (four p() of eq. 4) + 1 reciprocal (SAD/|r_a|)
 FP32_LANES_PER_SM = 128
 MUFU_LANES_PER_SM = 16
-ISSUE_LANES_PER_SM = 4 * 32   # 4 schedulers, one warp instruction (32 lanes) per cycle each
 L2_FLUSH_BYTES = 256 << 20
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the dose kernel on the thorax9 plan, from an ncu capture of the kernel built
 # from the sources with these SHA-256 digests (the kernel and the structures it
 # reads; profiles/k_pairs_dose_thorax9.md); reported only while they are unchanged.
-DOSE_TRAFFIC_BYTES = 110275840 + 20685824
+DOSE_TRAFFIC_BYTES = 110434560 + 20635136
 DOSE_TRAFFIC_SOURCES = {
-    "paper_1103_1164_gb300/csrc/k_dose.cu": "3ff71f002c718d0c4b5d444089abc425719f65b47f857dbb4d24e3f9219b1d49",
-    "paper_1103_1164_gb300/csrc/dc_views.cuh": "876c93613262887f8c1924a9fd07ca736db19493e19ef78261ec02b35c671d3a",
+    "paper_1103_1164_gb300/csrc/k_dose.cu": "c9de7234dff5e8128d260d7aae312ddc7a8032fc1f73877a296ebdee1cd2320a",
+    "paper_1103_1164_gb300/csrc/dc_views.cuh": "604f1c61d84a82494049db8c574ff1384cee296c4ebbe27db75ba78b5c54a772",
 }
 
 
@@ -389,19 +388,18 @@ def run_ours(args, world, rank, local, pg):
     # roofline of the dominant kernel: the direct dose kernel (ALU bound)
     t_dose = float(stage[:, 1].mean()) * 1e-3
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    # every FP32 and MUFU operation also takes an issue slot, so the bound is the
-    # tightest of the FP32 lanes, the MUFU lanes and the issue slots
+    # the tighter of the FP32 lanes and the MUFU lanes (issue slots do not bound
+    # the method: packed FP32 instructions issue two of its operations at once)
     peak_pairs = props.multi_processor_count * sm_max * 1e6 * min(
-        FP32_LANES_PER_SM / ALG_FP32_PER_PAIR, MUFU_LANES_PER_SM / ALG_MUFU_PER_PAIR,
-        ISSUE_LANES_PER_SM / (ALG_FP32_PER_PAIR + ALG_MUFU_PER_PAIR))
+        FP32_LANES_PER_SM / ALG_FP32_PER_PAIR, MUFU_LANES_PER_SM / ALG_MUFU_PER_PAIR)
     achieved = pairs / t_dose
     roofline = {"kernel": "k_dose<dose,1> (eqs. 1-4)", "bound": "alu",
                 "achieved": achieved / 1e9, "peak": peak_pairs / 1e9, "unit": "Gpair/s",
                 "frac": achieved / peak_pairs, "traffic": dose_traffic(args.scale),
                 "traffic_unit": "bytes per launch (ncu dram read + write)",
                 "peak_basis": f"{props.multi_processor_count} SMs x {sm_max:.0f} MHz x "
-                              f"min(128/{ALG_FP32_PER_PAIR} FP32 lanes, 16/{ALG_MUFU_PER_PAIR} MUFU lanes, "
-                              f"128/{ALG_FP32_PER_PAIR + ALG_MUFU_PER_PAIR} issue slots) pairs per cycle and SM",
+                              f"min(128/{ALG_FP32_PER_PAIR} FP32 lanes, 16/{ALG_MUFU_PER_PAIR} MUFU lanes) "
+                              f"pairs per cycle and SM",
                 "dose_kernel_ms": t_dose * 1e3,
                 "timing": "CUDA events around dc_fspb_dose on the plan's stream: the pair kernel plus "
                           "the per-beam sum and two small memsets (the pair kernel alone is ~2 % shorter)"}

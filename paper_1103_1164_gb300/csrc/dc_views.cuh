@@ -65,7 +65,7 @@ struct PlanView {
     const BeamletDev* bl;
     const float4* tab;
     // when the water tables' step equals d: [B][Kmax][3] float4
-    //   (t_eq, dt_eq, O1, dO1), (O2, dO2, u1w, du1w), (u2w, du2w, 0, 0)
+    //   (t_eq, dt_eq, O1, O2), (dO1, dO2, u1w, u2w), (du1w, du2w, 0, 0)
     // with O_i = omega_i^w + omega_i^corr (times 0 without density correction)
     const float4* tabm;
     // per-(voxel, beam) lateral factors for every voxel-list entry (axis and

@@ -78,16 +78,24 @@ __device__ __forceinline__ uint32_t grid_bits_mul(float a, float b, float& frac)
     return __float_as_uint(f);
 }
 
-// Eq. (4) with k = u log2(e), kx0 = k x0: with e1 = exp(-u ||x| - x0|) and
+// Eq. (4) with k = u log2(e): with e1 = exp(-u ||x| - x0|) and
 // e2 = exp(-u (|x| + x0)) it is (e1 - e2)/2 outside |x| <= x0 and
-// 1 - (e1 + e2)/2 inside, i.e. (e1 - e2)/2 + [inside] (1 - e1).
-__device__ __forceinline__ float penumbra(float x, float k, float kx0, float x0)
+// 1 - (e1 + e2)/2 inside.
+// Evaluated for the x and y profiles of one component at once, in packed FP32
+// pairs (one instruction for both axes wherever the two run the same
+// operation): ax = (|x|, |y|), nk = -k per axis, x0 = (x0, y0).  With
+// d = |x| - x0 and c = copysign(1 - e1, d), eq. (4) is 1/2 - (c + e2)/2 on
+// both sides of |x| = x0 (c = -(1 - e1) inside, 1 - e1 outside).
+__device__ __forceinline__ float2 penumbra2(float2 ax, float2 nk, float2 x0, float2 nx0)
 {
-    const float ax = fabsf(x);
-    const float e1 = ex2(-k * fabsf(ax - x0));
-    const float e2 = ex2(fmaf(-k, ax, -kx0));
-    const float ins = ax <= x0 ? 1.0f : 0.0f;
-    return fmaf(0.5f, e1 - e2, fmaf(-ins, e1, ins));
+    const float2 d = __fadd2_rn(ax, nx0);
+    const float2 t1 = __fmul2_rn(nk, make_float2(fabsf(d.x), fabsf(d.y)));
+    const float2 t2 = __ffma2_rn(nk, ax, __fmul2_rn(nk, x0));
+    const float2 e1 = make_float2(ex2(t1.x), ex2(t1.y));
+    const float2 e2 = make_float2(ex2(t2.x), ex2(t2.y));
+    const float2 c = __ffma2_rn(e1, make_float2(-1.f, -1.f), make_float2(1.f, 1.f));
+    const float2 q = __fadd2_rn(make_float2(copysignf(c.x, d.x), copysignf(c.y, d.y)), e2);
+    return __ffma2_rn(make_float2(-0.5f, -0.5f), q, make_float2(0.5f, 0.5f));
 }
 
 // Lateral correction of step 11: the paper's rho(r), rho_hat(r) per voxel
@@ -152,10 +160,13 @@ __device__ __forceinline__ float pair_eval(const PlanView& P, const Lane& ln, co
         const float4* tb = P.tabm + (i * (3u * (uint32_t)P.Kmax) + 3u * (kb - kGridBits));
         const float4 e0 = __ldg(tb), e1 = __ldg(tb + 1), e2 = __ldg(tb + 2);
         teq = fmaf(fr, e0.y, e0.x);
-        O1 = fmaf(fr, e0.w, e0.z);
-        O2 = fmaf(fr, e1.y, e1.x);
-        u1w = fmaf(fr, e1.w, e1.z);
-        u2w = fmaf(fr, e2.y, e2.x);
+        const float2 frr = make_float2(fr, fr);
+        const float2 O = __ffma2_rn(frr, make_float2(e1.x, e1.y), make_float2(e0.z, e0.w));
+        const float2 U = __ffma2_rn(frr, make_float2(e2.x, e2.y), make_float2(e1.z, e1.w));
+        O1 = O.x;
+        O2 = O.y;
+        u1w = U.x;
+        u2w = U.y;
     } else {
         const float4* tb = P.tab + (i * (2u * (uint32_t)P.Kmax) + 2u * (kb - kGridBits));
         const float4 e0 = __ldg(tb), e1 = __ldg(tb + 1);
@@ -177,15 +188,19 @@ __device__ __forceinline__ float pair_eval(const PlanView& P, const Lane& ln, co
     const float2 ar = __ldg(P.arow + (i * (uint32_t)P.a_nt + (jb - kGridBits)));
     const float Av = fmaf(fa, ar.y, ar.x);
 
-    // density correction (step 11)
-    const float k1 = ln.cu1 * u1w, k2 = ln.cu2x * u2w;
-    const float k2y = LAT == kIso ? k2 : ln.cu2y * u2w;
-    const float om1 = fmaxf(ln.cw1 * O1, 0.f);
-    const float om2 = fmaxf(ln.cw2 * O2, 0.f);
+    // density correction (step 11), in pairs: -(k1, k2) with k = log2(e) f_u u^w,
+    // and (omega_1, omega_2)
+    const float2 nk = __fmul2_rn(make_float2(-ln.cu1, -ln.cu2x), make_float2(u1w, u2w));
+    const float nk2y = LAT == kIso ? nk.y : -ln.cu2y * u2w;
+    const float2 om = __fmul2_rn(make_float2(ln.cw1, ln.cw2), make_float2(O1, O2));
+    const float om1 = fmaxf(om.x, 0.f), om2 = fmaxf(om.y, 0.f);
 
-    // eqs. (3) and (2)
-    const float F = fmaf(om1 * penumbra(x, k1, k1 * P.x0, P.x0), penumbra(y, k1, k1 * P.y0, P.y0),
-                         om2 * penumbra(x, k2, k2 * P.x0, P.x0) * penumbra(y, k2y, k2y * P.y0, P.y0));
+    // eqs. (3) and (2): the x and y profiles of each component together
+    const float2 axy = make_float2(fabsf(x), fabsf(y));
+    const float2 x0 = make_float2(P.x0, P.y0), nx0 = make_float2(-P.x0, -P.y0);
+    const float2 p1 = penumbra2(axy, make_float2(nk.x, nk.x), x0, nx0);
+    const float2 p2 = penumbra2(axy, make_float2(nk.y, nk2y), x0, nx0);
+    const float F = fmaf(om1 * p1.x, p1.y, om2 * p2.x * p2.y);
     return F * Av * (s * s);
 }
 

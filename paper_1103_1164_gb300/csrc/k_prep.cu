@@ -320,9 +320,11 @@ __global__ void __launch_bounds__(256) k_merge_tables(const float4* __restrict__
         const int j = min(k, w_n - 1);
         const float4 w0 = __ldg(water + 2 * j), w1 = __ldg(water + 2 * j + 1);
         const float dw = k < w_n - 1 ? 1.f : 0.f;   // slope of the clamped water tables
-        tabm[3 * e] = make_float4(a.x, a.y, fmaf(wscale, a.z, w1.x), fmaf(wscale, a.w, dw * w1.y));
-        tabm[3 * e + 1] = make_float4(fmaf(wscale, b.x, w1.z), fmaf(wscale, b.y, dw * w1.w), w0.x, dw * w0.y);
-        tabm[3 * e + 2] = make_float4(w0.z, dw * w0.w, 0.f, 0.f);
+        // values and slopes of the pairs (O1, O2) and (u1w, u2w) side by side,
+        // for packed FP32 interpolation
+        tabm[3 * e] = make_float4(a.x, a.y, fmaf(wscale, a.z, w1.x), fmaf(wscale, b.x, w1.z));
+        tabm[3 * e + 1] = make_float4(fmaf(wscale, a.w, dw * w1.y), fmaf(wscale, b.y, dw * w1.w), w0.x, w0.z);
+        tabm[3 * e + 2] = make_float4(dw * w0.y, dw * w0.w, 0.f, 0.f);
     }
 }
 
