@@ -372,6 +372,9 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
             srow[3 * lane + 2] = q2;
         }
         __syncwarp();
+        // two beamlets per trip: their independent loads and arithmetic
+        // interleave (measured: 3.10 -> 2.90 ms on thorax9; 3 and 4 were slower)
+#pragma unroll 2
         for (int m = m0; m <= m1; ++m) {
             const uint32_t i = row + (uint32_t)m;
             const float4* rq = srow + 3 * (m - m0);
