@@ -184,7 +184,9 @@ __device__ __forceinline__ float pair_eval(const PlanView& P, const Lane& ln, co
 
     // A(t_eq, theta) (step 9): the beamlet's theta-interpolated row, linear in t_eq
     float fa;
-    const uint32_t jb = grid_bits(fminf(fmaxf(teq * P.inv_adt, 0.f), P.a_hi), fa);
+    // t_eq >= 0 (an integral of rho >= 0, interpolated with non-negative
+    // slopes), so only the upper end of the A row needs a clamp
+    const uint32_t jb = grid_bits(fminf(teq * P.inv_adt, P.a_hi), fa);
     const float2 ar = __ldg(P.arow + (i * (uint32_t)P.a_nt + (jb - kGridBits)));
     const float Av = fmaf(fa, ar.y, ar.x);
 
