@@ -143,7 +143,7 @@ static void beam_frame_host(const dc_beam& bm, double* ex, double* ey, double* e
 }
 
 // Beam's-eye-view binning: default cell size and the autotuner's candidates
-// (finest first: the plan's buffers are sized for the first pair).
+// (the plan's binning buffers are sized for the largest grid among them all).
 static const float kDefaultTile = 0.5f, kDefaultSlab = 2.0f;
 static const float kTuneTiles[] = {0.35f, 0.5f, 0.75f};
 static const float kTuneSlabs[] = {0.5f, 1.0f, 2.0f, 4.0f};
@@ -188,6 +188,23 @@ static void bin_geometry(dc_plan* p, float tile, float slab)
         p->tiles_max = std::max(p->tiles_max, G.nta * G.ntc);
         p->cells_max = std::max(p->cells_max, G.cells);
     }
+}
+
+// Tiles and cells per beam that any binning the plan can be given needs: the
+// default cell and every autotuner candidate.  Leaves the default geometry set.
+static void bin_capacity(dc_plan* p, int& tiles_cap, int& cells_cap)
+{
+    tiles_cap = 0;
+    cells_cap = 0;
+    for (float t : kTuneTiles)
+        for (float sl : kTuneSlabs) {
+            bin_geometry(p, t, sl);
+            tiles_cap = std::max(tiles_cap, p->tiles_max);
+            cells_cap = std::max(cells_cap, p->cells_max);
+        }
+    bin_geometry(p, kDefaultTile, kDefaultSlab);
+    tiles_cap = std::max(tiles_cap, p->tiles_max);
+    cells_cap = std::max(cells_cap, p->cells_max);
 }
 
 static dc_status check_inputs(const float* ct, const dc_grid* g, const dc_beam* beams, int32_t nb,
@@ -321,14 +338,16 @@ static dc_status create_impl(dc_plan* p, const float* ct, uint32_t flags)
     p->scan_tmp_bytes = nscan * sizeof(int64_t);
 
     // beam's-eye-view voxel lists and per-beam partial results
-    // capacity for the finest binning the autotuner may choose, then the default
-    bin_geometry(p, kTuneTiles[0], kTuneSlabs[0]);
+    // capacity for every binning the plan can be given; the default is set
+    int tiles_cap = 0, cells_cap = 0;
+    bin_capacity(p, tiles_cap, cells_cap);
     const size_t nb = (size_t)p->n_beams;
-    DC_CUDA(dalloc(&p->d_bounds, nb * p->tiles_max));
-    DC_CUDA(dalloc(&p->d_hist, nb * p->cells_max));
-    p->tiles_cap = p->tiles_max;
-    p->cells_cap = p->cells_max;
-    bin_geometry(p, kDefaultTile, kDefaultSlab);
+    DC_CUDA(dalloc(&p->d_bounds, nb * (size_t)tiles_cap));
+    DC_CUDA(dalloc(&p->d_hist, nb * (size_t)cells_cap));
+    p->tiles_cap = tiles_cap;
+    p->cells_cap = cells_cap;
+    if (p->tiles_max > p->tiles_cap || p->cells_max > p->cells_cap)
+        return invalid("dc_fspb_create: binning grid larger than allocated");
     DC_CUDA(dalloc(&p->d_bin, nb));
     DC_CUDA(dalloc(&p->d_cellof, nb * V));
     DC_CUDA(dalloc(&p->d_nitems, nb));
