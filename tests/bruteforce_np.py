@@ -11,7 +11,11 @@ Every step is computed by a different route from the oracle's:
   boundaries instead of the oracle's 3-D triple sum;
 * lookups (steps 9-10): numpy.interp and scipy's RegularGridInterpolator;
 * eq. (4): the paper's printed sinh/cosh form instead of the oracle's
-  exponential-difference form.
+  exponential-difference form;
+* the axis-stencil lateral form (lateral_mode = 1): all 48 taps of every
+  voxel at once through scipy.ndimage.map_coordinates (order 1, edge clamp)
+  and a matrix product with the normalised Gaussian weights, instead of the
+  oracle's per-tap trilinear loop.
 The readings of the paper are the same as the oracle's (they are the
 definition under test); the arithmetic route is not.
 """
@@ -138,8 +142,44 @@ def p_paper(x, u, x0):
     return out
 
 
-def dose(plan, fluence=None, density_correction=None):
-    """Eq. (1) on every voxel, vectorised over voxels for each beamlet."""
+def axis_densities(plan, beam, d):
+    """Per voxel of the grid, the three densities of the axis-stencil form.
+
+    16 taps at (j - 7.5) d, j = 0..15, along each of the beam's axes e_x', e_y',
+    e_z' through the voxel centre; trilinear density with clamp-to-edge; each
+    axis averaged with Gaussian weights exp(-s^2 / 2 sigma^2) normalised to
+    one.  Returns (mean of the three averages, e_x' average, e_y' average),
+    the densities at which f_omega, f_u2 along x and f_u2 along y are read.
+    """
+    g, cm = plan.grid, plan.comm
+    x, y, z = g.centres()
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    r = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
+    s = (np.arange(16) - 7.5) * d
+    sig = cm.smooth_sigma
+    wts = np.exp(-s * s / (2 * sig * sig)) if sig > 0 else np.ones(16)
+    wts = wts / wts.sum()
+    org = np.array([g.ox, g.oy, g.oz])
+    dlt = np.array([g.dx, g.dy, g.dz])
+    hi = np.array([g.nx, g.ny, g.nz], float) - 1
+    rho = plan.rho.astype(float)
+    avgs = []
+    for ax in beam_axes(beam):
+        pts = r[:, None, :] + s[None, :, None] * ax[None, None, :]      # (V, 16, 3)
+        idx = np.clip((pts - org) / dlt, 0.0, hi).reshape(-1, 3)
+        taps = ndimage.map_coordinates(rho, idx[:, ::-1].T, order=1, mode="nearest")
+        avgs.append(taps.reshape(-1, 16) @ wts)
+    return (avgs[0] + avgs[1] + avgs[2]) / 3.0, avgs[0], avgs[1]
+
+
+def dose(plan, fluence=None, density_correction=None, lateral_mode=0):
+    """Eq. (1) on every voxel, vectorised over voxels for each beamlet.
+
+    lateral_mode 0: u_2 and omega at rho_hat(r) of the voxel, u_x = u_y (the
+    paper's form).  lateral_mode 1: the axis-stencil form (axis_densities):
+    u_2 along x at the e_x' average, along y at the e_y' average, omega at the
+    mean of the three averages; u_1 stays at rho(r).
+    """
     g, cm = plan.grid, plan.comm
     dc = cm.density_correction if density_correction is None else density_correction
     f = plan.fluence if fluence is None else fluence
@@ -154,6 +194,16 @@ def dose(plan, fluence=None, density_correction=None):
     rho_dom = cm.f_rho0 + cm.f_drho * np.arange(cm.dens.shape[1])
     fac = [np.interp(rho.ravel() if q == 0 else rhos.ravel(), rho_dom, cm.dens[q].astype(float))
            for q in range(4)]
+    fu2 = lambda dens: np.interp(dens, rho_dom, cm.dens[1].astype(float))
+    # per beam: (f_u2 along x, f_u2 along y, f_omega1, f_omega2) of every voxel
+    lat = []
+    for beam in plan.beams:
+        if lateral_mode == 1:
+            rw, rx, ry = axis_densities(plan, beam, d)
+            lat.append((fu2(rx), fu2(ry), np.interp(rw, rho_dom, cm.dens[2].astype(float)),
+                        np.interp(rw, rho_dom, cm.dens[3].astype(float))))
+        else:
+            lat.append((fac[1], fac[1], fac[2], fac[3]))
     A = cm.A.astype(float)
     Aint = RegularGridInterpolator((cm.a_dtheta * np.arange(A.shape[0]), cm.a_dt * np.arange(A.shape[1])), A)
     out = np.zeros(g.n_voxels)
@@ -179,12 +229,14 @@ def dose(plan, fluence=None, density_correction=None):
         th = np.clip(np.full_like(teq, bl["theta"]), 0, cm.a_dtheta * (A.shape[0] - 1))
         Av = Aint(np.stack([th, np.clip(teq, 0, cm.a_dt * (A.shape[1] - 1))], 1))
         if dc:
-            u1, u2 = fac[0][m] * u1w, fac[1][m] * u2w
-            w1 = np.maximum(fac[2][m] * (w1w + c1), 0.0)
-            w2 = np.maximum(fac[3][m] * (w2w + c2), 0.0)
+            fx, fy, fw1, fw2 = lat[bl["beam"]]
+            u1 = fac[0][m] * u1w
+            u2x, u2y = fx[m] * u2w, fy[m] * u2w
+            w1 = np.maximum(fw1[m] * (w1w + c1), 0.0)
+            w2 = np.maximum(fw2[m] * (w2w + c2), 0.0)
         else:
-            u1, u2, w1, w2 = u1w, u2w, w1w, w2w
+            u1, u2x, u2y, w1, w2 = u1w, u2w, u2w, w1w, w2w
         x0, y0 = plan.beamlet_x / 2, plan.beamlet_y / 2
-        F = w1 * p_paper(xs, u1, x0) * p_paper(ys, u1, y0) + w2 * p_paper(xs, u2, x0) * p_paper(ys, u2, y0)
+        F = w1 * p_paper(xs, u1, x0) * p_paper(ys, u1, y0) + w2 * p_paper(xs, u2x, x0) * p_paper(ys, u2y, y0)
         out[m] += f[i] * F * Av * (bl["sad"] / L) ** 2
     return out.reshape(g.shape)

@@ -6,7 +6,8 @@ bar); stencil samples equal to the oracle's (nearest taps exact, effective
 densities to 1e-5); GPU FP32 gradients within 1e-4 of the oracle's FP64
 analytic gradients (themselves pinned by finite differences); BF16 inference
 within 2e-2 of the FP64 forward; the network-corrected dose within 1 % of the
-plain axis form, closer to it than the paper's form is.
+plain axis form, closer to it than the paper's form is, and within 1 % of the
+FP64 oracle's axis-form dose per voxel.
 """
 import numpy as np
 import pytest
@@ -119,3 +120,8 @@ def test_trained_surrogate_dose(dc, oracle_mod):
     err_iso = float(np.abs(iso - axis).max()) / dmax
     assert err_net <= 1e-2, err_net
     assert err_net < err_iso, (err_net, err_iso)
+    # the network-corrected dose against the FP64 oracle's axis form, per voxel:
+    # the surrogate bar (1 % of the oracle's maximum, plus the dose of pairs
+    # whose ROI or depth decision lies within rounding of its boundary)
+    want, amb = oracle_mod.OraclePlan(p, lateral_mode=1).dose(with_amb=True)
+    assert_dose_close(net, want, amb, tol=1e-2, label="network slab64 vs FP64 oracle")
