@@ -22,6 +22,7 @@
 // bounded; a wait that gives up sets an error word and the CTA stops.
 // Per-beam partial results are combined with compensated (Neumaier) sums.
 #include <stdint.h>
+#include <stdlib.h>
 
 #include <algorithm>
 #include <mutex>
@@ -290,6 +291,7 @@ struct SpmmArgs {
     float* Y;                    // single beam: [V][k]
     float* P;                    // several beams: partial rows [item][k] per beam list position
     int direct;
+    int stall;                   // test only: the producer issues no copies
     int32_t* err;
     const int32_t* zero;         // single beam: voxels in no list, whose rows are written as zeros
     int64_t n_zero;
@@ -321,7 +323,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r)
 __global__ void __launch_bounds__(kSpmmThreads) k_spmm(const SpmmArgs a)
 {
     extern __shared__ __align__(1024) uint8_t sm[];
-    __shared__ uint64_t full[kStages], empty[kStages], acc_full[kAcc], acc_empty[kAcc];
+    __shared__ uint64_t full[kStages], empty[kStages], acc_full[kAcc], acc_empty[kAcc], drained;
     __shared__ uint32_t tmem_base;
     __shared__ volatile int s_abort;
     __shared__ float s_epi[kEpiWarps][32 * 33];   // epilogue transpose, one 32 x 32 block per warp
@@ -338,6 +340,7 @@ __global__ void __launch_bounds__(kSpmmThreads) k_spmm(const SpmmArgs a)
             mbar_init(&acc_full[q], 1);
             mbar_init(&acc_empty[q], kEpiWarps);
         }
+        mbar_init(&drained, 1);
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -371,7 +374,9 @@ __global__ void __launch_bounds__(kSpmmThreads) k_spmm(const SpmmArgs a)
                 if (rb >= a.n_rb) break;
                 const int64_t ch0 = __shfl_sync(0xffffffffu, my_c0, j);
                 const int64_t nch = __shfl_sync(0xffffffffu, my_c1, j) - ch0;
-                for (int64_t cb = 0; cb < nch && ok; cb += 32) {
+                // test-only stall (a.stall): no copy is issued, so the
+                // consumers' bounded waits run out with nothing in flight
+                for (int64_t cb = 0; cb < nch && ok && !a.stall; cb += 32) {
                     const int my_kb = cb + lane < nch ? a.chunk_kb[ch0 + cb + lane] : 0;
                     const int n_in = (int)(nch - cb < 32 ? nch - cb : 32);
                     for (int c = 0; c < n_in; ++c, ++g) {
@@ -440,6 +445,11 @@ __global__ void __launch_bounds__(kSpmmThreads) k_spmm(const SpmmArgs a)
             if (!ok) {
                 s_abort = 1;
                 atomicExch(a.err, 1);
+                // no MMA may still write tensor memory when the CTA frees it:
+                // one more commit arrives once every MMA this thread issued
+                // has completed (at once if there is none); wait for it, bounded
+                umma_commit(&drained);
+                mbar_wait(&drained, 0);
             }
         }
     } else {
@@ -781,6 +791,17 @@ dc_status spmm_prepare(dc_plan* p, const int64_t* rowptr, const int32_t* cols, c
     return DC_OK;
 }
 
+// Test hook of the bounded waits: with DC_FSPB_TEST_SPMM_STALL=1 in the
+// environment, k_spmm's producer issues no copies, so every consumer wait runs
+// out (after its 2 s bound) with nothing in flight and the call ends with the
+// status word set (dc_fspb_device_status then returns DC_ETIMEOUT).  Read on
+// every call of dc_fspb_spmm; unset, the kernel runs normally.
+static int spmm_test_stall()
+{
+    const char* s = getenv("DC_FSPB_TEST_SPMM_STALL");
+    return s && s[0] == '1' ? 1 : 0;
+}
+
 cudaError_t spmm_run(dc_plan* p, const float* F, int k, float* Y)
 {
     const int nkb = (p->sp_cols + 7) / 8 + 2;
@@ -823,6 +844,7 @@ cudaError_t spmm_run(dc_plan* p, const float* F, int k, float* Y)
     a.Y = Y;
     a.P = p->d_sp_p;
     a.direct = direct ? 1 : 0;
+    a.stall = spmm_test_stall();
     a.err = p->d_err;
     a.zero = p->d_sp_zero;
     a.n_zero = direct ? p->sp_n_zero : 0;

@@ -161,10 +161,15 @@ def _is_torch(a):
 
 
 def _ptr(a, dtype=np.float32):
-    """(pointer, device flag) of a host NumPy array or a CUDA torch tensor."""
+    """(pointer, device flag) of a host NumPy array or a CUDA torch tensor.
+
+    dtype is the element type the C entry point reads (None: any, for value
+    arrays whose type travels as a separate argument)."""
     if _is_torch(a):
         if not a.is_cuda or not a.is_contiguous():
             raise ValueError("torch tensors must be contiguous CUDA tensors")
+        if dtype is not None and str(a.dtype) != "torch." + np.dtype(dtype).name:
+            raise ValueError(f"expected a {np.dtype(dtype).name} tensor, got {a.dtype}")
         return C.c_void_p(a.data_ptr()), DC_DEVICE_PTRS
     if not (isinstance(a, np.ndarray) and a.flags.c_contiguous and a.dtype == dtype):
         raise ValueError(f"host arrays must be C-contiguous {np.dtype(dtype).name} NumPy arrays")
@@ -273,11 +278,21 @@ def dc_fspb_spmm_info(plan: Plan):
     return c.value, r.value
 
 
+def _spmm_shapes(plan: Plan, F, Y):
+    """k of F [B, k], after checking F and Y [V, k] against the plan (before any launch)."""
+    if len(F.shape) != 2 or int(F.shape[0]) != plan.n_beamlets:
+        raise ValueError(f"F must be [n_beamlets={plan.n_beamlets}, k], got {tuple(F.shape)}")
+    k = int(F.shape[1])
+    if tuple(int(s) for s in Y.shape) != (plan.n_voxels, k):
+        raise ValueError(f"Y must be [n_voxels={plan.n_voxels}, k={k}], got {tuple(Y.shape)}")
+    return k
+
+
 def dc_fspb_spmm(plan: Plan, F, Y=None):
     """Y [V, k] = M F for F [B, k] (k <= 64) on the tensor cores."""
-    k = F.shape[1]
     if Y is None:
-        Y = np.empty((plan.n_voxels, k), np.float32)
+        Y = np.empty((plan.n_voxels, F.shape[1] if len(F.shape) == 2 else 0), np.float32)
+    k = _spmm_shapes(plan, F, Y)
     pf, f1 = _ptr(F)
     py, f2 = _ptr(Y)
     _check(load().dc_fspb_spmm(plan.handle, pf, k, py, _same_kind(f1, f2)))
@@ -286,6 +301,7 @@ def dc_fspb_spmm(plan: Plan, F, Y=None):
 
 def dc_fspb_spmm_noalloc(plan: Plan, F, Y):
     """dc_fspb_spmm for device tensors F [B, k], Y [V, k] with static scratch (no device allocation)."""
+    _spmm_shapes(plan, F, Y)
     pf, f1 = _ptr(F)
     py, f2 = _ptr(Y)
     if not (f1 & f2 & DC_DEVICE_PTRS):

@@ -97,3 +97,20 @@ def test_null_arguments(lib):
     assert lib.dc_fspb_dose(None, None, None, 0) == dc_fspb.DC_EINVAL
     assert lib.dc_fspb_n_beamlets(None, None) == dc_fspb.DC_EINVAL
     assert lib.dc_fspb_destroy(None) == dc_fspb.DC_OK
+
+
+def test_spmm_wrappers_reject_bad_shapes_before_any_call():
+    # a plan object with no library handle: the checks must fire before the
+    # binding reaches the C entry point
+    plan = dc_fspb.Plan(None, 10, 100, (4, 5, 5))
+    good_F, good_Y = np.zeros((10, 4), np.float32), np.zeros((100, 4), np.float32)
+    for F, Y in [(np.zeros((9, 4), np.float32), good_Y),          # F rows != n_beamlets
+                 (np.zeros(10, np.float32), good_Y),              # F not 2-D
+                 (good_F, np.zeros((100, 3), np.float32)),         # Y columns != k
+                 (good_F, np.zeros((99, 4), np.float32))]:         # Y rows != n_voxels
+        with pytest.raises(ValueError):
+            dc_fspb.dc_fspb_spmm(plan, F, Y)
+        with pytest.raises(ValueError):
+            dc_fspb.dc_fspb_spmm_noalloc(plan, F, Y)
+    with pytest.raises(ValueError):                                  # host arrays must be float32
+        dc_fspb.dc_fspb_spmm(plan, good_F.astype(np.float64), good_Y)

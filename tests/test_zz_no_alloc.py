@@ -3,8 +3,9 @@
 The variant must give what dc_fspb_spmm gives (same kernels, same arithmetic;
 only where the packed fluences and partial rows live differs) on two calls in
 a row, for a single-beam plan (output written directly) and a multi-beam plan
-(partials in the static array, reduced in beam order), and must reject
-problems larger than its fixed scratch with DC_EINVAL.
+(partials in the static array, reduced in beam order), must leave the
+device's free memory unchanged, and must reject problems larger than its fixed
+scratch with DC_EINVAL.
 """
 import numpy as np
 import pytest
@@ -58,6 +59,26 @@ def test_noalloc_single_beam(dc):
 def test_noalloc_multi_beam(dc, k):
     p = synth.small_plan(31, n=(26, 22, 18), vox=0.3, n_beams=3, roi=2.0, field=4.0)
     _two_calls(dc, p, k, 100 + k)
+
+
+def test_noalloc_allocates_no_device_memory(dc):
+    # the defining property: after a first call (which looks up the static
+    # arrays' addresses), further calls leave the device's free memory as it was
+    import torch
+    p = synth.small_plan(32, n=(26, 22, 18), vox=0.3, n_beams=3, roi=2.0, field=4.0)
+    plan = dc.dc_fspb_create_from(p)
+    dc.dc_fspb_spmm_prepare(plan)
+    F = torch.rand(plan.n_beamlets, 16, device="cuda")
+    Y = torch.zeros(plan.n_voxels, 16, device="cuda")
+    dc.dc_fspb_spmm_noalloc(plan, F, Y)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        dc.dc_fspb_spmm_noalloc(plan, F, Y)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    dc.dc_fspb_device_status(plan)
+    assert free1 >= free0, (free0, free1)
 
 
 def test_noalloc_rejects_oversize(dc):
