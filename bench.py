@@ -3,11 +3,11 @@
 One step = the whole hot path of one plan on synthetic inputs resident in HBM:
   Algorithm A1 steps 1-6 for the plan's density (smoothing, beamlet geometry,
   FP64 Siddon trace, depth tables; dc_fspb_set_density),
-  eq. (1) direct dose (dc_fspb_dose),
-  the dose-deposition matrix: pair count, row pointers and FP32 CSR fill
-  (dc_fspb_pair_count + dc_fspb_dose_matrix).
-Every pair of the plan is evaluated twice per step (once for the dose, once for
-its matrix entry), so the metric counts 2 x pairs voxel-beamlet evaluations.
+  the row pattern of the dose-deposition matrix (pair tests, per-voxel counts
+  and their scan; dc_fspb_pair_count),
+  eq. (1) and the FP32 CSR matrix from ONE evaluation of each (voxel, beamlet)
+  pair (dc_fspb_dose_and_matrix).
+The metric counts each pair once: evaluations = pairs of the plan.
 
 Default workload: the 9-field coplanar thorax plan on a 128 x 128 x 96 grid of
 0.25 cm voxels (0.5 cm beamlets, fields 8-15 cm, ROI 5 cm).
@@ -33,40 +33,57 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "voxel-beamlet evals/s (full plan: steps 1-6 + eq. 1 dose + FP32 dose matrix)"
+METRIC = "voxel-beamlet evals/s (full plan: steps 1-6 + eq. 1 dose and FP32 dose matrix, one evaluation per pair)"
 UNIT = "evals/s"
 # Algorithmic work of one (voxel, beamlet) evaluation of eqs. (2)-(4) with the
-# lookups of Algorithm A1 steps 9-11 (counted from the method's definition):
-ALG_FP32_PER_PAIR = 98     # FP32 add/mul/fma/compare/round operations (itemised in the design doc)
-ALG_MUFU_PER_PAIR = 9      # 8 exponentials (four p() of eq. 4) + 1 reciprocal (SAD/|r_a|)
+# lookups of Algorithm A1 steps 9-11, counted from the method's definition:
+# 8 exponentials (four profiles p of eq. 4, two each) and 1 reciprocal
+# (SAD/|r_a|) on the special-function units, and about 65 FP32 add/mul/fma
+# (geometry ~20, five linear lookups ~15, the bilinear A ~8, eqs. 3-4 ~16,
+# fluence weight and accumulation ~3).  16 SFU lanes per SM against 9
+# operations bind before 128 FP32 lanes against 65.
+ALG_FP32_PER_PAIR = 65
+ALG_MUFU_PER_PAIR = 9
+# The kernel's own operation count (index arithmetic, clamps and the rounding
+# trick of its table coordinates included), reported beside the primary figure.
+IMPL_FP32_PER_PAIR = 98
 FP32_LANES_PER_SM = 128
 MUFU_LANES_PER_SM = 16
 L2_FLUSH_BYTES = 256 << 20
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
-# the dose kernel on the thorax9 plan, from an ncu capture of the kernel built
+# a pair kernel on the thorax9 plan, from an ncu capture of the kernel built
 # from the sources with these SHA-256 digests (the kernel and the structures it
-# reads; profiles/k_pairs_dose_thorax9.md); reported only while they are unchanged.
-DOSE_TRAFFIC_BYTES = 110389248 + 20729344
-DOSE_TRAFFIC_SOURCES = {
-    "paper_1103_1164_gb300/csrc/k_dose.cu": "70ece8998f2945e076ecef028daaf234232d4b3e7fd3d9d6e96961a68bf3742f",
-    "paper_1103_1164_gb300/csrc/dc_views.cuh": "604f1c61d84a82494049db8c574ff1384cee296c4ebbe27db75ba78b5c54a772",
+# reads; the summaries are under profiles/); reported only while they are unchanged.
+KERNEL_TRAFFIC = {
+    "dose": (110389248 + 20729344, {
+        "paper_1103_1164_gb300/csrc/k_dose.cu": "70ece8998f2945e076ecef028daaf234232d4b3e7fd3d9d6e96961a68bf3742f",
+        "paper_1103_1164_gb300/csrc/dc_views.cuh": "604f1c61d84a82494049db8c574ff1384cee296c4ebbe27db75ba78b5c54a772",
+    }),
 }
 
 
-def dose_traffic(scale):
-    """The captured per-launch DRAM traffic, or None if the kernel's sources
-    changed since the capture or the workload is not the captured one."""
+def kernel_traffic(kernel, scale):
+    """The captured per-launch DRAM traffic of `kernel`, or None if there is no
+    capture, the kernel's sources changed since it, or the workload is not the
+    captured one."""
     import hashlib
-    if scale != 1.0:
+    if scale != 1.0 or kernel not in KERNEL_TRAFFIC:
         return None
-    for rel, digest in DOSE_TRAFFIC_SOURCES.items():
+    nbytes, sources = KERNEL_TRAFFIC[kernel]
+    for rel, digest in sources.items():
         try:
             with open(os.path.join(ROOT, rel), "rb") as f:
                 if hashlib.sha256(f.read()).hexdigest() != digest:
                     return None
         except OSError:
             return None
-    return DOSE_TRAFFIC_BYTES
+    return nbytes
+
+
+def pair_peak(sms, mhz, fp32_ops=ALG_FP32_PER_PAIR):
+    """Pairs/s bound of the direct evaluation: the tighter of the FP32 lanes and
+    the special-function lanes at the given SM clock."""
+    return sms * mhz * 1e6 * min(FP32_LANES_PER_SM / fp32_ops, MUFU_LANES_PER_SM / ALG_MUFU_PER_PAIR)
 
 
 def parse():
@@ -257,19 +274,22 @@ def aggregate_throughput(pg, torch, evals_rank, t_rank_ms):
 # CPU oracle timings (the cpu_baseline leg and the reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_sample_rate(plan_in, budget_s=12.0, seed=3):
+def oracle_sample_rate(plan_in, budget_s=4.0, seed=3, threads=None, op=None):
     """Times the FP64 oracle on a seeded sample of voxels of the workload.
 
-    Returns per-step CPU estimates: the oracle's plan set-up time (steps 1-6,
-    measured in full) and its dose + matrix time scaled from the sample by the
-    ratio of pair counts."""
+    The sample grows until one pass takes about budget_s / 2; the pass is then
+    repeated and the best of 3 kept.  Returns the oracle's plan set-up time
+    (steps 1-6, measured in full) and its dose + matrix time on the sample."""
     from oracle import oracle
-    threads = oracle.default_threads()
-    t0 = time.perf_counter()
-    op = oracle.OraclePlan(plan_in, threads=threads)
-    t_create = time.perf_counter() - t0
+    threads = threads or oracle.default_threads()
+    t_create = None
+    if op is None:
+        t0 = time.perf_counter()
+        op = oracle.OraclePlan(plan_in, threads=threads)
+        t_create = time.perf_counter() - t0
+    op.threads = threads
     rng = np.random.default_rng(seed)
-    n = 256
+    n = 64
     while True:
         vox = np.sort(rng.choice(op.V, size=min(n, op.V), replace=False))
         t0 = time.perf_counter()
@@ -279,9 +299,36 @@ def oracle_sample_rate(plan_in, budget_s=12.0, seed=3):
         if dt >= 0.4 * budget_s or n >= op.V:
             break
         n = int(min(op.V, n * max(2.0, 0.5 * budget_s / max(dt, 1e-3))))
+    best = dt
+    for _ in range(2):
+        t0 = time.perf_counter()
+        op.dose_voxels(vox)
+        op.matrix(vox)
+        best = min(best, time.perf_counter() - t0)
     pairs_sample = int(op.pairs_voxels(vox).sum())
-    return dict(op=op, t_create=t_create, t_sample=dt, n_vox=int(vox.size), pairs_sample=pairs_sample,
+    return dict(op=op, t_create=t_create, t_sample=best, n_vox=int(vox.size), pairs_sample=pairs_sample,
                 threads=threads)
+
+
+def cpu_baseline(p, pairs):
+    """The FP64 oracle (as it stands) on the host cores, all threads and one
+    thread, best of 3 on bounded voxel samples, scaled by pair count to the
+    whole plan (plan set-up timed in full, with all threads)."""
+    est = oracle_sample_rate(p)
+    one = oracle_sample_rate(p, threads=1, op=est["op"], budget_s=3.0, seed=5)
+    out = {}
+    for key, e in (("all", est), ("one", one)):
+        t_step = est["t_create"] + e["t_sample"] * pairs / max(e["pairs_sample"], 1)
+        out[key] = dict(value=pairs / t_step, threads=e["threads"], n_vox=e["n_vox"],
+                        pairs_sample=e["pairs_sample"], t_sample=e["t_sample"])
+    a = out["all"]
+    return {"value": a["value"], "unit": UNIT, "cores": a["threads"], "kind": "oracle",
+            "one_thread": {"value": out["one"]["value"], "cores": 1},
+            "sample": f"FP64 oracle, best of 3: plan set-up timed in full ({est['t_create']:.2f} s), dose + "
+                      f"matrix rows timed on {a['n_vox']} seeded voxels ({a['pairs_sample']} pairs, "
+                      f"{a['t_sample']:.2f} s, {a['threads']} threads) and on {out['one']['n_vox']} voxels "
+                      f"({out['one']['pairs_sample']} pairs, {out['one']['t_sample']:.2f} s, 1 thread), "
+                      f"scaled by pair count to the {pairs} pairs of the plan"}
 
 
 # ---------------------------------------------------------------------------
@@ -309,7 +356,7 @@ def run_reference(args, world, rank, pg):
         if s >= args.warmup:
             times.append(dt)
     t = sum(times)
-    value = 2 * pairs * len(times) / t
+    value = pairs * len(times) / t
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -354,19 +401,17 @@ def run_ours(args, world, rank, local, pg):
         if ev: ev[0].record(stream)
         dc.dc_fspb_set_density(plan, rho_d)
         if ev: ev[1].record(stream)
-        dc.dc_fspb_dose(plan, flu_d, dose_d)
-        if ev: ev[2].record(stream)
-        n = dc.dc_fspb_pair_count(plan)
+        n = dc.dc_fspb_pair_count(plan)               # row pattern: pair tests, counts, scan
         assert n == pairs
+        if ev: ev[2].record(stream)
+        dc.dc_fspb_dose_and_matrix(plan, flu_d, dose_d, dc.DC_F32, rowptr_d, cols_d, vals_d)
         if ev: ev[3].record(stream)
-        dc.dc_fspb_dose_matrix(plan, dc.DC_F32, rowptr_d, cols_d, vals_d)
-        if ev: ev[4].record(stream)
 
     for _ in range(args.warmup):
         flush.zero_()
         step()
     torch.cuda.synchronize()
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     launches0 = dc.dc_fspb_launch_count()
     barrier(pg, torch)
     torch.cuda.synchronize()
@@ -379,35 +424,39 @@ def run_ours(args, world, rank, local, pg):
         wall = time.perf_counter() - w0
     barrier(pg, torch)
     launches = dc.dc_fspb_launch_count() - launches0
-    stage = np.array([[evs[k][j].elapsed_time(evs[k][j + 1]) for j in range(4)] for k in range(args.steps)])
+    stage = np.array([[evs[k][j].elapsed_time(evs[k][j + 1]) for j in range(3)] for k in range(args.steps)])
     step_ms = stage.sum(1)
-    evals_step = 2 * pairs
+    evals_step = pairs
     value, t_total_ms = aggregate_throughput(pg, torch, evals_step * args.steps, float(step_ms.sum()))
     ms_per_step = t_total_ms / args.steps
+    clocks = clk.summary()
 
-    # roofline of the dominant kernel: the direct dose kernel (ALU bound)
-    t_dose = float(stage[:, 1].mean()) * 1e-3
+    # roofline of the step's dominant kernel: the fill pass, which evaluates
+    # every pair (eqs. 2-4), accumulates eq. (1) and writes the matrix
+    sms = props.multi_processor_count
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    # the tighter of the FP32 lanes and the MUFU lanes (issue slots do not bound
-    # the method: packed FP32 instructions issue two of its operations at once)
-    peak_pairs = props.multi_processor_count * sm_max * 1e6 * min(
-        FP32_LANES_PER_SM / ALG_FP32_PER_PAIR, MUFU_LANES_PER_SM / ALG_MUFU_PER_PAIR)
-    achieved = pairs / t_dose
-    roofline = {"kernel": "k_dose<dose,1> (eqs. 1-4)", "bound": "alu",
-                "achieved": achieved / 1e9, "peak": peak_pairs / 1e9, "unit": "Gpair/s",
-                "frac": achieved / peak_pairs, "traffic": dose_traffic(args.scale),
+    sm_med = float(clocks.get("sm_mhz") or sm_max)
+    t_fill = float(stage[:, 2].mean()) * 1e-3
+    achieved = pairs / t_fill
+    peak_max = pair_peak(sms, sm_max)
+    peak_med = pair_peak(sms, sm_med)
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    bytes_matrix = pairs * 8 + (V + 1) * 8 + V * 4     # cols + values, row pointers, dose
+    roofline = {"kernel": "k_pairs<fill> (eqs. 1-4 + FP32 CSR emit, one evaluation per pair)",
+                "bound": "alu", "achieved": achieved / 1e9, "peak": peak_max / 1e9, "unit": "Gpair/s",
+                "frac": achieved / peak_max, "traffic": kernel_traffic("fill", args.scale),
                 "traffic_unit": "bytes per launch (ncu dram read + write)",
-                "peak_basis": f"{props.multi_processor_count} SMs x {sm_max:.0f} MHz x "
-                              f"min(128/{ALG_FP32_PER_PAIR} FP32 lanes, 16/{ALG_MUFU_PER_PAIR} MUFU lanes) "
-                              f"pairs per cycle and SM",
-                "dose_kernel_ms": t_dose * 1e3,
-                "timing": "CUDA events around dc_fspb_dose on the plan's stream: the pair kernel plus "
-                          "the per-beam sum and two small memsets (the pair kernel alone is ~2 % shorter)"}
-    fill_ms = float(stage[:, 3].mean())
-    bytes_matrix = pairs * 8 + (V + 1) * 8
-    matrix = {"fill_ms": fill_ms, "fill_GBps": bytes_matrix / (fill_ms * 1e-3) / 1e9,
-              "hbm_peak_GBps": peaks.get("hbm_gbs"), "count_scan_ms": float(stage[:, 2].mean()),
-              "nnz": pairs, "bytes": bytes_matrix}
+                "peak_basis": f"{sms} SMs x {sm_max:.0f} MHz x min(128/{ALG_FP32_PER_PAIR} FP32 lanes, "
+                              f"16/{ALG_MUFU_PER_PAIR} SFU lanes) pairs per cycle and SM: the SFU binds",
+                "at_median_clock": {"sm_mhz": sm_med, "peak": peak_med / 1e9, "frac": achieved / peak_med},
+                "impl_count_peak": {"fp32_ops_per_pair": IMPL_FP32_PER_PAIR,
+                                    "peak": pair_peak(sms, sm_max, IMPL_FP32_PER_PAIR) / 1e9,
+                                    "frac": achieved / pair_peak(sms, sm_max, IMPL_FP32_PER_PAIR)},
+                "hbm_write": {"bytes": bytes_matrix, "achieved_GBps": bytes_matrix / t_fill / 1e9,
+                              "peak_GBps": hbm, "frac": bytes_matrix / t_fill / 1e9 / hbm},
+                "fill_ms": t_fill * 1e3,
+                "timing": "CUDA events on the plan's stream around dc_fspb_dose_and_matrix in every timed "
+                          "step: the fill kernel plus a row-pointer copy and the per-beam dose sum"}
 
     # the other forms of the path; one that fails is reported as such and does
     # not take the benchmark line with it
@@ -419,10 +468,12 @@ def run_ours(args, world, rank, local, pg):
             return {"error": f"{type(exc).__name__}: {exc}"[:300]}
 
     forms = form(run_forms, args, dc, torch, stream, peaks)
-    forms["fused_plan"] = form(run_fused_form, args, dc, torch, stream, plan, rho_d, flu_d, dose_d, rowptr_d,
-                               cols_d, vals_d, flush, float(step_ms.mean()), pairs)
+    forms["dose_only"] = form(run_dose_form, args, dc, torch, stream, plan, p, flu_d, dose_d, flush, pairs,
+                              sms, sm_max, sm_med)
+    forms["two_pass_plan"] = form(run_two_pass_form, args, dc, torch, stream, plan, rho_d, flu_d, dose_d,
+                                  rowptr_d, cols_d, vals_d, flush, float(step_ms.mean()), pairs)
     forms["surrogate"] = form(run_surrogate_form, args, dc, torch, stream)
-    forms["batch"] = form(run_batch_form, args, dc, torch, stream, peak_pairs)
+    forms["batch"] = form(run_batch_form, args, dc, torch, stream, peak_max)
     forms["gamma"] = form(run_gamma_form, args, dc, torch, stream, p, rho_d, flu_d)
     forms["table1"] = form(run_table1_form, args, dc, torch, stream, flush)
     forms["leaf_sequences"] = form(run_leaf_form, args, dc, torch, stream, flush)
@@ -431,13 +482,8 @@ def run_ours(args, world, rank, local, pg):
         e2e = run_e2e(args, dc, p, plan, pairs, torch)
     cpu = None
     if not args.no_cpu and rank == 0:
-        est = oracle_sample_rate(p)
-        scale_pairs = pairs / max(est["pairs_sample"], 1)
-        t_cpu_step = est["t_create"] + est["t_sample"] * scale_pairs
-        cpu = {"value": evals_step / t_cpu_step, "unit": UNIT, "cores": est["threads"], "kind": "oracle",
-               "sample": f"FP64 oracle: plan set-up timed in full ({est['t_create']:.2f} s), dose + "
-                         f"matrix rows timed on {est['n_vox']} seeded voxels ({est['pairs_sample']} pairs, "
-                         f"{est['t_sample']:.2f} s) and scaled by pair count to the {pairs} pairs of the plan"}
+        cpu = cpu_baseline(p, pairs)
+        forms["plan_error_vs_oracle"] = form(plan_error_vs_oracle, p, dose_d.cpu().numpy())
     if rank != 0:
         return
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -449,33 +495,69 @@ def run_ours(args, world, rank, local, pg):
                        "l2": f"flushed before each step ({L2_FLUSH_BYTES >> 20} MiB write, untimed)",
                        "ranks": "independent plans (one per GPU)",
                        "autotuned_bev_cell_cm": {"tile": tuned[0], "slab": tuned[1]}},
-            "stages_ms": {"steps_1_6": float(stage[:, 0].mean()), "dose": float(stage[:, 1].mean()),
-                          "pair_count": float(stage[:, 2].mean()), "matrix_fill": fill_ms},
+            "stages_ms": {"steps_1_6": float(stage[:, 0].mean()), "pair_count": float(stage[:, 1].mean()),
+                          "dose_and_matrix": float(stage[:, 2].mean())},
             "wall_ms_per_step": 1e3 * wall / args.steps,
-            "roofline": roofline, "peaks": peak_kind, "dose_matrix": matrix, "forms": forms,
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk.summary()}
+            "roofline": roofline, "peaks": peak_kind, "forms": forms,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks}
     print(json.dumps(line), flush=True)
 
 
-def run_fused_form(args, dc, torch, stream, plan, rho_d, flu_d, dose_d, rowptr_d, cols_d, vals_d, flush,
-                   step_ms, pairs):
-    """The same plan (thorax9: steps 1-6, dose and FP32 matrix) with the dose
-    accumulated by the matrix fill (dc_fspb_dose_and_matrix): one evaluation
-    of each pair instead of two, after a pair-count pass for the row pattern.
-    Full-plan device time against the benchmark step's."""
-    def fused():
+def run_two_pass_form(args, dc, torch, stream, plan, rho_d, flu_d, dose_d, rowptr_d, cols_d, vals_d, flush,
+                      step_ms, pairs):
+    """The same plan with the dose and the matrix from two evaluation passes
+    (dc_fspb_dose, which also records the row pattern, then the FP32 fill):
+    full-plan device time against the benchmark step's single pass, and the
+    check that both give the same dose bit for bit."""
+    def two_pass():
         dc.dc_fspb_set_density(plan, rho_d)
-        dc.dc_fspb_dose_and_matrix(plan, flu_d, dose_d, dc.DC_F32, rowptr_d, cols_d, vals_d)
+        dc.dc_fspb_dose(plan, flu_d, dose_d)
+        dc.dc_fspb_pair_count(plan)
+        dc.dc_fspb_dose_matrix(plan, dc.DC_F32, rowptr_d, cols_d, vals_d)
 
     ref = dose_d.clone()
-    fused()
+    two_pass()
     torch.cuda.synchronize()
     same = bool(torch.equal(ref, dose_d))
     reps = max(3, min(args.steps, 5))
-    t = time_on_stream(torch, stream, fused, reps, flush)
-    return {"workload": "thorax9 plan, dose + FP32 matrix from one pass (after a pair-count pass)",
-            "full_plan_ms": t, "benchmark_step_ms": step_ms, "speedup": step_ms / t,
-            "pairs_per_s": pairs / (t * 1e-3), "dose_identical_to_step": same}
+    t = time_on_stream(torch, stream, two_pass, reps, flush)
+    return {"workload": "thorax9 plan, dose pass then FP32 matrix fill (each pair evaluated twice)",
+            "full_plan_ms": t, "benchmark_step_ms": step_ms, "step_speedup_over_two_pass": t / step_ms,
+            "dose_identical_to_step": same}
+
+
+def run_dose_form(args, dc, torch, stream, plan, p, flu_d, dose_d, flush, pairs, sms, sm_max, sm_med):
+    """Eq. (1) alone on the thorax9 plan (dc_fspb_dose: the dose kernel, the
+    per-beam sum, two small clears), with the roofline of the dose kernel."""
+    reps = max(5, args.steps)
+    dc.dc_fspb_dose(plan, flu_d, dose_d)
+    t = time_on_stream(torch, stream, lambda: dc.dc_fspb_dose(plan, flu_d, dose_d), reps, flush) * 1e-3
+    ach = pairs / t
+    return {"workload": "thorax9 plan, eq. (1) only", "ms": t * 1e3, "evals_per_s": ach,
+            "roofline": {"kernel": "k_pairs<dose>", "bound": "alu", "achieved": ach / 1e9,
+                         "peak": pair_peak(sms, sm_max) / 1e9, "unit": "Gpair/s",
+                         "frac": ach / pair_peak(sms, sm_max),
+                         "at_median_clock": {"sm_mhz": sm_med, "frac": ach / pair_peak(sms, sm_med)},
+                         "traffic": kernel_traffic("dose", args.scale)}}
+
+
+def plan_error_vs_oracle(p, dose, n_vox=1500, seed=12):
+    """The step's dose against the FP64 oracle on seeded voxels of the plan:
+    max |D_gpu - D_oracle| over the GPU dose maximum, the same with the dose of
+    pairs whose ROI or depth decision lies within rounding taken out, and the
+    voxels past the 0.5 % bar."""
+    from oracle import oracle
+    op = oracle.OraclePlan(p)
+    rng = np.random.default_rng(seed)
+    d = np.asarray(dose, np.float64).ravel()
+    vox = np.sort(rng.choice(d.size, size=min(n_vox, d.size), replace=False))
+    want, amb = op.dose_voxels(vox, with_amb=True)
+    dmax = float(d.max())
+    err = np.abs(d[vox] - want)
+    return {"voxels": int(vox.size), "max_err_over_dmax": float(err.max() / dmax),
+            "max_err_beyond_ambiguous_over_dmax": float(np.maximum(err - amb, 0).max() / dmax),
+            "voxels_over_0p5pct": int((err > 5e-3 * dmax + amb).sum()),
+            "normaliser": "GPU dose maximum over the whole plan"}
 
 
 def time_on_stream(torch, stream, fn, reps, flush):
@@ -521,6 +603,12 @@ def run_forms(args, dc, torch, stream, peaks, k=64):
     t_spmm = time_on_stream(torch, stream, lambda: dc.dc_fspb_spmm(plan, F, Y), reps, flush)
     dc.dc_fspb_device_status(plan)
     err = float(((Y.t() - dose).abs().max(1).values / dose.abs().max(1).values).max())
+    oracle_err = None
+    if not args.no_cpu:
+        # per fluence column: max over voxels of |result - M_oracle F| / max of M_oracle F
+        want = oracle_multi_fluence(p1, F.cpu().numpy())
+        oracle_err = {"bf16_spmm": column_error(Y.cpu().numpy(), want),
+                      "plain_fp32": column_error(dose.t().cpu().numpy(), want)}
     bytes_alg = chunks * 4096 + chunks * 4 + plan.n_voxels * k * 4 + plan.n_beamlets * k * 4
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     return {"workload": f"slab64 64^3 @0.25cm, 1 beam, {plan.n_beamlets} beamlets, ROI 3 cm, {k} fluences U[0,1]",
@@ -534,7 +622,27 @@ def run_forms(args, dc, torch, stream, peaks, k=64):
                                        "frac": bytes_alg / (t_spmm * 1e-3) / 1e9 / hbm,
                                        "bytes": bytes_alg},
                           "max_err_vs_fp32_over_colmax": err},
+            "max_err_vs_fp64_oracle_over_colmax": oracle_err,
             "speedup_bf16_over_fp32": t_plain / t_spmm}
+
+
+def oracle_multi_fluence(p, F, lateral_mode=0, voxels=None):
+    """M_oracle F in FP64: the oracle's dose-deposition matrix (all voxels, or
+    the listed ones) times the fluence columns F [B, k]."""
+    from scipy import sparse
+    from oracle import oracle
+    op = oracle.OraclePlan(p, lateral_mode=lateral_mode)
+    rowptr, cols, vals, flags = op.matrix(voxels)
+    inside = (flags & 1).astype(bool)
+    n = op.V if voxels is None else len(voxels)
+    M = sparse.csr_matrix((np.where(inside, vals, 0.0), cols, rowptr), shape=(n, op.B))
+    return M @ np.asarray(F, np.float64)
+
+
+def column_error(got, want):
+    """max over columns of max_v |got - want| / max_v |want| (got, want: [V, k])."""
+    got = np.asarray(got, np.float64)
+    return float((np.abs(got - want).max(0) / (np.abs(want).max(0) + 1e-300)).max())
 
 
 def run_surrogate_form(args, dc, torch, stream, k=64):
@@ -574,22 +682,48 @@ def run_surrogate_form(args, dc, torch, stream, k=64):
     dc.dc_fspb_set_surrogate(plan, params, surrogate.RHO_LO, surrogate.RHO_HI)
     dc.dc_fspb_set_lateral_mode(plan, dc.DC_LATERAL_MLP)
     t_set_mlp = time_on_stream(torch, stream, lambda: dc.dc_fspb_set_density(plan, rho), reps, flush)
-    t0 = time.perf_counter()
     dc.dc_fspb_spmm_prepare(plan)
-    t_prep = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    preps = []
+    for _ in range(3):
+        # the BF16 matrix and its tiles, rebuilt for the current density (host wall clock:
+        # the call synchronises to learn the pattern's size)
+        dc.dc_fspb_set_density(plan, rho)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dc.dc_fspb_spmm_prepare(plan)
+        torch.cuda.synchronize()
+        preps.append((time.perf_counter() - t0) * 1e3)
+    t_prep = float(np.median(preps))
     dc.dc_fspb_spmm(plan, F, Y)
     t_spmm = time_on_stream(torch, stream, lambda: dc.dc_fspb_spmm(plan, F, Y), reps, flush)
     dc.dc_fspb_device_status(plan)
     err = float(((Y.t() - plain).abs().max(1).values / plain.abs().max(1).values).max())
+    oracle_err = None
+    if not args.no_cpu:
+        # against the FP64 oracle's axis-stencil form (the method the network
+        # stands in for) on seeded voxels, all 64 fluence columns
+        vox = np.sort(np.random.default_rng(21).choice(plan.n_voxels, 3000, replace=False))
+        want = oracle_multi_fluence(p1, F.cpu().numpy(), lateral_mode=1, voxels=vox)
+        oracle_err = {"surrogate_bf16": column_error(Y.cpu().numpy()[vox], want),
+                      "plain_fp32_axis": column_error(plain.t().cpu().numpy()[vox], want),
+                      "voxels": int(vox.size)}
+    per_set = t_plain - 3.0 * t_spmm
+    sets_3x = math.ceil((3.0 * (t_set_mlp + t_prep) - t_set_axis) / per_set) if per_set > 0 else None
     return {"workload": f"slab64 64^3 @0.25cm, 1 beam, {plan.n_beamlets} beamlets, {k} fluences U[0,1]; "
                         f"network 48-64-64-3 SiLU trained on {n_tr} stencils from 200 random phantoms",
             "samples_generate_s": t_gen, "train_s": t_train, "train_loss": loss,
             "held_out_abs_err_density": {"p50": float(np.median(held)), "p99": float(np.percentile(held, 99))},
             "plain_fp32_axis": {"set_density_ms": t_set_axis, "dose_64_ms": t_plain},
-            "surrogate_bf16": {"set_density_ms": t_set_mlp, "spmm_prepare_s": t_prep, "spmm_64_ms": t_spmm,
+            "surrogate_bf16": {"set_density_ms": t_set_mlp, "spmm_prepare_ms": t_prep, "spmm_64_ms": t_spmm,
                                "fallbacks": dc.dc_fspb_lateral_fallbacks(plan)},
-            "speedup_64_fluences": t_plain / t_spmm,
-            "max_err_vs_plain_over_colmax": err}
+            "speedup_one_set_of_64": (t_set_axis + t_plain) / (t_set_mlp + t_prep + t_spmm),
+            "speedup_per_further_set_of_64": t_plain / t_spmm,
+            "sets_of_64_for_3x": sets_3x,
+            "accounting": "per density: factors (+ matrix build for the BF16 form); per set of 64 "
+                          "fluences: the direct batch or the SpMM",
+            "max_err_vs_plain_over_colmax": err,
+            "max_err_vs_fp64_oracle_over_colmax": oracle_err}
 
 
 def run_gamma_form(args, dc, torch, stream, p, rho_d, flu_d):
@@ -845,8 +979,10 @@ def dc_view(torch, ptr, n):
 
 
 def run_e2e(args, dc, p, plan, pairs, torch):
-    """The same step through the C ABI with pinned host buffers: every H2D/D2H
-    copy of the step's inputs and results is inside the timed region."""
+    """The benchmark step through the C ABI with pinned host buffers: every
+    H2D/D2H copy of the step's inputs and results is inside the timed region
+    (host wall clock over the same number of steps as the device-timed value).
+    Variants: the matrix values in BF16, and the dose alone (no matrix)."""
     V, B = plan.n_voxels, plan.n_beamlets
     pin = lambda shape, dt: torch.empty(shape, dtype=dt, pin_memory=True).numpy()
     rho_h = pin(p.rho.shape, torch.float32)
@@ -857,27 +993,42 @@ def run_e2e(args, dc, p, plan, pairs, torch):
     rowptr_h = pin((V + 1,), torch.int64)
     cols_h = pin((max(pairs, 1),), torch.int32)
     vals_h = pin((max(pairs, 1),), torch.float32)
+    vals16_h = pin((max(pairs, 1),), torch.int16).view(np.uint16)
 
-    def step():
+    def full(vals, dtype):
+        def step():
+            dc.dc_fspb_set_density(plan, rho_h)
+            dc.dc_fspb_pair_count(plan)
+            dc.dc_fspb_dose_and_matrix(plan, flu_h, dose_h, dtype, rowptr_h, cols_h, vals)
+        return step
+
+    def dose_only():
         dc.dc_fspb_set_density(plan, rho_h)
         dc.dc_fspb_dose(plan, flu_h, dose_h)
-        n = dc.dc_fspb_pair_count(plan)
-        dc.dc_fspb_dose_matrix(plan, dc.DC_F32, rowptr_h, cols_h, vals_h)
-        return n
 
-    for _ in range(max(1, args.warmup)):
-        step()
-    torch.cuda.synchronize()
-    k = max(1, min(args.steps, 5))
-    t0 = time.perf_counter()
-    for _ in range(k):
-        step()
-    torch.cuda.synchronize()
-    dt = (time.perf_counter() - t0) / k
+    def timed(step):
+        for _ in range(max(1, min(args.warmup, 2))):
+            step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) / args.steps
+
     h2d = 4 * V + 4 * B
-    d2h = 4 * V + 8 * (V + 1) + 8 * pairs + 8
-    return {"value": 2 * pairs / dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "ms_per_step": dt * 1e3, "steps": k}
+    dt = timed(full(vals_h, dc.DC_F32))
+    out = {"value": pairs / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": 4 * V + 8 * (V + 1) + 8 * pairs + 8, "ms_per_step": dt * 1e3,
+           "steps": args.steps}
+    dt16 = timed(full(vals16_h, dc.DC_BF16))
+    dtd = timed(dose_only)
+    out["variants"] = {
+        "bf16_matrix": {"value": pairs / dt16, "ms_per_step": dt16 * 1e3, "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": 4 * V + 8 * (V + 1) + 6 * pairs + 8},
+        "dose_only": {"value": pairs / dtd, "ms_per_step": dtd * 1e3, "h2d_bytes_per_step": h2d,
+                      "d2h_bytes_per_step": 4 * V}}
+    return out
 
 
 def main():
