@@ -309,6 +309,25 @@ dc_status dc_fspb_set_surrogate(dc_plan* plan, const float* params, float rho_lo
  * Asynchronous on the plan's stream.  Errors: DC_EINVAL, DC_ECUDA. */
 dc_status dc_fspb_set_lateral_mode(dc_plan* plan, int32_t mode);
 
+/* ---- Arithmetic of the direct pair evaluation ----
+ *
+ * Section 2.2 evaluates the exponentials of eq. (4) with the fast,
+ * reduced-accuracy hardware function.  DC_PRECISION_FP32 (the default) does
+ * the same in FP32.  DC_PRECISION_BF16 is this library's reduced-precision
+ * form: the two exponentials of each profile kind of eq. (4) are taken for
+ * the x and the y profile at once, as one packed BF16 pair (arguments and
+ * results rounded to 8 significant bits); geometry, lookups, eq. (3), eq. (2)
+ * and the sum of eq. (1) stay FP32.  Its error against the FP64 oracle is
+ * measured against the surrogate bar of 1 % of the maximum dose, not
+ * guaranteed.  It applies to dc_fspb_dose (and dc_fspb_dose_batch with k = 1)
+ * and to the plan's share of a multi-plan batch; the matrix calls, the SpMM and
+ * k > 1 stay FP32.  Takes effect at the next call; a batch picks it up at its
+ * next run.  Errors: DC_EINVAL (NULL plan, unknown value).
+ */
+#define DC_PRECISION_FP32 0
+#define DC_PRECISION_BF16 1
+dc_status dc_fspb_set_precision(dc_plan* plan, int32_t precision);
+
 /* Entries of the last network-form factor pass that fell back to the AXIS
  * computation (0 in the other forms).  Synchronises. */
 dc_status dc_fspb_lateral_fallbacks(dc_plan* plan, int64_t* n);

@@ -78,6 +78,7 @@ dc::PlanView dc_plan::view() const
     v.a_hi = (float)(coeffs.a_nt - 1);
     v.w_hi = (float)(coeffs.w_n - 1);
     v.item_rt = (coeffs.density_correction && lateral_mode != DC_LATERAL_ISO) ? 1 : 0;
+    v.prec_rt = precision;
     return v;
 }
 

@@ -122,6 +122,16 @@ dc_status dc_fspb_set_lateral_mode(dc_plan* plan, int32_t mode)
     return DC_OK;
 }
 
+dc_status dc_fspb_set_precision(dc_plan* plan, int32_t precision)
+{
+    if (!plan) return bad("dc_fspb_set_precision: NULL argument");
+    if (precision != DC_PRECISION_FP32 && precision != DC_PRECISION_BF16)
+        return bad("dc_fspb_set_precision: unknown precision");
+    plan->precision = precision;
+    ++plan->layout_gen;   // a captured batch graph picks its kernel by it
+    return DC_OK;
+}
+
 dc_status dc_fspb_lateral_fallbacks(dc_plan* plan, int64_t* n)
 {
     if (!plan || !n) return bad("dc_fspb_lateral_fallbacks: NULL argument");

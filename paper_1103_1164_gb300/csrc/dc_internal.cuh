@@ -39,6 +39,7 @@ struct dc_plan {
     bool merged = false;
     // lateral form of step 11 (DC_LATERAL_*) and its per-entry factors
     int lateral_mode = 0;
+    int precision = DC_PRECISION_FP32;   // arithmetic of the direct dose (dc_fspb_set_precision)
     float4* d_lfac = nullptr;        // [n_beams][V + 32]
     float* d_leaf = nullptr;         // leaf sequences of dc_fluence_from_leaves (packed)
     size_t leaf_cap = 0;             // floats allocated at d_leaf

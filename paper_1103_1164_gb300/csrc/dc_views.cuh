@@ -80,6 +80,7 @@ struct PlanView {
     float gw[16];                 // normalised Gaussian weights of the 16 stencil taps
     int merged_rt;                // tabm is in use (runtime copy of the plan's choice)
     int item_rt;                  // lfac is in use
+    int prec_rt;                  // direct-dose arithmetic (DC_PRECISION_*)
     float a_hi, w_hi;             // a_nt - 1, w_n - 1 as floats (clamps of the table coordinates)
 };
 

@@ -86,13 +86,28 @@ __device__ __forceinline__ uint32_t grid_bits_mul(float a, float b, float& frac)
 // operation): ax = (|x|, |y|), nk = -k per axis, x0 = (x0, y0).  With
 // d = |x| - x0 and c = copysign(1 - e1, d), eq. (4) is 1/2 - (c + e2)/2 on
 // both sides of |x| = x0 (c = -(1 - e1) inside, 1 - e1 outside).
+// 2^a.x and 2^a.y from one special-function instruction on a packed BF16
+// pair: the arguments are rounded to BF16 (8 significant bits), the results
+// come back as BF16 and are widened exactly to FP32.
+__device__ __forceinline__ float2 ex2_bf16x2(float2 a)
+{
+    uint32_t in, out;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(in) : "f"(a.y), "f"(a.x));   // high half a.y, low half a.x
+    asm("ex2.approx.ftz.bf16x2 %0, %1;" : "=r"(out) : "r"(in));
+    return make_float2(__uint_as_float(out << 16), __uint_as_float(out & 0xffff0000u));
+}
+
+// PREC 0: four FP32 exponentials; PREC 1 (the reduced-precision form): the
+// x and y exponentials of each kind in one packed BF16 instruction, the rest
+// in FP32.
+template <int PREC>
 __device__ __forceinline__ float2 penumbra2(float2 ax, float2 nk, float2 x0, float2 nx0)
 {
     const float2 d = __fadd2_rn(ax, nx0);
     const float2 t1 = __fmul2_rn(nk, make_float2(fabsf(d.x), fabsf(d.y)));
     const float2 t2 = __ffma2_rn(nk, ax, __fmul2_rn(nk, x0));
-    const float2 e1 = make_float2(ex2(t1.x), ex2(t1.y));
-    const float2 e2 = make_float2(ex2(t2.x), ex2(t2.y));
+    const float2 e1 = PREC ? ex2_bf16x2(t1) : make_float2(ex2(t1.x), ex2(t1.y));
+    const float2 e2 = PREC ? ex2_bf16x2(t2) : make_float2(ex2(t2.x), ex2(t2.y));
     const float2 c = __ffma2_rn(e1, make_float2(-1.f, -1.f), make_float2(1.f, 1.f));
     const float2 q = __fadd2_rn(make_float2(copysignf(c.x, d.x), copysignf(c.y, d.y)), e2);
     return __ffma2_rn(make_float2(-0.5f, -0.5f), q, make_float2(0.5f, 0.5f));
@@ -140,7 +155,7 @@ __device__ __forceinline__ PairTest pair_test(const PlanView& P, const Lane& ln,
 }
 
 // D_i(r) of eq. (2) for unit fluence (called only where the pair is in).
-template <bool MERGED, int LAT>
+template <bool MERGED, int LAT, int PREC>
 __device__ __forceinline__ float pair_eval(const PlanView& P, const Lane& ln, const uint32_t i, const float sad,
                                            const float4* __restrict__ sW, const PairTest& pt)
 {
@@ -200,8 +215,8 @@ __device__ __forceinline__ float pair_eval(const PlanView& P, const Lane& ln, co
     // eqs. (3) and (2): the x and y profiles of each component together
     const float2 axy = make_float2(fabsf(x), fabsf(y));
     const float2 x0 = make_float2(P.x0, P.y0), nx0 = make_float2(-P.x0, -P.y0);
-    const float2 p1 = penumbra2(axy, make_float2(nk.x, nk.x), x0, nx0);
-    const float2 p2 = penumbra2(axy, make_float2(nk.y, nk2y), x0, nx0);
+    const float2 p1 = penumbra2<PREC>(axy, make_float2(nk.x, nk.x), x0, nx0);
+    const float2 p2 = penumbra2<PREC>(axy, make_float2(nk.y, nk2y), x0, nx0);
     const float F = fmaf(om1 * p1.x, p1.y, om2 * p2.x * p2.y);
     return F * Av * (s * s);
 }
@@ -280,7 +295,7 @@ __device__ __forceinline__ void flush_stage(const DoseArgs& a, const int2* st, i
 
 // Evaluates one warp work unit: the 32 list entries starting at e0 of beam b
 // (one voxel per lane) against the beamlets of the warp's union window.
-template <int MODE, int NF, bool MERGED, int LAT>
+template <int MODE, int NF, bool MERGED, int LAT, int PREC = 0>
 __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi, const int64_t e0, const int b,
                                              const float4* __restrict__ sW, int2* sst, float4* srow,
                                              const int lane)
@@ -388,7 +403,7 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
             if (MODE == kDose) {
                 if (NF == 1) cnt += pt.in ? 1 : 0;
                 if (pt.in) {
-                    const float D = pair_eval<MERGED, LAT>(P, ln, i, sad, sW, pt);
+                    const float D = pair_eval<MERGED, LAT, PREC>(P, ln, i, sad, sW, pt);
                     if (NF == 1) {
                         acc[0] = fmaf(rq[2].w, D, acc[0]);
                     } else {
@@ -399,7 +414,7 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
                 }
             } else {
                 if (pt.in) {
-                    const float D = pair_eval<MERGED, LAT>(P, ln, i, sad, sW, pt);
+                    const float D = pair_eval<MERGED, LAT, 0>(P, ln, i, sad, sW, pt);
                     sst[lane * kRingLd + (int)(((uint32_t)pos + (uint32_t)cnt) & (kRing - 1))] =
                         make_int2((int)i, __float_as_int(D));
                     ++cnt;
@@ -434,7 +449,7 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
 template <int MODE, int NF>
 constexpr int min_ctas() { return MODE == kCount ? 4 : (MODE == kFill ? 4 : (NF == 1 ? 5 : 3)); }
 
-template <int MODE, int NF, bool MERGED, int LAT>
+template <int MODE, int NF, bool MERGED, int LAT, int PREC>
 __global__ void __launch_bounds__(kThreads, min_ctas<MODE, NF>()) k_pairs(const DoseArgs a)
 {
     extern __shared__ float4 smem[];
@@ -461,7 +476,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<MODE, NF>()) k_pairs(const 
         int b = 0;
         while (b + 1 < P.n_beams && s_base[b + 1] <= e0) ++b;
         const int32_t vi = __ldg(a.items + e0 + lane);
-        process_unit<MODE, NF, MERGED, LAT>(a, vi, e0, b, sW, sst, s_row[warp], lane);
+        process_unit<MODE, NF, MERGED, LAT, PREC>(a, vi, e0, b, sW, sst, s_row[warp], lane);
     }
 }
 
@@ -479,7 +494,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<MODE, NF>()) k_pairs(const 
 // (one commissioned beam model), they are staged in shared memory once per
 // CTA; otherwise each plan's are read through L1.
 constexpr int kMaxBatch = 64;
-constexpr int kBatchGroups = 2;   // per-voxel or per-item lateral factors
+constexpr int kBatchGroups = 4;   // (per-voxel or per-item lateral factors) x (FP32 or BF16 exponentials)
 
 struct BatchParams {
     DoseArgs a[kMaxBatch];
@@ -509,7 +524,7 @@ __global__ void k_batch_prefix(const DoseArgs* __restrict__ args, const BatchGro
 
 // MINB: CTAs per SM the register budget is set for (4: 64 registers; 5: 48).
 // SHARED_W: all plans share the water tables of plan 0.
-template <int MINB, bool SHARED_W, bool MERGED, int LAT>
+template <int MINB, bool SHARED_W, bool MERGED, int LAT, int PREC>
 __global__ void __launch_bounds__(kThreads, MINB) k_pairs_batch(const __grid_constant__ BatchParams bp,
                                                                 const __grid_constant__ BatchGroup g,
                                                                 const int64_t* __restrict__ prefix,
@@ -539,15 +554,15 @@ __global__ void __launch_bounds__(kThreads, MINB) k_pairs_batch(const __grid_con
         while (b + 1 < nb && __ldg(a.base + b + 1) <= e0) ++b;
         const int32_t vi = __ldg(a.items + e0 + lane);
         const float4* wt = SHARED_W ? smem : a.P.water;
-        process_unit<kDose, 1, MERGED, LAT>(a, vi, e0, b, wt, nullptr, s_row[threadIdx.x >> 5], lane);
+        process_unit<kDose, 1, MERGED, LAT, PREC>(a, vi, e0, b, wt, nullptr, s_row[threadIdx.x >> 5], lane);
     }
 }
 
-template <int MINB, bool SHARED_W, bool MERGED, int LAT>
+template <int MINB, bool SHARED_W, bool MERGED, int LAT, int PREC>
 cudaError_t batch_kernel(cudaStream_t s, const BatchParams& bp, const BatchGroup& g, const int64_t* d_prefix,
                          unsigned int* d_counter, int device, int w_n)
 {
-    auto kern = k_pairs_batch<MINB, SHARED_W, MERGED, LAT>;
+    auto kern = k_pairs_batch<MINB, SHARED_W, MERGED, LAT, PREC>;
     const size_t sm = (SHARED_W && !MERGED) ? 2 * sizeof(float4) * (size_t)w_n : 0;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
@@ -560,15 +575,24 @@ cudaError_t batch_kernel(cudaStream_t s, const BatchParams& bp, const BatchGroup
     return cudaGetLastError();
 }
 
-template <bool MERGED, int LAT>
+template <bool MERGED, int LAT, int PREC>
 cudaError_t batch_group(cudaStream_t s, const BatchParams& bp, const BatchGroup& g, const int64_t* d_prefix,
                         unsigned int* d_counter, int device, int w_n, int variant, bool shared_water)
 {
     if (variant == 0)
-        return shared_water ? batch_kernel<4, true, MERGED, LAT>(s, bp, g, d_prefix, d_counter, device, w_n)
-                            : batch_kernel<4, false, MERGED, LAT>(s, bp, g, d_prefix, d_counter, device, w_n);
-    return shared_water ? batch_kernel<5, true, MERGED, LAT>(s, bp, g, d_prefix, d_counter, device, w_n)
-                        : batch_kernel<5, false, MERGED, LAT>(s, bp, g, d_prefix, d_counter, device, w_n);
+        return shared_water ? batch_kernel<4, true, MERGED, LAT, PREC>(s, bp, g, d_prefix, d_counter, device, w_n)
+                            : batch_kernel<4, false, MERGED, LAT, PREC>(s, bp, g, d_prefix, d_counter, device, w_n);
+    return shared_water ? batch_kernel<5, true, MERGED, LAT, PREC>(s, bp, g, d_prefix, d_counter, device, w_n)
+                        : batch_kernel<5, false, MERGED, LAT, PREC>(s, bp, g, d_prefix, d_counter, device, w_n);
+}
+
+template <int LAT, int PREC>
+cudaError_t batch_group_tables(bool merged, cudaStream_t s, const BatchParams& bp, const BatchGroup& g,
+                               const int64_t* d_prefix, unsigned int* d_counter, int device, int w_n, int variant,
+                               bool shared_water)
+{
+    return merged ? batch_group<true, LAT, PREC>(s, bp, g, d_prefix, d_counter, device, w_n, variant, shared_water)
+                  : batch_group<false, LAT, PREC>(s, bp, g, d_prefix, d_counter, device, w_n, variant, shared_water);
 }
 
 // dose_j[v] = sum over plan j's beams of its partial doses (fixed beam order)
@@ -734,11 +758,11 @@ int grid_for(int64_t n)
 }
 
 // Persistent launch: as many CTAs as fit on the device at once.
-template <int MODE, int NF, bool MERGED, int LAT>
+template <int MODE, int NF, bool MERGED, int LAT, int PREC = 0>
 cudaError_t run_variant(const dc_plan* p, const DoseArgs& a)
 {
     const size_t sm = smem_bytes(p, MODE);
-    auto kern = k_pairs<MODE, NF, MERGED, LAT>;
+    auto kern = k_pairs<MODE, NF, MERGED, LAT, PREC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     int per_sm = 0, sms = 0;
@@ -759,6 +783,11 @@ cudaError_t run(const dc_plan* p, const DoseArgs& a)
     if (MODE == kCount) return run_variant<kCount, 1, false, kIso>(p, a);
     // per-item factors exist for the axis and network forms with the density correction on
     const bool item = p->coeffs.density_correction && p->lateral_mode != DC_LATERAL_ISO;
+    if (MODE == kDose && NF == 1 && p->precision == DC_PRECISION_BF16) {
+        if (p->merged)
+            return item ? run_variant<kDose, 1, true, kItem, 1>(p, a) : run_variant<kDose, 1, true, kIso, 1>(p, a);
+        return item ? run_variant<kDose, 1, false, kItem, 1>(p, a) : run_variant<kDose, 1, false, kIso, 1>(p, a);
+    }
     if (p->merged) return item ? run_variant<MODE, NF, true, kItem>(p, a) : run_variant<MODE, NF, true, kIso>(p, a);
     return item ? run_variant<MODE, NF, false, kItem>(p, a) : run_variant<MODE, NF, false, kIso>(p, a);
 }
@@ -792,11 +821,12 @@ cudaError_t launch_batch(cudaStream_t s, const DoseArgs* h_args, const DoseArgs*
     memcpy(bp.a, h_args, sizeof(DoseArgs) * n);
     const int w_n = h_args[0].P.w_n;
     for (int gi = 0; gi < kBatchGroups; ++gi) {
-        const bool item = gi == 1;
+        const bool item = (gi & 1) != 0;
+        const int prec = gi >> 1;
         BatchGroup g{};
         bool merged = true;
         for (int j = 0; j < n; ++j)
-            if ((h_args[j].P.item_rt != 0) == item) {
+            if ((h_args[j].P.item_rt != 0) == item && h_args[j].P.prec_rt == prec) {
                 g.j[g.n++] = (int8_t)j;
                 merged = merged && h_args[j].P.merged_rt != 0;
             }
@@ -806,12 +836,12 @@ cudaError_t launch_batch(cudaStream_t s, const DoseArgs* h_args, const DoseArgs*
         k_batch_prefix<<<1, 32, 0, s>>>(d_args, g, pre, cnt);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        if (merged)
-            e = item ? batch_group<true, kItem>(s, bp, g, pre, cnt, device, w_n, variant, shared_water)
-                     : batch_group<true, kIso>(s, bp, g, pre, cnt, device, w_n, variant, shared_water);
+        if (prec == 0)
+            e = item ? batch_group_tables<kItem, 0>(merged, s, bp, g, pre, cnt, device, w_n, variant, shared_water)
+                     : batch_group_tables<kIso, 0>(merged, s, bp, g, pre, cnt, device, w_n, variant, shared_water);
         else
-            e = item ? batch_group<false, kItem>(s, bp, g, pre, cnt, device, w_n, variant, shared_water)
-                     : batch_group<false, kIso>(s, bp, g, pre, cnt, device, w_n, variant, shared_water);
+            e = item ? batch_group_tables<kItem, 1>(merged, s, bp, g, pre, cnt, device, w_n, variant, shared_water)
+                     : batch_group_tables<kIso, 1>(merged, s, bp, g, pre, cnt, device, w_n, variant, shared_water);
         if (e != cudaSuccess) return e;
         count_launches(2);
     }

@@ -21,6 +21,7 @@ DC_DEVICE_PTRS = 1
 DC_BATCH_DENSITY = 2
 DC_F32, DC_BF16 = 0, 1
 DC_LATERAL_ISO, DC_LATERAL_AXIS, DC_LATERAL_MLP = 0, 1, 2
+DC_PRECISION_FP32, DC_PRECISION_BF16 = 0, 1
 MLP_PARAMS = 7491
 DC_SPMM_STATIC_MAX_BEAMLETS, DC_SPMM_STATIC_MAX_PARTIALS = 8192, 4194304
 
@@ -76,7 +77,7 @@ EXPORTS = ["dc_last_error", "dc_status_str", "dc_fspb_create", "dc_fspb_destroy"
            "dc_fspb_get_beamlets", "dc_fspb_get_tables", "dc_fspb_set_density",
            "dc_fspb_launch_count", "dc_fspb_autotune", "dc_fspb_spmm_prepare", "dc_fspb_spmm_info",
            "dc_fspb_spmm", "dc_fspb_spmm_noalloc", "dc_fspb_device_status", "dc_fspb_set_surrogate",
-           "dc_fspb_set_lateral_mode", "dc_fspb_lateral_fallbacks", "dc_fspb_stencils",
+           "dc_fspb_set_lateral_mode", "dc_fspb_set_precision", "dc_fspb_lateral_fallbacks", "dc_fspb_stencils",
            "dc_mlp_create", "dc_mlp_destroy", "dc_mlp_get_params", "dc_mlp_gradient", "dc_mlp_train",
            "dc_mlp_predict", "dc_fspb_batch_create", "dc_fspb_batch_destroy", "dc_fspb_batch_buffers",
            "dc_fspb_batch_run", "dc_fspb_batch_dose", "dc_fspb_batch_synchronize", "dc_fspb_batch_kernels",
@@ -125,6 +126,7 @@ def load():
     L.dc_fspb_device_status.argtypes = [vp]
     L.dc_fspb_set_surrogate.argtypes = [vp, vp, C.c_float, C.c_float]
     L.dc_fspb_set_lateral_mode.argtypes = [vp, i32]
+    L.dc_fspb_set_precision.argtypes = [vp, i32]
     L.dc_fspb_lateral_fallbacks.argtypes = [vp, C.POINTER(i64)]
     L.dc_fspb_stencils.argtypes = [vp, vp, vp, i32, vp, vp, u32]
     L.dc_mlp_create.argtypes = [vp, vp, C.POINTER(vp)]
@@ -323,6 +325,11 @@ def dc_fspb_set_surrogate(plan: Plan, params, rho_lo=0.05, rho_hi=2.0):
 
 def dc_fspb_set_lateral_mode(plan: Plan, mode: int):
     _check(load().dc_fspb_set_lateral_mode(plan.handle, int(mode)))
+
+
+def dc_fspb_set_precision(plan: Plan, precision: int):
+    """Arithmetic of the direct dose: DC_PRECISION_FP32 or DC_PRECISION_BF16."""
+    _check(load().dc_fspb_set_precision(plan.handle, int(precision)))
 
 
 def dc_fspb_lateral_fallbacks(plan: Plan) -> int:
