@@ -309,6 +309,45 @@ dc_status dc_fspb_set_surrogate(dc_plan* plan, const float* params, float rho_lo
  * Asynchronous on the plan's stream.  Errors: DC_EINVAL, DC_ECUDA. */
 dc_status dc_fspb_set_lateral_mode(dc_plan* plan, int32_t mode);
 
+/* ---- Commissioning (Section 2.1: u, omega, f and b fitted to reference doses) ----
+ *
+ * Section 2.1 obtains the model's parameters u, omega, f(.) and b(.) by
+ * fitting the DC-FSPB dose to reference doses of a slab phantom.  These two
+ * calls are what such a fit needs from the engine: new tables for a plan, and
+ * the gradient of a weighted dose sum with respect to them.
+ *
+ * dc_fspb_set_tables replaces the plan's water tables water [4][w_n]
+ * (u_1^w, u_2^w, omega_1^w, omega_2^w) and density functions dens [6][f_n]
+ * (f_u1, f_u2, f_omega1, f_omega2, b_1, b_2), on the sampling given at
+ * creation (host float32; copied before return), and recomputes the
+ * density-dependent steps for the plan's current density (the omega_corr
+ * tables integrate b).  The depth-dose table A stays.  Errors: DC_EINVAL
+ * (NULL, non-finite entry), DC_ECUDA.
+ */
+dc_status dc_fspb_set_tables(dc_plan* plan, const float* water, const float* dens);
+
+/*
+ * Backward pass of eq. (1) with respect to the tables (the vector-Jacobian
+ * product of the dose): for voxel weights weights [V] and fluence [B],
+ *   g_water[q][j] = sum_v weights[v] dD(v)/d water[q][j]   (q = u_1^w, u_2^w,
+ *                                                          omega_1^w, omega_2^w)
+ *   g_dens[q][j]  = sum_v weights[v] dD(v)/d dens[q][j]    (q = f_u1, f_u2,
+ *                                                          f_omega1, f_omega2)
+ *   g_corr[i]     = d/ds at s = 1 of sum_v weights[v] D(v) with b_i scaled
+ *                   by s (omega_i^corr scales with b_i), i = 1, 2.
+ * The derivative of a table lookup is the weight of the entry in its linear
+ * interpolation; a clamp at a table's end puts it on the end entry; where
+ * omega_i is clamped at 0 its derivatives are 0.  The b tables enter only
+ * through that common scale (their entries act through the ray integrals).
+ * Needs the density correction on and DC_LATERAL_ISO (else DC_EUNSUPPORTED).
+ * FP32 arithmetic; the sums are accumulated with atomics, so their order (and
+ * the last bits) may change between calls.  Pointers host or device
+ * (DC_DEVICE_PTRS for all).  Errors: DC_EINVAL, DC_EUNSUPPORTED (also when
+ * 4 (w_n + f_n) floats of bins do not fit in shared memory), DC_ENOMEM, DC_ECUDA.
+ */
+dc_status dc_fspb_dose_vjp(dc_plan* plan, const float* fluence, const float* weights, float* g_water,
+                           float* g_dens, float* g_corr, uint32_t flags);
+
 /* ---- Arithmetic of the direct pair evaluation ----
  *
  * Section 2.2 evaluates the exponentials of eq. (4) with the fast,

@@ -66,6 +66,7 @@ dc::PlanView dc_plan::view() const
     v.tabm = d_tabm;
     v.lfac = d_lfac;
     v.rho = d_rho;
+    v.rhos = d_rhos;
     v.dens = d_dens;
     v.f_n = coeffs.f_n;
     v.f_rho0 = coeffs.f_rho0;
@@ -272,11 +273,9 @@ static dc_status check_inputs(const float* ct, const dc_grid* g, const dc_beam* 
     return DC_OK;
 }
 
-// Algorithm A1 steps 1-6 on the plan's stream for density `ct`.
-static dc_status compute_density_steps(dc_plan* p, const float* ct, uint32_t flags)
+// Algorithm A1 steps 1-6 on the plan's stream for the density in d_rho.
+static dc_status rerun_density_steps(dc_plan* p)
 {
-    cudaMemcpyKind k = (flags & DC_DEVICE_PTRS) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    DC_CUDA(cudaMemcpyAsync(p->d_rho, ct, p->V * sizeof(float), k, p->stream));
     DC_CUDA(launch_smooth(p, p->coeffs.smooth_sigma));
     DC_CUDA(launch_factors(p));
     DC_CUDA(launch_beamlets(p));
@@ -285,6 +284,39 @@ static dc_status compute_density_steps(dc_plan* p, const float* ct, uint32_t fla
     p->pairs = -1;
     p->counts_fresh = false;
     if (p->sp_ready) p->spmm_free();   // the SpMM tiles follow the voxel lists
+    return DC_OK;
+}
+
+// The same for density `ct` (host or device memory).
+static dc_status compute_density_steps(dc_plan* p, const float* ct, uint32_t flags)
+{
+    cudaMemcpyKind k = (flags & DC_DEVICE_PTRS) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    DC_CUDA(cudaMemcpyAsync(p->d_rho, ct, p->V * sizeof(float), k, p->stream));
+    return rerun_density_steps(p);
+}
+
+// Water tables (value + slope per depth sample) and density functions to the
+// device: (u_1^w, du_1^w, u_2^w, du_2^w), (omega_1^w, domega_1^w, omega_2^w,
+// domega_2^w) per sample; dens as given.  Synchronises (the host arrays may
+// be released on return).
+static dc_status upload_tables(dc_plan* p, const float* water, const float* dens)
+{
+    const dc_kernel_coeffs& c = p->coeffs;
+    std::vector<float4> w(2 * (size_t)c.w_n);
+    auto vs = [&](int q, int j, float* val, float* slope) {
+        const float* r = water + (size_t)q * c.w_n;
+        *val = r[j];
+        *slope = j + 1 < c.w_n ? r[j + 1] - r[j] : 0.f;
+    };
+    for (int j = 0; j < c.w_n; ++j) {
+        float a[8];
+        for (int q = 0; q < 4; ++q) vs(q, j, &a[2 * q], &a[2 * q + 1]);
+        w[2 * j] = make_float4(a[0], a[1], a[2], a[3]);
+        w[2 * j + 1] = make_float4(a[4], a[5], a[6], a[7]);
+    }
+    DC_CUDA(cudaMemcpyAsync(p->d_water, w.data(), w.size() * sizeof(float4), cudaMemcpyHostToDevice, p->stream));
+    DC_CUDA(cudaMemcpyAsync(p->d_dens, dens, sizeof(float) * 6 * (size_t)c.f_n, cudaMemcpyHostToDevice, p->stream));
+    DC_CUDA(cudaStreamSynchronize(p->stream));
     return DC_OK;
 }
 
@@ -365,25 +397,10 @@ static dc_status create_impl(dc_plan* p, const float* ct, uint32_t flags)
     DC_CUDA(cudaMemcpyAsync(p->d_bin, p->bin_host.data(), nb * sizeof(BinGeom), cudaMemcpyHostToDevice,
                             p->stream));
 
-    // water table per depth sample as value + slope to the next sample:
-    // (u_1^w, du_1^w, u_2^w, du_2^w), (omega_1^w, domega_1^w, omega_2^w, domega_2^w)
-    std::vector<float4> w(2 * (size_t)c.w_n);
-    auto vs = [&](int q, int j, float* val, float* slope) {
-        const float* r = c.water + (size_t)q * c.w_n;
-        *val = r[j];
-        *slope = j + 1 < c.w_n ? r[j + 1] - r[j] : 0.f;
-    };
-    for (int j = 0; j < c.w_n; ++j) {
-        float a[8];
-        for (int q = 0; q < 4; ++q) vs(q, j, &a[2 * q], &a[2 * q + 1]);
-        w[2 * j] = make_float4(a[0], a[1], a[2], a[3]);
-        w[2 * j + 1] = make_float4(a[4], a[5], a[6], a[7]);
-    }
-    DC_CUDA(cudaMemcpyAsync(p->d_water, w.data(), w.size() * sizeof(float4), cudaMemcpyHostToDevice, p->stream));
+    dc_status st = upload_tables(p, c.water, c.dens);
+    if (st != DC_OK) return st;
     DC_CUDA(cudaMemcpyAsync(p->d_A, c.A, sizeof(float) * (size_t)c.a_nt * c.a_ntheta,
                             cudaMemcpyHostToDevice, p->stream));
-    DC_CUDA(cudaMemcpyAsync(p->d_dens, c.dens, sizeof(float) * 6 * (size_t)c.f_n, cudaMemcpyHostToDevice,
-                            p->stream));
     DC_CUDA(cudaMemcpyAsync(p->d_beamin, p->beams.data(), sizeof(dc_beam) * p->n_beams,
                             cudaMemcpyHostToDevice, p->stream));
     dc_status s = compute_density_steps(p, ct, flags);
@@ -721,6 +738,61 @@ dc_status dc_fspb_dose_and_matrix(dc_plan* plan, const float* fluence, float* do
 {
     if (!fluence || !dose) return invalid("dc_fspb_dose_and_matrix: NULL argument");
     return matrix_impl(plan, value_dtype, rowptr, cols, vals, fluence, dose, flags, "dc_fspb_dose_and_matrix");
+}
+
+dc_status dc_fspb_set_tables(dc_plan* plan, const float* water, const float* dens)
+{
+    if (!plan || !water || !dens) return invalid("dc_fspb_set_tables: NULL argument");
+    const dc_kernel_coeffs& c = plan->coeffs;
+    for (size_t q = 0; q < 4 * (size_t)c.w_n; ++q)
+        if (!isfinite(water[q])) return invalid("dc_fspb_set_tables: non-finite water table entry");
+    for (size_t q = 0; q < 6 * (size_t)c.f_n; ++q)
+        if (!isfinite(dens[q])) return invalid("dc_fspb_set_tables: non-finite density-function entry");
+    DC_CUDA(cudaStreamSynchronize(plan->stream));
+    dc_status s = upload_tables(plan, water, dens);
+    if (s != DC_OK) return s;
+    return rerun_density_steps(plan);
+}
+
+dc_status dc_fspb_dose_vjp(dc_plan* plan, const float* fluence, const float* weights, float* g_water, float* g_dens,
+                           float* g_corr, uint32_t flags)
+{
+    if (!plan || !fluence || !weights || !g_water || !g_dens || !g_corr)
+        return invalid("dc_fspb_dose_vjp: NULL argument");
+    if (!plan->coeffs.density_correction || plan->lateral_mode != DC_LATERAL_ISO) {
+        set_error("dc_fspb_dose_vjp: needs the density correction on and the paper's lateral form (DC_LATERAL_ISO)");
+        return DC_EUNSUPPORTED;
+    }
+    const dc_kernel_coeffs& c = plan->coeffs;
+    const size_t nw = 4 * (size_t)c.w_n, nd = 4 * (size_t)c.f_n;
+    if (2 * sizeof(float4) * c.w_n + sizeof(float) * (nw + nd + 2) > 200 * 1024) {
+        set_error("dc_fspb_dose_vjp: water and density tables too long for the shared-memory gradient bins");
+        return DC_EUNSUPPORTED;
+    }
+    if (flags & DC_DEVICE_PTRS) {
+        DC_CUDA(launch_dose_vjp(plan, fluence, weights, g_water, g_dens, g_corr));
+        return DC_OK;
+    }
+    // host buffers: staged through the plan's fluence/dose staging plus one
+    // gradient block
+    dc_status s = ensure_staging(plan, plan->B, plan->V);
+    if (s != DC_OK) return s;
+    float* d_g = nullptr;
+    DC_CUDA(dalloc(&d_g, nw + nd + 2));
+    cudaError_t e = cudaMemcpyAsync(plan->d_fluence, fluence, plan->B * sizeof(float), cudaMemcpyHostToDevice,
+                                    plan->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(plan->d_dose, weights, plan->V * sizeof(float), cudaMemcpyHostToDevice, plan->stream);
+    if (e == cudaSuccess) e = launch_dose_vjp(plan, plan->d_fluence, plan->d_dose, d_g, d_g + nw, d_g + nw + nd);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g_water, d_g, nw * sizeof(float), cudaMemcpyDeviceToHost, plan->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g_dens, d_g + nw, nd * sizeof(float), cudaMemcpyDeviceToHost, plan->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g_corr, d_g + nw + nd, 2 * sizeof(float), cudaMemcpyDeviceToHost, plan->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(plan->stream);
+    cudaFree(d_g);
+    if (e != cudaSuccess) return cuda_fail(e, "dc_fspb_dose_vjp");
+    return DC_OK;
 }
 
 static dc_status check_device_status(dc_plan* p)

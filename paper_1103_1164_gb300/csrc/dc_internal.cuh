@@ -165,6 +165,10 @@ cudaError_t launch_fill(const dc_plan* p, const int64_t* rowptr, int32_t* cols, 
                         int value_dtype, const float* fluence = nullptr, float* dose = nullptr);
 cudaError_t launch_scan_counts(const dc_plan* p, const int32_t* counts, int64_t* rowptr,
                                int64_t* total_dev);
+// backward pass of eq. (1) with respect to the commissioning tables (device
+// buffers; the gradients are cleared first)
+cudaError_t launch_dose_vjp(const dc_plan* p, const float* fluence, const float* wv, float* g_water, float* g_dens,
+                            float* g_corr);
 // lateral factors, stencil samples and the surrogate network (k_lateral.cu)
 cudaError_t launch_lateral(const dc_plan* p);
 cudaError_t launch_stencils(const dc_plan* p, const int32_t* vox, const int32_t* beam, int n, float* X, float* T);

@@ -73,6 +73,7 @@ struct PlanView {
     const float4* lfac;
     // density and density-function tables for the lateral stencils
     const float* rho;
+    const float* rhos;            // smoothed density (backward pass)
     const float* dens;
     int f_n;
     float f_rho0, inv_drho;
@@ -101,6 +102,12 @@ struct DoseArgs {
     const int32_t* items;   // beam voxel lists (k_bin.cu)
     const int64_t* base;    // [n_beams + 1]
     int32_t* work;          // [0] work units, [1] counter
+    // backward pass with respect to the commissioning tables: voxel weights
+    // [V] and the gradients [4][w_n], [4][f_n], [2]
+    const float* wv;
+    float* g_water;
+    float* g_dens;
+    float* g_corr;
 };
 
 }  // namespace dc

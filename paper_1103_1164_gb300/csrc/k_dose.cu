@@ -37,7 +37,7 @@ constexpr int kRingLd = kRing + 1;
 // fill, whose CSR staging shares the CTA's shared memory)
 constexpr int row_max(int mode) { return mode == 2 ? 16 : 32; }
 
-enum Mode { kDose = 0, kCount = 1, kFill = 2 };
+enum Mode { kDose = 0, kCount = 1, kFill = 2, kGrad = 3 };
 
 __device__ __forceinline__ float ex2(float x)
 {
@@ -221,6 +221,94 @@ __device__ __forceinline__ float pair_eval(const PlanView& P, const Lane& ln, co
     return F * Av * (s * s);
 }
 
+// Eq. (4) and its derivative with respect to the width u (natural units):
+// with e1 = exp(-u ||x| - x0|), e2 = exp(-u (|x| + x0)),
+// dp/du = ((x0 - |x|) e1 + (|x| + x0) e2) / 2 on both sides of |x| = x0.
+__device__ __forceinline__ void penumbra_du(float ax, float u, float x0, float& p, float& dp)
+{
+    const float dd = ax - x0;
+    const float e1 = ex2(-kLog2e * u * fabsf(dd));
+    const float e2 = ex2(-kLog2e * u * (ax + x0));
+    p = dd > 0.f ? 0.5f * (e1 - e2) : 1.f - 0.5f * (e1 + e2);
+    dp = 0.5f * (fmaf(-dd, e1, 0.f) + (ax + x0) * e2);
+}
+
+// Backward pass of one pair (commissioning fit, Section 2.1): with
+// c = w_v f_i, accumulates c dD_i(r)/d(entry) into the shared bins of the
+// water tables u_1^w, u_2^w, omega_1^w, omega_2^w (the two samples around t);
+// into the lane's per-voxel sums the derivatives with respect to the values
+// f_u1(rho), f_u2(rho_hat), f_omega1(rho_hat), f_omega2(rho_hat) (scattered to
+// the density-function bins once per work unit); and into gc the derivatives
+// with respect to a common scale of b_1 and b_2 (omega_i^corr scales with it).
+// Paper's lateral form, general (unmerged) tables, density correction on.
+__device__ __forceinline__ void pair_grad(const PlanView& P, const float4 facv, const uint32_t i, const float sad,
+                                          const float4* __restrict__ sW, const PairTest& pt, const float c,
+                                          float* sgw, float gl[4], float gc[2])
+{
+    const float L = pt.L;
+    const float t = L - pt.L_in;
+    const float s = sad * rcp_approx(L);
+    const float x = pt.pq.x * s, y = pt.pq.y * s;
+    float fr;
+    const uint32_t kb = grid_bits_mul(t, P.inv_d, fr);
+    const float4* tb = P.tab + (i * (2u * (uint32_t)P.Kmax) + 2u * (kb - kGridBits));
+    const float4 e0 = __ldg(tb), e1 = __ldg(tb + 1);
+    const float teq = fmaf(fr, e0.y, e0.x);
+    const float c1 = fmaf(fr, e0.w, e0.z);
+    const float c2 = fmaf(fr, e1.y, e1.x);
+    float fw;
+    const int jw = (int)(grid_bits(fminf(t * P.inv_wdt, P.w_hi), fw) - kGridBits);
+    const float4 w0 = sW[2 * jw], w1 = sW[2 * jw + 1];
+    const float u1w = fmaf(fw, w0.y, w0.x), u2w = fmaf(fw, w0.w, w0.z);
+    const float o1w = fmaf(fw, w1.y, w1.x), o2w = fmaf(fw, w1.w, w1.z);
+    float fa;
+    const uint32_t jb = grid_bits(fminf(teq * P.inv_adt, P.a_hi), fa);
+    const float2 ar = __ldg(P.arow + (i * (uint32_t)P.a_nt + (jb - kGridBits)));
+    const float Av = fmaf(fa, ar.y, ar.x);
+
+    const float u1 = facv.x * u1w, u2 = facv.y * u2w;
+    const float O1 = facv.z * (o1w + c1), O2 = facv.w * (o2w + c2);
+    const float om1 = fmaxf(O1, 0.f), om2 = fmaxf(O2, 0.f);
+    float p1x, d1x, p1y, d1y, p2x, d2x, p2y, d2y;
+    penumbra_du(fabsf(x), u1, P.x0, p1x, d1x);
+    penumbra_du(fabsf(y), u1, P.y0, p1y, d1y);
+    penumbra_du(fabsf(x), u2, P.x0, p2x, d2x);
+    penumbra_du(fabsf(y), u2, P.y0, p2y, d2y);
+    const float K = c * Av * (s * s);
+    const float g_om1 = O1 > 0.f ? K * p1x * p1y : 0.f;     // dD/d omega_1 (zero where the clamp holds)
+    const float g_om2 = O2 > 0.f ? K * p2x * p2y : 0.f;
+    const float g_u1 = K * om1 * fmaf(d1x, p1y, p1x * d1y);  // dD/d u_1
+    const float g_u2 = K * om2 * fmaf(d2x, p2y, p2x * d2y);
+    // water tables: val = w[jw] + fw (w[jw + 1] - w[jw])
+    const int wn = P.w_n;
+    const float a0 = 1.f - fw;
+    atomicAdd(sgw + 0 * wn + jw, a0 * g_u1 * facv.x);
+    atomicAdd(sgw + 1 * wn + jw, a0 * g_u2 * facv.y);
+    atomicAdd(sgw + 2 * wn + jw, a0 * g_om1 * facv.z);
+    atomicAdd(sgw + 3 * wn + jw, a0 * g_om2 * facv.w);
+    if (jw + 1 < wn && fw != 0.f) {
+        atomicAdd(sgw + 0 * wn + jw + 1, fw * g_u1 * facv.x);
+        atomicAdd(sgw + 1 * wn + jw + 1, fw * g_u2 * facv.y);
+        atomicAdd(sgw + 2 * wn + jw + 1, fw * g_om1 * facv.z);
+        atomicAdd(sgw + 3 * wn + jw + 1, fw * g_om2 * facv.w);
+    }
+    gl[0] = fmaf(g_u1, u1w, gl[0]);
+    gl[1] = fmaf(g_u2, u2w, gl[1]);
+    gl[2] = fmaf(g_om1, o1w + c1, gl[2]);
+    gl[3] = fmaf(g_om2, o2w + c2, gl[3]);
+    gc[0] = fmaf(g_om1 * facv.z, c1, gc[0]);
+    gc[1] = fmaf(g_om2 * facv.w, c2, gc[1]);
+}
+
+// The interpolation of a density-function table at density r (clamped to
+// its domain), as k_factors reads it: entry j with weight 1 - w, j + 1 with w.
+__device__ __forceinline__ void dens_bins(const PlanView& P, float r, int& j, float& w)
+{
+    const float sx = fminf(fmaxf((r - P.f_rho0) * P.inv_drho, 0.f), (float)(P.f_n - 1));
+    j = min((int)sx, P.f_n - 2);
+    w = sx - (float)j;
+}
+
 // Writes nw staged CSR entries of every lane (nw <= kRing).  A quarter-warp
 // takes one lane's run at a time, 8 entries (one 32-byte sector of the column
 // array once the run is aligned) per pass: first the leading 8 entries of all
@@ -310,8 +398,12 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
     const float rx = fmaf((float)ix, P.dx, P.ox), ry = fmaf((float)iy, P.dy, P.oy),
                 rz = fmaf((float)iz, P.dz, P.oz);
     const BeamDev& bm = P.beams[b];
+    float4 facv = make_float4(0.f, 0.f, 0.f, 0.f);
+    float gl[4] = {0.f, 0.f, 0.f, 0.f}, gc[2] = {0.f, 0.f};
+    const float wgt = MODE == kGrad && ln.valid ? __ldg(a.wv + v) : 0.f;   // voxel weight of the backward pass
     if (MODE != kCount) {
         const float4 fac = __ldg(P.fac + v);   // f_u1(rho), f_u2(rho_hat), f_w1(rho_hat), f_w2(rho_hat)
+        facv = fac;
         ln.cu1 = kLog2e * fac.x;
         ln.cu2x = ln.cu2y = kLog2e * fac.y;
         ln.cw1 = fac.z;
@@ -400,6 +492,12 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
                 cnt += pt.in ? 1 : 0;
                 continue;
             }
+            if (MODE == kGrad) {
+                if (pt.in && wgt != 0.f)
+                    pair_grad(P, facv, i, sad, sW, pt, wgt * rq[2].w,
+                              reinterpret_cast<float*>(sst), gl, gc);
+                continue;
+            }
             if (MODE == kDose) {
                 if (NF == 1) cnt += pt.in ? 1 : 0;
                 if (pt.in) {
@@ -425,7 +523,25 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
         }
         }
     }
-    if (MODE == kFill) {
+    if (MODE == kGrad) {
+        if (ln.valid && wgt != 0.f) {
+            // the per-voxel derivatives go to the bins of rho (f_u1) and rho_hat (the others)
+            float* sgd = reinterpret_cast<float*>(sst) + 4 * P.w_n;
+            int j;
+            float w;
+            dens_bins(P, __ldg(P.rho + v), j, w);
+            atomicAdd(sgd + j, (1.f - w) * gl[0]);
+            atomicAdd(sgd + j + 1, w * gl[0]);
+            dens_bins(P, __ldg(P.rhos + v), j, w);
+#pragma unroll
+            for (int q = 1; q < 4; ++q) {
+                atomicAdd(sgd + q * P.f_n + j, (1.f - w) * gl[q]);
+                atomicAdd(sgd + q * P.f_n + j + 1, w * gl[q]);
+            }
+            atomicAdd(sgd + 4 * P.f_n, gc[0]);
+            atomicAdd(sgd + 4 * P.f_n + 1, gc[1]);
+        }
+    } else if (MODE == kFill) {
         flush_stage(a, sst, lane, cnt, pos, pend, mis, true);
         if (NF == 1 && ln.valid) a.part[(size_t)b * V + v] = acc[0];
     } else if (ln.valid) {
@@ -447,7 +563,7 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
 // SM), 64 for the pair count and the CSR fill (4 CTAs; the fill's extra state
 // would otherwise be recomputed in the hot loop), 80 for 16 fluence vectors.
 template <int MODE, int NF>
-constexpr int min_ctas() { return MODE == kCount ? 4 : (MODE == kFill ? 4 : (NF == 1 ? 5 : 3)); }
+constexpr int min_ctas() { return MODE == kCount || MODE == kFill || MODE == kGrad ? 4 : (NF == 1 ? 5 : 3); }
 
 template <int MODE, int NF, bool MERGED, int LAT, int PREC>
 __global__ void __launch_bounds__(kThreads, min_ctas<MODE, NF>()) k_pairs(const DoseArgs a)
@@ -459,6 +575,14 @@ __global__ void __launch_bounds__(kThreads, min_ctas<MODE, NF>()) k_pairs(const 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float4* sstage = smem + (MERGED ? 0 : 2 * P.w_n);
     int2* sst = reinterpret_cast<int2*>(sstage) + warp * (32 * kRingLd);
+    // backward pass: the CTA's gradient bins (4 water tables, 4 density
+    // functions, 2 scales of b) instead of the CSR staging
+    float* sgrad = reinterpret_cast<float*>(sstage);
+    const int ngrad = 4 * P.w_n + 4 * P.f_n + 2;
+    if (MODE == kGrad) {
+        sst = reinterpret_cast<int2*>(sgrad);
+        for (int q = threadIdx.x; q < ngrad; q += blockDim.x) sgrad[q] = 0.f;
+    }
     __shared__ float4 s_row[kWarps][3 * row_max(MODE)];
     // the water tables are read from shared memory unless merged into the depth tables
     if (MODE != kCount && !MERGED)
@@ -477,6 +601,16 @@ __global__ void __launch_bounds__(kThreads, min_ctas<MODE, NF>()) k_pairs(const 
         while (b + 1 < P.n_beams && s_base[b + 1] <= e0) ++b;
         const int32_t vi = __ldg(a.items + e0 + lane);
         process_unit<MODE, NF, MERGED, LAT, PREC>(a, vi, e0, b, sW, sst, s_row[warp], lane);
+    }
+    if (MODE == kGrad) {
+        __syncthreads();
+        for (int q = threadIdx.x; q < ngrad; q += blockDim.x) {
+            const float g = sgrad[q];
+            if (g == 0.f) continue;
+            if (q < 4 * P.w_n) atomicAdd(a.g_water + q, g);
+            else if (q < 4 * P.w_n + 4 * P.f_n) atomicAdd(a.g_dens + (q - 4 * P.w_n), g);
+            else atomicAdd(a.g_corr + (q - 4 * P.w_n - 4 * P.f_n), g);
+        }
     }
 }
 
@@ -746,6 +880,8 @@ DoseArgs make_args(const dc_plan* p)
 size_t smem_bytes(const dc_plan* p, int mode)
 {
     if (mode == kCount) return 0;
+    if (mode == kGrad)   // water tables + gradient bins (always the general tables)
+        return 2 * sizeof(float4) * p->coeffs.w_n + sizeof(float) * (4 * (size_t)p->coeffs.w_n + 4 * p->coeffs.f_n + 2);
     size_t s = p->merged ? 0 : 2 * sizeof(float4) * p->coeffs.w_n;
     if (mode == kFill) s += sizeof(int2) * kWarps * 32 * kRingLd;
     return s;
@@ -919,6 +1055,25 @@ cudaError_t launch_fill(const dc_plan* p, const int64_t* rowptr, int32_t* cols, 
     k_sum_beams<<<grid_for((int64_t)p->V), 256, 0, p->stream>>>(p->d_part, p->n_beams, 1, 1, p->V, dose, p->V);
     count_launches(1);
     return cudaGetLastError();
+}
+
+cudaError_t launch_dose_vjp(const dc_plan* p, const float* fluence, const float* wv, float* g_water, float* g_dens,
+                            float* g_corr)
+{
+    if (smem_bytes(p, kGrad) > 200 * 1024) return cudaErrorInvalidValue;
+    DoseArgs a = make_args(p);
+    a.fluence = fluence;
+    a.nf = 1;
+    a.ldf = p->B;
+    a.wv = wv;
+    a.g_water = g_water;
+    a.g_dens = g_dens;
+    a.g_corr = g_corr;
+    cudaError_t e = cudaMemsetAsync(g_water, 0, sizeof(float) * 4 * (size_t)p->coeffs.w_n, p->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g_dens, 0, sizeof(float) * 4 * (size_t)p->coeffs.f_n, p->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g_corr, 0, sizeof(float) * 2, p->stream);
+    if (e != cudaSuccess) return e;
+    return run_variant<kGrad, 1, false, kIso>(p, a);
 }
 
 cudaError_t launch_scan_counts(const dc_plan* p, const int32_t* counts, int64_t* rowptr,

@@ -77,7 +77,7 @@ EXPORTS = ["dc_last_error", "dc_status_str", "dc_fspb_create", "dc_fspb_destroy"
            "dc_fspb_get_beamlets", "dc_fspb_get_tables", "dc_fspb_set_density",
            "dc_fspb_launch_count", "dc_fspb_autotune", "dc_fspb_spmm_prepare", "dc_fspb_spmm_info",
            "dc_fspb_spmm", "dc_fspb_spmm_noalloc", "dc_fspb_device_status", "dc_fspb_set_surrogate",
-           "dc_fspb_set_lateral_mode", "dc_fspb_set_precision", "dc_fspb_lateral_fallbacks", "dc_fspb_stencils",
+           "dc_fspb_set_lateral_mode", "dc_fspb_set_precision", "dc_fspb_set_tables", "dc_fspb_dose_vjp", "dc_fspb_lateral_fallbacks", "dc_fspb_stencils",
            "dc_mlp_create", "dc_mlp_destroy", "dc_mlp_get_params", "dc_mlp_gradient", "dc_mlp_train",
            "dc_mlp_predict", "dc_fspb_batch_create", "dc_fspb_batch_destroy", "dc_fspb_batch_buffers",
            "dc_fspb_batch_run", "dc_fspb_batch_dose", "dc_fspb_batch_synchronize", "dc_fspb_batch_kernels",
@@ -127,6 +127,8 @@ def load():
     L.dc_fspb_set_surrogate.argtypes = [vp, vp, C.c_float, C.c_float]
     L.dc_fspb_set_lateral_mode.argtypes = [vp, i32]
     L.dc_fspb_set_precision.argtypes = [vp, i32]
+    L.dc_fspb_set_tables.argtypes = [vp, vp, vp]
+    L.dc_fspb_dose_vjp.argtypes = [vp, vp, vp, vp, vp, vp, u32]
     L.dc_fspb_lateral_fallbacks.argtypes = [vp, C.POINTER(i64)]
     L.dc_fspb_stencils.argtypes = [vp, vp, vp, i32, vp, vp, u32]
     L.dc_mlp_create.argtypes = [vp, vp, C.POINTER(vp)]
@@ -325,6 +327,36 @@ def dc_fspb_set_surrogate(plan: Plan, params, rho_lo=0.05, rho_hi=2.0):
 
 def dc_fspb_set_lateral_mode(plan: Plan, mode: int):
     _check(load().dc_fspb_set_lateral_mode(plan.handle, int(mode)))
+
+
+def dc_fspb_set_tables(plan: Plan, water, dens):
+    """New water tables [4, w_n] and density functions [6, f_n] (host float32) for the plan."""
+    w = np.ascontiguousarray(water, np.float32)
+    d = np.ascontiguousarray(dens, np.float32)
+    _check(load().dc_fspb_set_tables(plan.handle, w.ctypes.data_as(C.c_void_p), d.ctypes.data_as(C.c_void_p)))
+
+
+def dc_fspb_dose_vjp(plan: Plan, fluence, weights, w_n: int, f_n: int, out=None):
+    """Gradients of sum_v weights[v] D(v) with respect to the tables:
+    (g_water [4, w_n], g_dens [4, f_n], g_corr [2]).  Host arrays, or CUDA
+    tensors for all (out = the three device tensors then)."""
+    if len(fluence.shape) != 1 or int(fluence.shape[0]) != plan.n_beamlets:
+        raise ValueError("fluence must have n_beamlets entries")
+    if int(np.prod(weights.shape)) != plan.n_voxels:
+        raise ValueError("weights must have n_voxels entries")
+    if out is None:
+        out = (np.empty((4, w_n), np.float32), np.empty((4, f_n), np.float32), np.empty(2, np.float32))
+    pf, f1 = _ptr(fluence)
+    pw, f2 = _ptr(weights)
+    ptrs, flags = [], [f1, f2]
+    for a, n in zip(out, (4 * w_n, 4 * f_n, 2)):
+        if int(np.prod(a.shape)) != n:
+            raise ValueError("gradient buffers must hold 4 w_n, 4 f_n and 2 entries")
+        p, f = _ptr(a)
+        ptrs.append(p)
+        flags.append(f)
+    _check(load().dc_fspb_dose_vjp(plan.handle, pf, pw, *ptrs, _same_kind(*flags)))
+    return out
 
 
 def dc_fspb_set_precision(plan: Plan, precision: int):

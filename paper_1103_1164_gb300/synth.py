@@ -129,19 +129,46 @@ class Plan:
 # Commissioning tables
 # ---------------------------------------------------------------------------
 
+# Parameters of the synthetic beam model's lateral and density-correction
+# tables (the quantities Section 2.1 fits to reference doses), in the order
+# they are drawn.
+MODEL_PARAMS = ("u10", "k1", "u20", "k2", "w20", "w21", "tau", "a1", "a2", "gam", "beta1", "beta2")
+
+
+def model_params(seed: int = COEFF_SEED) -> dict:
+    """The seeded synthetic model: depth-dose shape (beta, mu, horn) and the
+    twelve MODEL_PARAMS."""
+    rng = np.random.default_rng(seed)
+    u = lambda lo, hi: float(rng.uniform(lo, hi))
+    names = ("beta", "mu", "horn") + MODEL_PARAMS
+    ranges = ((2.0, 4.0), (0.04, 0.06), (2.0, 6.0), (3.0, 8.0), (0.0, 0.02), (0.3, 1.0), (0.0, 0.02),
+              (0.03, 0.10), (0.0, 0.08), (2.0, 8.0), (0.5, 1.0), (0.5, 1.0), (0.3, 1.0), (0.0, 0.005),
+              (0.002, 0.01))
+    return {n: u(*r) for n, r in zip(names, ranges)}
+
+
+def model_tables(prm: dict, w_dt: float, w_n: int, f_rho0: float, f_drho: float, f_n: int):
+    """(water [4, w_n], dens [6, f_n]) in float64 from the model's closed forms:
+    u_1^w = u10 / (1 + k1 t), u_2^w = u20 / (1 + k2 t), omega_2^w = w20 +
+    w21 (1 - exp(-t / tau)), omega_1^w = 1 - omega_2^w; f_u1 = rho^a1, f_u2 =
+    rho^a2, f_omega1 = 1, f_omega2 = rho^gam, b_1 = beta1 (1 - rho), b_2 =
+    beta2 (rho - 1)."""
+    tw = w_dt * np.arange(w_n)
+    w2 = prm["w20"] + prm["w21"] * (1.0 - np.exp(-tw / prm["tau"]))
+    water = np.stack([prm["u10"] / (1.0 + prm["k1"] * tw), prm["u20"] / (1.0 + prm["k2"] * tw), 1.0 - w2, w2])
+    r = f_rho0 + f_drho * np.arange(f_n)
+    dens = np.stack([r ** prm["a1"], r ** prm["a2"], np.ones_like(r), r ** prm["gam"],
+                     prm["beta1"] * (1.0 - r), prm["beta2"] * (r - 1.0)])
+    return water, dens
+
+
 def make_commissioning(seed: int = COEFF_SEED, *, roi_radius=5.0, smooth_sigma=0.5,
                        rho_surface=0.02, density_correction=1,
                        a_dt=0.125, a_tmax=80.0, a_dtheta=0.025, a_thmax=0.2,
                        w_dt=0.125, w_tmax=80.0, f_rho0=0.1, f_rho1=2.0,
                        f_drho=0.01) -> Commissioning:
-    rng = np.random.default_rng(seed)
-    u = lambda lo, hi: float(rng.uniform(lo, hi))
-    beta, mu, horn = u(2.0, 4.0), u(0.04, 0.06), u(2.0, 6.0)
-    u10, k1 = u(3.0, 8.0), u(0.0, 0.02)
-    u20, k2 = u(0.3, 1.0), u(0.0, 0.02)
-    w20, w21, tau = u(0.03, 0.10), u(0.0, 0.08), u(2.0, 8.0)
-    a1, a2, gam = u(0.5, 1.0), u(0.5, 1.0), u(0.3, 1.0)
-    beta1, beta2 = u(0.0, 0.005), u(0.002, 0.01)
+    prm = model_params(seed)
+    beta, mu, horn = prm["beta"], prm["mu"], prm["horn"]
 
     nt = int(round(a_tmax / a_dt)) + 1
     nth = int(round(a_thmax / a_dtheta)) + 1
@@ -152,14 +179,8 @@ def make_commissioning(seed: int = COEFF_SEED, *, roi_radius=5.0, smooth_sigma=0
     A = A / depth.max()
 
     nw = int(round(w_tmax / w_dt)) + 1
-    tw = w_dt * np.arange(nw)
-    w2 = w20 + w21 * (1.0 - np.exp(-tw / tau))
-    water = np.stack([u10 / (1.0 + k1 * tw), u20 / (1.0 + k2 * tw), 1.0 - w2, w2])
-
     nf = int(round((f_rho1 - f_rho0) / f_drho)) + 1
-    r = f_rho0 + f_drho * np.arange(nf)
-    dens = np.stack([r ** a1, r ** a2, np.ones_like(r), r ** gam,
-                     beta1 * (1.0 - r), beta2 * (r - 1.0)])
+    water, dens = model_tables(prm, w_dt, nw, f_rho0, f_drho, nf)
     return Commissioning(A.astype(np.float32), a_dt, a_dtheta, water.astype(np.float32),
                          w_dt, dens.astype(np.float32), f_rho0, f_drho, roi_radius,
                          smooth_sigma, rho_surface, density_correction)
