@@ -391,6 +391,14 @@ dc_status dc_mlp_create(const float* params, void* cuda_stream, dc_mlp** out);
 dc_status dc_mlp_destroy(dc_mlp* m);
 /* Current parameters into out [7491] (host).  Synchronises. */
 dc_status dc_mlp_get_params(const dc_mlp* m, float* out);
+/* Checkpoint and resume of training (no counterpart in the paper, which
+ * trains nothing): the parameters, Adam's first and second moments (each
+ * [7491], host float32) and the step count.  A trainer given a saved state
+ * continues exactly as the trainer it was saved from would have.
+ * Synchronise.  Errors: DC_EINVAL (NULL; set_state: a non-finite value, a
+ * negative second moment or step), DC_ECUDA. */
+dc_status dc_mlp_get_state(const dc_mlp* m, float* theta, float* m1, float* m2, int64_t* step);
+dc_status dc_mlp_set_state(dc_mlp* m, const float* theta, const float* m1, const float* m2, int64_t step);
 /*
  * Gradient grad [7491] (host) and loss (host, may be NULL) of
  * L = sum_s sum_o (1 + y_so - T_so)^2 / (3 n) over the n samples X [n][48],

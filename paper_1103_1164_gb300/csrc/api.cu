@@ -4,6 +4,9 @@
 #include <math.h>
 #include <string.h>
 
+#include <stdlib.h>
+
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -31,10 +34,34 @@ static dc_status invalid(const std::string& msg)
     return DC_EINVAL;
 }
 
+cudaError_t dev_malloc_bytes(void** p, size_t bytes)
+{
+    static std::mutex mu;
+    static std::string armed;     // value of DC_FSPB_FAIL_ALLOC_AT the count belongs to
+    static long long count = 0;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        const char* s = getenv("DC_FSPB_FAIL_ALLOC_AT");
+        const std::string now = s ? s : "";
+        if (now != armed) {
+            armed = now;
+            count = 0;
+        }
+        if (!armed.empty()) {
+            const long long at = atoll(armed.c_str());
+            if (++count == at) {
+                *p = nullptr;
+                return cudaErrorMemoryAllocation;
+            }
+        }
+    }
+    return cudaMalloc(p, bytes);
+}
+
 template <typename T>
 static cudaError_t dalloc(T** p, size_t n)
 {
-    return cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T) > 0 ? n * sizeof(T) : 16);
+    return dev_malloc(p, n * sizeof(T) > 0 ? n * sizeof(T) : 16);
 }
 
 }  // namespace dc
@@ -80,6 +107,7 @@ dc::PlanView dc_plan::view() const
     v.w_hi = (float)(coeffs.w_n - 1);
     v.item_rt = (coeffs.density_correction && lateral_mode != DC_LATERAL_ISO) ? 1 : 0;
     v.prec_rt = precision;
+    v.chk = d_chk;
     return v;
 }
 
@@ -92,7 +120,7 @@ static void free_plan(dc_plan* p)
                     p->d_bin, p->d_bounds, p->d_cellof, p->d_hist, p->d_nitems, p->d_bstart, p->d_bscan,
                     p->d_base, p->d_work,
                     p->d_items, p->d_part, p->d_bcount, p->d_sp_fp, p->d_sp_p, p->d_err,
-                    p->d_lfac, p->d_mlp_frag, p->d_mlp_bias, p->d_nfall, p->d_leaf};
+                    p->d_lfac, p->d_mlp_frag, p->d_mlp_bias, p->d_nfall, p->d_leaf, p->d_chk};
     for (void* b : bufs)
         if (b) cudaFree(b);
     p->spmm_free();
@@ -367,7 +395,7 @@ static dc_status create_impl(dc_plan* p, const float* ct, uint32_t flags)
     DC_CUDA(dalloc(&p->d_water, 2 * (size_t)c.w_n));
     DC_CUDA(dalloc(&p->d_dens, 6 * (size_t)c.f_n));
     size_t nscan = (size_t)((V + 4095) / 4096) + 2;
-    DC_CUDA(cudaMalloc(&p->d_scan_tmp, nscan * sizeof(int64_t)));
+    DC_CUDA(dc::dev_malloc(&p->d_scan_tmp, nscan * sizeof(int64_t)));
     p->scan_tmp_bytes = nscan * sizeof(int64_t);
 
     // beam's-eye-view voxel lists and per-beam partial results
@@ -394,6 +422,8 @@ static dc_status create_impl(dc_plan* p, const float* ct, uint32_t flags)
     DC_CUDA(dalloc(&p->d_bcount, nb * V));
     DC_CUDA(dalloc(&p->d_lfac, nb * (V + 32)));
     DC_CUDA(dalloc(&p->d_nfall, 1));
+    DC_CUDA(dalloc(&p->d_chk, 1));
+    DC_CUDA(cudaMemsetAsync(p->d_chk, 0, sizeof(int32_t), p->stream));
     DC_CUDA(cudaMemcpyAsync(p->d_bin, p->bin_host.data(), nb * sizeof(BinGeom), cudaMemcpyHostToDevice,
                             p->stream));
 
@@ -418,6 +448,7 @@ dc_status dc_fspb_create(const float* ct_density, const dc_grid* grid, const dc_
                          const dc_kernel_coeffs* coeffs, uint32_t flags, void* cuda_stream,
                          dc_plan** out)
 {
+    DC_NVTX("dc_fspb_create");
     if (!out) return invalid("dc_fspb_create: out is NULL");
     *out = nullptr;
     dc_status s = check_inputs(ct_density, grid, beams, n_beams, beamlet_x, beamlet_y, coeffs, flags);
@@ -461,6 +492,7 @@ dc_status dc_fspb_create(const float* ct_density, const dc_grid* grid, const dc_
 
 dc_status dc_fspb_set_density(dc_plan* plan, const float* ct_density, uint32_t flags)
 {
+    DC_NVTX("dc_fspb_set_density");
     if (!plan || !ct_density) return invalid("dc_fspb_set_density: NULL argument");
     if (!(flags & DC_DEVICE_PTRS)) {
         for (int64_t v = 0; v < plan->V; ++v)
@@ -498,6 +530,7 @@ static dc_status rebin(dc_plan* p, float tile, float slab)
 dc_status dc_fspb_autotune(dc_plan* plan, const float* fluence, uint32_t flags, float* tile, float* slab,
                            float* best_ms)
 {
+    DC_NVTX("dc_fspb_autotune");
     if (!plan || !fluence) return invalid("dc_fspb_autotune: NULL argument");
     const float* f = fluence;
     dc_status s = ensure_staging(plan, (size_t)plan->B, (size_t)plan->V);
@@ -560,6 +593,7 @@ dc_status dc_fspb_launch_count(uint64_t* n)
 
 dc_status dc_fspb_destroy(dc_plan* plan)
 {
+    DC_NVTX("dc_fspb_destroy");
     if (plan) {
         cudaStreamSynchronize(plan->stream);
         free_plan(plan);
@@ -616,6 +650,7 @@ static dc_status ensure_staging(dc_plan* p, size_t nflu, size_t ndose)
 
 dc_status dc_fspb_dose_batch(dc_plan* plan, const float* fluence, int32_t k, float* dose, uint32_t flags)
 {
+    DC_NVTX("dc_fspb_dose_batch");
     if (!plan || !fluence || !dose) return invalid("dc_fspb_dose: NULL argument");
     if (k < 1 || k > 64) return invalid("dc_fspb_dose_batch: k must be in [1, 64]");
     const size_t nf = (size_t)k * plan->B, nd = (size_t)k * plan->V;
@@ -666,6 +701,7 @@ static dc_status ensure_pattern(dc_plan* p)
 
 dc_status dc_fspb_pair_count(dc_plan* plan, int64_t* pairs)
 {
+    DC_NVTX("dc_fspb_pair_count");
     if (!plan || !pairs) return invalid("dc_fspb_pair_count: NULL argument");
     dc_status s = ensure_pattern(plan);
     if (s != DC_OK) return s;
@@ -700,8 +736,8 @@ static dc_status matrix_impl(dc_plan* plan, int32_t value_dtype, int64_t* rowptr
         plan->d_mcols = nullptr;
         plan->d_mvals = nullptr;
         plan->mstage_bytes = 0;
-        DC_CUDA(cudaMalloc(&plan->d_mcols, need));
-        DC_CUDA(cudaMalloc(&plan->d_mvals, need));
+        DC_CUDA(dc::dev_malloc(&plan->d_mcols, need));
+        DC_CUDA(dc::dev_malloc(&plan->d_mvals, need));
         plan->mstage_bytes = need;
     }
     if (fluence) {
@@ -730,18 +766,21 @@ static dc_status matrix_impl(dc_plan* plan, int32_t value_dtype, int64_t* rowptr
 dc_status dc_fspb_dose_matrix(dc_plan* plan, int32_t value_dtype, int64_t* rowptr, int32_t* cols,
                               void* vals, uint32_t flags)
 {
+    DC_NVTX("dc_fspb_dose_matrix");
     return matrix_impl(plan, value_dtype, rowptr, cols, vals, nullptr, nullptr, flags, "dc_fspb_dose_matrix");
 }
 
 dc_status dc_fspb_dose_and_matrix(dc_plan* plan, const float* fluence, float* dose, int32_t value_dtype,
                                   int64_t* rowptr, int32_t* cols, void* vals, uint32_t flags)
 {
+    DC_NVTX("dc_fspb_dose_and_matrix");
     if (!fluence || !dose) return invalid("dc_fspb_dose_and_matrix: NULL argument");
     return matrix_impl(plan, value_dtype, rowptr, cols, vals, fluence, dose, flags, "dc_fspb_dose_and_matrix");
 }
 
 dc_status dc_fspb_set_tables(dc_plan* plan, const float* water, const float* dens)
 {
+    DC_NVTX("dc_fspb_set_tables");
     if (!plan || !water || !dens) return invalid("dc_fspb_set_tables: NULL argument");
     const dc_kernel_coeffs& c = plan->coeffs;
     for (size_t q = 0; q < 4 * (size_t)c.w_n; ++q)
@@ -757,6 +796,7 @@ dc_status dc_fspb_set_tables(dc_plan* plan, const float* water, const float* den
 dc_status dc_fspb_dose_vjp(dc_plan* plan, const float* fluence, const float* weights, float* g_water, float* g_dens,
                            float* g_corr, uint32_t flags)
 {
+    DC_NVTX("dc_fspb_dose_vjp");
     if (!plan || !fluence || !weights || !g_water || !g_dens || !g_corr)
         return invalid("dc_fspb_dose_vjp: NULL argument");
     if (!plan->coeffs.density_correction || plan->lateral_mode != DC_LATERAL_ISO) {
@@ -797,6 +837,18 @@ dc_status dc_fspb_dose_vjp(dc_plan* plan, const float* fluence, const float* wei
 
 static dc_status check_device_status(dc_plan* p)
 {
+    if (p->d_chk) {
+        int32_t c = 0;
+        DC_CUDA(cudaMemcpyAsync(&c, p->d_chk, sizeof(int32_t), cudaMemcpyDeviceToHost, p->stream));
+        DC_CUDA(cudaStreamSynchronize(p->stream));
+        if (c != 0) {
+            static const char* what[] = {"", "depth-table sample", "A-row sample", "water-table sample",
+                                         "voxel-list work unit", "beamlet record or fluence", "CSR row segment"};
+            set_error(std::string("bounds check: a pair kernel's ") + (c > 0 && c < 7 ? what[c] : "index") +
+                      " index was out of range (DC_BOUNDS_CHECK build)");
+            return DC_ECUDA;
+        }
+    }
     if (!p->d_err) return DC_OK;
     int32_t h = 0;
     DC_CUDA(cudaMemcpyAsync(&h, p->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, p->stream));
@@ -817,6 +869,7 @@ dc_status dc_fspb_device_status(dc_plan* plan)
 
 dc_status dc_fspb_spmm_prepare(dc_plan* plan)
 {
+    DC_NVTX("dc_fspb_spmm_prepare");
     if (!plan) return invalid("dc_fspb_spmm_prepare: NULL argument");
     dc_status s = ensure_pattern(plan);
     if (s != DC_OK) return s;
@@ -828,8 +881,8 @@ dc_status dc_fspb_spmm_prepare(dc_plan* plan)
         plan->d_mcols = nullptr;
         plan->d_mvals = nullptr;
         plan->mstage_bytes = 0;
-        DC_CUDA(cudaMalloc(&plan->d_mcols, need));
-        DC_CUDA(cudaMalloc(&plan->d_mvals, need));
+        DC_CUDA(dc::dev_malloc(&plan->d_mcols, need));
+        DC_CUDA(dc::dev_malloc(&plan->d_mvals, need));
         plan->mstage_bytes = need;
     }
     DC_CUDA(launch_fill(plan, plan->d_rowptr, plan->d_mcols, plan->d_mvals, DC_BF16));
@@ -847,6 +900,7 @@ dc_status dc_fspb_spmm_info(const dc_plan* plan, int64_t* chunks, int64_t* row_b
 
 dc_status dc_fspb_spmm(dc_plan* plan, const float* F, int32_t k, float* Y, uint32_t flags)
 {
+    DC_NVTX("dc_fspb_spmm");
     if (!plan || !F || !Y) return invalid("dc_fspb_spmm: NULL argument");
     if (k < 1 || k > 64) return invalid("dc_fspb_spmm: k must be in [1, 64]");
     if (!plan->sp_ready) return invalid("dc_fspb_spmm: call dc_fspb_spmm_prepare first");
@@ -866,6 +920,7 @@ dc_status dc_fspb_spmm(dc_plan* plan, const float* F, int32_t k, float* Y, uint3
 
 dc_status dc_fspb_spmm_noalloc(dc_plan* plan, const float* F, int32_t k, float* Y)
 {
+    DC_NVTX("dc_fspb_spmm_noalloc");
     if (!plan || !F || !Y) return invalid("dc_fspb_spmm_noalloc: NULL argument");
     if (k < 1 || k > 64) return invalid("dc_fspb_spmm_noalloc: k must be in [1, 64]");
     if (!plan->sp_ready) return invalid("dc_fspb_spmm_noalloc: call dc_fspb_spmm_prepare first");

@@ -207,6 +207,7 @@ extern "C" {
 
 dc_status dc_fspb_batch_create(dc_plan* const* plans, int32_t n, void* cuda_stream, dc_batch** out)
 {
+    DC_NVTX("dc_fspb_batch_create");
     if (!out) return bad("dc_fspb_batch_create: out is NULL");
     *out = nullptr;
     if (!plans) return bad("dc_fspb_batch_create: plans is NULL");
@@ -265,15 +266,15 @@ dc_status dc_fspb_batch_create(dc_plan* const* plans, int32_t n, void* cuda_stre
     for (int j = 0; j < n; ++j) vpre[j + 1] = vpre[j] + plans[bt->order[j]]->V;
     bt->v_total = vpre[n];
     for (int i = 0; i < n; ++i) {
-        e = cudaMalloc(&bt->d_fluence[i], sizeof(float) * (size_t)plans[i]->B);
-        if (e == cudaSuccess) e = cudaMalloc(&bt->d_dose[i], sizeof(float) * (size_t)plans[i]->V);
+        e = dc::dev_malloc(&bt->d_fluence[i], sizeof(float) * (size_t)plans[i]->B);
+        if (e == cudaSuccess) e = dc::dev_malloc(&bt->d_dose[i], sizeof(float) * (size_t)plans[i]->V);
         if (e == cudaSuccess) e = cudaMemset(bt->d_fluence[i], 0, sizeof(float) * (size_t)plans[i]->B);
         if (e != cudaSuccess) return fail(cuda_fail(e, "batch buffers"));
     }
-    e = cudaMalloc(&bt->d_args, sizeof(DoseArgs) * n);
-    if (e == cudaSuccess) e = cudaMalloc(&bt->d_prefix, sizeof(int64_t) * batch_groups() * (n + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&bt->d_vpre, sizeof(int64_t) * (n + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&bt->d_counter, sizeof(unsigned int) * batch_groups());
+    e = dc::dev_malloc(&bt->d_args, sizeof(DoseArgs) * n);
+    if (e == cudaSuccess) e = dc::dev_malloc(&bt->d_prefix, sizeof(int64_t) * batch_groups() * (n + 1));
+    if (e == cudaSuccess) e = dc::dev_malloc(&bt->d_vpre, sizeof(int64_t) * (n + 1));
+    if (e == cudaSuccess) e = dc::dev_malloc(&bt->d_counter, sizeof(unsigned int) * batch_groups());
     if (e == cudaSuccess) e = cudaMemcpy(bt->d_vpre, vpre.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return fail(cuda_fail(e, "batch set-up"));
     // one set of water tables for all plans (the usual case: one beam model)?
@@ -324,6 +325,7 @@ dc_status dc_fspb_batch_buffers(dc_batch* batch, int32_t i, float** fluence, flo
 
 dc_status dc_fspb_batch_run(dc_batch* batch, uint32_t flags)
 {
+    DC_NVTX("dc_fspb_batch_run");
     if (!batch) return bad("dc_fspb_batch_run: NULL batch");
     if (flags & ~(uint32_t)DC_BATCH_DENSITY) return bad("dc_fspb_batch_run: unknown flags");
     return run(batch, flags);
@@ -331,6 +333,7 @@ dc_status dc_fspb_batch_run(dc_batch* batch, uint32_t flags)
 
 dc_status dc_fspb_batch_dose(dc_batch* batch, const float* const* fluence, float* const* dose, uint32_t flags)
 {
+    DC_NVTX("dc_fspb_batch_dose");
     if (!batch || !fluence || !dose) return bad("dc_fspb_batch_dose: NULL argument");
     if (flags & ~(uint32_t)(DC_DEVICE_PTRS | DC_BATCH_DENSITY)) return bad("dc_fspb_batch_dose: unknown flags");
     for (int i = 0; i < batch->n; ++i)
@@ -358,6 +361,7 @@ dc_status dc_fspb_batch_synchronize(dc_batch* batch)
 
 dc_status dc_fspb_batch_autotune(dc_batch* batch, int32_t* variant, float* ms)
 {
+    DC_NVTX("dc_fspb_batch_autotune");
     if (!batch) return bad("dc_fspb_batch_autotune: NULL batch");
     float best_ms = 0.f;
     int best = -1;

@@ -85,6 +85,7 @@ extern "C" {
 
 dc_status dc_fspb_set_surrogate(dc_plan* plan, const float* params, float rho_lo, float rho_hi)
 {
+    DC_NVTX("dc_fspb_set_surrogate");
     if (!plan || !params) return bad("dc_fspb_set_surrogate: NULL argument");
     if (!(rho_lo < rho_hi)) return bad("dc_fspb_set_surrogate: need rho_lo < rho_hi");
     for (int q = 0; q < kMlpParams; ++q)
@@ -92,8 +93,8 @@ dc_status dc_fspb_set_surrogate(dc_plan* plan, const float* params, float rho_lo
     std::vector<uint2> frag;
     std::vector<float> bias;
     mlp_pack(params, frag, bias);
-    if (!plan->d_mlp_frag) DC_CUDA(cudaMalloc(&plan->d_mlp_frag, kMlpFragU2 * sizeof(uint2)));
-    if (!plan->d_mlp_bias) DC_CUDA(cudaMalloc(&plan->d_mlp_bias, kMlpBias * sizeof(float)));
+    if (!plan->d_mlp_frag) DC_CUDA(dc::dev_malloc(&plan->d_mlp_frag, kMlpFragU2 * sizeof(uint2)));
+    if (!plan->d_mlp_bias) DC_CUDA(dc::dev_malloc(&plan->d_mlp_bias, kMlpBias * sizeof(float)));
     DC_CUDA(cudaMemcpyAsync(plan->d_mlp_frag, frag.data(), frag.size() * sizeof(uint2), cudaMemcpyHostToDevice,
                             plan->stream));
     DC_CUDA(cudaMemcpyAsync(plan->d_mlp_bias, bias.data(), bias.size() * sizeof(float), cudaMemcpyHostToDevice,
@@ -110,6 +111,7 @@ dc_status dc_fspb_set_surrogate(dc_plan* plan, const float* params, float rho_lo
 
 dc_status dc_fspb_set_lateral_mode(dc_plan* plan, int32_t mode)
 {
+    DC_NVTX("dc_fspb_set_lateral_mode");
     if (!plan) return bad("dc_fspb_set_lateral_mode: NULL argument");
     if (mode != DC_LATERAL_ISO && mode != DC_LATERAL_AXIS && mode != DC_LATERAL_MLP)
         return bad("dc_fspb_set_lateral_mode: unknown mode");
@@ -145,6 +147,7 @@ dc_status dc_fspb_lateral_fallbacks(dc_plan* plan, int64_t* n)
 dc_status dc_fspb_stencils(dc_plan* plan, const int32_t* vox, const int32_t* beam, int32_t n, float* X, float* T,
                            uint32_t flags)
 {
+    DC_NVTX("dc_fspb_stencils");
     if (!plan || !vox || !beam || !X || !T) return bad("dc_fspb_stencils: NULL argument");
     if (n < 0) return bad("dc_fspb_stencils: n < 0");
     if (n == 0) return DC_OK;
@@ -157,10 +160,10 @@ dc_status dc_fspb_stencils(dc_plan* plan, const int32_t* vox, const int32_t* bea
             return bad("dc_fspb_stencils: voxel or beam index out of range (sample " + std::to_string(s) + ")");
     int32_t *dv = nullptr, *db = nullptr;
     float *dX = nullptr, *dT = nullptr;
-    cudaError_t e = cudaMalloc(&dv, n * sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMalloc(&db, n * sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMalloc(&dX, (size_t)n * 48 * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&dT, (size_t)n * 3 * sizeof(float));
+    cudaError_t e = dc::dev_malloc(&dv, n * sizeof(int32_t));
+    if (e == cudaSuccess) e = dc::dev_malloc(&db, n * sizeof(int32_t));
+    if (e == cudaSuccess) e = dc::dev_malloc(&dX, (size_t)n * 48 * sizeof(float));
+    if (e == cudaSuccess) e = dc::dev_malloc(&dT, (size_t)n * 3 * sizeof(float));
     if (e == cudaSuccess) e = cudaMemcpyAsync(dv, vox, n * sizeof(int32_t), cudaMemcpyHostToDevice, plan->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(db, beam, n * sizeof(int32_t), cudaMemcpyHostToDevice, plan->stream);
     if (e == cudaSuccess) e = launch_stencils(plan, dv, db, n, dX, dT);
@@ -183,12 +186,12 @@ dc_status dc_mlp_create(const float* params, void* cuda_stream, dc_mlp** out)
     dc_mlp* m = new (std::nothrow) dc_mlp();
     if (!m) return DC_ENOMEM;
     m->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
-    cudaError_t e = cudaMalloc(&m->theta, kMlpParams * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&m->m1, kMlpParams * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&m->m2, kMlpParams * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&m->grad, kMlpParams * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&m->partial, (size_t)kGradCtas * kMlpParams * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&m->loss_part, kGradCtas * sizeof(float));
+    cudaError_t e = dc::dev_malloc(&m->theta, kMlpParams * sizeof(float));
+    if (e == cudaSuccess) e = dc::dev_malloc(&m->m1, kMlpParams * sizeof(float));
+    if (e == cudaSuccess) e = dc::dev_malloc(&m->m2, kMlpParams * sizeof(float));
+    if (e == cudaSuccess) e = dc::dev_malloc(&m->grad, kMlpParams * sizeof(float));
+    if (e == cudaSuccess) e = dc::dev_malloc(&m->partial, (size_t)kGradCtas * kMlpParams * sizeof(float));
+    if (e == cudaSuccess) e = dc::dev_malloc(&m->loss_part, kGradCtas * sizeof(float));
     if (e == cudaSuccess) e = cudaMemcpyAsync(m->theta, params, kMlpParams * sizeof(float), cudaMemcpyHostToDevice, m->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(m->m1, 0, kMlpParams * sizeof(float), m->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(m->m2, 0, kMlpParams * sizeof(float), m->stream);
@@ -218,6 +221,33 @@ dc_status dc_mlp_get_params(const dc_mlp* m, float* out)
     return DC_OK;
 }
 
+dc_status dc_mlp_get_state(const dc_mlp* m, float* theta, float* m1, float* m2, int64_t* step)
+{
+    if (!m || !theta || !m1 || !m2 || !step) return bad("dc_mlp_get_state: NULL argument");
+    DC_CUDA(cudaMemcpyAsync(theta, m->theta, kMlpParams * sizeof(float), cudaMemcpyDeviceToHost, m->stream));
+    DC_CUDA(cudaMemcpyAsync(m1, m->m1, kMlpParams * sizeof(float), cudaMemcpyDeviceToHost, m->stream));
+    DC_CUDA(cudaMemcpyAsync(m2, m->m2, kMlpParams * sizeof(float), cudaMemcpyDeviceToHost, m->stream));
+    DC_CUDA(cudaStreamSynchronize(m->stream));
+    *step = m->step;
+    return DC_OK;
+}
+
+dc_status dc_mlp_set_state(dc_mlp* m, const float* theta, const float* m1, const float* m2, int64_t step)
+{
+    if (!m || !theta || !m1 || !m2) return bad("dc_mlp_set_state: NULL argument");
+    if (step < 0) return bad("dc_mlp_set_state: step < 0");
+    for (int q = 0; q < kMlpParams; ++q)
+        if (!isfinite(theta[q]) || !isfinite(m1[q]) || !(m2[q] >= 0.f) || !isfinite(m2[q]))
+            return bad("dc_mlp_set_state: non-finite parameter or moment, or a negative second moment");
+    DC_CUDA(cudaStreamSynchronize(m->stream));
+    DC_CUDA(cudaMemcpyAsync(m->theta, theta, kMlpParams * sizeof(float), cudaMemcpyHostToDevice, m->stream));
+    DC_CUDA(cudaMemcpyAsync(m->m1, m1, kMlpParams * sizeof(float), cudaMemcpyHostToDevice, m->stream));
+    DC_CUDA(cudaMemcpyAsync(m->m2, m2, kMlpParams * sizeof(float), cudaMemcpyHostToDevice, m->stream));
+    DC_CUDA(cudaStreamSynchronize(m->stream));
+    m->step = (int)step;
+    return DC_OK;
+}
+
 // Device copies of the samples (host inputs are uploaded into the trainer's buffers).
 static dc_status stage(dc_mlp* m, const float*& X, const float*& T, int n, uint32_t flags)
 {
@@ -227,8 +257,8 @@ static dc_status stage(dc_mlp* m, const float*& X, const float*& T, int n, uint3
         if (m->dT) cudaFree(m->dT);
         m->dX = m->dT = nullptr;
         m->cap = 0;
-        DC_CUDA(cudaMalloc(&m->dX, (size_t)n * 48 * sizeof(float)));
-        DC_CUDA(cudaMalloc(&m->dT, (size_t)n * 3 * sizeof(float)));
+        DC_CUDA(dc::dev_malloc(&m->dX, (size_t)n * 48 * sizeof(float)));
+        DC_CUDA(dc::dev_malloc(&m->dT, (size_t)n * 3 * sizeof(float)));
         m->cap = n;
     }
     DC_CUDA(cudaMemcpyAsync(m->dX, X, (size_t)n * 48 * sizeof(float), cudaMemcpyHostToDevice, m->stream));
@@ -258,6 +288,7 @@ static dc_status grad_pass(dc_mlp* m, const float* X, const float* T, int n, flo
 
 dc_status dc_mlp_gradient(dc_mlp* m, const float* X, const float* T, int32_t n, float* grad, float* loss, uint32_t flags)
 {
+    DC_NVTX("dc_mlp_gradient");
     if (!m || !X || !T || !grad) return bad("dc_mlp_gradient: NULL argument");
     if (n < 1) return bad("dc_mlp_gradient: n < 1");
     dc_status s = stage(m, X, T, n, flags);
@@ -272,6 +303,7 @@ dc_status dc_mlp_gradient(dc_mlp* m, const float* X, const float* T, int32_t n, 
 dc_status dc_mlp_train(dc_mlp* m, const float* X, const float* T, int32_t n, int32_t batch, int32_t epochs, float lr,
                        float* loss, uint32_t flags)
 {
+    DC_NVTX("dc_mlp_train");
     if (!m || !X || !T) return bad("dc_mlp_train: NULL argument");
     if (n < 1 || batch < 1 || epochs < 0 || !(lr > 0)) return bad("dc_mlp_train: bad n, batch, epochs or lr");
     dc_status s = stage(m, X, T, n, flags);
@@ -294,6 +326,7 @@ dc_status dc_mlp_train(dc_mlp* m, const float* X, const float* T, int32_t n, int
 
 dc_status dc_mlp_predict(const float* params, const float* X, int32_t n, float* Y, uint32_t flags, void* cuda_stream)
 {
+    DC_NVTX("dc_mlp_predict");
     if (!params || !X || !Y) return bad("dc_mlp_predict: NULL argument");
     if (n < 1) return bad("dc_mlp_predict: n < 1");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
@@ -303,13 +336,13 @@ dc_status dc_mlp_predict(const float* params, const float* X, int32_t n, float* 
     uint2* df = nullptr;
     float *db = nullptr, *dX = nullptr, *dY = nullptr;
     const bool dev = flags & DC_DEVICE_PTRS;
-    cudaError_t e = cudaMalloc(&df, frag.size() * sizeof(uint2));
-    if (e == cudaSuccess) e = cudaMalloc(&db, bias.size() * sizeof(float));
+    cudaError_t e = dc::dev_malloc(&df, frag.size() * sizeof(uint2));
+    if (e == cudaSuccess) e = dc::dev_malloc(&db, bias.size() * sizeof(float));
     if (e == cudaSuccess) e = cudaMemcpyAsync(df, frag.data(), frag.size() * sizeof(uint2), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(db, bias.data(), bias.size() * sizeof(float), cudaMemcpyHostToDevice, st);
     if (!dev) {
-        if (e == cudaSuccess) e = cudaMalloc(&dX, (size_t)n * 48 * sizeof(float));
-        if (e == cudaSuccess) e = cudaMalloc(&dY, (size_t)n * 3 * sizeof(float));
+        if (e == cudaSuccess) e = dc::dev_malloc(&dX, (size_t)n * 48 * sizeof(float));
+        if (e == cudaSuccess) e = dc::dev_malloc(&dY, (size_t)n * 3 * sizeof(float));
         if (e == cudaSuccess) e = cudaMemcpyAsync(dX, X, (size_t)n * 48 * sizeof(float), cudaMemcpyHostToDevice, st);
     }
     if (e == cudaSuccess) e = launch_mlp_predict_bf16(st, dev ? X : dX, n, df, db, dev ? Y : dY);

@@ -9,6 +9,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "dc_fspb.h"
 #include "dc_views.cuh"
 
@@ -99,6 +101,7 @@ struct dc_plan {
     float* d_sp_p = nullptr;
     size_t sp_p_cap = 0;
     int32_t* d_err = nullptr;        // device status word of bounded waits
+    int32_t* d_chk = nullptr;        // status word of the DC_BOUNDS_CHECK build
     void spmm_free()
     {
         void* bufs[] = {d_sp_rbfirst, d_sp_first, d_sp_nchunk, d_sp_off, d_sp_kb, d_sp_tiles, d_sp_inv, d_sp_zero};
@@ -136,6 +139,28 @@ namespace dc {
 
 // number of kernels launched by the library (dc_fspb_launch_count)
 void count_launches(int n);
+
+// An NVTX range around each C-ABI call, named after the call: a profiler's
+// timeline then groups the kernels by the call that launched them (NVTX costs
+// a pointer test when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define DC_NVTX(name) dc::NvtxRange dc_nvtx_range_(name)
+
+// Every device allocation of the library goes through dev_malloc.  Test hook
+// of the out-of-memory paths: with DC_FSPB_FAIL_ALLOC_AT=N in the environment,
+// the N-th allocation counted since the variable last changed value fails
+// with cudaErrorMemoryAllocation (nothing is allocated).
+cudaError_t dev_malloc_bytes(void** p, size_t bytes);
+template <typename T>
+inline cudaError_t dev_malloc(T** p, size_t bytes)
+{
+    return dev_malloc_bytes(reinterpret_cast<void**>(p), bytes);
+}
 
 // error plumbing -------------------------------------------------------------
 void set_error(const std::string& msg);

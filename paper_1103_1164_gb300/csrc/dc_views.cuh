@@ -83,7 +83,24 @@ struct PlanView {
     int item_rt;                  // lfac is in use
     int prec_rt;                  // direct-dose arithmetic (DC_PRECISION_*)
     float a_hi, w_hi;             // a_nt - 1, w_n - 1 as floats (clamps of the table coordinates)
+    int32_t* chk;                 // status word of the DC_BOUNDS_CHECK build (first violated guard)
 };
+
+// DC_BOUNDS_CHECK builds: every index the pair kernels use to read a table,
+// a beamlet record, a voxel list or the fluence is checked against its
+// extent; a violation records the guard's code in the plan's status word
+// (first one wins) and reads element 0 instead.  Other builds: no check.
+#if DC_BOUNDS_CHECK
+__device__ __forceinline__ uint32_t dc_guard(int32_t* chk, uint32_t idx, uint32_t n, int code)
+{
+    if (idx < n) return idx;
+    atomicCAS(chk, 0, code);
+    return 0u;
+}
+#define DC_GUARD(P, idx, n, code) dc::dc_guard((P).chk, (uint32_t)(idx), (uint32_t)(n), (code))
+#else
+#define DC_GUARD(P, idx, n, code) (idx)
+#endif
 
 // Arguments of the pair kernels (k_dose.cu) for one plan.
 struct DoseArgs {

@@ -172,7 +172,7 @@ __device__ __forceinline__ float pair_eval(const PlanView& P, const Lane& ln, co
     const uint32_t kb = grid_bits_mul(t, P.inv_d, fr);
     float teq, O1, O2, u1w, u2w;
     if (MERGED) {
-        const float4* tb = P.tabm + (i * (3u * (uint32_t)P.Kmax) + 3u * (kb - kGridBits));
+        const float4* tb = P.tabm + (i * (3u * (uint32_t)P.Kmax) + 3u * DC_GUARD(P, kb - kGridBits, P.Kmax, 1));
         const float4 e0 = __ldg(tb), e1 = __ldg(tb + 1), e2 = __ldg(tb + 2);
         teq = fmaf(fr, e0.y, e0.x);
         const float2 frr = make_float2(fr, fr);
@@ -183,13 +183,13 @@ __device__ __forceinline__ float pair_eval(const PlanView& P, const Lane& ln, co
         u1w = U.x;
         u2w = U.y;
     } else {
-        const float4* tb = P.tab + (i * (2u * (uint32_t)P.Kmax) + 2u * (kb - kGridBits));
+        const float4* tb = P.tab + (i * (2u * (uint32_t)P.Kmax) + 2u * DC_GUARD(P, kb - kGridBits, P.Kmax, 1));
         const float4 e0 = __ldg(tb), e1 = __ldg(tb + 1);
         teq = fmaf(fr, e0.y, e0.x);
         const float c1 = fmaf(fr, e0.w, e0.z);
         const float c2 = fmaf(fr, e1.y, e1.x);
         float fw;
-        const uint32_t jw = grid_bits(fminf(t * P.inv_wdt, P.w_hi), fw) - kGridBits;
+        const uint32_t jw = DC_GUARD(P, grid_bits(fminf(t * P.inv_wdt, P.w_hi), fw) - kGridBits, P.w_n, 3);
         const float4 w0 = sW[2 * jw], w1 = sW[2 * jw + 1];
         u1w = fmaf(fw, w0.y, w0.x);
         u2w = fmaf(fw, w0.w, w0.z);
@@ -202,7 +202,7 @@ __device__ __forceinline__ float pair_eval(const PlanView& P, const Lane& ln, co
     // t_eq >= 0 (an integral of rho >= 0, interpolated with non-negative
     // slopes), so only the upper end of the A row needs a clamp
     const uint32_t jb = grid_bits(fminf(teq * P.inv_adt, P.a_hi), fa);
-    const float2 ar = __ldg(P.arow + (i * (uint32_t)P.a_nt + (jb - kGridBits)));
+    const float2 ar = __ldg(P.arow + (i * (uint32_t)P.a_nt + DC_GUARD(P, jb - kGridBits, P.a_nt, 2)));
     const float Av = fmaf(fa, ar.y, ar.x);
 
     // density correction (step 11), in pairs: -(k1, k2) with k = log2(e) f_u u^w,
@@ -251,19 +251,19 @@ __device__ __forceinline__ void pair_grad(const PlanView& P, const float4 facv, 
     const float x = pt.pq.x * s, y = pt.pq.y * s;
     float fr;
     const uint32_t kb = grid_bits_mul(t, P.inv_d, fr);
-    const float4* tb = P.tab + (i * (2u * (uint32_t)P.Kmax) + 2u * (kb - kGridBits));
+    const float4* tb = P.tab + (i * (2u * (uint32_t)P.Kmax) + 2u * DC_GUARD(P, kb - kGridBits, P.Kmax, 1));
     const float4 e0 = __ldg(tb), e1 = __ldg(tb + 1);
     const float teq = fmaf(fr, e0.y, e0.x);
     const float c1 = fmaf(fr, e0.w, e0.z);
     const float c2 = fmaf(fr, e1.y, e1.x);
     float fw;
-    const int jw = (int)(grid_bits(fminf(t * P.inv_wdt, P.w_hi), fw) - kGridBits);
+    const int jw = (int)DC_GUARD(P, grid_bits(fminf(t * P.inv_wdt, P.w_hi), fw) - kGridBits, P.w_n, 3);
     const float4 w0 = sW[2 * jw], w1 = sW[2 * jw + 1];
     const float u1w = fmaf(fw, w0.y, w0.x), u2w = fmaf(fw, w0.w, w0.z);
     const float o1w = fmaf(fw, w1.y, w1.x), o2w = fmaf(fw, w1.w, w1.z);
     float fa;
     const uint32_t jb = grid_bits(fminf(teq * P.inv_adt, P.a_hi), fa);
-    const float2 ar = __ldg(P.arow + (i * (uint32_t)P.a_nt + (jb - kGridBits)));
+    const float2 ar = __ldg(P.arow + (i * (uint32_t)P.a_nt + DC_GUARD(P, jb - kGridBits, P.a_nt, 2)));
     const float Av = fmaf(fa, ar.y, ar.x);
 
     const float u1 = facv.x * u1w, u2 = facv.y * u2w;
@@ -328,6 +328,8 @@ __device__ __forceinline__ void store_entry(int32_t* cols, VT* vals, int64_t g, 
 template <typename VT>
 __device__ __forceinline__ void flush_runs(int32_t* cols, VT* vals, const int2* st, int lane, int nw, int64_t pos)
 {
+    // (a lane's run never passes the end of its row segment: flush_stage cuts
+    // nw at pend - pos, and the DC_BOUNDS_CHECK build verifies it there)
     const int q = lane >> 3, j = lane & 7;
 #pragma unroll 2
     for (int o4 = 0; o4 < 32; o4 += 4) {
@@ -371,6 +373,10 @@ __device__ __forceinline__ void flush_stage(const DoseArgs& a, const int2* st, i
         nw = end > pos ? (int)(end - pos) : 0;
     }
     nw = (int)min((int64_t)nw, pend - pos);
+#if DC_BOUNDS_CHECK
+    if (nw > 0 && (pos < a.rowptr[0] || pos + nw > a.rowptr[(int64_t)a.P.nx * a.P.ny * a.P.nz]))
+        atomicCAS(a.P.chk, 0, 6);
+#endif
     __syncwarp();
     if (a.value_dtype == DC_BF16)
         flush_runs(a.cols, reinterpret_cast<__nv_bfloat16*>(a.vals), st, lane, nw, pos);
@@ -410,7 +416,7 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
         ln.cw2 = fac.w;
         if (LAT == kItem) {
             // (log2(e) f_u2 along x, along y, f_w1, f_w2) of this (voxel, beam)
-            const float4 lf = __ldg(P.lfac + e0 + lane);
+            const float4 lf = __ldg(P.lfac + e0 + lane);   // e0 + lane: guarded with the list entry (code 4)
             ln.cu2x = lf.x;
             ln.cu2y = lf.y;
             ln.cw1 = lf.z;
@@ -471,13 +477,14 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
         const int m1 = min(wmhi, m0 + row_max(MODE) - 1);
         __syncwarp();
         if (m0 + lane <= m1) {
-            const float4* src = reinterpret_cast<const float4*>(P.bl) + 4u * (row + (uint32_t)(m0 + lane));
+            const uint32_t ib = DC_GUARD(P, row + (uint32_t)(m0 + lane), P.B, 5);
+            const float4* src = reinterpret_cast<const float4*>(P.bl) + 4u * ib;
             srow[3 * lane] = __ldg(src);
             srow[3 * lane + 1] = __ldg(src + 1);
             float4 q2 = __ldg(src + 2);
             // one fluence vector: the staged record carries f_i in place of the
             // theta weight (which only the table set-up uses)
-            if (MODE != kCount && NF == 1) q2.w = __ldg(a.fluence + row + (uint32_t)(m0 + lane));
+            if (MODE != kCount && NF == 1) q2.w = __ldg(a.fluence + ib);
             srow[3 * lane + 2] = q2;
         }
         __syncwarp();
@@ -507,7 +514,8 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
                     } else {
 #pragma unroll
                         for (int q = 0; q < NF; ++q)
-                            if (q < a.nf) acc[q] = fmaf(__ldg(a.fluence + (q * (uint32_t)a.ldf + i)), D, acc[q]);
+                            if (q < a.nf)
+                                acc[q] = fmaf(__ldg(a.fluence + (q * (uint32_t)a.ldf + DC_GUARD(P, i, P.B, 5))), D, acc[q]);
                     }
                 }
             } else {
@@ -596,7 +604,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<MODE, NF>()) k_pairs(const 
         if (lane == 0) w = atomicAdd(a.work + 1, 1);
         w = __shfl_sync(0xffffffffu, w, 0);
         if (w >= total) break;
-        const int64_t e0 = (int64_t)w * 32;
+        const int64_t e0 = (int64_t)DC_GUARD(P, w, (s_base[P.n_beams] + 31) / 32, 4) * 32;
         int b = 0;
         while (b + 1 < P.n_beams && s_base[b + 1] <= e0) ++b;
         const int32_t vi = __ldg(a.items + e0 + lane);
@@ -682,7 +690,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_pairs_batch(const __grid_con
         int q = 0;
         while (q + 1 < n && s_pre[q + 1] <= (int64_t)w) ++q;
         const DoseArgs& a = bp.a[g.j[q]];
-        const int64_t e0 = ((int64_t)w - s_pre[q]) * 32;
+        const int64_t e0 = ((int64_t)w - s_pre[q]) * 32;   // w < s_pre[n]: inside plan q's units
         const int nb = a.P.n_beams;
         int b = 0;
         while (b + 1 < nb && __ldg(a.base + b + 1) <= e0) ++b;

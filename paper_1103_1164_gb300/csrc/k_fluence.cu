@@ -125,6 +125,7 @@ using namespace dc;
 extern "C" dc_status dc_fluence_from_leaves(dc_plan* plan, const dc_leaf_sequence* seqs, float* fluence,
                                             uint32_t flags)
 {
+    DC_NVTX("dc_fluence_from_leaves");
     if (!plan || !seqs || !fluence) return leaf_invalid("NULL argument");
     const int nb = plan->n_beams;
     LeafArgs A{};
@@ -189,7 +190,7 @@ extern "C" dc_status dc_fluence_from_leaves(dc_plan* plan, const dc_leaf_sequenc
         if (plan->d_leaf) cudaFree(plan->d_leaf);
         plan->d_leaf = nullptr;
         plan->leaf_cap = 0;
-        DC_CUDA(cudaMalloc(&plan->d_leaf, need * sizeof(float)));
+        DC_CUDA(dc::dev_malloc(&plan->d_leaf, need * sizeof(float)));
         plan->leaf_cap = need;
     }
     // pageable source: the call returns once the data is staged for the copy

@@ -184,7 +184,7 @@ struct GammaBuffers {
     cudaError_t get(T** p, size_t n)
     {
         void* q = nullptr;
-        const cudaError_t e = cudaMalloc(&q, n * sizeof(T) > 0 ? n * sizeof(T) : 16);
+        const cudaError_t e = dc::dev_malloc(&q, n * sizeof(T) > 0 ? n * sizeof(T) : 16);
         if (e == cudaSuccess) ptrs.push_back(q);
         *p = reinterpret_cast<T*>(q);
         return e;
@@ -200,6 +200,7 @@ extern "C" dc_status dc_gamma_index(const float* ref, const float* eval, const d
                                     float dta_cm, float search_cm, float* gamma, dc_gamma_stats* stats,
                                     void* cuda_stream, uint32_t flags)
 {
+    DC_NVTX("dc_gamma_index");
     if (!ref || !eval || !grid) {
         set_error("dc_gamma_index: NULL argument");
         return DC_EINVAL;

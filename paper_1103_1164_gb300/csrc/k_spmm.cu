@@ -711,11 +711,11 @@ dc_status spmm_prepare(dc_plan* p, const int64_t* rowptr, const int32_t* cols, c
     beam[nb] = make_int4(p->B, 0, 0, cols_total);
     p->spmm_free();
     p->sp_n_rb = n_rb;
-    DC_CUDA(cudaMalloc(&p->d_sp_rbfirst, (nb + 1) * sizeof(int32_t)));
-    DC_CUDA(cudaMalloc(&p->d_sp_first, (nb + 1) * sizeof(int4)));
+    DC_CUDA(dc::dev_malloc(&p->d_sp_rbfirst, (nb + 1) * sizeof(int32_t)));
+    DC_CUDA(dc::dev_malloc(&p->d_sp_first, (nb + 1) * sizeof(int4)));
     p->sp_cols = cols_total;
-    DC_CUDA(cudaMalloc(&p->d_sp_nchunk, (size_t)(n_rb + 1) * sizeof(int32_t)));
-    DC_CUDA(cudaMalloc(&p->d_sp_off, (size_t)(n_rb + 1) * sizeof(int64_t)));
+    DC_CUDA(dc::dev_malloc(&p->d_sp_nchunk, (size_t)(n_rb + 1) * sizeof(int32_t)));
+    DC_CUDA(dc::dev_malloc(&p->d_sp_off, (size_t)(n_rb + 1) * sizeof(int64_t)));
     DC_CUDA(cudaMemcpyAsync(p->d_sp_rbfirst, rb_first.data(), (nb + 1) * sizeof(int32_t), cudaMemcpyHostToDevice,
                             p->stream));
     DC_CUDA(cudaMemcpyAsync(p->d_sp_first, beam.data(), (nb + 1) * sizeof(int4), cudaMemcpyHostToDevice,
@@ -746,8 +746,8 @@ dc_status spmm_prepare(dc_plan* p, const int64_t* rowptr, const int32_t* cols, c
     p->sp_chunks = off[n_rb];
     DC_CUDA(cudaMemcpyAsync(p->d_sp_off, off.data(), (n_rb + 1) * sizeof(int64_t), cudaMemcpyHostToDevice,
                             p->stream));
-    DC_CUDA(cudaMalloc(&p->d_sp_kb, (size_t)(p->sp_chunks + 1) * sizeof(int32_t)));
-    DC_CUDA(cudaMalloc(&p->d_sp_tiles, (size_t)(p->sp_chunks + 1) * kTileA));
+    DC_CUDA(dc::dev_malloc(&p->d_sp_kb, (size_t)(p->sp_chunks + 1) * sizeof(int32_t)));
+    DC_CUDA(dc::dev_malloc(&p->d_sp_tiles, (size_t)(p->sp_chunks + 1) * kTileA));
     ta.chunk_off = p->d_sp_off;
     ta.chunk_kb = p->d_sp_kb;
     ta.tiles = reinterpret_cast<uint16_t*>(p->d_sp_tiles);
@@ -759,7 +759,7 @@ dc_status spmm_prepare(dc_plan* p, const int64_t* rowptr, const int32_t* cols, c
     {
         // inverse of the beam lists (the reduction of several beams' partial
         // rows reads it; one-beam plans keep only the voxels in no list)
-        DC_CUDA(cudaMalloc(&p->d_sp_inv, (size_t)nb * p->V * sizeof(int32_t)));
+        DC_CUDA(dc::dev_malloc(&p->d_sp_inv, (size_t)nb * p->V * sizeof(int32_t)));
         DC_CUDA(cudaMemsetAsync(p->d_sp_inv, 0xff, (size_t)nb * p->V * sizeof(int32_t), p->stream));
         int maxn = 0;
         for (int b = 0; b < nb; ++b) maxn = std::max(maxn, n_items[b]);
@@ -771,7 +771,7 @@ dc_status spmm_prepare(dc_plan* p, const int64_t* rowptr, const int32_t* cols, c
         for (int b = 0; b < nb; ++b) items_total += ((int64_t)n_items[b] + 31) / 32 * 32;
         p->sp_items_total = items_total;
         if (nb == 1) {
-            DC_CUDA(cudaMalloc(&p->d_sp_zero, (size_t)p->V * sizeof(int32_t) + sizeof(unsigned long long)));
+            DC_CUDA(dc::dev_malloc(&p->d_sp_zero, (size_t)p->V * sizeof(int32_t) + sizeof(unsigned long long)));
             unsigned long long* cnt = reinterpret_cast<unsigned long long*>(p->d_sp_zero + p->V);
             DC_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), p->stream));
             k_unlisted<<<gsize(p->V), 256, 0, p->stream>>>(p->d_sp_inv, p->V, p->d_sp_zero, cnt);
@@ -785,7 +785,7 @@ dc_status spmm_prepare(dc_plan* p, const int64_t* rowptr, const int32_t* cols, c
             p->d_sp_inv = nullptr;
         }
     }
-    if (!p->d_err) DC_CUDA(cudaMalloc(&p->d_err, sizeof(int32_t)));
+    if (!p->d_err) DC_CUDA(dc::dev_malloc(&p->d_err, sizeof(int32_t)));
     DC_CUDA(cudaStreamSynchronize(p->stream));
     p->sp_ready = true;
     return DC_OK;
@@ -810,7 +810,7 @@ cudaError_t spmm_run(dc_plan* p, const float* F, int k, float* Y)
         if (p->d_sp_fp) cudaFree(p->d_sp_fp);
         p->d_sp_fp = nullptr;
         p->sp_fp_cap = 0;
-        e = cudaMalloc(&p->d_sp_fp, (size_t)nkb * 8 * kN * sizeof(__nv_bfloat16));
+        e = dc::dev_malloc(&p->d_sp_fp, (size_t)nkb * 8 * kN * sizeof(__nv_bfloat16));
         if (e != cudaSuccess) return e;
         p->sp_fp_cap = (size_t)nkb * 8 * kN;
     }
@@ -821,7 +821,7 @@ cudaError_t spmm_run(dc_plan* p, const float* F, int k, float* Y)
             if (p->d_sp_p) cudaFree(p->d_sp_p);
             p->d_sp_p = nullptr;
             p->sp_p_cap = 0;
-            e = cudaMalloc(&p->d_sp_p, need * sizeof(float));
+            e = dc::dev_malloc(&p->d_sp_p, need * sizeof(float));
             if (e != cudaSuccess) return e;
             p->sp_p_cap = need;
         }

@@ -78,14 +78,16 @@ EXPORTS = ["dc_last_error", "dc_status_str", "dc_fspb_create", "dc_fspb_destroy"
            "dc_fspb_launch_count", "dc_fspb_autotune", "dc_fspb_spmm_prepare", "dc_fspb_spmm_info",
            "dc_fspb_spmm", "dc_fspb_spmm_noalloc", "dc_fspb_device_status", "dc_fspb_set_surrogate",
            "dc_fspb_set_lateral_mode", "dc_fspb_set_precision", "dc_fspb_set_tables", "dc_fspb_dose_vjp", "dc_fspb_lateral_fallbacks", "dc_fspb_stencils",
-           "dc_mlp_create", "dc_mlp_destroy", "dc_mlp_get_params", "dc_mlp_gradient", "dc_mlp_train",
+           "dc_mlp_create", "dc_mlp_destroy", "dc_mlp_get_params", "dc_mlp_get_state", "dc_mlp_set_state", "dc_mlp_gradient", "dc_mlp_train",
            "dc_mlp_predict", "dc_fspb_batch_create", "dc_fspb_batch_destroy", "dc_fspb_batch_buffers",
            "dc_fspb_batch_run", "dc_fspb_batch_dose", "dc_fspb_batch_synchronize", "dc_fspb_batch_kernels",
            "dc_fspb_batch_autotune", "dc_gamma_index", "dc_fluence_from_leaves"]
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The library this binding loads: the bounds-checked build when
+    DC_FSPB_CHECKED=1 is set in the environment (read at the first load)."""
+    return _build.LIB_CHECKED if os.environ.get("DC_FSPB_CHECKED") == "1" else _build.LIB
 
 
 def load():
@@ -128,6 +130,8 @@ def load():
     L.dc_fspb_set_lateral_mode.argtypes = [vp, i32]
     L.dc_fspb_set_precision.argtypes = [vp, i32]
     L.dc_fspb_set_tables.argtypes = [vp, vp, vp]
+    L.dc_mlp_get_state.argtypes = [vp, vp, vp, vp, C.POINTER(i64)]
+    L.dc_mlp_set_state.argtypes = [vp, vp, vp, vp, i64]
     L.dc_fspb_dose_vjp.argtypes = [vp, vp, vp, vp, vp, vp, u32]
     L.dc_fspb_lateral_fallbacks.argtypes = [vp, C.POINTER(i64)]
     L.dc_fspb_stencils.argtypes = [vp, vp, vp, i32, vp, vp, u32]
@@ -402,6 +406,22 @@ class Mlp:
         out = np.empty(MLP_PARAMS, np.float32)
         _check(load().dc_mlp_get_params(self.handle, out.ctypes.data_as(C.c_void_p)))
         return out
+
+    def state(self):
+        """(theta, m1, m2, step): everything training continues from."""
+        th, m1, m2 = (np.empty(MLP_PARAMS, np.float32) for _ in range(3))
+        st = C.c_int64()
+        vp = C.c_void_p
+        _check(load().dc_mlp_get_state(self.handle, th.ctypes.data_as(vp), m1.ctypes.data_as(vp),
+                                       m2.ctypes.data_as(vp), C.byref(st)))
+        return th, m1, m2, st.value
+
+    def set_state(self, theta, m1, m2, step):
+        th, a, b = (np.ascontiguousarray(x, np.float32) for x in (theta, m1, m2))
+        assert th.size == a.size == b.size == MLP_PARAMS
+        vp = C.c_void_p
+        _check(load().dc_mlp_set_state(self.handle, th.ctypes.data_as(vp), a.ctypes.data_as(vp),
+                                       b.ctypes.data_as(vp), int(step)))
 
     def gradient(self, X, T):
         X = np.ascontiguousarray(X, np.float32)

@@ -51,3 +51,75 @@ def test_spmm_bounded_wait_runs_out_and_plan_recovers(dc):
     dc.dc_fspb_spmm(plan, F, Y2)
     dc.dc_fspb_device_status(plan)
     assert torch.equal(Y2, Y_ref)
+
+
+def test_allocation_failure_reports_enomem_and_frees_everything(dc):
+    # host-side injection: the N-th device allocation fails; plan creation
+    # must report DC_ENOMEM and release what it had allocated, for every N
+    import torch
+    p = synth.small_plan(90, n=(16, 14, 12), vox=0.3, n_beams=2)
+    dc.dc_fspb_destroy(dc.dc_fspb_create_from(p))       # first-use allocations of the driver
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    failed = 0
+    for n in range(1, 200):
+        os.environ["DC_FSPB_FAIL_ALLOC_AT"] = str(n)
+        try:
+            plan = dc.dc_fspb_create_from(p)
+        except dc.DcError as e:
+            assert e.status == dc.DC_ENOMEM, (n, str(e))
+            failed += 1
+            torch.cuda.synchronize()
+            assert torch.cuda.mem_get_info()[0] >= free0, n
+            continue
+        finally:
+            del os.environ["DC_FSPB_FAIL_ALLOC_AT"]
+        dc.dc_fspb_destroy(plan)      # n is past the last allocation: creation succeeds
+        break
+    assert failed >= 20, failed
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] >= free0
+
+
+_CHECKED_RUN = r"""
+import sys, numpy as np
+sys.path.insert(0, {root!r})
+from paper_1103_1164_gb300 import dc_fspb as dc, synth
+out = {{}}
+for seed, kw in ((95, dict(n=(13, 11, 9), vox=0.35, n_beams=3, couch=True)),
+                 (96, dict(n=(17, 9, 7), vox=0.3, n_beams=2, beamlet=0.2, beamlet_y=0.5)),
+                 (97, dict(n=(10, 12, 14), vox=0.25, n_beams=1, field=3.0))):
+    p = synth.small_plan(seed, **kw)
+    plan = dc.dc_fspb_create_from(p)
+    out[f"dose{{seed}}"] = dc.dc_fspb_dose(plan, p.fluence)
+    d, rowptr, cols, vals = dc.dc_fspb_dose_and_matrix(plan, p.fluence)
+    out[f"fused{{seed}}"] = d
+    out[f"rowptr{{seed}}"] = rowptr
+    out[f"cols{{seed}}"] = cols
+    out[f"vals{{seed}}"] = vals
+    dc.dc_fspb_device_status(plan)
+np.savez({out!r}, **out)
+print("run ok")
+"""
+
+
+def test_bounds_checked_build_runs_clean_and_identical(dc, tmp_path):
+    # the DC_BOUNDS_CHECK build guards every index of the pair kernels; on
+    # tiny ragged grids it must report no violation and give the normal
+    # build's results bit for bit
+    import subprocess
+    import sys
+    from paper_1103_1164_gb300 import build
+    build.build(checked=True)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = {}
+    for tag, checked in (("plain", "0"), ("checked", "1")):
+        out = str(tmp_path / f"{tag}.npz")
+        env = dict(os.environ, DC_FSPB_CHECKED=checked)
+        r = subprocess.run([sys.executable, "-c", _CHECKED_RUN.format(root=root, out=out)], env=env,
+                           capture_output=True, text=True, timeout=300)
+        assert r.returncode == 0, r.stderr[-2000:]
+        res[tag] = dict(np.load(out))
+    assert res["plain"].keys() == res["checked"].keys()
+    for k in res["plain"]:
+        assert np.array_equal(res["plain"][k], res["checked"][k]), k

@@ -125,3 +125,22 @@ def test_trained_surrogate_dose(dc, oracle_mod):
     # whose ROI or depth decision lies within rounding of its boundary)
     want, amb = oracle_mod.OraclePlan(p, lateral_mode=1).dose(with_amb=True)
     assert_dose_close(net, want, amb, tol=1e-2, label="network slab64 vs FP64 oracle")
+
+
+def test_trainer_checkpoint_resumes_bit_for_bit(dc, tmp_path):
+    # a trainer saved after one epoch and resumed in a new trainer takes the
+    # same steps as the original (deterministic FP32 training, Adam state and
+    # step count restored)
+    from paper_1103_1164_gb300 import checkpoint as ck, surrogate
+    X, T = surrogate.generate_samples(n_phantoms=4, per_phantom=2000, seed=91)
+    a = dc.Mlp(surrogate.init_params(3))
+    a.train(X, T, batch=500, epochs=1, lr=2e-3)
+    path = str(tmp_path / "trainer.npz")
+    ck.save_trainer(path, a, extra={"epochs": 1})
+    b = ck.load_trainer(path)
+    a.train(X, T, batch=500, epochs=1, lr=2e-3)
+    b.train(X, T, batch=500, epochs=1, lr=2e-3)
+    sa, sb = a.state(), b.state()
+    for x, y in zip(sa[:3], sb[:3]):
+        assert np.array_equal(x, y)
+    assert sa[3] == sb[3] == 2 * (X.shape[0] // 500)
