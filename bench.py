@@ -475,6 +475,7 @@ def run_ours(args, world, rank, local, pg):
     forms["surrogate"] = form(run_surrogate_form, args, dc, torch, stream)
     forms["batch"] = form(run_batch_form, args, dc, torch, stream, peak_max)
     forms["gamma"] = form(run_gamma_form, args, dc, torch, stream, p, rho_d, flu_d)
+    forms["commissioning"] = form(run_commission_form, args, dc, torch, stream)
     forms["table1"] = form(run_table1_form, args, dc, torch, stream, flush)
     forms["leaf_sequences"] = form(run_leaf_form, args, dc, torch, stream, flush)
     e2e = None
@@ -741,6 +742,56 @@ def trained_network(dc):
         held = np.abs(dc.dc_mlp_predict(params, X[n_tr:]) - T[n_tr:]).max(1)
         _NETWORK.update(params=params, loss=loss, held=held, n_train=n_tr, generate_s=t_gen, train_s=t_train)
     return _NETWORK
+
+
+def run_commission_form(args, dc, torch, stream, iterations=400):
+    """The commissioning fit of Section 2.1 on the synthetic model: reference
+    doses of the six slab phantoms (30 cm water cube, 15 cm slab of density
+    0.1-2.0 at 8 cm, 10 x 10 cm2 field, SSD 90 cm, 0.5 cm voxels and beamlets)
+    computed with the seeded model; the fit starts 20 % away and runs Adam on
+    the model's twelve parameters with gradients from the backward-pass kernel.
+    Device time of one backward pass, host wall time per iteration (six
+    plans: new tables, density steps, dose, backward pass), the loss and the
+    recovered parameters."""
+    from paper_1103_1164_gb300 import commission as cmn, synth
+    true = synth.model_params()
+    cm = synth.make_commissioning(roi_radius=5.0)
+    dens = (0.1, 0.25, 0.5, 1.0, 1.5, 2.0)
+    inputs = [cmn.slab_phantom(r, vox=0.5, comm=cm) for r in dens]
+    refp = [dc.dc_fspb_create_from(q, stream=stream.cuda_stream) for q in inputs]
+    ref = [dc.dc_fspb_dose(pl, q.fluence) for pl, q in zip(refp, inputs)]
+    pairs = sum(dc.dc_fspb_pair_count(pl) for pl in refp)
+    for pl in refp:
+        dc.dc_fspb_destroy(pl)
+    fit = cmn.CommissioningFit(inputs, ref, stream=stream.cuda_stream)
+    rng = np.random.default_rng(3)
+    th0 = {k: (true[k] + 0.006 if k in cmn.LINEAR else true[k] * float(rng.uniform(0.8, 1.2))) for k in cmn.PARAMS}
+    # device time of the backward pass on one phantom (device buffers)
+    q0, pl0 = inputs[3], fit.plans[3]
+    w_n, f_n = cm.water.shape[1], cm.dens.shape[1]
+    flu = torch.from_numpy(q0.fluence).cuda()
+    wv = torch.rand(pl0.n_voxels, device="cuda")
+    out = (torch.empty(4, w_n, device="cuda"), torch.empty(4, f_n, device="cuda"), torch.empty(2, device="cuda"))
+    dummy = torch.empty(1, device="cuda")
+    vjp = lambda: dc.dc_fspb_dose_vjp(pl0, flu, wv, w_n, f_n, out=out)
+    vjp()
+    t_vjp = time_on_stream(torch, stream, vjp, 5, dummy)
+    t_dose = time_on_stream(torch, stream, lambda: dc.dc_fspb_dose(pl0, flu, wv), 5, dummy)
+    pairs0 = dc.dc_fspb_pair_count(pl0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = fit.fit(th0, iterations=iterations, lr=0.02)
+    wall = time.perf_counter() - t0
+    fit.destroy()
+    rel = {k: (r.theta[k] - true[k]) / abs(true[k]) for k in cmn.PARAMS}
+    return {"workload": "6 slab phantoms (Section 2.1 geometry), 60^3 voxels of 0.5 cm, 400 beamlets each, "
+                        f"{pairs} pairs in all; 12 model parameters from 20 % away",
+            "iterations": r.iterations, "fit_s": wall, "ms_per_iteration": 1e3 * wall / r.iterations,
+            "loss_first": r.loss[0], "loss_last": r.loss[-1],
+            "param_rel_err": rel,
+            "backward_pass": {"ms": t_vjp, "pairs": pairs0, "pairs_per_s": pairs0 / (t_vjp * 1e-3),
+                              "forward_dose_ms": t_dose},
+            "reference": "doses of the seeded model computed by the library (a synthetic reference)"}
 
 
 def run_gamma_form(args, dc, torch, stream, p, rho_d, flu_d):
