@@ -95,7 +95,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--scale", type=float, default=1.0, help="grid scale of the thorax plan")
-    ap.add_argument("--profile", default=None, choices=["dose", "fill", "prep", "spmm", "step", "table1"],
+    ap.add_argument("--profile", default=None, choices=["dose", "fill", "fused", "prep", "spmm", "step", "table1"],
                     help="small fixed run of one stage for profiler captures (prints no bench line)")
     return ap.parse_args()
 
@@ -122,8 +122,9 @@ def run_profile(args):
     flu_d = torch.from_numpy(p.fluence).cuda()
     plan = dc.dc_fspb_create_from(p, device_density=rho_d)
     dose_d = torch.empty(plan.shape, device="cuda")
-    if args.profile == "step":
-        # the benchmark's step after the same plan set-up (autotuned binning)
+    if args.profile in ("step", "fused"):
+        # "step": the benchmark's step after the same plan set-up (autotuned
+        # binning); "fused": its dose-and-matrix pass alone (pattern known)
         dc.dc_fspb_autotune(plan, flu_d)
         pairs = dc.dc_fspb_pair_count(plan)
         rowptr = torch.empty(plan.n_voxels + 1, dtype=torch.int64, device="cuda")
@@ -131,13 +132,13 @@ def run_profile(args):
         vals = torch.empty(pairs, dtype=torch.float32, device="cuda")
         n0 = dc.dc_fspb_launch_count()
         for _ in range(args.warmup + args.steps):
-            dc.dc_fspb_set_density(plan, rho_d)
-            dc.dc_fspb_dose(plan, flu_d, dose_d)
-            dc.dc_fspb_pair_count(plan)
-            dc.dc_fspb_dose_matrix(plan, dc.DC_F32, rowptr, cols, vals)
+            if args.profile == "step":
+                dc.dc_fspb_set_density(plan, rho_d)
+                dc.dc_fspb_pair_count(plan)
+            dc.dc_fspb_dose_and_matrix(plan, flu_d, dose_d, dc.DC_F32, rowptr, cols, vals)
         torch.cuda.synchronize()
         per_step = (dc.dc_fspb_launch_count() - n0) // (args.warmup + args.steps)
-        print(f"profile run done: step, {per_step} library launches per step")
+        print(f"profile run done: {args.profile}, {per_step} library launches per step")
         return
     if args.profile == "fill":
         pairs = dc.dc_fspb_pair_count(plan)
