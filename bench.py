@@ -94,6 +94,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="the step only (quick runs)")
     ap.add_argument("--scale", type=float, default=1.0, help="grid scale of the thorax plan")
     ap.add_argument("--profile", default=None, choices=["dose", "fill", "fused", "prep", "spmm", "step", "table1"],
                     help="small fixed run of one stage for profiler captures (prints no bench line)")
@@ -468,24 +469,19 @@ def run_ours(args, world, rank, local, pg):
             torch.cuda.synchronize()
             return {"error": f"{type(exc).__name__}: {exc}"[:300]}
 
-    forms = form(run_forms, args, dc, torch, stream, peaks)
-    forms["dose_only"] = form(run_dose_form, args, dc, torch, stream, plan, p, flu_d, dose_d, flush, pairs,
-                              sms, sm_max, sm_med)
-    forms["two_pass_plan"] = form(run_two_pass_form, args, dc, torch, stream, plan, rho_d, flu_d, dose_d,
-                                  rowptr_d, cols_d, vals_d, flush, float(step_ms.mean()), pairs)
-    forms["surrogate"] = form(run_surrogate_form, args, dc, torch, stream)
-    forms["batch"] = form(run_batch_form, args, dc, torch, stream, peak_max)
-    forms["gamma"] = form(run_gamma_form, args, dc, torch, stream, p, rho_d, flu_d)
-    forms["commissioning"] = form(run_commission_form, args, dc, torch, stream)
-    forms["table1"] = form(run_table1_form, args, dc, torch, stream, flush)
-    forms["leaf_sequences"] = form(run_leaf_form, args, dc, torch, stream, flush)
+    if args.no_forms:
+        forms = {}
+    else:
+        forms = run_all_forms(form, args, dc, torch, stream, peaks, plan, p, rho_d, flu_d, dose_d, rowptr_d,
+                              cols_d, vals_d, flush, step_ms, pairs, sms, sm_max, sm_med, peak_max)
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, dc, p, plan, pairs, torch)
     cpu = None
     if not args.no_cpu and rank == 0:
         cpu = cpu_baseline(p, pairs)
-        forms["plan_error_vs_oracle"] = form(plan_error_vs_oracle, p, dose_d.cpu().numpy())
+        if not args.no_forms:
+            forms["plan_error_vs_oracle"] = form(plan_error_vs_oracle, p, dose_d.cpu().numpy())
     if rank != 0:
         return
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -503,6 +499,24 @@ def run_ours(args, world, rank, local, pg):
             "roofline": roofline, "peaks": peak_kind, "forms": forms,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks}
     print(json.dumps(line), flush=True)
+
+
+def run_all_forms(form, args, dc, torch, stream, peaks, plan, p, rho_d, flu_d, dose_d, rowptr_d, cols_d, vals_d,
+                  flush, step_ms, pairs, sms, sm_max, sm_med, peak_max):
+    """Every other form of the path; one that fails is reported as such and
+    does not take the benchmark line with it."""
+    forms = form(run_forms, args, dc, torch, stream, peaks)
+    forms["dose_only"] = form(run_dose_form, args, dc, torch, stream, plan, p, flu_d, dose_d, flush, pairs,
+                              sms, sm_max, sm_med)
+    forms["two_pass_plan"] = form(run_two_pass_form, args, dc, torch, stream, plan, rho_d, flu_d, dose_d,
+                                  rowptr_d, cols_d, vals_d, flush, float(step_ms.mean()), pairs)
+    forms["surrogate"] = form(run_surrogate_form, args, dc, torch, stream)
+    forms["batch"] = form(run_batch_form, args, dc, torch, stream, peak_max)
+    forms["gamma"] = form(run_gamma_form, args, dc, torch, stream, p, rho_d, flu_d)
+    forms["commissioning"] = form(run_commission_form, args, dc, torch, stream)
+    forms["table1"] = form(run_table1_form, args, dc, torch, stream, flush)
+    forms["leaf_sequences"] = form(run_leaf_form, args, dc, torch, stream, flush)
+    return forms
 
 
 def run_two_pass_form(args, dc, torch, stream, plan, rho_d, flu_d, dose_d, rowptr_d, cols_d, vals_d, flush,

@@ -398,6 +398,14 @@ dc_status dc_mlp_get_params(const dc_mlp* m, float* out);
  * Synchronise.  Errors: DC_EINVAL (NULL; set_state: a non-finite value, a
  * negative second moment or step), DC_ECUDA. */
 dc_status dc_mlp_get_state(const dc_mlp* m, float* theta, float* m1, float* m2, int64_t* step);
+/* Arithmetic of the trainer's gradient (dc_mlp_gradient, dc_mlp_train):
+ * DC_PRECISION_FP32 (default, FP32 throughout) or DC_PRECISION_BF16 (the
+ * forward and backward products on the tensor cores with BF16 operands and
+ * FP32 accumulation, FP32 master parameters and Adam state; per-CTA partial
+ * gradients summed in a fixed order, so both stay deterministic).  The
+ * network has no counterpart in the paper (it stands in for the AXIS
+ * sampling).  Errors: DC_EINVAL. */
+dc_status dc_mlp_set_precision(dc_mlp* m, int32_t precision);
 dc_status dc_mlp_set_state(dc_mlp* m, const float* theta, const float* m1, const float* m2, int64_t step);
 /*
  * Gradient grad [7491] (host) and loss (host, may be NULL) of

@@ -69,6 +69,7 @@ struct dc_mlp {
     float* dT = nullptr;
     size_t cap = 0;
     int step = 0;
+    int precision = DC_PRECISION_FP32;   // arithmetic of the gradient kernel
 };
 
 static const int kGradCtas = 152;
@@ -268,12 +269,29 @@ static dc_status stage(dc_mlp* m, const float*& X, const float*& T, int n, uint3
     return DC_OK;
 }
 
+// Per-CTA partial gradients of n samples in the trainer's precision.
+static cudaError_t grad_kernel(dc_mlp* m, int nctas, const float* X, const float* T, int n)
+{
+    if (m->precision == DC_PRECISION_BF16)
+        return launch_mlp_grad_bf16(m->stream, nctas, m->theta, X, T, n, m->partial, m->loss_part);
+    return launch_mlp_grad(m->stream, nctas, m->theta, X, T, n, m->partial, m->loss_part);
+}
+
+dc_status dc_mlp_set_precision(dc_mlp* m, int32_t precision)
+{
+    if (!m) return bad("dc_mlp_set_precision: NULL argument");
+    if (precision != DC_PRECISION_FP32 && precision != DC_PRECISION_BF16)
+        return bad("dc_mlp_set_precision: unknown precision");
+    m->precision = precision;
+    return DC_OK;
+}
+
 // Loss and gradient (FP32) of the current parameters on n samples, summed in a fixed order.
 static dc_status grad_pass(dc_mlp* m, const float* X, const float* T, int n, float* loss_host)
 {
     const int tiles = (n + 63) / 64;
     const int nctas = tiles < kGradCtas ? tiles : kGradCtas;
-    DC_CUDA(launch_mlp_grad(m->stream, nctas, m->theta, X, T, n, m->partial, m->loss_part));
+    DC_CUDA(grad_kernel(m, nctas, X, T, n));
     DC_CUDA(launch_mlp_adam(m->stream, m->partial, nctas, m->theta, m->m1, m->m2, m->grad, 0.f, 0.9f, 0.999f, 1e-8f, 1));
     if (loss_host) {
         std::vector<float> lp(nctas);
@@ -312,8 +330,7 @@ dc_status dc_mlp_train(dc_mlp* m, const float* X, const float* T, int32_t n, int
         for (int b0 = 0; b0 + batch <= n; b0 += batch) {   // whole batches in the given (pre-shuffled) order
             const int tiles = (batch + 63) / 64;
             const int nctas = tiles < kGradCtas ? tiles : kGradCtas;
-            DC_CUDA(launch_mlp_grad(m->stream, nctas, m->theta, X + (size_t)b0 * 48, T + (size_t)b0 * 3, batch,
-                                    m->partial, m->loss_part));
+            DC_CUDA(grad_kernel(m, nctas, X + (size_t)b0 * 48, T + (size_t)b0 * 3, batch));
             ++m->step;
             DC_CUDA(launch_mlp_adam(m->stream, m->partial, nctas, m->theta, m->m1, m->m2, nullptr, lr, 0.9f, 0.999f,
                                     1e-8f, m->step));

@@ -201,6 +201,9 @@ cudaError_t launch_mlp_predict_bf16(cudaStream_t s, const float* X, int n, const
                                     float* Y);
 cudaError_t launch_mlp_grad(cudaStream_t s, int nctas, const float* theta, const float* X, const float* T, int n,
                             float* partial, float* loss_part);
+// the same gradient with BF16 tensor-core products (k_mlp_bf16.cu)
+cudaError_t launch_mlp_grad_bf16(cudaStream_t s, int nctas, const float* theta, const float* X, const float* T, int n,
+                                 float* partial, float* loss_part);
 cudaError_t launch_mlp_adam(cudaStream_t s, const float* partial, int nparts, float* theta, float* m1, float* m2,
                             float* grad, float lr, float b1, float b2, float eps, int step);
 constexpr int kMlpParams = 7491;

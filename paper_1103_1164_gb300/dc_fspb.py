@@ -78,7 +78,7 @@ EXPORTS = ["dc_last_error", "dc_status_str", "dc_fspb_create", "dc_fspb_destroy"
            "dc_fspb_launch_count", "dc_fspb_autotune", "dc_fspb_spmm_prepare", "dc_fspb_spmm_info",
            "dc_fspb_spmm", "dc_fspb_spmm_noalloc", "dc_fspb_device_status", "dc_fspb_set_surrogate",
            "dc_fspb_set_lateral_mode", "dc_fspb_set_precision", "dc_fspb_set_tables", "dc_fspb_dose_vjp", "dc_fspb_lateral_fallbacks", "dc_fspb_stencils",
-           "dc_mlp_create", "dc_mlp_destroy", "dc_mlp_get_params", "dc_mlp_get_state", "dc_mlp_set_state", "dc_mlp_gradient", "dc_mlp_train",
+           "dc_mlp_create", "dc_mlp_destroy", "dc_mlp_get_params", "dc_mlp_get_state", "dc_mlp_set_state", "dc_mlp_set_precision", "dc_mlp_gradient", "dc_mlp_train",
            "dc_mlp_predict", "dc_fspb_batch_create", "dc_fspb_batch_destroy", "dc_fspb_batch_buffers",
            "dc_fspb_batch_run", "dc_fspb_batch_dose", "dc_fspb_batch_synchronize", "dc_fspb_batch_kernels",
            "dc_fspb_batch_autotune", "dc_gamma_index", "dc_fluence_from_leaves"]
@@ -132,6 +132,7 @@ def load():
     L.dc_fspb_set_tables.argtypes = [vp, vp, vp]
     L.dc_mlp_get_state.argtypes = [vp, vp, vp, vp, C.POINTER(i64)]
     L.dc_mlp_set_state.argtypes = [vp, vp, vp, vp, i64]
+    L.dc_mlp_set_precision.argtypes = [vp, i32]
     L.dc_fspb_dose_vjp.argtypes = [vp, vp, vp, vp, vp, vp, u32]
     L.dc_fspb_lateral_fallbacks.argtypes = [vp, C.POINTER(i64)]
     L.dc_fspb_stencils.argtypes = [vp, vp, vp, i32, vp, vp, u32]
@@ -387,15 +388,18 @@ def dc_fspb_stencils(plan: Plan, voxels, beams):
 
 
 class Mlp:
-    """Trainer of the surrogate network (dc_mlp_*), FP32 on the GPU."""
+    """Trainer of the surrogate network (dc_mlp_*) on the GPU: FP32, or BF16
+    tensor-core products with FP32 master parameters (precision)."""
 
-    def __init__(self, params, stream=None):
+    def __init__(self, params, stream=None, precision=DC_PRECISION_FP32):
         p = np.ascontiguousarray(params, np.float32)
         assert p.size == MLP_PARAMS
         h = C.c_void_p()
         s = _current_stream() if stream is None else stream
         _check(load().dc_mlp_create(p.ctypes.data_as(C.c_void_p), C.c_void_p(s), C.byref(h)))
         self.handle = h
+        if precision != DC_PRECISION_FP32:
+            _check(load().dc_mlp_set_precision(self.handle, int(precision)))
 
     def __del__(self):
         if getattr(self, "handle", None) and _lib is not None:

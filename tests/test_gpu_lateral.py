@@ -144,3 +144,48 @@ def test_trainer_checkpoint_resumes_bit_for_bit(dc, tmp_path):
     for x, y in zip(sa[:3], sb[:3]):
         assert np.array_equal(x, y)
     assert sa[3] == sb[3] == 2 * (X.shape[0] // 500)
+
+
+def test_mlp_bf16_gradient_matches_oracle(dc):
+    # the tensor-core BF16 gradient kernel against the FP64 analytic gradient:
+    # BF16 operands (8 significant bits) in the products, so the bound is the
+    # BF16 one (3 % of the gradient's norm), far below the gradient's own scale
+    from oracle import mlp as omlp
+    from paper_1103_1164_gb300 import surrogate
+    rng = np.random.default_rng(14)
+    th = surrogate.init_params(15) + rng.normal(0, 0.05, omlp.N_PARAMS).astype(np.float32)
+    p = synth.small_plan(56, n=(20, 18, 16), vox=0.3, n_beams=3)
+    plan = dc.dc_fspb_create_from(p)
+    X, T = dc.dc_fspb_stencils(plan, rng.integers(0, plan.n_voxels, 1000).astype(np.int32),
+                               rng.integers(0, 3, 1000).astype(np.int32))
+    net = dc.Mlp(th, precision=dc.DC_PRECISION_BF16)
+    loss, g = net.gradient(X, T)
+    lo, go = omlp.loss_grad(th.astype(np.float64), X, T)
+    assert abs(loss - lo) <= 2e-2 * lo
+    assert np.linalg.norm(g - go) <= 3e-2 * np.linalg.norm(go)
+    assert np.abs(g - go).max() <= 5e-2 * np.abs(go).max()
+    # every parameter block is written (no stale or missing partials)
+    for a, b in ((0, 48 * 64), (48 * 64, 48 * 64 + 64), (48 * 64 + 64, 48 * 64 + 64 + 4096),
+                 (7491 - 195, 7491 - 3), (7491 - 3, 7491)):
+        assert np.linalg.norm(g[a:b] - go[a:b]) <= 5e-2 * np.linalg.norm(go[a:b]) + 1e-9, (a, b)
+    # deterministic: the same gradient twice
+    _, g2 = net.gradient(X, T)
+    assert np.array_equal(g, g2)
+
+
+def test_bf16_training_matches_fp32_training(dc):
+    # the network trained with the BF16 gradient reaches the held-out error of
+    # the FP32-trained one (same data, same schedule)
+    from paper_1103_1164_gb300 import surrogate
+    X, T = surrogate.generate_samples(n_phantoms=48, per_phantom=4000, seed=78)
+    n_tr = int(0.9 * X.shape[0])
+    perm = np.random.default_rng(9).permutation(n_tr)
+    held = {}
+    for prec in (dc.DC_PRECISION_FP32, dc.DC_PRECISION_BF16):
+        net = dc.Mlp(surrogate.init_params(9), precision=prec)
+        loss = net.train(X[perm], T[perm], batch=2048, epochs=8, lr=3e-3)
+        assert np.isfinite(loss)
+        pred = dc.dc_mlp_predict(net.params(), X[n_tr:])
+        held[prec] = float(np.median(np.abs(pred - T[n_tr:]).max(1)))
+    assert held[dc.DC_PRECISION_BF16] < 0.01
+    assert held[dc.DC_PRECISION_BF16] <= 2.0 * held[dc.DC_PRECISION_FP32] + 1e-3, held
