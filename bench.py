@@ -510,7 +510,7 @@ def run_all_forms(form, args, dc, torch, stream, peaks, plan, p, rho_d, flu_d, d
                               sms, sm_max, sm_med)
     forms["two_pass_plan"] = form(run_two_pass_form, args, dc, torch, stream, plan, rho_d, flu_d, dose_d,
                                   rowptr_d, cols_d, vals_d, flush, float(step_ms.mean()), pairs)
-    forms["surrogate"] = form(run_surrogate_form, args, dc, torch, stream)
+    forms["surrogate"] = form(run_surrogate_form, args, dc, torch, stream, peaks)
     forms["batch"] = form(run_batch_form, args, dc, torch, stream, peak_max)
     forms["gamma"] = form(run_gamma_form, args, dc, torch, stream, p, rho_d, flu_d)
     forms["commissioning"] = form(run_commission_form, args, dc, torch, stream)
@@ -661,7 +661,7 @@ def column_error(got, want):
     return float((np.abs(got - want).max(0) / (np.abs(want).max(0) + 1e-300)).max())
 
 
-def run_surrogate_form(args, dc, torch, stream, k=64):
+def run_surrogate_form(args, dc, torch, stream, peaks, k=64):
     """The learned lateral correction: 2M (nearest-tap stencil, plain axis
     densities) samples from 200 random slab/sphere phantoms, trained with the
     library's kernels, then the slab plan's 64-fluence dose with the network's
@@ -710,6 +710,27 @@ def run_surrogate_form(args, dc, torch, stream, k=64):
     t_spmm = time_on_stream(torch, stream, lambda: dc.dc_fspb_spmm(plan, F, Y), reps, flush)
     dc.dc_fspb_device_status(plan)
     err = float(((Y.t() - plain).abs().max(1).values / plain.abs().max(1).values).max())
+    # the network's factor pass alone (k_mlp_factors: 48 nearest taps and the
+    # network per (voxel, beam) entry), against the BF16 tensor peak
+    entries = dc.dc_fspb_list_entries(plan)
+    t_fac = time_on_stream(torch, stream, lambda: dc.dc_fspb_set_lateral_mode(plan, dc.DC_LATERAL_MLP), reps, flush)
+    t_axis_fac = time_on_stream(torch, stream, lambda: dc.dc_fspb_set_lateral_mode(plan, dc.DC_LATERAL_AXIS),
+                                reps, flush)
+    dc.dc_fspb_set_lateral_mode(plan, dc.DC_LATERAL_MLP)
+    bf_peak = float(peaks.get("bf16_tflops", 1900.0))
+    samples = 8 * n_tr
+    net32 = net["fp32"]
+    mlp = {"factor_pass": {"kernel": "k_mlp_factors (mma.sync BF16)", "entries": entries, "ms": t_fac,
+                           "axis_stencil_pass_ms": t_axis_fac,
+                           "tflops": entries * MLP_FWD_FLOP / (t_fac * 1e-3) / 1e12,
+                           "frac_of_bf16_peak": entries * MLP_FWD_FLOP / (t_fac * 1e-3) / 1e12 / bf_peak},
+           "training_bf16": {"kernel": "k_mlp_grad_bf16 + k_mlp_adam (8 epochs, host wall clock, staging included)",
+                             "s": t_train, "samples_per_s": samples / t_train,
+                             "tflops": samples * MLP_TRAIN_FLOP / t_train / 1e12,
+                             "frac_of_bf16_peak": samples * MLP_TRAIN_FLOP / t_train / 1e12 / bf_peak},
+           "training_fp32": {"s": net32["train_s"], "samples_per_s": samples / net32["train_s"],
+                             "held_out_p50": float(np.median(net32["held"])),
+                             "held_out_p99": float(np.percentile(net32["held"], 99))}}
     oracle_err = None
     if not args.no_cpu:
         # against the FP64 oracle's axis-stencil form (the method the network
@@ -734,28 +755,42 @@ def run_surrogate_form(args, dc, torch, stream, k=64):
             "accounting": "per density: factors (+ matrix build for the BF16 form); per set of 64 "
                           "fluences: the direct batch or the SpMM",
             "max_err_vs_plain_over_colmax": err,
-            "max_err_vs_fp64_oracle_over_colmax": oracle_err}
+            "max_err_vs_fp64_oracle_over_colmax": oracle_err,
+            "network_kernels": mlp}
 
 
 _NETWORK = {}
 
 
+MLP_FWD_FLOP = 2 * (48 * 64 + 64 * 64 + 64 * 3)      # 14,720 per sample
+MLP_TRAIN_FLOP = 3 * MLP_FWD_FLOP                     # forward + the two products of the backward pass
+
+
 def trained_network(dc):
     """The surrogate network of config 4, trained once per process: 2M
     (nearest-tap stencil, plain axis densities) samples from 200 random
-    slab/sphere phantoms, 90 % trained with the library's kernels (8 epochs,
-    batch 4096, Adam), 10 % held out."""
+    slab/sphere phantoms, 90 % trained with the library's BF16 tensor-core
+    kernels (8 epochs, batch 4096, Adam, FP32 master parameters), 10 % held
+    out; the same schedule with the FP32 kernels for comparison."""
     if not _NETWORK:
         from paper_1103_1164_gb300 import surrogate
         t0 = time.perf_counter()
         X, T = surrogate.generate_samples(n_phantoms=200, per_phantom=10000, seed=2024)
         t_gen = time.perf_counter() - t0
         n_tr = int(0.9 * X.shape[0])
-        t0 = time.perf_counter()
-        params, loss = surrogate.train(X[:n_tr], T[:n_tr], epochs=8, batch=4096, lr=2e-3, seed=17)
-        t_train = time.perf_counter() - t0
-        held = np.abs(dc.dc_mlp_predict(params, X[n_tr:]) - T[n_tr:]).max(1)
-        _NETWORK.update(params=params, loss=loss, held=held, n_train=n_tr, generate_s=t_gen, train_s=t_train)
+        res = {}
+        for name, prec in (("bf16", dc.DC_PRECISION_BF16), ("fp32", dc.DC_PRECISION_FP32)):
+            import torch
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            params, loss = surrogate.train(X[:n_tr], T[:n_tr], epochs=8, batch=4096, lr=2e-3, seed=17,
+                                           precision=prec)
+            t_train = time.perf_counter() - t0
+            held = np.abs(dc.dc_mlp_predict(params, X[n_tr:]) - T[n_tr:]).max(1)
+            res[name] = dict(params=params, loss=loss, held=held, train_s=t_train)
+        b = res["bf16"]
+        _NETWORK.update(params=b["params"], loss=b["loss"], held=b["held"], n_train=n_tr, generate_s=t_gen,
+                        train_s=b["train_s"], fp32=res["fp32"])
     return _NETWORK
 
 

@@ -169,6 +169,10 @@ dc_status dc_fspb_n_beamlets(const dc_plan* plan, int32_t* n);
 
 /* Number of voxels V = nx ny nz. */
 dc_status dc_fspb_n_voxels(const dc_plan* plan, int64_t* n);
+/* Number of (voxel, beam) entries in the plan's beam's-eye-view voxel lists:
+ * the units of work of the per-(voxel, beam) lateral-factor passes (the AXIS
+ * stencils or the network).  Synchronises.  Errors: DC_EINVAL, DC_ECUDA. */
+dc_status dc_fspb_list_entries(dc_plan* plan, int64_t* n);
 
 /*
  * Eq. (1): dose[v] = sum_i f_i D_i(r_v) over the pairs whose voxel lies in

@@ -615,6 +615,19 @@ dc_status dc_fspb_n_voxels(const dc_plan* plan, int64_t* n)
     return DC_OK;
 }
 
+dc_status dc_fspb_list_entries(dc_plan* plan, int64_t* n)
+{
+    if (!plan || !n) return invalid("dc_fspb_list_entries: NULL argument");
+    std::vector<int32_t> items(plan->n_beams);
+    DC_CUDA(cudaMemcpyAsync(items.data(), plan->d_nitems, plan->n_beams * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                            plan->stream));
+    DC_CUDA(cudaStreamSynchronize(plan->stream));
+    int64_t s = 0;
+    for (int32_t x : items) s += x;
+    *n = s;
+    return DC_OK;
+}
+
 // Per-beam partial dose buffer of at least `need` floats.
 static dc_status ensure_part(dc_plan* p, size_t need)
 {

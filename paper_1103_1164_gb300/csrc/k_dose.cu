@@ -571,7 +571,7 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
 // SM), 64 for the pair count and the CSR fill (4 CTAs; the fill's extra state
 // would otherwise be recomputed in the hot loop), 80 for 16 fluence vectors.
 template <int MODE, int NF>
-constexpr int min_ctas() { return MODE == kCount ? 6 : (MODE == kFill || MODE == kGrad ? 4 : (NF == 1 ? 5 : 3)); }
+constexpr int min_ctas() { return MODE == kCount || MODE == kFill || MODE == kGrad ? 4 : (NF == 1 ? 5 : 3); }
 
 template <int MODE, int NF, bool MERGED, int LAT, int PREC>
 __global__ void __launch_bounds__(kThreads, min_ctas<MODE, NF>()) k_pairs(const DoseArgs a)

@@ -72,7 +72,7 @@ class dc_kernel_coeffs(C.Structure):
 
 
 EXPORTS = ["dc_last_error", "dc_status_str", "dc_fspb_create", "dc_fspb_destroy",
-           "dc_fspb_n_beamlets", "dc_fspb_n_voxels", "dc_fspb_dose", "dc_fspb_dose_batch",
+           "dc_fspb_n_beamlets", "dc_fspb_n_voxels", "dc_fspb_list_entries", "dc_fspb_dose", "dc_fspb_dose_batch",
            "dc_fspb_pair_count", "dc_fspb_dose_matrix", "dc_fspb_dose_and_matrix", "dc_fspb_get_smoothed",
            "dc_fspb_get_beamlets", "dc_fspb_get_tables", "dc_fspb_set_density",
            "dc_fspb_launch_count", "dc_fspb_autotune", "dc_fspb_spmm_prepare", "dc_fspb_spmm_info",
@@ -130,6 +130,7 @@ def load():
     L.dc_fspb_set_lateral_mode.argtypes = [vp, i32]
     L.dc_fspb_set_precision.argtypes = [vp, i32]
     L.dc_fspb_set_tables.argtypes = [vp, vp, vp]
+    L.dc_fspb_list_entries.argtypes = [vp, C.POINTER(i64)]
     L.dc_mlp_get_state.argtypes = [vp, vp, vp, vp, C.POINTER(i64)]
     L.dc_mlp_set_state.argtypes = [vp, vp, vp, vp, i64]
     L.dc_mlp_set_precision.argtypes = [vp, i32]
@@ -332,6 +333,13 @@ def dc_fspb_set_surrogate(plan: Plan, params, rho_lo=0.05, rho_hi=2.0):
 
 def dc_fspb_set_lateral_mode(plan: Plan, mode: int):
     _check(load().dc_fspb_set_lateral_mode(plan.handle, int(mode)))
+
+
+def dc_fspb_list_entries(plan: Plan) -> int:
+    """(voxel, beam) entries of the plan's voxel lists (the lateral-factor passes' work)."""
+    n = C.c_int64()
+    _check(load().dc_fspb_list_entries(plan.handle, C.byref(n)))
+    return n.value
 
 
 def dc_fspb_set_tables(plan: Plan, water, dens):

@@ -2,7 +2,8 @@
 
 Orchestration only: samples come from the library's plain axis-stencil kernel
 (dc_fspb_stencils) on seeded random slab/sphere phantoms, and the network is
-trained by the library's FP32 forward/backward/Adam kernels (dc_fspb.Mlp).
+trained by the library's forward/backward/Adam kernels (dc_fspb.Mlp; FP32, or
+BF16 tensor-core products with FP32 master parameters).
 Network: 48 nearest-voxel density taps -> 64 -> 64 (SiLU) -> 3 effective
 densities (omega, u_2 along x, u_2 along y), 7491 parameters.
 """
@@ -52,11 +53,14 @@ def generate_samples(n_phantoms: int = 200, per_phantom: int = 10000, seed: int 
     return np.concatenate(Xs), np.concatenate(Ts)
 
 
-def train(X, T, epochs: int = 8, batch: int = 4096, lr: float = 2e-3, seed: int = 17, params=None):
-    """Trains on a seeded shuffle of (X, T); returns (parameters, final loss)."""
+def train(X, T, epochs: int = 8, batch: int = 4096, lr: float = 2e-3, seed: int = 17, params=None,
+          precision: int = dc_fspb.DC_PRECISION_FP32):
+    """Trains on a seeded shuffle of (X, T); returns (parameters, final loss).
+    precision: the gradient kernel's arithmetic (FP32, or BF16 tensor-core
+    products with FP32 master parameters)."""
     rng = np.random.default_rng(seed)
     perm = rng.permutation(X.shape[0])
-    net = dc_fspb.Mlp(init_params(seed) if params is None else params)
+    net = dc_fspb.Mlp(init_params(seed) if params is None else params, precision=precision)
     loss = net.train(X[perm], T[perm], batch=batch, epochs=epochs, lr=lr)
     return net.params(), loss
 
