@@ -33,19 +33,9 @@ constexpr float kLog2e = 1.4426950408889634f;
 // needs moving when only its head is written out
 constexpr int kRing = 16;
 constexpr int kRingLd = kRing + 1;
-// Wide staging of the fill: 32 entries per lane, the values (4 B) and the
-// columns as 16-bit offsets from the beam's first beamlet (2 B) in separate
-// arrays; a flush then writes one lane's run per warp-wide store (up to 32
-// consecutive entries, whole lines).  Used when every beam has at most 65536
-// beamlets; otherwise the 16-entry ring of (column, value) pairs.
-constexpr int kRingW = 32;
-constexpr int kValLd = 33;   // floats per lane row (odd: equal slots of different lanes in different banks)
-constexpr int kColLd = 34;   // 16-bit columns per lane row (17 words)
-constexpr int kStageWBytes = 32 * kValLd * 4 + 32 * kColLd * 2;   // per warp
-
 // beamlet records of a row window staged per warp at a time (fewer in the
 // fill, whose CSR staging shares the CTA's shared memory)
-constexpr int row_max(int mode, int ring = 16) { return mode == 2 ? (ring == kRingW ? 12 : 16) : 32; }
+constexpr int row_max(int mode) { return mode == 2 ? 16 : 32; }
 
 enum Mode { kDose = 0, kCount = 1, kFill = 2, kGrad = 3 };
 
@@ -397,60 +387,13 @@ __device__ __forceinline__ void flush_stage(const DoseArgs& a, const int2* st, i
     cnt -= nw;
 }
 
-// The wide ring's flush: the same sector rule as flush_stage; then, for each
-// lane with entries to write, the whole warp writes that lane's run (lane j
-// its j-th entry), so each store covers up to 32 consecutive entries.
-template <typename VT>
-__device__ __forceinline__ void flush_wide_runs(int32_t* cols, VT* vals, const float* sv, const uint16_t* sc,
-                                                int lane, int nw, int64_t pos, int col0)
-{
-    uint32_t todo = __ballot_sync(0xffffffffu, nw > 0);
-    while (todo) {
-        const int o = __ffs((int)todo) - 1;
-        todo &= todo - 1u;
-        const int c = __shfl_sync(0xffffffffu, nw, o);
-        const int64_t base = __shfl_sync(0xffffffffu, pos, o);
-        if (lane < c) {
-            const int slot = (int)(((uint32_t)base + (uint32_t)lane) & (kRingW - 1));
-            store_entry(cols, vals, base + lane,
-                        make_int2(col0 + (int)sc[o * kColLd + slot], __float_as_int(sv[o * kValLd + slot])));
-        }
-    }
-}
-
-__device__ __forceinline__ void flush_wide(const DoseArgs& a, const float* sv, const uint16_t* sc, int lane, int& cnt,
-                                           int64_t& pos, int64_t pend, int mis, bool last, int col0)
-{
-    int nw = cnt;
-    if (!last) {
-        const int64_t end = ((pos + cnt + mis) & ~(int64_t)7) - mis;
-        nw = end > pos ? (int)(end - pos) : 0;
-    }
-    nw = (int)min((int64_t)nw, pend - pos);
-#if DC_BOUNDS_CHECK
-    if (nw > 0 && (pos < a.rowptr[0] || pos + nw > a.rowptr[(int64_t)a.P.nx * a.P.ny * a.P.nz]))
-        atomicCAS(a.P.chk, 0, 6);
-#endif
-    __syncwarp();
-    if (a.value_dtype == DC_BF16)
-        flush_wide_runs(a.cols, reinterpret_cast<__nv_bfloat16*>(a.vals), sv, sc, lane, nw, pos, col0);
-    else
-        flush_wide_runs(a.cols, reinterpret_cast<float*>(a.vals), sv, sc, lane, nw, pos, col0);
-    __syncwarp();
-    pos += nw;
-    cnt -= nw;
-}
-
 // Evaluates one warp work unit: the 32 list entries starting at e0 of beam b
 // (one voxel per lane) against the beamlets of the warp's union window.
-template <int MODE, int NF, bool MERGED, int LAT, int PREC = 0, int RING = 16>
+template <int MODE, int NF, bool MERGED, int LAT, int PREC = 0>
 __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi, const int64_t e0, const int b,
                                              const float4* __restrict__ sW, int2* sst, float4* srow,
                                              const int lane)
 {
-    // wide ring (RING == kRingW): this warp's value and 16-bit column arrays
-    float* wsv = reinterpret_cast<float*>(sst);
-    uint16_t* wsc = reinterpret_cast<uint16_t*>(reinterpret_cast<char*>(sst) + 32 * kValLd * 4);
     const PlanView& P = a.P;
     const int64_t V = (int64_t)P.nx * P.ny * P.nz;
     Lane ln;
@@ -500,7 +443,6 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
     const float pa = ln.vx * __ldg(&bm.ex[0]) + ln.vy * __ldg(&bm.ex[1]) + ln.vz * __ldg(&bm.ex[2]);
     const float pc = ln.vx * __ldg(&bm.ey[0]) + ln.vy * __ldg(&bm.ey[1]) + ln.vz * __ldg(&bm.ey[2]);
     const int M = __ldg(&bm.M), N = __ldg(&bm.N), first = __ldg(&bm.first);
-    constexpr int kRingN = RING == kRingW ? kRingW : kRing;
     const float hfx = __ldg(&bm.half_fx), hfy = __ldg(&bm.half_fy);
     const bool live = ln.valid && zz > 1e-3f;
     // isocentre-plane projection of the voxel and a conservative radius of
@@ -531,8 +473,8 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
         // the records of the row's window go to shared memory with one
         // coalesced load per lane, so the traversal reads them without a
         // global-memory round trip per beamlet
-        for (int m0 = wmlo; m0 <= wmhi; m0 += row_max(MODE, RING)) {
-        const int m1 = min(wmhi, m0 + row_max(MODE, RING) - 1);
+        for (int m0 = wmlo; m0 <= wmhi; m0 += row_max(MODE)) {
+        const int m1 = min(wmhi, m0 + row_max(MODE) - 1);
         __syncwarp();
         if (m0 + lane <= m1) {
             const uint32_t ib = DC_GUARD(P, row + (uint32_t)(m0 + lane), P.B, 5);
@@ -579,21 +521,12 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
             } else {
                 if (pt.in) {
                     const float D = pair_eval<MERGED, LAT, 0>(P, ln, i, sad, sW, pt);
-                    if (RING == kRingW) {
-                        const int slot = (int)(((uint32_t)pos + (uint32_t)cnt) & (kRingW - 1));
-                        wsv[lane * kValLd + slot] = D;
-                        wsc[lane * kColLd + slot] = (uint16_t)(i - (uint32_t)first);
-                    } else {
-                        sst[lane * kRingLd + (int)(((uint32_t)pos + (uint32_t)cnt) & (kRing - 1))] =
-                            make_int2((int)i, __float_as_int(D));
-                    }
+                    sst[lane * kRingLd + (int)(((uint32_t)pos + (uint32_t)cnt) & (kRing - 1))] =
+                        make_int2((int)i, __float_as_int(D));
                     ++cnt;
                     if (NF == 1) acc[0] = fmaf(rq[2].w, D, acc[0]);   // eq. (1) from the same evaluation
                 }
-                if (__any_sync(0xffffffffu, cnt >= kRingN)) {
-                    if (RING == kRingW) flush_wide(a, wsv, wsc, lane, cnt, pos, pend, mis, false, first);
-                    else flush_stage(a, sst, lane, cnt, pos, pend, mis, false);
-                }
+                if (__any_sync(0xffffffffu, cnt >= kRing)) flush_stage(a, sst, lane, cnt, pos, pend, mis, false);
             }
         }
         }
@@ -617,8 +550,7 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
             atomicAdd(sgd + 4 * P.f_n + 1, gc[1]);
         }
     } else if (MODE == kFill) {
-        if (RING == kRingW) flush_wide(a, wsv, wsc, lane, cnt, pos, pend, mis, true, first);
-        else flush_stage(a, sst, lane, cnt, pos, pend, mis, true);
+        flush_stage(a, sst, lane, cnt, pos, pend, mis, true);
         if (NF == 1 && ln.valid) a.part[(size_t)b * V + v] = acc[0];
     } else if (ln.valid) {
         if (MODE == kDose) {
@@ -641,7 +573,7 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
 template <int MODE, int NF>
 constexpr int min_ctas() { return MODE == kCount || MODE == kFill || MODE == kGrad ? 4 : (NF == 1 ? 5 : 3); }
 
-template <int MODE, int NF, bool MERGED, int LAT, int PREC, int RING = 16>
+template <int MODE, int NF, bool MERGED, int LAT, int PREC>
 __global__ void __launch_bounds__(kThreads, min_ctas<MODE, NF>()) k_pairs(const DoseArgs a)
 {
     extern __shared__ float4 smem[];
@@ -650,8 +582,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<MODE, NF>()) k_pairs(const 
     float4* sW = smem;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float4* sstage = smem + (MERGED ? 0 : 2 * P.w_n);
-    int2* sst = RING == kRingW ? reinterpret_cast<int2*>(reinterpret_cast<char*>(sstage) + warp * kStageWBytes)
-                               : reinterpret_cast<int2*>(sstage) + warp * (32 * kRingLd);
+    int2* sst = reinterpret_cast<int2*>(sstage) + warp * (32 * kRingLd);
     // backward pass: the CTA's gradient bins (4 water tables, 4 density
     // functions, 2 scales of b) instead of the CSR staging
     float* sgrad = reinterpret_cast<float*>(sstage);
@@ -660,7 +591,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<MODE, NF>()) k_pairs(const 
         sst = reinterpret_cast<int2*>(sgrad);
         for (int q = threadIdx.x; q < ngrad; q += blockDim.x) sgrad[q] = 0.f;
     }
-    __shared__ float4 s_row[kWarps][3 * row_max(MODE, RING)];
+    __shared__ float4 s_row[kWarps][3 * row_max(MODE)];
     // the water tables are read from shared memory unless merged into the depth tables
     if (MODE != kCount && !MERGED)
         for (int q = threadIdx.x; q < 2 * P.w_n; q += blockDim.x) sW[q] = __ldg(P.water + q);
@@ -677,7 +608,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<MODE, NF>()) k_pairs(const 
         int b = 0;
         while (b + 1 < P.n_beams && s_base[b + 1] <= e0) ++b;
         const int32_t vi = __ldg(a.items + e0 + lane);
-        process_unit<MODE, NF, MERGED, LAT, PREC, RING>(a, vi, e0, b, sW, sst, s_row[warp], lane);
+        process_unit<MODE, NF, MERGED, LAT, PREC>(a, vi, e0, b, sW, sst, s_row[warp], lane);
     }
     if (MODE == kGrad) {
         __syncthreads();
@@ -954,22 +885,14 @@ DoseArgs make_args(const dc_plan* p)
     return a;
 }
 
-size_t smem_bytes(const dc_plan* p, int mode, int ring = 16)
+size_t smem_bytes(const dc_plan* p, int mode)
 {
     if (mode == kCount) return 0;
     if (mode == kGrad)   // water tables + gradient bins (always the general tables)
         return 2 * sizeof(float4) * p->coeffs.w_n + sizeof(float) * (4 * (size_t)p->coeffs.w_n + 4 * p->coeffs.f_n + 2);
     size_t s = p->merged ? 0 : 2 * sizeof(float4) * p->coeffs.w_n;
-    if (mode == kFill) s += ring == kRingW ? (size_t)kWarps * kStageWBytes : sizeof(int2) * kWarps * 32 * kRingLd;
+    if (mode == kFill) s += sizeof(int2) * kWarps * 32 * kRingLd;
     return s;
-}
-
-// The wide fill ring stores columns as 16-bit offsets from the beam's first beamlet.
-bool wide_ring_ok(const dc_plan* p)
-{
-    for (int b = 0; b < p->n_beams; ++b)
-        if ((int64_t)p->M[b] * p->N[b] > 65536) return false;
-    return true;
 }
 
 int grid_for(int64_t n)
@@ -979,11 +902,11 @@ int grid_for(int64_t n)
 }
 
 // Persistent launch: as many CTAs as fit on the device at once.
-template <int MODE, int NF, bool MERGED, int LAT, int PREC = 0, int RING = 16>
+template <int MODE, int NF, bool MERGED, int LAT, int PREC = 0>
 cudaError_t run_variant(const dc_plan* p, const DoseArgs& a)
 {
-    const size_t sm = smem_bytes(p, MODE, RING);
-    auto kern = k_pairs<MODE, NF, MERGED, LAT, PREC, RING>;
+    const size_t sm = smem_bytes(p, MODE);
+    auto kern = k_pairs<MODE, NF, MERGED, LAT, PREC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     int per_sm = 0, sms = 0;
@@ -1008,13 +931,6 @@ cudaError_t run(const dc_plan* p, const DoseArgs& a)
         if (p->merged)
             return item ? run_variant<kDose, 1, true, kItem, 1>(p, a) : run_variant<kDose, 1, true, kIso, 1>(p, a);
         return item ? run_variant<kDose, 1, false, kItem, 1>(p, a) : run_variant<kDose, 1, false, kIso, 1>(p, a);
-    }
-    if (MODE == kFill && wide_ring_ok(p)) {
-        if (p->merged)
-            return item ? run_variant<MODE, NF, true, kItem, 0, kRingW>(p, a)
-                        : run_variant<MODE, NF, true, kIso, 0, kRingW>(p, a);
-        return item ? run_variant<MODE, NF, false, kItem, 0, kRingW>(p, a)
-                    : run_variant<MODE, NF, false, kIso, 0, kRingW>(p, a);
     }
     if (p->merged) return item ? run_variant<MODE, NF, true, kItem>(p, a) : run_variant<MODE, NF, true, kIso>(p, a);
     return item ? run_variant<MODE, NF, false, kItem>(p, a) : run_variant<MODE, NF, false, kIso>(p, a);
