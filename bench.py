@@ -96,7 +96,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="the step only (quick runs)")
     ap.add_argument("--scale", type=float, default=1.0, help="grid scale of the thorax plan")
-    ap.add_argument("--profile", default=None, choices=["dose", "fill", "fused", "prep", "spmm", "step", "table1"],
+    ap.add_argument("--profile", default=None, choices=["dose", "fill", "fused", "mlp", "prep", "spmm", "step", "table1", "train"],
                     help="small fixed run of one stage for profiler captures (prints no bench line)")
     return ap.parse_args()
 
@@ -107,6 +107,26 @@ def run_profile(args):
     import torch
     from paper_1103_1164_gb300 import build, dc_fspb as dc, synth
     build.build()
+    if args.profile in ("mlp", "train"):
+        # the network's factor pass on slab64 (weights from the initialiser:
+        # its cost does not depend on them), or the BF16 training gradient on
+        # 8192 stencil samples
+        from paper_1103_1164_gb300 import surrogate
+        if args.profile == "mlp":
+            p1 = synth.config1()
+            plan = dc.dc_fspb_create_from(p1, lateral_mode=dc.DC_LATERAL_AXIS)
+            dc.dc_fspb_set_surrogate(plan, surrogate.init_params(1), surrogate.RHO_LO, surrogate.RHO_HI)
+            for _ in range(args.warmup + args.steps):
+                dc.dc_fspb_set_lateral_mode(plan, dc.DC_LATERAL_MLP)
+            torch.cuda.synchronize()
+            print(f"profile run done: mlp factor pass, {dc.dc_fspb_list_entries(plan)} entries")
+        else:
+            X, T = surrogate.generate_samples(n_phantoms=2, per_phantom=4096, seed=5)
+            net = dc.Mlp(surrogate.init_params(2), precision=dc.DC_PRECISION_BF16)
+            for _ in range(args.warmup + args.steps):
+                net.gradient(X, T)
+            print(f"profile run done: BF16 training gradient, {X.shape[0]} samples")
+        return
     if args.profile == "spmm":
         p1 = synth.config1()
         plan = dc.dc_fspb_create_from(p1)
