@@ -55,9 +55,14 @@ L2_FLUSH_BYTES = 256 << 20
 # from the sources with these SHA-256 digests (the kernel and the structures it
 # reads; the summaries are under profiles/); reported only while they are unchanged.
 KERNEL_TRAFFIC = {
-    "dose": (110389248 + 20729344, {
-        "paper_1103_1164_gb300/csrc/k_dose.cu": "70ece8998f2945e076ecef028daaf234232d4b3e7fd3d9d6e96961a68bf3742f",
-        "paper_1103_1164_gb300/csrc/dc_views.cuh": "604f1c61d84a82494049db8c574ff1384cee296c4ebbe27db75ba78b5c54a772",
+    # k_pairs<kFill, 1> (the step's fill + eq. 1) and k_pairs<kDose> on thorax9
+    "fill": (1179481600 + 5331267584, {
+        "paper_1103_1164_gb300/csrc/k_dose.cu": "886028920f7a33923d7e292521ee3933c7735705b27bd40ec55e39382803ff7b",
+        "paper_1103_1164_gb300/csrc/dc_views.cuh": "f1be087b7a0acad7b8f7cef88a48640b076f1fa27a2cd95059a18729a05be3a6",
+    }),
+    "dose": (110870016 + 20681728, {
+        "paper_1103_1164_gb300/csrc/k_dose.cu": "886028920f7a33923d7e292521ee3933c7735705b27bd40ec55e39382803ff7b",
+        "paper_1103_1164_gb300/csrc/dc_views.cuh": "f1be087b7a0acad7b8f7cef88a48640b076f1fa27a2cd95059a18729a05be3a6",
     }),
 }
 
