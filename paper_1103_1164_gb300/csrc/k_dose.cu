@@ -623,128 +623,6 @@ __global__ void __launch_bounds__(kThreads, min_ctas<MODE, NF>()) k_pairs(const 
 }
 
 // ---------------------------------------------------------------------------
-// Pair counts of the matrix pattern, transposed.  Per work unit (32 voxels of
-// one beam's list) the union window of the unit's voxels (the same rows and
-// row ranges process_unit walks) is flattened row by row and taken 32
-// beamlets at a time, one per lane, whose record stays in the lane's
-// registers; the lanes then test their beamlets against the unit's 32 voxels
-// in turn (each voxel broadcast from shared memory) and a ballot counts the
-// passes of that voxel.  pair_test runs on the same operands as in the fill,
-// so the counts are exactly the fill's entries per (voxel, beam).
-constexpr int kCountRows = 64;   // window rows per block of the flattening
-
-__global__ void __launch_bounds__(kThreads, 5) k_count_t(const DoseArgs a)
-{
-    __shared__ int64_t s_base[kMaxBeams + 1];
-    __shared__ float4 s_vox[kWarps][32];
-    __shared__ int s_lo[kWarps][kCountRows];
-    __shared__ int s_pre[kWarps][kCountRows + 1];
-    const PlanView& P = a.P;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int q = threadIdx.x; q <= P.n_beams; q += blockDim.x) s_base[q] = a.base[q];
-    __syncthreads();
-    const int total_units = a.work[0];
-    const int64_t V = (int64_t)P.nx * P.ny * P.nz;
-    for (;;) {
-        int w = 0;
-        if (lane == 0) w = atomicAdd(a.work + 1, 1);
-        w = __shfl_sync(0xffffffffu, w, 0);
-        if (w >= total_units) break;
-        const int64_t e0 = (int64_t)DC_GUARD(P, w, (s_base[P.n_beams] + 31) / 32, 4) * 32;
-        int b = 0;
-        while (b + 1 < P.n_beams && s_base[b + 1] <= e0) ++b;
-        const int32_t vi = __ldg(a.items + e0 + lane);
-        // the lane's voxel, exactly as process_unit places it
-        Lane ln;
-        ln.valid = vi >= 0;
-        const int64_t v = ln.valid ? vi : 0;
-        const int ix = (int)(v % P.nx), iy = (int)((v / P.nx) % P.ny), iz = (int)(v / ((int64_t)P.nx * P.ny));
-        const float rx = fmaf((float)ix, P.dx, P.ox), ry = fmaf((float)iy, P.dy, P.oy),
-                    rz = fmaf((float)iz, P.dz, P.oz);
-        const BeamDev& bm = P.beams[b];
-        const float sx = __ldg(&bm.src[0]), sy = __ldg(&bm.src[1]), sz = __ldg(&bm.src[2]);
-        const float sad = __ldg(&bm.sad);
-        ln.vx = rx - sx; ln.vy = ry - sy; ln.vz = rz - sz;
-        if (!ln.valid) ln.vx = __int_as_float(0x7fffffff);   // NaN: no pair test passes
-        const float zz = ln.vx * __ldg(&bm.ez[0]) + ln.vy * __ldg(&bm.ez[1]) + ln.vz * __ldg(&bm.ez[2]);
-        const float pa = ln.vx * __ldg(&bm.ex[0]) + ln.vy * __ldg(&bm.ex[1]) + ln.vz * __ldg(&bm.ex[2]);
-        const float pc = ln.vx * __ldg(&bm.ey[0]) + ln.vy * __ldg(&bm.ey[1]) + ln.vz * __ldg(&bm.ey[2]);
-        const int M = __ldg(&bm.M), N = __ldg(&bm.N), first = __ldg(&bm.first);
-        const float hfx = __ldg(&bm.half_fx), hfy = __ldg(&bm.half_fy);
-        const bool live = ln.valid && zz > 1e-3f;
-        const float sz_ = sad / zz;
-        const float ca = pa * sz_, cc = pc * sz_;
-        const float rw = live ? (P.roi * sz_ * __ldg(&bm.inv_cos_max)) * 1.0005f + 1e-3f : 0.f;
-        int nlo = INT_MAX, nhi = INT_MIN;
-        if (live) {
-            nlo = max(0, (int)ceilf((cc - rw + hfy) / P.by - 0.5f));
-            nhi = min(N - 1, (int)floorf((cc + rw + hfy) / P.by - 0.5f));
-        }
-        const int wnlo = __reduce_min_sync(0xffffffffu, nlo);
-        const int wnhi = __reduce_max_sync(0xffffffffu, nhi);
-        __syncwarp();
-        s_vox[warp][lane] = make_float4(ln.vx, ln.vy, ln.vz, 0.f);
-        int cnt = 0;
-        for (int nb0 = wnlo; nb0 <= wnhi; nb0 += kCountRows) {
-            const int nrows = min(kCountRows, wnhi - nb0 + 1);
-            // the union row ranges of this block of rows (widths, then their prefix)
-            for (int r = 0; r < nrows; ++r) {
-                const int n = nb0 + r;
-                const float dc_ = cc - (-hfy + (n + 0.5f) * P.by);
-                const float h2 = rw * rw - dc_ * dc_;
-                int mlo = INT_MAX, mhi = INT_MIN;
-                if (live && h2 >= 0.f) {
-                    const float hx = sqrtf(h2);
-                    mlo = max(0, (int)ceilf((ca - hx + hfx) / P.bx - 0.5f));
-                    mhi = min(M - 1, (int)floorf((ca + hx + hfx) / P.bx - 0.5f));
-                }
-                const int wmlo = __reduce_min_sync(0xffffffffu, mlo);
-                const int wmhi = __reduce_max_sync(0xffffffffu, mhi);
-                if (lane == 0) {
-                    s_lo[warp][r] = wmlo;
-                    s_pre[warp][r + 1] = wmhi >= wmlo ? wmhi - wmlo + 1 : 0;
-                }
-            }
-            __syncwarp();
-            if (lane == 0) {
-                s_pre[warp][0] = 0;
-                for (int r = 0; r < nrows; ++r) s_pre[warp][r + 1] += s_pre[warp][r];
-            }
-            __syncwarp();
-            const int tot = s_pre[warp][nrows];
-            for (int c0 = 0; c0 < tot; c0 += 32) {
-                const int j = c0 + lane;
-                const bool has = j < tot;
-                // the lane's beamlet: row r with s_pre[r] <= j < s_pre[r + 1]
-                int lo = 0, hi = nrows - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (s_pre[warp][mid] <= j) lo = mid;
-                    else hi = mid - 1;
-                }
-                const int m = s_lo[warp][lo] + (j - s_pre[warp][lo]);
-                const uint32_t i = has ? (uint32_t)(first + (nb0 + lo) * M + m) : (uint32_t)first;
-                const float4* src = reinterpret_cast<const float4*>(P.bl) + 4u * DC_GUARD(P, i, P.B, 5);
-                const float4 q0 = __ldg(src), q1 = __ldg(src + 1), q2 = __ldg(src + 2);
-#pragma unroll 4
-                for (int u = 0; u < 32; ++u) {
-                    const float4 vv = s_vox[warp][u];
-                    Lane lv;
-                    lv.vx = vv.x;
-                    lv.vy = vv.y;
-                    lv.vz = vv.z;
-                    const PairTest pt = pair_test(P, lv, q0, q1, q2);
-                    const unsigned ball = __ballot_sync(0xffffffffu, has && pt.in);
-                    if (lane == u) cnt += __popc(ball);
-                }
-            }
-            __syncwarp();
-        }
-        if (ln.valid) a.bcount[(size_t)b * V + v] = cnt;
-    }
-}
-
-// ---------------------------------------------------------------------------
 // Several plans in one persistent launch.  The plans are grouped by lateral
 // form (per-voxel or per-item factors); a group runs on the merged depth tables
 // when all its plans have them, else on the general tables (which every plan
@@ -1148,16 +1026,7 @@ cudaError_t launch_count(const dc_plan* p, int32_t* counts)
     DoseArgs a = make_args(p);
     cudaError_t e = cudaMemsetAsync(p->d_bcount, 0, sizeof(int32_t) * (size_t)p->n_beams * p->V, p->stream);
     if (e != cudaSuccess) return e;
-    {
-        int per_sm = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_t, kThreads, 0);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
-        if (e == cudaSuccess) e = cudaMemsetAsync(p->d_work + 1, 0, sizeof(int32_t), p->stream);
-        if (e != cudaSuccess) return e;
-        k_count_t<<<sms * (per_sm > 0 ? per_sm : 1), kThreads, 0, p->stream>>>(a);
-        count_launches(1);
-        e = cudaGetLastError();
-    }
+    e = run<kCount, 1>(p, a);
     if (e != cudaSuccess) return e;
     k_rowsum<<<grid_for(p->V), 256, 0, p->stream>>>(p->d_bcount, p->n_beams, p->V, counts);
     count_launches(1);
