@@ -101,7 +101,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="the step only (quick runs)")
     ap.add_argument("--scale", type=float, default=1.0, help="grid scale of the thorax plan")
-    ap.add_argument("--profile", default=None, choices=["dose", "fill", "fused", "mlp", "prep", "spmm", "step", "table1", "train"],
+    ap.add_argument("--profile", default=None, choices=["count", "dose", "fill", "fused", "mlp", "prep", "spmm", "step", "table1", "train"],
                     help="small fixed run of one stage for profiler captures (prints no bench line)")
     return ap.parse_args()
 
@@ -180,6 +180,9 @@ def run_profile(args):
             dc.dc_fspb_dose(plan, flu_d, dose_d)
         elif args.profile == "fill":
             dc.dc_fspb_dose_matrix(plan, dc.DC_F32, rowptr, cols, vals)
+        elif args.profile == "count":
+            dc.dc_fspb_set_density(plan, rho_d)      # forgets the pattern: the next call counts again
+            dc.dc_fspb_pair_count(plan)
         else:
             dc.dc_fspb_set_density(plan, rho_d)
     torch.cuda.synchronize()
