@@ -623,6 +623,164 @@ __global__ void __launch_bounds__(kThreads, min_ctas<MODE, NF>()) k_pairs(const 
 }
 
 // ---------------------------------------------------------------------------
+// Pair counts of the matrix pattern, two voxels per lane: a warp takes two
+// consecutive work units of one beam (lane l holds entry l of each) and walks
+// the union of their windows; each staged beamlet record is tested against
+// both of the lane's voxels, so the record reads and the loop's bookkeeping
+// are shared by 64 pair tests instead of 32.  The voxels, the windows and
+// pair_test are computed as process_unit computes them, so the counts are
+// exactly the fill's entries per (voxel, beam).  A pair of units that
+// straddles two beams is taken one unit at a time.
+struct CountVoxel {
+    Lane ln;
+    bool live;
+    float ca, cc, rw;
+    int64_t v;
+};
+
+__device__ __forceinline__ CountVoxel count_voxel(const PlanView& P, const BeamDev& bm, int32_t vi, float sad)
+{
+    CountVoxel c;
+    c.ln.valid = vi >= 0;
+    c.v = c.ln.valid ? vi : 0;
+    const int ix = (int)(c.v % P.nx), iy = (int)((c.v / P.nx) % P.ny), iz = (int)(c.v / ((int64_t)P.nx * P.ny));
+    const float rx = fmaf((float)ix, P.dx, P.ox), ry = fmaf((float)iy, P.dy, P.oy), rz = fmaf((float)iz, P.dz, P.oz);
+    const float sx = __ldg(&bm.src[0]), sy = __ldg(&bm.src[1]), sz = __ldg(&bm.src[2]);
+    c.ln.vx = rx - sx;
+    c.ln.vy = ry - sy;
+    c.ln.vz = rz - sz;
+    if (!c.ln.valid) c.ln.vx = __int_as_float(0x7fffffff);   // NaN: no pair test passes
+    const float zz = c.ln.vx * __ldg(&bm.ez[0]) + c.ln.vy * __ldg(&bm.ez[1]) + c.ln.vz * __ldg(&bm.ez[2]);
+    const float pa = c.ln.vx * __ldg(&bm.ex[0]) + c.ln.vy * __ldg(&bm.ex[1]) + c.ln.vz * __ldg(&bm.ex[2]);
+    const float pc = c.ln.vx * __ldg(&bm.ey[0]) + c.ln.vy * __ldg(&bm.ey[1]) + c.ln.vz * __ldg(&bm.ey[2]);
+    c.live = c.ln.valid && zz > 1e-3f;
+    const float sz_ = sad / zz;
+    c.ca = pa * sz_;
+    c.cc = pc * sz_;
+    c.rw = c.live ? (P.roi * sz_ * __ldg(&bm.inv_cos_max)) * 1.0005f + 1e-3f : 0.f;
+    return c;
+}
+
+// The voxel's range of beamlet rows, and of columns in row n (empty: lo > hi).
+__device__ __forceinline__ void count_rows(const PlanView& P, const CountVoxel& c, int N, float hfy, int& lo, int& hi)
+{
+    lo = INT_MAX;
+    hi = INT_MIN;
+    if (c.live) {
+        lo = max(0, (int)ceilf((c.cc - c.rw + hfy) / P.by - 0.5f));
+        hi = min(N - 1, (int)floorf((c.cc + c.rw + hfy) / P.by - 0.5f));
+    }
+}
+
+__device__ __forceinline__ void count_cols(const PlanView& P, const CountVoxel& c, int n, int M, float hfx, float hfy,
+                                           int& lo, int& hi)
+{
+    const float dc_ = c.cc - (-hfy + (n + 0.5f) * P.by);
+    const float h2 = c.rw * c.rw - dc_ * dc_;
+    lo = INT_MAX;
+    hi = INT_MIN;
+    if (c.live && h2 >= 0.f) {
+        const float hx = sqrtf(h2);
+        lo = max(0, (int)ceilf((c.ca - hx + hfx) / P.bx - 0.5f));
+        hi = min(M - 1, (int)floorf((c.ca + hx + hfx) / P.bx - 0.5f));
+    }
+}
+
+template <int NV>
+__device__ __forceinline__ void count_units(const DoseArgs& a, const int64_t e0, const int b, float4* srow, int lane)
+{
+    const PlanView& P = a.P;
+    const int64_t V = (int64_t)P.nx * P.ny * P.nz;
+    const BeamDev& bm = P.beams[b];
+    const float sad = __ldg(&bm.sad);
+    const int M = __ldg(&bm.M), N = __ldg(&bm.N), first = __ldg(&bm.first);
+    const float hfx = __ldg(&bm.half_fx), hfy = __ldg(&bm.half_fy);
+    CountVoxel c[NV];
+    int nlo = INT_MAX, nhi = INT_MIN;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        c[k] = count_voxel(P, bm, __ldg(a.items + e0 + 32 * k + lane), sad);
+        int lo, hi;
+        count_rows(P, c[k], N, hfy, lo, hi);
+        nlo = min(nlo, lo);
+        nhi = max(nhi, hi);
+    }
+    int cnt[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) cnt[k] = 0;
+    const int wnlo = __reduce_min_sync(0xffffffffu, nlo);
+    const int wnhi = __reduce_max_sync(0xffffffffu, nhi);
+    for (int n = wnlo; n <= wnhi; ++n) {
+        int mlo = INT_MAX, mhi = INT_MIN;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            int lo, hi;
+            count_cols(P, c[k], n, M, hfx, hfy, lo, hi);
+            mlo = min(mlo, lo);
+            mhi = max(mhi, hi);
+        }
+        const int wmlo = __reduce_min_sync(0xffffffffu, mlo);
+        const int wmhi = __reduce_max_sync(0xffffffffu, mhi);
+        const uint32_t row = (uint32_t)(first + n * M);
+        for (int m0 = wmlo; m0 <= wmhi; m0 += 32) {
+            const int m1 = min(wmhi, m0 + 31);
+            __syncwarp();
+            if (m0 + lane <= m1) {
+                const uint32_t ib = DC_GUARD(P, row + (uint32_t)(m0 + lane), P.B, 5);
+                const float4* src = reinterpret_cast<const float4*>(P.bl) + 4u * ib;
+                srow[3 * lane] = __ldg(src);
+                srow[3 * lane + 1] = __ldg(src + 1);
+                srow[3 * lane + 2] = __ldg(src + 2);
+            }
+            __syncwarp();
+#pragma unroll 2
+            for (int m = m0; m <= m1; ++m) {
+                const float4* rq = srow + 3 * (m - m0);
+                const float4 q0 = rq[0], q1 = rq[1], q2 = rq[2];
+#pragma unroll
+                for (int k = 0; k < NV; ++k) cnt[k] += pair_test(P, c[k].ln, q0, q1, q2).in ? 1 : 0;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+        if (c[k].ln.valid) a.bcount[(size_t)b * V + c[k].v] = cnt[k];
+}
+
+__global__ void __launch_bounds__(kThreads, 4) k_count2(const DoseArgs a)
+{
+    __shared__ int64_t s_base[kMaxBeams + 1];
+    __shared__ float4 s_row[kWarps][3 * 32];
+    const PlanView& P = a.P;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int q = threadIdx.x; q <= P.n_beams; q += blockDim.x) s_base[q] = a.base[q];
+    __syncthreads();
+    const int units = a.work[0];
+    const int pairs = (units + 1) / 2;
+    for (;;) {
+        int w = 0;
+        if (lane == 0) w = atomicAdd(a.work + 1, 1);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if (w >= pairs) break;
+        const int u0 = 2 * w;
+        const int64_t e0 = (int64_t)DC_GUARD(P, u0, (s_base[P.n_beams] + 31) / 32, 4) * 32;
+        int b = 0;
+        while (b + 1 < P.n_beams && s_base[b + 1] <= e0) ++b;
+        const bool two = u0 + 1 < units && e0 + 32 < s_base[b + 1];   // the next unit is in the same beam
+        if (two) {
+            count_units<2>(a, e0, b, s_row[warp], lane);
+        } else {
+            count_units<1>(a, e0, b, s_row[warp], lane);
+            if (u0 + 1 < units) {
+                int b1 = b;
+                while (b1 + 1 < P.n_beams && s_base[b1 + 1] <= e0 + 32) ++b1;
+                count_units<1>(a, e0 + 32, b1, s_row[warp], lane);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Several plans in one persistent launch.  The plans are grouped by lateral
 // form (per-voxel or per-item factors); a group runs on the merged depth tables
 // when all its plans have them, else on the general tables (which every plan
@@ -1026,7 +1184,16 @@ cudaError_t launch_count(const dc_plan* p, int32_t* counts)
     DoseArgs a = make_args(p);
     cudaError_t e = cudaMemsetAsync(p->d_bcount, 0, sizeof(int32_t) * (size_t)p->n_beams * p->V, p->stream);
     if (e != cudaSuccess) return e;
-    e = run<kCount, 1>(p, a);
+    {
+        int per_sm = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count2, kThreads, 0);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+        if (e == cudaSuccess) e = cudaMemsetAsync(p->d_work + 1, 0, sizeof(int32_t), p->stream);
+        if (e != cudaSuccess) return e;
+        k_count2<<<sms * (per_sm > 0 ? per_sm : 1), kThreads, 0, p->stream>>>(a);
+        count_launches(1);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) return e;
     k_rowsum<<<grid_for(p->V), 256, 0, p->stream>>>(p->d_bcount, p->n_beams, p->V, counts);
     count_launches(1);
