@@ -16,6 +16,7 @@
 // exponentials); every table stores value + slope so an interpolation is one
 // load and one fma; eq. (4) is evaluated without branches.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <mutex>
@@ -623,13 +624,13 @@ __global__ void __launch_bounds__(kThreads, min_ctas<MODE, NF>()) k_pairs(const 
 }
 
 // ---------------------------------------------------------------------------
-// Pair counts of the matrix pattern, two voxels per lane: a warp takes two
+// Pair counts of the matrix pattern, several voxels per lane: a warp takes NV
 // consecutive work units of one beam (lane l holds entry l of each) and walks
 // the union of their windows; each staged beamlet record is tested against
-// both of the lane's voxels, so the record reads and the loop's bookkeeping
-// are shared by 64 pair tests instead of 32.  The voxels, the windows and
+// all of the lane's voxels, so the record reads and the loop's bookkeeping
+// are shared by 32 NV pair tests instead of 32.  The voxels, the windows and
 // pair_test are computed as process_unit computes them, so the counts are
-// exactly the fill's entries per (voxel, beam).  A pair of units that
+// exactly the fill's entries per (voxel, beam).  A group of units that
 // straddles two beams is taken one unit at a time.
 struct CountVoxel {
     Lane ln;
@@ -747,7 +748,8 @@ __device__ __forceinline__ void count_units(const DoseArgs& a, const int64_t e0,
         if (c[k].ln.valid) a.bcount[(size_t)b * V + c[k].v] = cnt[k];
 }
 
-__global__ void __launch_bounds__(kThreads, 4) k_count2(const DoseArgs a)
+template <int NV>
+__global__ void __launch_bounds__(kThreads, NV <= 2 ? 4 : (NV == 3 ? 3 : 2)) k_count_units(const DoseArgs a)
 {
     __shared__ int64_t s_base[kMaxBeams + 1];
     __shared__ float4 s_row[kWarps][3 * 32];
@@ -756,29 +758,34 @@ __global__ void __launch_bounds__(kThreads, 4) k_count2(const DoseArgs a)
     for (int q = threadIdx.x; q <= P.n_beams; q += blockDim.x) s_base[q] = a.base[q];
     __syncthreads();
     const int units = a.work[0];
-    const int pairs = (units + 1) / 2;
+    const int groups = (units + NV - 1) / NV;
     for (;;) {
         int w = 0;
         if (lane == 0) w = atomicAdd(a.work + 1, 1);
         w = __shfl_sync(0xffffffffu, w, 0);
-        if (w >= pairs) break;
-        const int u0 = 2 * w;
+        if (w >= groups) break;
+        const int u0 = NV * w;
         const int64_t e0 = (int64_t)DC_GUARD(P, u0, (s_base[P.n_beams] + 31) / 32, 4) * 32;
         int b = 0;
         while (b + 1 < P.n_beams && s_base[b + 1] <= e0) ++b;
-        const bool two = u0 + 1 < units && e0 + 32 < s_base[b + 1];   // the next unit is in the same beam
-        if (two) {
-            count_units<2>(a, e0, b, s_row[warp], lane);
+        // all NV units in this beam: together; else one at a time
+        if (u0 + NV <= units && e0 + 32 * NV <= s_base[b + 1]) {
+            count_units<NV>(a, e0, b, s_row[warp], lane);
         } else {
-            count_units<1>(a, e0, b, s_row[warp], lane);
-            if (u0 + 1 < units) {
-                int b1 = b;
-                while (b1 + 1 < P.n_beams && s_base[b1 + 1] <= e0 + 32) ++b1;
-                count_units<1>(a, e0 + 32, b1, s_row[warp], lane);
+            for (int k = 0; k < NV && u0 + k < units; ++k) {
+                const int64_t ek = e0 + 32 * k;
+                int bk = b;
+                while (bk + 1 < P.n_beams && s_base[bk + 1] <= ek) ++bk;
+                count_units<1>(a, ek, bk, s_row[warp], lane);
             }
         }
     }
 }
+
+// voxels per lane in the pair-count pass (measured on thorax9: 2 -> 0.722 ms,
+// 3 -> 0.725 ms, 4 -> 0.796 ms; one voxel per lane, the pair kernel's count
+// mode, took 0.847 ms)
+constexpr int kCountVoxels = 2;
 
 // ---------------------------------------------------------------------------
 // Several plans in one persistent launch.  The plans are grouped by lateral
@@ -1185,12 +1192,13 @@ cudaError_t launch_count(const dc_plan* p, int32_t* counts)
     cudaError_t e = cudaMemsetAsync(p->d_bcount, 0, sizeof(int32_t) * (size_t)p->n_beams * p->V, p->stream);
     if (e != cudaSuccess) return e;
     {
+        auto kern = k_count_units<kCountVoxels>;
         int per_sm = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count2, kThreads, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
         if (e == cudaSuccess) e = cudaMemsetAsync(p->d_work + 1, 0, sizeof(int32_t), p->stream);
         if (e != cudaSuccess) return e;
-        k_count2<<<sms * (per_sm > 0 ? per_sm : 1), kThreads, 0, p->stream>>>(a);
+        kern<<<sms * (per_sm > 0 ? per_sm : 1), kThreads, 0, p->stream>>>(a);
         count_launches(1);
         e = cudaGetLastError();
     }
