@@ -204,11 +204,7 @@ dc_status dc_fspb_pair_count(dc_plan* plan, int64_t* pairs);
  *   rowptr [V + 1] int64, cols [nnz] int32, vals [nnz] float32 (value_dtype
  *   DC_F32) or bfloat16 bits (DC_BF16, round-to-nearest-even of the FP32 value);
  *   nnz = dc_fspb_pair_count().  All three buffers are caller-owned, and all
- *   host or all device memory per `flags`.  Host cols and vals that are
- *   page-locked and mapped for the device (cudaHostAlloc, or cudaHostRegister
- *   with cudaHostRegisterMapped) are written by the fill kernel directly, over
- *   the host link, without a device copy; other host memory is staged on the
- *   device and copied.  Synchronises before returning to host buffers.
+ *   host or all device memory per `flags`.
  */
 dc_status dc_fspb_dose_matrix(dc_plan* plan, int32_t value_dtype, int64_t* rowptr, int32_t* cols,
                               void* vals, uint32_t flags);

@@ -742,17 +742,8 @@ static dc_status matrix_impl(dc_plan* plan, int32_t value_dtype, int64_t* rowptr
         DC_CUDA(launch_fill(plan, plan->d_rowptr, cols, vals, value_dtype, fluence, dose));
         return DC_OK;
     }
-    // page-locked host buffers that the device can address (cudaHostAlloc,
-    // cudaHostRegister with mapping): the fill writes the columns and values
-    // straight into them over the host link, with no device copy and no
-    // separate transfer; other host memory goes through device staging
-    int32_t* hcols = nullptr;
-    void* hvals = nullptr;
-    const bool direct = cudaHostGetDevicePointer(reinterpret_cast<void**>(&hcols), cols, 0) == cudaSuccess &&
-                        cudaHostGetDevicePointer(&hvals, vals, 0) == cudaSuccess;
-    if (!direct) (void)cudaGetLastError();   // the probe's error is not the call's
     const size_t need = nnz * sizeof(int32_t) + 16;
-    if (!direct && need > plan->mstage_bytes) {
+    if (need > plan->mstage_bytes) {
         if (plan->d_mcols) cudaFree(plan->d_mcols);
         if (plan->d_mvals) cudaFree(plan->d_mvals);
         plan->d_mcols = nullptr;
@@ -768,16 +759,16 @@ static dc_status matrix_impl(dc_plan* plan, int32_t value_dtype, int64_t* rowptr
         DC_CUDA(cudaMemcpyAsync(plan->d_fluence, fluence, plan->B * sizeof(float), cudaMemcpyHostToDevice,
                                 plan->stream));
     }
-    int32_t* dcols = direct ? hcols : plan->d_mcols;
-    void* dvals = direct ? hvals : plan->d_mvals;
+    int32_t* dcols = plan->d_mcols;
+    void* dvals = plan->d_mvals;
     cudaError_t e = launch_fill(plan, plan->d_rowptr, dcols, dvals, value_dtype, fluence ? plan->d_fluence : nullptr,
                                 fluence ? plan->d_dose : nullptr);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(rowptr, plan->d_rowptr, (plan->V + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost,
                             plan->stream);
-    if (e == cudaSuccess && !direct)
+    if (e == cudaSuccess)
         e = cudaMemcpyAsync(cols, dcols, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost, plan->stream);
-    if (e == cudaSuccess && !direct) e = cudaMemcpyAsync(vals, dvals, nnz * vsz, cudaMemcpyDeviceToHost, plan->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(vals, dvals, nnz * vsz, cudaMemcpyDeviceToHost, plan->stream);
     if (e == cudaSuccess && fluence)
         e = cudaMemcpyAsync(dose, plan->d_dose, plan->V * sizeof(float), cudaMemcpyDeviceToHost, plan->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(plan->stream);
