@@ -7,7 +7,8 @@
   to one lane for rays with more segments per piece than its buffer holds
   (rays of ~1000 voxel crossings here, FP64 sums: rays > 40 cm);
 * dc_fspb_dose_and_matrix fills the matrix and accumulates eq. (1) in one
-  pass: both results bit-identical to the separate calls;
+  pass: both results bit-identical to the separate calls, into device
+  buffers, pageable host buffers and page-locked host buffers;
 * the SpMM numbers its tile columns in 4 x 4 beamlet patches, including
   beamlet grids whose sides are not multiples of 4, and a one-beam plan zeroes
   the output rows of voxels that are in no beam list.
@@ -84,6 +85,22 @@ def test_dose_and_matrix_in_one_pass(dc, value_dtype):
     assert np.array_equal(d_dev.cpu().numpy(), dose_a)
     assert np.array_equal(r_dev.cpu().numpy(), ra) and np.array_equal(c_dev.cpu().numpy(), ca)
     assert np.array_equal(v_dev.cpu().numpy().view(va.dtype), va)
+    # page-locked host buffers: the same dose and matrix, and the guard cells
+    # past nnz stay untouched
+    pin = lambda n, dt: torch.empty(n, dtype=dt, pin_memory=True).numpy()
+    d_h = pin(p.grid.n_voxels, torch.float32).reshape(p.grid.shape)
+    r_h = pin(p.grid.n_voxels + 1, torch.int64)
+    c_h = pin(nnz + 8, torch.int32)
+    v_h = pin(nnz + 8, vt)
+    c_h[nnz:] = -7
+    v_h.view(np.uint8)[:] = 0xAB
+    guard_v = v_h[nnz:].copy()
+    f2c = np.ascontiguousarray(f2)
+    dc.dc_fspb_dose_and_matrix(b, f2c, d_h, value_dtype, r_h, c_h, v_h.view(va.dtype))
+    assert np.array_equal(d_h, dose_a)
+    assert np.array_equal(r_h, ra) and np.array_equal(c_h[:nnz], ca)
+    assert np.array_equal(v_h[:nnz].view(va.dtype), va)
+    assert np.all(c_h[nnz:] == -7) and np.array_equal(v_h[nnz:], guard_v)
 
 
 def test_long_rays_take_the_single_lane_trace(dc, oracle_mod):
