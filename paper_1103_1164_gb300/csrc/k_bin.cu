@@ -109,7 +109,10 @@ __global__ void __launch_bounds__(256) k_bin_hist(const PlanView P, const BinGeo
         const int64_t v = v0 + lane;
         int cell = -1;
         if (v < V) {
-            const int ix = (int)(v % P.nx), iy = (int)((v / P.nx) % P.ny), iz = (int)(v / ((int64_t)P.nx * P.ny));
+            // voxel indices fit 32 bits (the voxel lists hold int32): 32-bit division
+            const uint32_t u = (uint32_t)v, nx = (uint32_t)P.nx, ny = (uint32_t)P.ny;
+            const uint32_t q = u / nx;
+            const int ix = (int)(u - q * nx), iy = (int)(q % ny), iz = (int)(q / ny);
             cell = voxel_cell(g, bm, bounds + (size_t)b * tiles_max, P.R2, fmaf((float)ix, P.dx, P.ox),
                               fmaf((float)iy, P.dy, P.oy), fmaf((float)iz, P.dz, P.oz));
             cellof[(size_t)b * V + v] = cell;
