@@ -75,7 +75,9 @@ __device__ __forceinline__ float rho_nearest(const PlanView& P, float px, float 
 
 __device__ __forceinline__ void voxel_centre(const PlanView& P, int64_t v, float& rx, float& ry, float& rz)
 {
-    const int ix = (int)(v % P.nx), iy = (int)((v / P.nx) % P.ny), iz = (int)(v / ((int64_t)P.nx * P.ny));
+    // plan grids hold at most 2^31 voxels: 32-bit division
+    const uint32_t u = (uint32_t)v, q = u / (uint32_t)P.nx;
+    const int ix = (int)(u - q * (uint32_t)P.nx), iy = (int)(q % (uint32_t)P.ny), iz = (int)(q / (uint32_t)P.ny);
     rx = fmaf((float)ix, P.dx, P.ox);
     ry = fmaf((float)iy, P.dy, P.oy);
     rz = fmaf((float)iz, P.dz, P.oz);

@@ -26,9 +26,11 @@ __global__ void __launch_bounds__(256) k_smooth_axis(const SmoothArgs a)
     int64_t V = (int64_t)a.nx * a.ny * a.nz;
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V;
          v += (int64_t)gridDim.x * blockDim.x) {
-        int i = (int)(v % a.nx);
-        int j = (int)((v / a.nx) % a.ny);
-        int k = (int)(v / ((int64_t)a.nx * a.ny));
+        // plan grids hold at most 2^31 voxels: 32-bit division
+        const uint32_t u = (uint32_t)v, qx = u / (uint32_t)a.nx;
+        int i = (int)(u - qx * (uint32_t)a.nx);
+        int j = (int)(qx % (uint32_t)a.ny);
+        int k = (int)(qx / (uint32_t)a.ny);
         float s = 0.f;
         for (int q = -a.r; q <= a.r; ++q) {
             int ii = i, jj = j, kk = k;
