@@ -120,7 +120,7 @@ static void free_plan(dc_plan* p)
                     p->d_bin, p->d_bounds, p->d_cellof, p->d_hist, p->d_nitems, p->d_bstart, p->d_bscan,
                     p->d_base, p->d_work,
                     p->d_items, p->d_part, p->d_bcount, p->d_sp_fp, p->d_sp_p, p->d_err,
-                    p->d_lfac, p->d_mlp_frag, p->d_mlp_bias, p->d_nfall, p->d_leaf, p->d_chk};
+                    p->d_lfac, p->d_mlp_frag, p->d_mlp_bias, p->d_nfall, p->d_leaf, p->d_chk, p->d_grad};
     for (void* b : bufs)
         if (b) cudaFree(b);
     p->spmm_free();
@@ -830,8 +830,10 @@ dc_status dc_fspb_dose_vjp(dc_plan* plan, const float* fluence, const float* wei
     // gradient block
     dc_status s = ensure_staging(plan, plan->B, plan->V);
     if (s != DC_OK) return s;
-    float* d_g = nullptr;
-    DC_CUDA(dalloc(&d_g, nw + nd + 2));
+    if (!plan->d_grad) {   // the plan's gradient block, kept for later calls
+        DC_CUDA(dalloc(&plan->d_grad, nw + nd + 2));
+    }
+    float* d_g = plan->d_grad;
     cudaError_t e = cudaMemcpyAsync(plan->d_fluence, fluence, plan->B * sizeof(float), cudaMemcpyHostToDevice,
                                     plan->stream);
     if (e == cudaSuccess)
@@ -843,7 +845,6 @@ dc_status dc_fspb_dose_vjp(dc_plan* plan, const float* fluence, const float* wei
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(g_corr, d_g + nw + nd, 2 * sizeof(float), cudaMemcpyDeviceToHost, plan->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(plan->stream);
-    cudaFree(d_g);
     if (e != cudaSuccess) return cuda_fail(e, "dc_fspb_dose_vjp");
     return DC_OK;
 }

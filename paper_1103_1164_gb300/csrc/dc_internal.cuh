@@ -102,6 +102,7 @@ struct dc_plan {
     size_t sp_p_cap = 0;
     int32_t* d_err = nullptr;        // device status word of bounded waits
     int32_t* d_chk = nullptr;        // status word of the DC_BOUNDS_CHECK build
+    float* d_grad = nullptr;         // dc_fspb_dose_vjp with host buffers: the gradients on the device
     void spmm_free()
     {
         void* bufs[] = {d_sp_rbfirst, d_sp_first, d_sp_nchunk, d_sp_off, d_sp_kb, d_sp_tiles, d_sp_inv, d_sp_zero};
