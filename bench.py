@@ -653,7 +653,11 @@ def run_forms(args, dc, torch, stream, peaks, k=64):
         want = oracle_multi_fluence(p1, F.cpu().numpy())
         oracle_err = {"bf16_spmm": column_error(Y.cpu().numpy(), want),
                       "plain_fp32": column_error(dose.t().cpu().numpy(), want)}
-    bytes_alg = chunks * 4096 + chunks * 4 + plan.n_voxels * k * 4 + plan.n_beamlets * k * 4
+    # SURVEY 8(d)'s algorithmic bytes of the SpMM: the BF16 matrix (2 B value + 4 B column per
+    # nonzero), the FP32 output, the BF16 fluences; the tile bytes the kernel actually streams
+    # (128 x 16 BF16 tiles with their zero fill, tile indices, FP32 fluences) beside it
+    bytes_alg = pairs * 6 + plan.n_voxels * k * 4 + plan.n_beamlets * k * 2
+    bytes_tiles = chunks * 4096 + chunks * 4 + plan.n_voxels * k * 4 + plan.n_beamlets * k * 4
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     return {"workload": f"slab64 64^3 @0.25cm, 1 beam, {plan.n_beamlets} beamlets, ROI 3 cm, {k} fluences U[0,1]",
             "pairs": pairs,
@@ -664,7 +668,9 @@ def run_forms(args, dc, torch, stream, peaks, k=64):
                           "roofline": {"bound": "hbm", "achieved": bytes_alg / (t_spmm * 1e-3) / 1e9,
                                        "peak": hbm, "unit": "GB/s",
                                        "frac": bytes_alg / (t_spmm * 1e-3) / 1e9 / hbm,
-                                       "bytes": bytes_alg},
+                                       "bytes": bytes_alg,
+                                       "tile_bytes": bytes_tiles,
+                                       "tile_bytes_frac": bytes_tiles / (t_spmm * 1e-3) / 1e9 / hbm},
                           "max_err_vs_fp32_over_colmax": err},
             "max_err_vs_fp64_oracle_over_colmax": oracle_err,
             "speedup_bf16_over_fp32": t_plain / t_spmm}
