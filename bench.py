@@ -653,7 +653,7 @@ def run_forms(args, dc, torch, stream, peaks, k=64):
         want = oracle_multi_fluence(p1, F.cpu().numpy())
         oracle_err = {"bf16_spmm": column_error(Y.cpu().numpy(), want),
                       "plain_fp32": column_error(dose.t().cpu().numpy(), want)}
-    # SURVEY 8(d)'s algorithmic bytes of the SpMM: the BF16 matrix (2 B value + 4 B column per
+    # the SpMM's algorithmic bytes: the BF16 matrix (2 B value + 4 B column per
     # nonzero), the FP32 output, the BF16 fluences; the tile bytes the kernel actually streams
     # (128 x 16 BF16 tiles with their zero fill, tile indices, FP32 fluences) beside it
     bytes_alg = pairs * 6 + plan.n_voxels * k * 4 + plan.n_beamlets * k * 2
