@@ -700,7 +700,7 @@ def run_surrogate_form(args, dc, torch, stream, peaks, k=64):
     densities) samples from 200 random slab/sphere phantoms, trained with the
     library's kernels, then the slab plan's 64-fluence dose with the network's
     correction and the BF16 tensor-core SpMM, against the plain FP32 form (axis
-    stencils, direct evaluation), which is also the judge of its error."""
+    stencils, direct evaluation), which is also the reference for its error."""
     from paper_1103_1164_gb300 import surrogate, synth
     net = trained_network(dc)
     params, loss, held, n_tr, t_gen, t_train = (net[k] for k in ("params", "loss", "held", "n_train",

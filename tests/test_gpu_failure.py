@@ -58,7 +58,7 @@ def test_allocation_failure_reports_enomem_and_frees_everything(dc):
     # must report DC_ENOMEM and release what it had allocated, for every N
     import torch
     p = synth.small_plan(90, n=(16, 14, 12), vox=0.3, n_beams=2)
-    dc.dc_fspb_destroy(dc.dc_fspb_create_from(p))       # first-use allocations of the driver
+    dc.dc_fspb_destroy(dc.dc_fspb_create_from(p))       # the CUDA runtime's first-use allocations
     torch.cuda.synchronize()
     free0 = torch.cuda.mem_get_info()[0]
     failed = 0
