@@ -314,16 +314,17 @@ __device__ __forceinline__ void dens_bins(const PlanView& P, float r, int& j, fl
 // takes one lane's run at a time, 8 entries (one 32-byte sector of the column
 // array once the run is aligned) per pass: first the leading 8 entries of all
 // 32 runs, then entries 8..15 of the runs that are longer, four runs per pass.
-// Streaming stores: the matrix is written once and should not evict the depth
-// tables from L2.  Each staged entry is (column, value bits).
+// Plain write-back stores: with evict-first (streaming) stores the thorax9
+// fill took 4.58 ms, with these 4.40 ms, for the same matrix.  Each staged
+// entry is (column, value bits).
 template <typename VT>
 __device__ __forceinline__ void store_entry(int32_t* cols, VT* vals, int64_t g, int2 e)
 {
-    __stcs(cols + g, e.x);
+    cols[g] = e.x;
     if (sizeof(VT) == 2)
-        __stcs(reinterpret_cast<__nv_bfloat16*>(vals) + g, __float2bfloat16_rn(__int_as_float(e.y)));
+        reinterpret_cast<__nv_bfloat16*>(vals)[g] = __float2bfloat16_rn(__int_as_float(e.y));
     else
-        __stcs(reinterpret_cast<float*>(vals) + g, __int_as_float(e.y));
+        reinterpret_cast<float*>(vals)[g] = __int_as_float(e.y);
 }
 
 template <typename VT>
