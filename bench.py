@@ -1059,7 +1059,8 @@ def run_leaf_form(args, dc, torch, stream, flush, n_cp=128):
 
 def run_batch_form(args, dc, torch, stream, peak_pairs):
     """The 16 uneven head-and-neck plans (grids 112 x 112 x 64 to 256 x 256 x 192
-    at 0.2-0.3 cm, 5-9 beams, 0.25 cm beamlets, ROI 5 cm): one persistent
+    at 0.2-0.3 cm, 5-9 beams, 0.25 cm beamlets, ROI 5 cm), each plan's binning
+    cell autotuned at set-up: one persistent
     graph-replayed launch over all plans (dc_fspb_batch_run) against the plans'
     own launches one after another, dose only and whole plans (density-dependent
     steps + dose), in the paper's lateral form.  Then the cross-form
@@ -1076,6 +1077,9 @@ def run_batch_form(args, dc, torch, stream, peak_pairs):
     flus = [torch.from_numpy(p.fluence).cuda() for p in inputs]
     plans = [dc.dc_fspb_create_from(p, stream=stream.cuda_stream, device_density=r) for p, r in zip(inputs, rhos)]
     doses = [torch.empty(pl.n_voxels, device="cuda") for pl in plans]
+    t0 = time.perf_counter()
+    cells = [dc.dc_fspb_autotune(pl, f)[:2] for pl, f in zip(plans, flus)]   # plan set-up, untimed
+    t_cells = time.perf_counter() - t0
     pairs = [dc.dc_fspb_pair_count(pl) for pl in plans]
     batch = dc.dc_fspb_batch_create(plans, stream=stream.cuda_stream)
     for j, pl in enumerate(plans):
@@ -1116,9 +1120,13 @@ def run_batch_form(args, dc, torch, stream, peak_pairs):
                        f"{sum(len(p.beams) for p in inputs)} beams, {sum(pl.n_beamlets for pl in plans)} "
                        f"beamlets (0.25 cm), ROI 5 cm, density correction on",
            "pairs": total, "generate_s": t_gen,
+           "bev_cells_cm": {"autotune_s": t_cells,
+                            "chosen": sorted({f"{t:g}x{sl:g}" for t, sl in cells})},
            "batch_graph": {"dose_ms": t_batch, "full_plans_ms": t_full, "evals_per_s": ach,
                            "kernels_per_replay": launches,
-                           "autotuned_ctas_per_sm": 4 + variant, "autotune_ms": tune_ms,
+                           "autotuned_variant": ("persistent, 4 CTAs per SM", "persistent, 5 CTAs per SM",
+                                                 "per-plan launches in the graph")[variant],
+                           "autotune_ms": tune_ms,
                            "roofline": {"bound": "alu", "achieved": ach / 1e9, "peak": peak_pairs / 1e9,
                                         "unit": "Gpair/s", "frac": ach / peak_pairs}},
            "sequential_plans": {"dose_ms": t_seq, "full_plans_ms": t_seq_full,

@@ -438,7 +438,9 @@ dc_status dc_mlp_predict(const float* params, const float* X, int32_t n, float* 
  * Eq. (1) for n plans of uneven grids and beam counts (one fluence vector per
  * plan) as ONE persistent launch of the pair kernel over the work units of all
  * plans (units of the costliest plans first), followed by one launch of the
- * per-plan beam sums, replayed from a CUDA graph built on the first run.  With
+ * per-plan beam sums, replayed from a CUDA graph built on the first run
+ * (dc_fspb_batch_autotune may instead put the plans' own dose launches, one
+ * after another, into the graph).  With
  * DC_BATCH_DENSITY the graph also holds each plan's density-dependent work
  * (Algorithm A1 steps 1-6, the beam's-eye-view binning, the lateral factors of
  * step 11) from the plan's resident density, one graph branch per plan, so a
@@ -479,13 +481,22 @@ dc_status dc_fspb_batch_run(dc_batch* batch, uint32_t flags);
 dc_status dc_fspb_batch_dose(dc_batch* batch, const float* const* fluence, float* const* dose, uint32_t flags);
 
 /*
- * Autotuner of the batch's pair kernel: replays the dose graph (twice, after a
- * warm-up) for each register budget of the persistent kernel (sized for 4 or
- * for 5 CTAs per SM) and keeps the faster; *variant (0 or 1) and *ms (mean
- * replay time) may be NULL.  Runs the batch (its dose buffers are written) and
- * synchronises.  Errors: DC_EINVAL, DC_ECUDA.
+ * Autotuner of the batch's dose graph: replays it (twice, after a warm-up) for
+ * each form of the pair work and keeps the fastest: the persistent multi-plan
+ * kernel with the register budget for 4 CTAs per SM (variant 0) or for 5
+ * (variant 1), or the plans' own dose launches one after another inside the
+ * graph (variant 2: each pair kernel specialised for its plan alone, which
+ * pays off when every plan fills the GPU by itself).  *variant and *ms (mean
+ * replay time) may be NULL.  The doses are the same in every variant.  Runs
+ * the batch (its dose buffers are written) and synchronises.
+ * Errors: DC_EINVAL, DC_ECUDA.
  */
 dc_status dc_fspb_batch_autotune(dc_batch* batch, int32_t* variant, float* ms);
+
+/* Sets the batch's form of the pair work without timing: variant 0, 1 or 2 as
+ * dc_fspb_batch_autotune numbers them (the graphs are rebuilt at the next run).
+ * Errors: DC_EINVAL (NULL batch, variant out of range). */
+dc_status dc_fspb_batch_set_variant(dc_batch* batch, int32_t variant);
 
 /* Waits for the batch's stream. */
 dc_status dc_fspb_batch_synchronize(dc_batch* batch);

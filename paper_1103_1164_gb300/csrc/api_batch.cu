@@ -35,7 +35,7 @@ struct dc_batch {
     std::vector<float*> d_fluence, d_dose;   // caller order, owned by the batch
     int64_t v_total = 0;
     bool shared_water = false;          // all plans use identical water tables
-    int kvariant = 0;                   // register budget of the pair kernel (dc_fspb_batch_autotune)
+    int kvariant = 0;                   // 0, 1: register budget of the batch pair kernel; kBatchPerPlan (dc_fspb_batch_autotune)
     cudaGraphExec_t exec[2] = {nullptr, nullptr};   // [0] dose, [1] density steps + dose
     int kernels[2] = {0, 0};                        // kernel nodes per replay
     std::vector<uint64_t> gen;                      // plans' layout_gen when args were written
@@ -136,12 +136,26 @@ cudaError_t enqueue(dc_batch* bt, bool density)
             e = cudaStreamWaitEvent(bt->cap, bt->join[j], 0);
             if (e != cudaSuccess) return e;
         }
-    } else {
+    } else if (bt->kvariant != kBatchPerPlan) {
         for (int j = 0; j < bt->n; ++j) {
             dc_plan* p = bt->plans[bt->order[j]];
             e = cudaMemsetAsync(p->d_part, 0, sizeof(float) * (size_t)p->n_beams * p->V, bt->cap);
             if (e != cudaSuccess) return e;
         }
+    }
+    if (bt->kvariant == kBatchPerPlan) {
+        // each plan's own dose launch (its pair kernel specialised for that
+        // plan alone, then its beam sums), one after another in the graph
+        for (int j = 0; j < bt->n; ++j) {
+            const int i = bt->order[j];
+            dc_plan* p = bt->plans[i];
+            cudaStream_t own = p->stream;
+            p->stream = bt->cap;
+            e = launch_dose(p, bt->d_fluence[i], 1, p->B, bt->d_dose[i], p->V);
+            p->stream = own;
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
     }
     return launch_batch(bt->cap, bt->h_args.data(), bt->d_args, bt->n, bt->d_vpre, bt->v_total, bt->d_prefix,
                         bt->d_counter, bt->device, bt->kvariant, bt->shared_water);
@@ -373,7 +387,7 @@ dc_status dc_fspb_batch_autotune(dc_batch* batch, int32_t* variant, float* ms)
         return cuda_fail(e, "cudaEventCreate");
     }
     dc_status s = DC_OK;
-    for (int v = 0; v < kBatchVariants && s == DC_OK; ++v) {
+    for (int v = 0; v <= kBatchPerPlan && s == DC_OK; ++v) {
         batch->kvariant = v;
         batch->drop_graphs();
         s = run(batch, 0);   // captures, and warms up
@@ -400,6 +414,16 @@ dc_status dc_fspb_batch_autotune(dc_batch* batch, int32_t* variant, float* ms)
     batch->drop_graphs();
     if (variant) *variant = best;
     if (ms) *ms = best_ms / 2;
+    return DC_OK;
+}
+
+dc_status dc_fspb_batch_set_variant(dc_batch* batch, int32_t variant)
+{
+    if (!batch) return bad("dc_fspb_batch_set_variant: NULL batch");
+    if (variant < 0 || variant > kBatchPerPlan) return bad("dc_fspb_batch_set_variant: variant must be 0, 1 or 2");
+    DC_CUDA(cudaStreamSynchronize(batch->stream));
+    batch->kvariant = variant;
+    batch->drop_graphs();
     return DC_OK;
 }
 

@@ -216,6 +216,7 @@ void mlp_pack(const float* theta, std::vector<uint2>& frag, std::vector<float>& 
 DoseArgs dose_args(const dc_plan* p, const float* fluence, float* dose);
 int batch_max_plans();
 constexpr int kBatchVariants = 2;   // register budgets of the batch pair kernel (4 or 5 CTAs per SM)
+constexpr int kBatchPerPlan = 2;    // batch variant: the plans' own dose launches, one after another
 // The plans are grouped by lateral form (at most batch_groups() groups); per
 // group, the prefix of its plans' unit counts and one persistent pair kernel
 // over all their units (one launch in all when the plans share the lateral

@@ -81,7 +81,7 @@ EXPORTS = ["dc_last_error", "dc_status_str", "dc_fspb_create", "dc_fspb_destroy"
            "dc_mlp_create", "dc_mlp_destroy", "dc_mlp_get_params", "dc_mlp_get_state", "dc_mlp_set_state", "dc_mlp_set_precision", "dc_mlp_gradient", "dc_mlp_train",
            "dc_mlp_predict", "dc_fspb_batch_create", "dc_fspb_batch_destroy", "dc_fspb_batch_buffers",
            "dc_fspb_batch_run", "dc_fspb_batch_dose", "dc_fspb_batch_synchronize", "dc_fspb_batch_kernels",
-           "dc_fspb_batch_autotune", "dc_gamma_index", "dc_fluence_from_leaves"]
+           "dc_fspb_batch_autotune", "dc_fspb_batch_set_variant", "dc_gamma_index", "dc_fluence_from_leaves"]
 
 
 def library_path() -> str:
@@ -151,6 +151,7 @@ def load():
     L.dc_fspb_batch_synchronize.argtypes = [vp]
     L.dc_fspb_batch_kernels.argtypes = [vp, u32, C.POINTER(i32)]
     L.dc_fspb_batch_autotune.argtypes = [vp, C.POINTER(i32), C.POINTER(C.c_float)]
+    L.dc_fspb_batch_set_variant.argtypes = [vp, i32]
     L.dc_gamma_index.argtypes = [vp, vp, C.POINTER(dc_grid), C.c_float, C.c_float, C.c_float, vp,
                                  C.POINTER(dc_gamma_stats), vp, u32]
     L.dc_fluence_from_leaves.argtypes = [vp, C.POINTER(dc_leaf_sequence), vp, u32]
@@ -609,10 +610,16 @@ def dc_fspb_batch_kernels(batch: Batch, density=False) -> int:
 
 
 def dc_fspb_batch_autotune(batch: Batch):
-    """Picks the batch kernel's register budget by timing; returns (variant, ms)."""
+    """Picks the batch's form of the pair work by timing (0, 1: the persistent
+    kernel for 4 or 5 CTAs per SM; 2: the plans' own launches); returns (variant, ms)."""
     v, ms = C.c_int32(), C.c_float()
     _check(load().dc_fspb_batch_autotune(batch.handle, C.byref(v), C.byref(ms)))
     return v.value, ms.value
+
+
+def dc_fspb_batch_set_variant(batch: Batch, variant: int):
+    """Sets the batch's form of the pair work (0, 1 or 2) without timing."""
+    _check(load().dc_fspb_batch_set_variant(batch.handle, int(variant)))
 
 
 def dc_fspb_batch_dose(batch: Batch, fluences, doses=None, density=False):

@@ -130,12 +130,27 @@ def test_batch_follows_plan_changes(dc):
     got = dc.dc_fspb_batch_dose(batch, flu)
     for j, (p, pl) in enumerate(zip(inputs, plans)):
         _close(got[j], dc.dc_fspb_dose(pl, p.fluence), f"plan {j} after changes")
-    # either register budget of the batch kernel gives the same doses
+    # every form of the pair work gives the same doses; the plans' own
+    # launches (variant 2) give each plan's dc_fspb_dose bit for bit
     variant, ms = dc.dc_fspb_batch_autotune(batch)
-    assert variant in (0, 1) and ms > 0
+    assert variant in (0, 1, 2) and ms > 0
     again = dc.dc_fspb_batch_dose(batch, flu)
     for j in range(len(plans)):
         _close(again[j], got[j], f"plan {j} after autotune")
+    for v in (0, 1, 2):
+        dc.dc_fspb_batch_set_variant(batch, v)
+        for density in (False, True):
+            res = dc.dc_fspb_batch_dose(batch, flu, density=density)
+            for j, (p, pl) in enumerate(zip(inputs, plans)):
+                own = dc.dc_fspb_dose(pl, p.fluence)
+                if v == 2:
+                    assert np.array_equal(np.reshape(res[j], -1), np.reshape(own, -1)), \
+                        f"plan {j}, per-plan launches, density {density}"
+                else:
+                    _close(res[j], own, f"plan {j}, variant {v}, density {density}")
+    with pytest.raises(dc.DcError) as ei:
+        dc.dc_fspb_batch_set_variant(batch, 3)
+    assert ei.value.status == dc.DC_EINVAL
 
 
 def test_batch_rejects_bad_arguments(dc):
