@@ -166,3 +166,28 @@ def test_spmm_ragged_patches_and_unlisted_rows(dc, n_beams):
     assert np.all(np.abs(y - D) <= 1e-2 * colmax)      # BF16 storage bar
     assert np.all(y[np.abs(D).max(1) == 0] == 0.0)     # voxels no pair reaches
     assert (np.abs(D).max(1) == 0).mean() > 0.3         # the case has many of them
+
+
+def test_plan_without_body_gives_empty_results(dc, oracle_mod):
+    """Every beamlet axis misses the body (air everywhere): no pair exists, so
+    the dose is zero, the matrix has no entry, and the SpMM gives zeros."""
+    g = synth.centred_grid(10, 12, 8, 0.5)
+    rho = np.full(g.shape, 0.001, np.float32)
+    for n_beams in (1, 2):
+        beams = [synth.Beam(90.0 * b, 100.0, (0, 0, 0), 3.0, 3.0) for b in range(n_beams)]
+        p = synth.Plan("air", g, rho, beams, 0.5, 0.5, synth.make_commissioning(roi_radius=1.0),
+                       np.ones(36 * n_beams, np.float32))
+        want = oracle_mod.OraclePlan(p).dose()
+        assert np.all(want == 0)
+        plan = dc.dc_fspb_create_from(p)
+        assert dc.dc_fspb_pair_count(plan) == 0
+        assert np.all(dc.dc_fspb_dose(plan, p.fluence) == 0)
+        rowptr, cols, vals = dc.dc_fspb_dose_matrix(plan)
+        assert np.all(rowptr == 0) and cols.size == 0 and vals.size == 0
+        dose, rowptr, cols, vals = dc.dc_fspb_dose_and_matrix(plan, p.fluence)
+        assert np.all(dose == 0) and np.all(rowptr == 0) and cols.size == 0
+        dc.dc_fspb_spmm_prepare(plan)
+        F = np.ones((plan.n_beamlets, 4), np.float32)
+        Y = dc.dc_fspb_spmm(plan, F)
+        assert np.all(Y == 0)
+        dc.dc_fspb_destroy(plan)
