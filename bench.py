@@ -833,7 +833,8 @@ def run_commission_form(args, dc, torch, stream, iterations=400):
     doses of the six slab phantoms (30 cm water cube, 15 cm slab of density
     0.1-2.0 at 8 cm, 10 x 10 cm2 field, SSD 90 cm, 0.5 cm voxels and beamlets)
     computed with the seeded model; the fit starts 20 % away and runs Adam on
-    the model's twelve parameters with gradients from the backward-pass kernel.
+    the model's twelve parameters with gradients from the backward-pass kernel,
+    then Levenberg-Marquardt from the same start.
     Device time of one backward pass, host wall time per iteration (six
     plans: new tables, density steps, dose, backward pass), the loss and the
     recovered parameters."""
@@ -866,13 +867,23 @@ def run_commission_form(args, dc, torch, stream, iterations=400):
     t0 = time.perf_counter()
     r = fit.fit(th0, iterations=iterations, lr=0.02)
     wall = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    rl = fit.fit_lm(th0, iterations=25)
+    wall_lm = time.perf_counter() - t0
     fit.destroy()
     rel = {k: (r.theta[k] - true[k]) / abs(true[k]) for k in cmn.PARAMS}
+    rel_lm = {k: (rl.theta[k] - true[k]) / abs(true[k]) for k in cmn.PARAMS}
     return {"workload": "6 slab phantoms (Section 2.1 geometry), 60^3 voxels of 0.5 cm, 400 beamlets each, "
                         f"{pairs} pairs in all; 12 model parameters from 20 % away",
             "iterations": r.iterations, "fit_s": wall, "ms_per_iteration": 1e3 * wall / r.iterations,
             "loss_first": r.loss[0], "loss_last": r.loss[-1],
             "param_rel_err": rel,
+            "levenberg_marquardt": {"iterations": rl.iterations, "fit_s": wall_lm,
+                                    "ms_per_iteration": 1e3 * wall_lm / rl.iterations,
+                                    "loss_last": rl.loss[-1], "param_rel_err": rel_lm,
+                                    "max_abs_rel_err": max(abs(v) for v in rel_lm.values()),
+                                    "jacobian": "gradient from the backward-pass kernel; J^T J from forward "
+                                                "differences of the doses (one set of doses per parameter and iteration)"},
             "backward_pass": {"ms": t_vjp, "pairs": pairs0, "pairs_per_s": pairs0 / (t_vjp * 1e-3),
                               "forward_dose_ms": t_dose},
             "reference": "doses of the seeded model computed by the library (a synthetic reference)"}

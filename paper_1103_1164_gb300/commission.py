@@ -9,7 +9,9 @@ This module is orchestration: the dose and its gradient with respect to the
 tables come from the library's kernels (dc_fspb_dose, dc_fspb_dose_vjp);
 here the tables are written from a parameter vector (the synthetic model
 family of synth.model_tables), the gradient is carried from the tables to the
-parameters (the tables' closed-form Jacobian), and Adam takes the steps.
+parameters (the tables' closed-form Jacobian), and Adam, or Levenberg-Marquardt
+with a Gauss-Newton matrix from forward differences of the doses, takes the
+steps.
 Positive parameters are optimised in log space; k1 and k2 (which may be 0) in
 linear space.  b_1 and b_2 are linear in the density with coefficients beta1
 and beta2, so d loss / d log(beta_i) is exactly the gradient with respect to a
@@ -132,19 +134,70 @@ class CommissioningFit:
         grad["beta2"] = float(gc[1]) / theta["beta2"]
         return loss, grad
 
+    @staticmethod
+    def to_z(th: dict) -> np.ndarray:
+        """Optimisation coordinates: log of the positive parameters, k / LIN_SCALE for the linear ones."""
+        return np.array([th[k] / LIN_SCALE if k in LINEAR else np.log(th[k]) for k in PARAMS])
+
+    @staticmethod
+    def from_z(z: np.ndarray) -> dict:
+        th = {k: (float(z[i]) * LIN_SCALE if k in LINEAR else float(np.exp(z[i]))) for i, k in enumerate(PARAMS)}
+        for k in LINEAR:
+            th[k] = max(th[k], 0.0)
+        return th
+
+    def residuals(self, theta: dict) -> np.ndarray:
+        """r with loss = r . r: every plan's (D - D_ref) / (max D_ref sqrt(voxels)), concatenated."""
+        c = 1.0 / (self.scale * np.sqrt(self.nvox))
+        return np.concatenate([(d - ref) * c for d, ref in zip(self.doses(theta), self.ref)])
+
+    def fit_lm(self, theta0: dict, iterations: int = 30, h: float = 1e-3, lam: float = 1e-3,
+               tol: float = 0.0) -> FitResult:
+        """Levenberg-Marquardt in the optimisation coordinates of fit(): the
+        gradient 2 J^T r from the backward-pass kernel (loss_grad), the
+        Gauss-Newton matrix J^T J from forward differences of the doses along
+        each coordinate (one set of doses per parameter and iteration), and
+        a damping lam diag(J^T J) that shrinks after an accepted step and
+        grows after a rejected one."""
+        names = list(PARAMS)
+        z = self.to_z(theta0)
+        hist = []
+        it = 0
+        for it in range(1, iterations + 1):
+            th = self.from_z(z)
+            loss, g = self.loss_grad(th)
+            hist.append(loss)
+            if loss <= tol:
+                break
+            gz = np.array([g[k] * LIN_SCALE if k in LINEAR else g[k] * th[k] for k in names])
+            r0 = self.residuals(th)
+            J = np.empty((r0.size, len(names)))
+            for i in range(len(names)):
+                zi = z.copy()
+                zi[i] += h
+                J[:, i] = (self.residuals(self.from_z(zi)) - r0) / h
+            A = J.T @ J
+            d = np.diag(A).copy()
+            d[d <= 0] = 1.0
+            for _ in range(12):
+                step = np.linalg.solve(A + lam * np.diag(d), -0.5 * gz)
+                trial = self.from_z(z + step)
+                r1 = self.residuals(trial)
+                if float(r1 @ r1) < loss:
+                    z = z + step
+                    lam = max(lam / 3.0, 1e-9)
+                    break
+                lam *= 4.0
+            else:
+                break                       # no descent along any damped step
+        return FitResult(self.from_z(z), hist, it)
+
     def fit(self, theta0: dict, iterations: int = 300, lr: float = 0.02, tol: float = 0.0) -> FitResult:
         """Adam in the optimisation coordinates (log of the positive
         parameters, k / LIN_SCALE for the linear ones)."""
         names = list(PARAMS)
-        to_z = lambda th: np.array([th[k] / LIN_SCALE if k in LINEAR else np.log(th[k]) for k in names])
-
-        def from_z(z):
-            th = {k: (z[i] * LIN_SCALE if k in LINEAR else float(np.exp(z[i]))) for i, k in enumerate(names)}
-            for k in LINEAR:
-                th[k] = max(th[k], 0.0)
-            return th
-
-        z = to_z(theta0)
+        from_z = self.from_z
+        z = self.to_z(theta0)
         m = np.zeros_like(z)
         v = np.zeros_like(z)
         b1, b2, eps = 0.9, 0.999, 1e-12

@@ -6,8 +6,9 @@ oracle's reference doses of the commissioning slab phantoms.
 Bars: directional derivatives along random table directions (and the b
 scales) within 2e-4 of the oracle's finite difference, relative to the
 largest of them (FP32 arithmetic and fast exponentials against FP64); the
-fit lowers the loss by three orders of magnitude and recovers the
-well-determined parameters within 3 %.
+Adam fit lowers the loss by three orders of magnitude and recovers the
+well-determined parameters within 3 %; the Levenberg-Marquardt fit reaches
+the true model's loss and recovers all twelve parameters within 1e-3.
 """
 import dataclasses
 
@@ -106,15 +107,22 @@ def test_vjp_rejects_other_forms(dc):
         dc.dc_fspb_dose_vjp(plan, p.fluence, wv[:-1], cm.water.shape[1], cm.dens.shape[1])
 
 
-def test_fit_recovers_model_from_oracle_doses(dc, oracle_mod):
-    # reference doses: the FP64 oracle with the seeded model on the slab
-    # phantoms of Section 2.1 (slab densities 0.1-2.0); the fit starts 20 %
-    # away and must find the model again through the GPU dose and its gradient
+@pytest.fixture(scope="module")
+def slab_refs(oracle_mod):
+    """The slab phantoms of Section 2.1 (slab densities 0.1-2.0) and the FP64
+    oracle's reference doses of them with the seeded model."""
     from paper_1103_1164_gb300 import commission as cmn
-    true = synth.model_params()
     cm = synth.make_commissioning(roi_radius=5.0)
     inputs = [cmn.slab_phantom(r, vox=0.5, comm=cm) for r in (0.1, 0.5, 1.0, 2.0)]
-    ref = [oracle_mod.OraclePlan(p).dose().reshape(-1) for p in inputs]
+    return inputs, [oracle_mod.OraclePlan(p).dose().reshape(-1) for p in inputs]
+
+
+def test_fit_recovers_model_from_oracle_doses(dc, slab_refs):
+    # the fit starts 20 % away and must find the model again through the GPU
+    # dose and its gradient
+    from paper_1103_1164_gb300 import commission as cmn
+    true = synth.model_params()
+    inputs, ref = slab_refs
     fit = cmn.CommissioningFit(inputs, ref)
     rng = np.random.default_rng(3)
     th0 = {k: (true[k] + 0.006 if k in cmn.LINEAR else true[k] * float(rng.uniform(0.8, 1.2))) for k in cmn.PARAMS}
@@ -124,4 +132,24 @@ def test_fit_recovers_model_from_oracle_doses(dc, oracle_mod):
     assert r.loss[-1] <= 100 * loss_true + 1e-9
     for k in ("u10", "u20", "a1", "a2", "gam", "beta2"):
         assert abs(r.theta[k] - true[k]) <= 0.03 * abs(true[k]), (k, r.theta[k], true[k])
+    fit.destroy()
+
+
+def test_lm_fit_recovers_every_parameter(dc, slab_refs):
+    # Levenberg-Marquardt (gradient from the backward-pass kernel, Gauss-Newton
+    # matrix from forward differences of the GPU doses) from the same start:
+    # the loss reaches that of the true model (FP32 against FP64 doses) and
+    # all twelve parameters come back within 1e-3, including the ones Adam
+    # leaves weakly determined (k1, k2, w21, tau)
+    from paper_1103_1164_gb300 import commission as cmn
+    true = synth.model_params()
+    inputs, ref = slab_refs
+    fit = cmn.CommissioningFit(inputs, ref)
+    rng = np.random.default_rng(3)
+    th0 = {k: (true[k] + 0.006 if k in cmn.LINEAR else true[k] * float(rng.uniform(0.8, 1.2))) for k in cmn.PARAMS}
+    loss_true, _ = fit.loss_grad(true)
+    r = fit.fit_lm(th0, iterations=25)
+    assert r.loss[-1] <= 1.5 * loss_true + 1e-15, (r.loss[-1], loss_true)
+    for k in cmn.PARAMS:
+        assert abs(r.theta[k] - true[k]) <= 1e-3 * abs(true[k]), (k, r.theta[k], true[k])
     fit.destroy()
