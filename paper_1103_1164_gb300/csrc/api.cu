@@ -314,7 +314,7 @@ static dc_status rerun_density_steps(dc_plan* p)
     if (p->coeffs.density_correction && p->lateral_mode != DC_LATERAL_ISO) DC_CUDA(launch_lateral(p));
     p->pairs = -1;
     p->counts_fresh = false;
-    if (p->sp_ready) p->spmm_free();   // the SpMM tiles follow the voxel lists
+    if (p->sp_ready) p->spmm_invalidate();   // the SpMM tiles follow the voxel lists
     return DC_OK;
 }
 
@@ -525,7 +525,7 @@ static dc_status rebin(dc_plan* p, float tile, float slab)
     if (p->coeffs.density_correction && p->lateral_mode != DC_LATERAL_ISO) DC_CUDA(launch_lateral(p));
     p->pairs = -1;
     p->counts_fresh = false;
-    if (p->sp_ready) p->spmm_free();
+    if (p->sp_ready) p->spmm_invalidate();
     ++p->layout_gen;
     return DC_OK;
 }

@@ -202,7 +202,7 @@ dc_status run(dc_batch* bt, uint32_t flags)
             DC_CUDA(cudaStreamSynchronize(p->stream));
             p->pairs = -1;
             p->counts_fresh = false;
-            if (p->sp_ready) p->spmm_free();
+            if (p->sp_ready) p->spmm_invalidate();
         }
     for (int i = 0; i < bt->n; ++i) {
         DC_CUDA(cudaEventRecord(bt->pre[i], bt->plans[i]->stream));

@@ -105,7 +105,7 @@ dc_status dc_fspb_set_surrogate(dc_plan* plan, const float* params, float rho_lo
     plan->mlp_ready = true;
     ++plan->layout_gen;
     if (plan->lateral_mode == DC_LATERAL_MLP && plan->coeffs.density_correction) DC_CUDA(launch_lateral(plan));
-    if (plan->sp_ready) plan->spmm_free();
+    if (plan->sp_ready) plan->spmm_invalidate();
     DC_CUDA(cudaStreamSynchronize(plan->stream));
     return DC_OK;
 }
@@ -121,7 +121,7 @@ dc_status dc_fspb_set_lateral_mode(dc_plan* plan, int32_t mode)
     plan->lateral_mode = mode;
     ++plan->layout_gen;
     if (plan->coeffs.density_correction && mode != DC_LATERAL_ISO) DC_CUDA(launch_lateral(plan));
-    if (plan->sp_ready) plan->spmm_free();   // matrix values depend on the form
+    if (plan->sp_ready) plan->spmm_invalidate();   // matrix values depend on the form
     return DC_OK;
 }
 

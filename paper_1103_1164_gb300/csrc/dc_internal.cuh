@@ -103,6 +103,20 @@ struct dc_plan {
     int32_t* d_err = nullptr;        // device status word of bounded waits
     int32_t* d_chk = nullptr;        // status word of the DC_BOUNDS_CHECK build
     float* d_grad = nullptr;         // dc_fspb_dose_vjp with host buffers: the gradients on the device
+    // bytes held by each block-sparse buffer: a new preparation reuses a
+    // buffer that is large enough (re-allocating tens of GB per density costs
+    // more than building the tiles)
+    size_t sp_cap[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    // The tiles no longer describe the plan (new voxel lists, lateral form or
+    // tables): dc_fspb_spmm needs a new dc_fspb_spmm_prepare.  The buffers stay.
+    void spmm_invalidate()
+    {
+        sp_ready = false;
+        sp_n_rb = 0;
+        sp_chunks = 0;
+        sp_n_zero = 0;
+    }
+    // Frees the block-sparse buffers.
     void spmm_free()
     {
         void* bufs[] = {d_sp_rbfirst, d_sp_first, d_sp_nchunk, d_sp_off, d_sp_kb, d_sp_tiles, d_sp_inv, d_sp_zero};
@@ -116,10 +130,8 @@ struct dc_plan {
         d_sp_tiles = nullptr;
         d_sp_inv = nullptr;
         d_sp_zero = nullptr;
-        sp_n_zero = 0;
-        sp_ready = false;
-        sp_n_rb = 0;
-        sp_chunks = 0;
+        for (size_t& c : sp_cap) c = 0;
+        spmm_invalidate();
     }
     // dose-deposition matrix pattern
     int32_t* d_rowcount = nullptr;

@@ -149,6 +149,8 @@ struct TileArgs {
     const int32_t* rb_first;     // [n_beams + 1] first row-block of each beam (host-computed)
     const int4* beam;            // [n_beams + 1] (first beamlet, M, N, first tile column) of each beam
     int n_beams;
+    const int32_t* bcount;       // [n_beams][V] pairs of each (beam, voxel): a row's segment of each beam
+    int64_t V;
     int32_t* nchunk;             // count pass output [n_rb]
     const int64_t* chunk_off;    // fill pass: first chunk of each row-block
     int32_t* chunk_kb;           // fill pass: k-block (beamlet / 8) of each chunk
@@ -170,6 +172,11 @@ __host__ __device__ __forceinline__ int patch_col(int n, int m, int M)
 }
 __host__ __device__ __forceinline__ int patch_cols(int M, int N) { return ((M + 3) >> 2) * ((N + 3) >> 2) * 16; }
 
+// Runs of four beamlets m..m+3 (m a multiple of 4) of one beamlet row are one
+// row of a 4 x 4 patch: four consecutive tile columns in one k-block, so the
+// count pass marks them once and the fill pass writes them with one 8-byte
+// store (on the largest head-and-neck plan the fill pass took 94 ms with one
+// 2-byte store per entry).
 template <bool FILL>
 __global__ void __launch_bounds__(kRB) k_tiles(const TileArgs a)
 {
@@ -185,25 +192,27 @@ __global__ void __launch_bounds__(kRB) k_tiles(const TileArgs a)
     const int4 bm = a.beam[b];
     const int c0 = bm.x, c1 = bm.x + bm.y * bm.z, M = bm.y;
     const int kb0 = bm.w / 8, nkb = (a.beam[b + 1].w - bm.w) / 8;
-    // tile column of beamlet c of this beam
-    auto col_of = [&](int c) {
-        const int l = c - c0, n = l / M;
-        return bm.w + patch_col(n, l - n * M, M);
-    };
     for (int q = t; q < kMaxKB / 32; q += blockDim.x) mark[q] = 0;
     __syncthreads();
     const int e = j * kRB + t;
     const int v = e < nit ? a.items[a.base[b] + e] : -1;
     int64_t r0 = 0, r1 = 0;
     if (v >= 0) {
+        // only this beam's segment of the row: it starts after the segments
+        // of the beams before b and holds bcount[b][v] entries (columns
+        // ascending, all of this beam)
         r0 = a.rowptr[v];
-        r1 = a.rowptr[v + 1];
-        for (int64_t q = r0; q < r1; ++q) {
+        for (int bb = 0; bb < b; ++bb) r0 += a.bcount[(size_t)bb * a.V + v];
+        r1 = r0 + a.bcount[(size_t)b * a.V + v];
+        for (int64_t q = r0; q < r1;) {
             const int c = a.cols[q];
+            const int l = c - c0, n = l / M, m = l - n * M;
+            const bool run = (m & 3) == 0 && m + 3 < M && q + 3 < r1 && a.cols[q + 3] == c + 3;
             if (c >= c0 && c < c1) {
-                const int kb = col_of(c) / 8 - kb0;
+                const int kb = (bm.w + patch_col(n, m, M)) / 8 - kb0;
                 atomicOr(&mark[kb >> 5], 1u << (kb & 31));
             }
+            q += run ? 4 : 1;
         }
     }
     __syncthreads();
@@ -235,17 +244,27 @@ __global__ void __launch_bounds__(kRB) k_tiles(const TileArgs a)
     const int nz = s_nc * (kTileA / 16);
     for (int q = t; q < nz; q += blockDim.x) tz[q] = make_uint4(0, 0, 0, 0);
     __syncthreads();
-    if (v >= 0) {
-        for (int64_t q = r0; q < r1; ++q) {
-            const int c = a.cols[q];
-            if (c < c0 || c >= c1) continue;
-            const int pc = col_of(c);
+    for (int64_t q = r0; q < r1;) {
+        const int c = a.cols[q];
+        const int l = c - c0, n = l / M, m = l - n * M;
+        const bool run = (m & 3) == 0 && m + 3 < M && q + 3 < r1 && a.cols[q + 3] == c + 3;
+        if (c >= c0 && c < c1) {
+            const int pc = bm.w + patch_col(n, m, M);
             const int ch = chunk_of[pc / 8 - kb0];
             const int k = pc - 8 * a.chunk_kb[a.chunk_off[rb] + ch];   // column within the chunk, 0..15
             // element (m = t, k) of the K-major core-matrix layout
             const int off = ((t >> 3) * 2 + (k >> 3)) * 64 + (t & 7) * 8 + (k & 7);
-            tiles[(size_t)ch * (kRB * kKC) + off] = a.vals[q];
+            uint16_t* dst = tiles + (size_t)ch * (kRB * kKC) + off;
+            if (run) {
+                // k is a multiple of 4 here, so dst is 8-byte aligned
+                const uint32_t lo = (uint32_t)a.vals[q] | ((uint32_t)a.vals[q + 1] << 16);
+                const uint32_t hi = (uint32_t)a.vals[q + 2] | ((uint32_t)a.vals[q + 3] << 16);
+                *reinterpret_cast<uint2*>(dst) = make_uint2(lo, hi);
+            } else {
+                *dst = a.vals[q];
+            }
         }
+        q += run ? 4 : 1;
     }
 }
 
@@ -687,6 +706,20 @@ int gsize(int64_t n)
 // ---------------------------------------------------------------------------
 // Host side
 
+// Buffer slot `slot` of the plan's block-sparse storage with at least `bytes`
+// (reused when it is large enough, else freed and allocated again).
+template <typename T>
+cudaError_t sp_buffer(dc_plan* p, int slot, T*& ptr, size_t bytes)
+{
+    if (ptr && p->sp_cap[slot] >= bytes) return cudaSuccess;
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    p->sp_cap[slot] = 0;
+    const cudaError_t e = dc::dev_malloc(&ptr, bytes);
+    if (e == cudaSuccess) p->sp_cap[slot] = bytes;
+    return e;
+}
+
 dc_status spmm_prepare(dc_plan* p, const int64_t* rowptr, const int32_t* cols, const uint16_t* vals)
 {
     const int nb = p->n_beams;
@@ -709,13 +742,13 @@ dc_status spmm_prepare(dc_plan* p, const int64_t* rowptr, const int32_t* cols, c
     }
     rb_first[nb] = n_rb;
     beam[nb] = make_int4(p->B, 0, 0, cols_total);
-    p->spmm_free();
+    p->spmm_invalidate();
     p->sp_n_rb = n_rb;
-    DC_CUDA(dc::dev_malloc(&p->d_sp_rbfirst, (nb + 1) * sizeof(int32_t)));
-    DC_CUDA(dc::dev_malloc(&p->d_sp_first, (nb + 1) * sizeof(int4)));
+    DC_CUDA(sp_buffer(p, 0, p->d_sp_rbfirst, (nb + 1) * sizeof(int32_t)));
+    DC_CUDA(sp_buffer(p, 1, p->d_sp_first, (nb + 1) * sizeof(int4)));
     p->sp_cols = cols_total;
-    DC_CUDA(dc::dev_malloc(&p->d_sp_nchunk, (size_t)(n_rb + 1) * sizeof(int32_t)));
-    DC_CUDA(dc::dev_malloc(&p->d_sp_off, (size_t)(n_rb + 1) * sizeof(int64_t)));
+    DC_CUDA(sp_buffer(p, 2, p->d_sp_nchunk, (size_t)(n_rb + 1) * sizeof(int32_t)));
+    DC_CUDA(sp_buffer(p, 3, p->d_sp_off, (size_t)(n_rb + 1) * sizeof(int64_t)));
     DC_CUDA(cudaMemcpyAsync(p->d_sp_rbfirst, rb_first.data(), (nb + 1) * sizeof(int32_t), cudaMemcpyHostToDevice,
                             p->stream));
     DC_CUDA(cudaMemcpyAsync(p->d_sp_first, beam.data(), (nb + 1) * sizeof(int4), cudaMemcpyHostToDevice,
@@ -730,6 +763,8 @@ dc_status spmm_prepare(dc_plan* p, const int64_t* rowptr, const int32_t* cols, c
     ta.rb_first = p->d_sp_rbfirst;
     ta.beam = p->d_sp_first;
     ta.n_beams = nb;
+    ta.bcount = p->d_bcount;
+    ta.V = p->V;
     ta.nchunk = p->d_sp_nchunk;
     if (n_rb > 0) {
         k_tiles<false><<<n_rb, kRB, 0, p->stream>>>(ta);
@@ -746,8 +781,8 @@ dc_status spmm_prepare(dc_plan* p, const int64_t* rowptr, const int32_t* cols, c
     p->sp_chunks = off[n_rb];
     DC_CUDA(cudaMemcpyAsync(p->d_sp_off, off.data(), (n_rb + 1) * sizeof(int64_t), cudaMemcpyHostToDevice,
                             p->stream));
-    DC_CUDA(dc::dev_malloc(&p->d_sp_kb, (size_t)(p->sp_chunks + 1) * sizeof(int32_t)));
-    DC_CUDA(dc::dev_malloc(&p->d_sp_tiles, (size_t)(p->sp_chunks + 1) * kTileA));
+    DC_CUDA(sp_buffer(p, 4, p->d_sp_kb, (size_t)(p->sp_chunks + 1) * sizeof(int32_t)));
+    DC_CUDA(sp_buffer(p, 5, p->d_sp_tiles, (size_t)(p->sp_chunks + 1) * kTileA));
     ta.chunk_off = p->d_sp_off;
     ta.chunk_kb = p->d_sp_kb;
     ta.tiles = reinterpret_cast<uint16_t*>(p->d_sp_tiles);
@@ -759,7 +794,7 @@ dc_status spmm_prepare(dc_plan* p, const int64_t* rowptr, const int32_t* cols, c
     {
         // inverse of the beam lists (the reduction of several beams' partial
         // rows reads it; one-beam plans keep only the voxels in no list)
-        DC_CUDA(dc::dev_malloc(&p->d_sp_inv, (size_t)nb * p->V * sizeof(int32_t)));
+        DC_CUDA(sp_buffer(p, 6, p->d_sp_inv, (size_t)nb * p->V * sizeof(int32_t)));
         DC_CUDA(cudaMemsetAsync(p->d_sp_inv, 0xff, (size_t)nb * p->V * sizeof(int32_t), p->stream));
         int maxn = 0;
         for (int b = 0; b < nb; ++b) maxn = std::max(maxn, n_items[b]);
@@ -771,7 +806,7 @@ dc_status spmm_prepare(dc_plan* p, const int64_t* rowptr, const int32_t* cols, c
         for (int b = 0; b < nb; ++b) items_total += ((int64_t)n_items[b] + 31) / 32 * 32;
         p->sp_items_total = items_total;
         if (nb == 1) {
-            DC_CUDA(dc::dev_malloc(&p->d_sp_zero, (size_t)p->V * sizeof(int32_t) + sizeof(unsigned long long)));
+            DC_CUDA(sp_buffer(p, 7, p->d_sp_zero, (size_t)p->V * sizeof(int32_t) + sizeof(unsigned long long)));
             unsigned long long* cnt = reinterpret_cast<unsigned long long*>(p->d_sp_zero + p->V);
             DC_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), p->stream));
             k_unlisted<<<gsize(p->V), 256, 0, p->stream>>>(p->d_sp_inv, p->V, p->d_sp_zero, cnt);
@@ -781,8 +816,6 @@ dc_status spmm_prepare(dc_plan* p, const int64_t* rowptr, const int32_t* cols, c
             DC_CUDA(cudaMemcpyAsync(&h, cnt, sizeof(h), cudaMemcpyDeviceToHost, p->stream));
             DC_CUDA(cudaStreamSynchronize(p->stream));
             p->sp_n_zero = (int64_t)h;
-            cudaFree(p->d_sp_inv);
-            p->d_sp_inv = nullptr;
         }
     }
     if (!p->d_err) DC_CUDA(dc::dev_malloc(&p->d_err, sizeof(int32_t)));
