@@ -1183,7 +1183,97 @@ def run_batch_form(args, dc, torch, stream, peak_pairs):
     for pl in plans:
         dc.dc_fspb_set_lateral_mode(pl, dc.DC_LATERAL_ISO)
         dc.dc_fspb_set_precision(pl, dc.DC_PRECISION_FP32)
+    # the same plans with 64 fluence vectors each, one plan resident at a time
+    # (the BF16 matrix of the largest is tens of GB)
+    del batch, plans, doses, rhos, flus
+    torch.cuda.synchronize()
+    out["multi_fluence_64"] = run_batch_multi_fluence(args, dc, torch, inputs, net)
     return out
+
+
+def run_batch_multi_fluence(args, dc, torch, inputs, net, k=64):
+    """The 16 head-and-neck plans with k fluence vectors each (uniform [0, 1],
+    seeded), the benchmark spec's two forms of the multi-fluence dose, plan after
+    plan: plain = axis-stencil lateral densities and the FP32 direct
+    evaluation of the k vectors (dc_fspb_dose_batch); surrogate + BF16 = the
+    network's lateral densities, the BF16 dose-deposition matrix
+    (dc_fspb_spmm_prepare) and the tensor-core SpMM (dc_fspb_spmm).  Host wall
+    clock around each plan's calls (both forms synchronise), cells autotuned at
+    set-up.  The surrogate form's cost per density (factors + matrix) and per
+    further set of k vectors (the SpMM) are reported apart, with the number of
+    sets at which it is 3x faster; its error against the FP64 oracle's axis
+    form on seeded voxels of the largest and the smallest plan, every column."""
+    from paper_1103_1164_gb300 import surrogate
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(1005)
+    big = int(np.argmax([p.grid.nx * p.grid.ny * p.grid.nz for p in inputs]))
+    small = int(np.argmin([p.grid.nx * p.grid.ny * p.grid.nz for p in inputs]))
+
+    def wall(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        return 1e3 * (time.perf_counter() - t0)
+
+    acc = {"plain_ms": 0.0, "surrogate_density_ms": 0.0, "surrogate_spmm_ms": 0.0}
+    errs = {}
+    pairs_total = 0
+    for j, p in enumerate(inputs):
+        rho = torch.from_numpy(p.rho).cuda()
+        plan = dc.dc_fspb_create_from(p, device_density=rho)
+        dc.dc_fspb_autotune(plan, torch.from_numpy(p.fluence).cuda())
+        B, V = plan.n_beamlets, plan.n_voxels
+        F = torch.rand(B, k, device="cuda", generator=gen)
+        Ft = F.t().contiguous()
+        D = torch.empty(k, V, device="cuda")
+        Y = torch.empty(V, k, device="cuda")
+        dc.dc_fspb_set_lateral_mode(plan, dc.DC_LATERAL_AXIS)
+        plain = lambda: (dc.dc_fspb_set_density(plan, rho), dc.dc_fspb_dose_batch(plan, Ft, D))
+        plain()
+        acc["plain_ms"] += wall(plain)
+        dc.dc_fspb_set_surrogate(plan, net["params"], surrogate.RHO_LO, surrogate.RHO_HI)
+        dc.dc_fspb_set_lateral_mode(plan, dc.DC_LATERAL_MLP)
+        per_density = lambda: (dc.dc_fspb_set_density(plan, rho), dc.dc_fspb_spmm_prepare(plan))
+        per_density()
+        dc.dc_fspb_spmm(plan, F, Y)
+        acc["surrogate_density_ms"] += wall(per_density)
+        acc["surrogate_spmm_ms"] += wall(lambda: dc.dc_fspb_spmm(plan, F, Y))
+        pairs_total += dc.dc_fspb_pair_count(plan)
+        if not args.no_cpu and j in (big, small):
+            # seeded voxels, half of them above 10 % of the first column's maximum
+            d0 = D[0].cpu().numpy()
+            rng = np.random.default_rng(41)
+            hot = np.flatnonzero(d0 > 0.1 * d0.max())
+            vox = np.unique(np.concatenate([rng.integers(0, V, 150), rng.choice(hot, 150)]))
+            want = oracle_multi_fluence(p, F.cpu().numpy(), lateral_mode=1, voxels=vox)
+            # per column: max over the voxels of |error| over the column's maximum dose (GPU plain form)
+            colmax = D.abs().max(1).values.cpu().numpy().astype(np.float64)
+            e = np.abs(Y.cpu().numpy()[vox].astype(np.float64) - want).max(0) / colmax
+            ep = np.abs(D.t().cpu().numpy()[vox].astype(np.float64) - want).max(0) / colmax
+            errs["largest" if j == big else "smallest"] = {"voxels": int(vox.size),
+                                                           "surrogate_bf16": float(e.max()),
+                                                           "plain_fp32_axis": float(ep.max())}
+        del plan, D, Y, F, Ft, rho
+        torch.cuda.empty_cache()
+    sur_one = acc["surrogate_density_ms"] + acc["surrogate_spmm_ms"]
+    per_set = acc["surrogate_spmm_ms"]
+    sets_3x = None
+    for n in range(1, 1001):
+        if n * acc["plain_ms"] >= 3.0 * (acc["surrogate_density_ms"] + n * per_set):
+            sets_3x = n
+            break
+    return {"workload": f"the 16 plans, {k} fluence vectors U[0,1] each ({pairs_total} pairs per vector)",
+            "plain_fp32_axis_ms": acc["plain_ms"],
+            "surrogate_bf16": {"per_density_ms": acc["surrogate_density_ms"],
+                               "per_set_of_64_ms": per_set, "one_set_ms": sur_one},
+            "speedup_one_set": acc["plain_ms"] / sur_one,
+            "speedup_per_further_set": acc["plain_ms"] / per_set,
+            "sets_of_64_for_3x": sets_3x,
+            "evals_per_s": {"plain": pairs_total * k / (acc["plain_ms"] * 1e-3),
+                            "surrogate_bf16_one_set": pairs_total * k / (sur_one * 1e-3)},
+            "timing": "host wall clock, synchronised, around each plan's calls; cells autotuned at set-up",
+            "max_err_vs_fp64_oracle_axis_over_colmax": errs or None}
 
 
 def batch_plan_error(p, dose, n_vox=800, seed=31):
