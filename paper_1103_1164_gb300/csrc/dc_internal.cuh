@@ -95,6 +95,7 @@ struct dc_plan {
     void* d_sp_tiles = nullptr;
     int32_t* d_sp_inv = nullptr;
     int32_t* d_sp_zero = nullptr;    // one-beam plans: voxels in no list (their output rows are zero)
+    uint32_t* d_sp_marks = nullptr;  // preparation: the occupied k-blocks of each row-block (bitmaps)
     int64_t sp_n_zero = 0;
     void* d_sp_fp = nullptr;
     size_t sp_fp_cap = 0;
@@ -106,7 +107,7 @@ struct dc_plan {
     // bytes held by each block-sparse buffer: a new preparation reuses a
     // buffer that is large enough (re-allocating tens of GB per density costs
     // more than building the tiles)
-    size_t sp_cap[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    size_t sp_cap[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     // The tiles no longer describe the plan (new voxel lists, lateral form or
     // tables): dc_fspb_spmm needs a new dc_fspb_spmm_prepare.  The buffers stay.
     void spmm_invalidate()
@@ -119,7 +120,8 @@ struct dc_plan {
     // Frees the block-sparse buffers.
     void spmm_free()
     {
-        void* bufs[] = {d_sp_rbfirst, d_sp_first, d_sp_nchunk, d_sp_off, d_sp_kb, d_sp_tiles, d_sp_inv, d_sp_zero};
+        void* bufs[] = {d_sp_rbfirst, d_sp_first, d_sp_nchunk, d_sp_off, d_sp_kb, d_sp_tiles, d_sp_inv, d_sp_zero,
+                        d_sp_marks};
         for (void* b : bufs)
             if (b) cudaFree(b);
         d_sp_rbfirst = d_sp_nchunk = nullptr;
@@ -130,6 +132,7 @@ struct dc_plan {
         d_sp_tiles = nullptr;
         d_sp_inv = nullptr;
         d_sp_zero = nullptr;
+        d_sp_marks = nullptr;
         for (size_t& c : sp_cap) c = 0;
         spmm_invalidate();
     }

@@ -152,6 +152,8 @@ struct TileArgs {
     const int32_t* bcount;       // [n_beams][V] pairs of each (beam, voxel): a row's segment of each beam
     int64_t V;
     int32_t* nchunk;             // count pass output [n_rb]
+    uint32_t* marks;             // count pass output, fill pass input: [n_rb][mark_words] occupied k-blocks
+    int mark_words;
     const int64_t* chunk_off;    // fill pass: first chunk of each row-block
     int32_t* chunk_kb;           // fill pass: k-block (beamlet / 8) of each chunk
     uint16_t* tiles;             // fill pass: [chunks][128 * 16]
@@ -172,47 +174,78 @@ __host__ __device__ __forceinline__ int patch_col(int n, int m, int M)
 }
 __host__ __device__ __forceinline__ int patch_cols(int M, int N) { return ((M + 3) >> 2) * ((N + 3) >> 2) * 16; }
 
-// Runs of four beamlets m..m+3 (m a multiple of 4) of one beamlet row are one
-// row of a 4 x 4 patch: four consecutive tile columns in one k-block, so the
-// count pass marks them once and the fill pass writes them with one 8-byte
-// store (on the largest head-and-neck plan the fill pass took 94 ms with one
-// 2-byte store per entry).
+// A warp takes one row of the row-block at a time and reads its segment 32
+// consecutive entries per step, so the loads of the column indices and values
+// are whole lines.  (With one thread per row, every 4-byte load of the 32
+// lanes touched its own sector: on a 1.7 G-entry plan the tile fill read
+// 27 GB from DRAM for 10 GB of matrix and took 24 ms.)
+static_assert(kRB == 4 * 32, "four warps of 32 rows each: lane i of warp w owns row w + 4 i");
 template <bool FILL>
 __global__ void __launch_bounds__(kRB) k_tiles(const TileArgs a)
 {
     __shared__ uint32_t mark[kMaxKB / 32];
-    __shared__ int16_t chunk_of[kMaxKB];   // chunk index of each k-block (-1: none)
+    // fill pass: per k-block, 2 * (its chunk) + (1 if it is the chunk's second half)
+    __shared__ int16_t chunk_of[kMaxKB];
     __shared__ int s_nc;
     const int rb = blockIdx.x;
     int b = 0;
     while (b + 1 < a.n_beams && a.rb_first[b + 1] <= rb) ++b;
     const int j = rb - a.rb_first[b];
     const int nit = a.n_items[b];
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int4 bm = a.beam[b];
-    const int c0 = bm.x, c1 = bm.x + bm.y * bm.z, M = bm.y;
+    const int c0 = bm.x, M = bm.y, nbl = bm.y * bm.z;
+    // n = l / M as a multiply-high: exact for l, M <= 2^15 (a beam has at most
+    // 32768 beamlets), since then l (ceil(2^32 / M) M - 2^32) < 2^32; M = 1
+    // (where ceil(2^32 / M) does not fit) is taken apart
+    const uint32_t mdiv = M > 1 ? 0xffffffffu / (uint32_t)M + 1u : 0u;
+    auto row_of = [&](int l) { return M > 1 ? (int)__umulhi((uint32_t)l, mdiv) : l; };
     const int kb0 = bm.w / 8, nkb = (a.beam[b + 1].w - bm.w) / 8;
     for (int q = t; q < kMaxKB / 32; q += blockDim.x) mark[q] = 0;
     __syncthreads();
-    const int e = j * kRB + t;
-    const int v = e < nit ? a.items[a.base[b] + e] : -1;
-    int64_t r0 = 0, r1 = 0;
-    if (v >= 0) {
-        // only this beam's segment of the row: it starts after the segments
-        // of the beams before b and holds bcount[b][v] entries (columns
-        // ascending, all of this beam)
-        r0 = a.rowptr[v];
-        for (int bb = 0; bb < b; ++bb) r0 += a.bcount[(size_t)bb * a.V + v];
-        r1 = r0 + a.bcount[(size_t)b * a.V + v];
-        for (int64_t q = r0; q < r1;) {
-            const int c = a.cols[q];
-            const int l = c - c0, n = l / M, m = l - n * M;
-            const bool run = (m & 3) == 0 && m + 3 < M && q + 3 < r1 && a.cols[q + 3] == c + 3;
-            if (c >= c0 && c < c1) {
-                const int kb = (bm.w + patch_col(n, m, M)) / 8 - kb0;
-                atomicOr(&mark[kb >> 5], 1u << (kb & 31));
+    // the warp's rows are warp, warp + 4, ..., and lane i finds the segment of
+    // row warp + 4 i at once for all of them: it starts after the segments of
+    // the beams before b and holds bcount[b][v] entries (columns ascending,
+    // all of this beam); len = 0 for padding rows
+    int64_t my_r0 = 0;
+    int my_len = 0;
+    {
+        const int e = j * kRB + warp + (kRB / 32) * lane;
+        const int v = e < nit ? a.items[a.base[b] + e] : -1;
+        if (v >= 0) {
+            int64_t r0 = a.rowptr[v];
+            for (int bb = 0; bb < b; ++bb) r0 += a.bcount[(size_t)bb * a.V + v];
+            my_r0 = r0;
+            my_len = a.bcount[(size_t)b * a.V + v];
+        }
+    }
+    auto segment = [&](int i, int64_t& r0, int& len) {
+        r0 = __shfl_sync(0xffffffffu, my_r0, i);
+        len = __shfl_sync(0xffffffffu, my_len, i);
+    };
+    uint32_t* gmark = a.marks + (size_t)rb * a.mark_words;
+    if (FILL) {
+        // the count pass left this row-block's occupied k-blocks
+        for (int q = t; q < a.mark_words; q += blockDim.x) mark[q] = gmark[q];
+    } else for (int i = 0; i < 32; ++i) {
+        int64_t r0;
+        int len;
+        segment(i, r0, len);
+#pragma unroll 2
+        for (int q0 = 0; q0 < len; q0 += 32) {
+            const int q = q0 + lane;
+            int kb = -1;
+            if (q < len) {
+                const int l = a.cols[r0 + q] - c0;
+                if ((unsigned)l < (unsigned)nbl) {   // always: the segment holds this beam's columns only
+                    const int n = row_of(l);
+                    kb = patch_col(n, l - n * M, M) / 8;
+                }
             }
-            q += run ? 4 : 1;
+            // neighbouring entries mostly share a k-block: one shared-memory
+            // atomic per change along the lanes
+            const int prev = __shfl_up_sync(0xffffffffu, kb, 1);
+            if (kb >= 0 && (lane == 0 || kb != prev)) atomicOr(&mark[kb >> 5], 1u << (kb & 31));
         }
     }
     __syncthreads();
@@ -223,48 +256,48 @@ __global__ void __launch_bounds__(kRB) k_tiles(const TileArgs a)
             if (mark[kb >> 5] & (1u << (kb & 31))) {
                 if (FILL) {
                     a.chunk_kb[a.chunk_off[rb] + nc] = kb0 + kb;
-                    chunk_of[kb] = (int16_t)nc;
-                    if (kb + 1 < nkb) chunk_of[kb + 1] = (int16_t)nc;
+                    chunk_of[kb] = (int16_t)(2 * nc);
+                    if (kb + 1 < nkb) chunk_of[kb + 1] = (int16_t)(2 * nc + 1);
                 }
                 ++nc;
                 kb += 2;
             } else {
-                if (FILL) chunk_of[kb] = -1;
                 ++kb;
             }
         }
         s_nc = nc;
         if (!FILL) a.nchunk[rb] = nc;
     }
+    if (!FILL) {
+        for (int q = t; q < a.mark_words; q += blockDim.x) gmark[q] = mark[q];
+        return;
+    }
     __syncthreads();
-    if (!FILL) return;
     // zero this row-block's tiles, then scatter the BF16 values
     uint16_t* tiles = a.tiles + (size_t)a.chunk_off[rb] * (kRB * kKC);
     uint4* tz = reinterpret_cast<uint4*>(tiles);
     const int nz = s_nc * (kTileA / 16);
     for (int q = t; q < nz; q += blockDim.x) tz[q] = make_uint4(0, 0, 0, 0);
     __syncthreads();
-    for (int64_t q = r0; q < r1;) {
-        const int c = a.cols[q];
-        const int l = c - c0, n = l / M, m = l - n * M;
-        const bool run = (m & 3) == 0 && m + 3 < M && q + 3 < r1 && a.cols[q + 3] == c + 3;
-        if (c >= c0 && c < c1) {
-            const int pc = bm.w + patch_col(n, m, M);
-            const int ch = chunk_of[pc / 8 - kb0];
-            const int k = pc - 8 * a.chunk_kb[a.chunk_off[rb] + ch];   // column within the chunk, 0..15
-            // element (m = t, k) of the K-major core-matrix layout
-            const int off = ((t >> 3) * 2 + (k >> 3)) * 64 + (t & 7) * 8 + (k & 7);
-            uint16_t* dst = tiles + (size_t)ch * (kRB * kKC) + off;
-            if (run) {
-                // k is a multiple of 4 here, so dst is 8-byte aligned
-                const uint32_t lo = (uint32_t)a.vals[q] | ((uint32_t)a.vals[q + 1] << 16);
-                const uint32_t hi = (uint32_t)a.vals[q + 2] | ((uint32_t)a.vals[q + 3] << 16);
-                *reinterpret_cast<uint2*>(dst) = make_uint2(lo, hi);
-            } else {
-                *dst = a.vals[q];
-            }
+    for (int i = 0; i < 32; ++i) {
+        const int row = warp + (kRB / 32) * i;
+        int64_t r0;
+        int len;
+        segment(i, r0, len);
+#pragma unroll 2
+        for (int q0 = 0; q0 < len; q0 += 32) {
+            const int q = q0 + lane;
+            if (q >= len) continue;
+            const int l = a.cols[r0 + q] - c0;
+            if ((unsigned)l >= (unsigned)nbl) continue;
+            const int n = row_of(l);
+            const int pc = patch_col(n, l - n * M, M);
+            const int code = chunk_of[pc / 8];
+            const int k = (pc & 7) + 8 * (code & 1);   // column within the chunk, 0..15
+            // element (m = row, k) of the K-major core-matrix layout
+            const int off = ((row >> 3) * 2 + (k >> 3)) * 64 + (row & 7) * 8 + (k & 7);
+            tiles[(size_t)(code >> 1) * (kRB * kKC) + off] = a.vals[r0 + q];
         }
-        q += run ? 4 : 1;
     }
 }
 
@@ -766,6 +799,11 @@ dc_status spmm_prepare(dc_plan* p, const int64_t* rowptr, const int32_t* cols, c
     ta.bcount = p->d_bcount;
     ta.V = p->V;
     ta.nchunk = p->d_sp_nchunk;
+    int max_kb = 0;
+    for (int b = 0; b < nb; ++b) max_kb = std::max(max_kb, patch_cols(p->M[b], p->N[b]) / 8);
+    ta.mark_words = (max_kb + 31) / 32;
+    DC_CUDA(sp_buffer(p, 8, p->d_sp_marks, (size_t)std::max(n_rb, 1) * ta.mark_words * sizeof(uint32_t)));
+    ta.marks = p->d_sp_marks;
     if (n_rb > 0) {
         k_tiles<false><<<n_rb, kRB, 0, p->stream>>>(ta);
         count_launches(1);
