@@ -226,9 +226,12 @@ dc_status dc_fspb_dose_and_matrix(dc_plan* plan, const float* fluence, float* do
  * (M[v][i] = D_i(r_v) over the pairs of eq. 1) with BF16 values, stored
  * block-sparse for the tensor cores: per beam, the voxels of the beam's
  * eye-view binning are cut into row-blocks of 128, and each row-block's
- * nonzeros are covered by dense 128 x 16 tiles of consecutive beamlets
- * (tile starts are multiples of 8).  Must be called again after
- * dc_fspb_set_density or dc_fspb_autotune.  Synchronises the plan's stream.
+ * nonzeros are covered by dense 128 x 16 tiles, one per 4 x 4 patch of the
+ * beam's beamlet grid that holds a pair of the row-block.  The values come
+ * straight from the pair evaluation (the same BF16 values, round-to-nearest-even
+ * of the FP32 D_i(r), as dc_fspb_dose_matrix with DC_BF16); no CSR is built.
+ * Must be called again after dc_fspb_set_density or dc_fspb_autotune.
+ * Synchronises the plan's stream.
  * Errors: DC_ENOMEM, DC_ECUDA, DC_EUNSUPPORTED (a beam of > 32768 beamlets).
  */
 dc_status dc_fspb_spmm_prepare(dc_plan* plan);

@@ -888,22 +888,8 @@ dc_status dc_fspb_spmm_prepare(dc_plan* plan)
 {
     DC_NVTX("dc_fspb_spmm_prepare");
     if (!plan) return invalid("dc_fspb_spmm_prepare: NULL argument");
-    dc_status s = ensure_pattern(plan);
-    if (s != DC_OK) return s;
-    const size_t nnz = (size_t)plan->pairs;
-    const size_t need = nnz * sizeof(int32_t) + 16;
-    if (need > plan->mstage_bytes) {
-        if (plan->d_mcols) cudaFree(plan->d_mcols);
-        if (plan->d_mvals) cudaFree(plan->d_mvals);
-        plan->d_mcols = nullptr;
-        plan->d_mvals = nullptr;
-        plan->mstage_bytes = 0;
-        DC_CUDA(dc::dev_malloc(&plan->d_mcols, need));
-        DC_CUDA(dc::dev_malloc(&plan->d_mvals, need));
-        plan->mstage_bytes = need;
-    }
-    DC_CUDA(launch_fill(plan, plan->d_rowptr, plan->d_mcols, plan->d_mvals, DC_BF16));
-    return spmm_prepare(plan, plan->d_rowptr, plan->d_mcols, reinterpret_cast<const uint16_t*>(plan->d_mvals));
+    // the tiles come straight from the pair evaluation (no CSR in between)
+    return spmm_prepare(plan);
 }
 
 dc_status dc_fspb_spmm_info(const dc_plan* plan, int64_t* chunks, int64_t* row_blocks)

@@ -95,7 +95,8 @@ struct dc_plan {
     void* d_sp_tiles = nullptr;
     int32_t* d_sp_inv = nullptr;
     int32_t* d_sp_zero = nullptr;    // one-beam plans: voxels in no list (their output rows are zero)
-    uint32_t* d_sp_marks = nullptr;  // preparation: the occupied k-blocks of each row-block (bitmaps)
+    uint32_t* d_sp_marks = nullptr;  // preparation: the occupied patches of each row-block (bitmaps)
+    uint16_t* d_sp_wpre = nullptr;   // preparation: chunks before each bitmap word
     int64_t sp_n_zero = 0;
     void* d_sp_fp = nullptr;
     size_t sp_fp_cap = 0;
@@ -107,7 +108,7 @@ struct dc_plan {
     // bytes held by each block-sparse buffer: a new preparation reuses a
     // buffer that is large enough (re-allocating tens of GB per density costs
     // more than building the tiles)
-    size_t sp_cap[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    size_t sp_cap[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     // The tiles no longer describe the plan (new voxel lists, lateral form or
     // tables): dc_fspb_spmm needs a new dc_fspb_spmm_prepare.  The buffers stay.
     void spmm_invalidate()
@@ -121,7 +122,7 @@ struct dc_plan {
     void spmm_free()
     {
         void* bufs[] = {d_sp_rbfirst, d_sp_first, d_sp_nchunk, d_sp_off, d_sp_kb, d_sp_tiles, d_sp_inv, d_sp_zero,
-                        d_sp_marks};
+                        d_sp_marks, d_sp_wpre};
         for (void* b : bufs)
             if (b) cudaFree(b);
         d_sp_rbfirst = d_sp_nchunk = nullptr;
@@ -133,6 +134,7 @@ struct dc_plan {
         d_sp_inv = nullptr;
         d_sp_zero = nullptr;
         d_sp_marks = nullptr;
+        d_sp_wpre = nullptr;
         for (size_t& c : sp_cap) c = 0;
         spmm_invalidate();
     }
@@ -206,6 +208,22 @@ cudaError_t launch_fill(const dc_plan* p, const int64_t* rowptr, int32_t* cols, 
                         int value_dtype, const float* fluence = nullptr, float* dose = nullptr);
 cudaError_t launch_scan_counts(const dc_plan* p, const int32_t* counts, int64_t* rowptr,
                                int64_t* total_dev);
+// The SpMM's block-sparse BF16 matrix straight from the pair evaluation
+// (k_dose.cu; the layout is k_spmm.cu's).  Row-block r of beam b holds its
+// list entries 128 r .. 128 r + 127; its chunks are the 4 x 4 beamlet patches
+// (16 tile columns) in which any of its pairs lies, in patch order.
+struct PatchTiles {
+    uint32_t* marks;            // [n_rb][words] patch bitmaps of each row-block
+    const uint16_t* wprefix;    // [n_rb][words] chunks of the row-block before each bitmap word
+    const int32_t* rb_first;    // [n_beams + 1] first row-block of each beam
+    const int64_t* chunk_off;   // [n_rb + 1] first chunk of each row-block
+    uint16_t* tiles;            // [chunks][128 x 16] BF16, zero where no pair
+    int words;
+};
+// sets the bit of every patch that holds a pair of the row-block (marks zeroed by the caller)
+cudaError_t launch_mark_patches(const dc_plan* p, const PatchTiles& t);
+// writes every pair's BF16 value into its tile (tiles zeroed by the caller)
+cudaError_t launch_tile_fill(const dc_plan* p, const PatchTiles& t);
 // backward pass of eq. (1) with respect to the commissioning tables (device
 // buffers; the gradients are cleared first)
 cudaError_t launch_dose_vjp(const dc_plan* p, const float* fluence, const float* wv, float* g_water, float* g_dens,
@@ -244,7 +262,7 @@ cudaError_t launch_batch(cudaStream_t s, const DoseArgs* h_args, const DoseArgs*
                          const int64_t* d_vpre, int64_t v_total, int64_t* d_prefix, unsigned int* d_counter,
                          int device, int variant, bool shared_water);
 // block-sparse tensor-core SpMM (k_spmm.cu)
-dc_status spmm_prepare(dc_plan* p, const int64_t* rowptr, const int32_t* cols, const uint16_t* vals);
+dc_status spmm_prepare(dc_plan* p);
 cudaError_t spmm_run(dc_plan* p, const float* F, int k, float* Y);
 cudaError_t spmm_run_static(dc_plan* p, const float* F, int k, float* Y);   // scratch in static device memory
 

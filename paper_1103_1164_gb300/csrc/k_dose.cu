@@ -783,6 +783,248 @@ __global__ void __launch_bounds__(kThreads, NV <= 2 ? 4 : (NV == 3 ? 3 : 2)) k_c
     }
 }
 
+// ---------------------------------------------------------------------------
+// The SpMM's block-sparse BF16 matrix straight from the pair evaluation, with
+// no CSR in between.  A warp's work unit (32 consecutive entries of a beam's
+// voxel list) lies inside one row-block of 128 entries.  Mark pass: the unit's
+// pair tests, as the count pass makes them, and the bit of every 4 x 4 beamlet
+// patch holding one of its pairs in the row-block's bitmap.  Fill pass: the
+// unit walks its window patch by patch (bands of four beamlet rows, patches
+// left to right), evaluates the patch's 16 beamlets, and writes each lane's
+// 16 BF16 values as two 16-byte pieces of the patch's tile: a warp's store
+// fills four 128-byte cores.
+
+__device__ __forceinline__ int unit_row_block(const PatchTiles& t, const DoseArgs& a, int64_t e0, int b, int& row0)
+{
+    const int64_t off = e0 - __ldg(a.base + b);
+    row0 = (int)(off & 127);
+    return __ldg(t.rb_first + b) + (int)(off >> 7);
+}
+
+__device__ __forceinline__ void mark_unit(const DoseArgs& a, const PatchTiles& t, const int64_t e0, const int b,
+                                          float4* srow, const int lane)
+{
+    const PlanView& P = a.P;
+    const BeamDev& bm = P.beams[b];
+    const float sad = __ldg(&bm.sad);
+    const int M = __ldg(&bm.M), N = __ldg(&bm.N), first = __ldg(&bm.first);
+    const float hfx = __ldg(&bm.half_fx), hfy = __ldg(&bm.half_fy);
+    const CountVoxel c = count_voxel(P, bm, __ldg(a.items + e0 + lane), sad);
+    int nlo, nhi;
+    count_rows(P, c, N, hfy, nlo, nhi);
+    const int wnlo = __reduce_min_sync(0xffffffffu, nlo);
+    const int wnhi = __reduce_max_sync(0xffffffffu, nhi);
+    int row0;
+    const int rb = unit_row_block(t, a, e0, b, row0);
+    uint32_t* mk = t.marks + (size_t)rb * t.words;
+    const int MB = (M + 3) >> 2;
+    int last = -1;
+    for (int n = wnlo; n <= wnhi; ++n) {
+        int mlo, mhi;
+        count_cols(P, c, n, M, hfx, hfy, mlo, mhi);
+        const int wmlo = __reduce_min_sync(0xffffffffu, mlo);
+        const int wmhi = __reduce_max_sync(0xffffffffu, mhi);
+        const uint32_t row = (uint32_t)(first + n * M);
+        for (int m0 = wmlo; m0 <= wmhi; m0 += 32) {
+            const int m1 = min(wmhi, m0 + 31);
+            __syncwarp();
+            if (m0 + lane <= m1) {
+                const uint32_t ib = DC_GUARD(P, row + (uint32_t)(m0 + lane), P.B, 5);
+                const float4* src = reinterpret_cast<const float4*>(P.bl) + 4u * ib;
+                srow[3 * lane] = __ldg(src);
+                srow[3 * lane + 1] = __ldg(src + 1);
+                srow[3 * lane + 2] = __ldg(src + 2);
+            }
+            __syncwarp();
+            for (int m = m0; m <= m1; ++m) {
+                const float4* rq = srow + 3 * (m - m0);
+                const bool in = pair_test(P, c.ln, rq[0], rq[1], rq[2]).in;
+                if (__any_sync(0xffffffffu, in)) {
+                    const int patch = (n >> 2) * MB + (m >> 2);
+                    if (patch != last) {
+                        if (lane == 0) atomicOr(mk + DC_GUARD(P, patch >> 5, t.words, 7), 1u << (patch & 31));
+                        last = patch;
+                    }
+                }
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 4) k_mark_patches(const DoseArgs a, const PatchTiles t)
+{
+    __shared__ int64_t s_base[kMaxBeams + 1];
+    __shared__ float4 s_row[kWarps][3 * 32];
+    const PlanView& P = a.P;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int q = threadIdx.x; q <= P.n_beams; q += blockDim.x) s_base[q] = a.base[q];
+    __syncthreads();
+    const int total = a.work[0];
+    for (;;) {
+        int w = 0;
+        if (lane == 0) w = atomicAdd(a.work + 1, 1);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if (w >= total) break;
+        const int64_t e0 = (int64_t)DC_GUARD(P, w, (s_base[P.n_beams] + 31) / 32, 4) * 32;
+        int b = 0;
+        while (b + 1 < P.n_beams && s_base[b + 1] <= e0) ++b;
+        mark_unit(a, t, e0, b, s_row[warp], lane);
+    }
+}
+
+template <bool MERGED, int LAT>
+__device__ __forceinline__ void tile_unit(const DoseArgs& a, const PatchTiles& t, const int32_t vi, const int64_t e0,
+                                          const int b, const float4* __restrict__ sW, float4* srow,
+                                          uint32_t* sval, const int lane)
+{
+    const PlanView& P = a.P;
+    Lane ln;
+    ln.valid = vi >= 0;
+    const int64_t v = ln.valid ? vi : 0;
+    const int ix = (int)(v % P.nx), iy = (int)((v / P.nx) % P.ny), iz = (int)(v / ((int64_t)P.nx * P.ny));
+    // the same roundings as the mark pass's count_voxel
+    const float rx = fmaf((float)ix, P.dx, P.ox), ry = fmaf((float)iy, P.dy, P.oy),
+                rz = fmaf((float)iz, P.dz, P.oz);
+    const BeamDev& bm = P.beams[b];
+    const float4 fac = __ldg(P.fac + v);
+    ln.cu1 = kLog2e * fac.x;
+    ln.cu2x = ln.cu2y = kLog2e * fac.y;
+    ln.cw1 = fac.z;
+    ln.cw2 = fac.w;
+    if (LAT == kItem) {
+        const float4 lf = __ldg(P.lfac + e0 + lane);
+        ln.cu2x = lf.x;
+        ln.cu2y = lf.y;
+        ln.cw1 = lf.z;
+        ln.cw2 = lf.w;
+    }
+    const float sx = __ldg(&bm.src[0]), sy = __ldg(&bm.src[1]), sz = __ldg(&bm.src[2]);
+    const float sad = __ldg(&bm.sad);
+    ln.vx = rx - sx;
+    ln.vy = ry - sy;
+    ln.vz = rz - sz;
+    if (!ln.valid) ln.vx = __int_as_float(0x7fffffff);   // NaN: no pair test passes
+    const float zz = ln.vx * __ldg(&bm.ez[0]) + ln.vy * __ldg(&bm.ez[1]) + ln.vz * __ldg(&bm.ez[2]);
+    const float pa = ln.vx * __ldg(&bm.ex[0]) + ln.vy * __ldg(&bm.ex[1]) + ln.vz * __ldg(&bm.ex[2]);
+    const float pc = ln.vx * __ldg(&bm.ey[0]) + ln.vy * __ldg(&bm.ey[1]) + ln.vz * __ldg(&bm.ey[2]);
+    const int M = __ldg(&bm.M), N = __ldg(&bm.N), first = __ldg(&bm.first);
+    const float hfx = __ldg(&bm.half_fx), hfy = __ldg(&bm.half_fy);
+    const bool live = ln.valid && zz > 1e-3f;
+    const float sz_ = sad / zz;
+    const float ca = pa * sz_, cc = pc * sz_;
+    const float rw = live ? (P.roi * sz_ * __ldg(&bm.inv_cos_max)) * 1.0005f + 1e-3f : 0.f;
+    int nlo = INT_MAX, nhi = INT_MIN;
+    if (live) {
+        nlo = max(0, (int)ceilf((cc - rw + hfy) / P.by - 0.5f));
+        nhi = min(N - 1, (int)floorf((cc + rw + hfy) / P.by - 0.5f));
+    }
+    const int wnlo = __reduce_min_sync(0xffffffffu, nlo);
+    const int wnhi = __reduce_max_sync(0xffffffffu, nhi);
+    int row0;
+    const int rb = unit_row_block(t, a, e0, b, row0);
+    const int row = row0 + lane;
+    const int MB = (M + 3) >> 2;
+    const uint32_t* mk = t.marks + (size_t)rb * t.words;
+    const uint16_t* wp = t.wprefix + (size_t)rb * t.words;
+    if (wnlo > wnhi) return;
+    for (int pb = wnlo >> 2; pb <= (wnhi >> 2); ++pb) {
+        // the band's beamlet columns: the union over its rows of the lanes' ROI chords
+        int mlo = INT_MAX, mhi = INT_MIN;
+        for (int r = 0; r < 4; ++r) {
+            const int n = 4 * pb + r;
+            if (!live || n < nlo || n > nhi) continue;
+            const float dc_ = cc - (-hfy + (n + 0.5f) * P.by);
+            const float h2 = rw * rw - dc_ * dc_;
+            if (h2 < 0.f) continue;
+            const float hx = sqrtf(h2);
+            mlo = min(mlo, max(0, (int)ceilf((ca - hx + hfx) / P.bx - 0.5f)));
+            mhi = max(mhi, min(M - 1, (int)floorf((ca + hx + hfx) / P.bx - 0.5f)));
+        }
+        const int wmlo = __reduce_min_sync(0xffffffffu, mlo);
+        const int wmhi = __reduce_max_sync(0xffffffffu, mhi);
+        if (wmlo > wmhi) continue;
+        for (int X = wmlo >> 2; X <= (wmhi >> 2); ++X) {
+            // the patch's 16 beamlet records (beamlets past the grid's edge get
+            // an entry depth no pair reaches)
+            __syncwarp();
+            if (lane < 16) {
+                const int n = 4 * pb + (lane >> 2), m = 4 * X + (lane & 3);
+                float4 q0 = make_float4(0.f, 0.f, 0.f, __int_as_float(0x7f800000)), q1 = make_float4(0.f, 0.f, 0.f, 0.f),
+                       q2 = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (n < N && m < M) {
+                    const uint32_t ib = DC_GUARD(P, (uint32_t)(first + n * M + m), P.B, 5);
+                    const float4* src = reinterpret_cast<const float4*>(P.bl) + 4u * ib;
+                    q0 = __ldg(src);
+                    q1 = __ldg(src + 1);
+                    q2 = __ldg(src + 2);
+                }
+                srow[3 * lane] = q0;
+                srow[3 * lane + 1] = q1;
+                srow[3 * lane + 2] = q2;
+            }
+            __syncwarp();
+            // the lane's 16 values, two BF16 per word (word j: columns 2j, 2j + 1)
+            bool any = false;
+#pragma unroll 1
+            for (int j = 0; j < 8; ++j) {
+                uint32_t word = 0u;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int k = 2 * j + h;
+                    const float4* rq = srow + 3 * k;
+                    const PairTest pt = pair_test(P, ln, rq[0], rq[1], rq[2]);
+                    if (pt.in) {
+                        const uint32_t i = (uint32_t)(first + (4 * pb + (k >> 2)) * M + 4 * X + (k & 3));
+                        const float D = pair_eval<MERGED, LAT, 0>(P, ln, i, sad, sW, pt);
+                        word |= (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(D)) << (16 * h);
+                        any = true;
+                    }
+                }
+                sval[9 * lane + j] = word;
+            }
+            if (__any_sync(0xffffffffu, any)) {
+                // the patch's chunk: the row-block's chunks before it
+                const int patch = pb * MB + X;
+                const int wi = DC_GUARD(P, patch >> 5, t.words, 7);
+                const int ch = __ldg(wp + wi) + __popc(__ldg(mk + wi) & ((1u << (patch & 31)) - 1u));
+                uint4* tile = reinterpret_cast<uint4*>(t.tiles + (size_t)(__ldg(t.chunk_off + rb) + ch) * (128 * 16));
+                // k-block h of the chunk is core (row / 8) * 2 + h; the row's 8 values of it are 16 contiguous bytes
+                const uint32_t* w = sval + 9 * lane;
+                tile[((row >> 3) * 2) * 8 + (row & 7)] = make_uint4(w[0], w[1], w[2], w[3]);
+                tile[((row >> 3) * 2 + 1) * 8 + (row & 7)] = make_uint4(w[4], w[5], w[6], w[7]);
+            }
+        }
+    }
+}
+
+template <bool MERGED, int LAT>
+__global__ void __launch_bounds__(kThreads, 4) k_tile_fill(const DoseArgs a, const PatchTiles t)
+{
+    extern __shared__ float4 smem[];
+    __shared__ int64_t s_base[kMaxBeams + 1];
+    __shared__ float4 s_row[kWarps][3 * 16];
+    __shared__ uint32_t s_val[kWarps][32 * 9];   // per lane 8 words, one of padding (no bank conflicts)
+    const PlanView& P = a.P;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float4* sW = smem;
+    if (!MERGED)
+        for (int q = threadIdx.x; q < 2 * P.w_n; q += blockDim.x) sW[q] = __ldg(P.water + q);
+    for (int q = threadIdx.x; q <= P.n_beams; q += blockDim.x) s_base[q] = a.base[q];
+    __syncthreads();
+    const int total = a.work[0];
+    for (;;) {
+        int w = 0;
+        if (lane == 0) w = atomicAdd(a.work + 1, 1);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if (w >= total) break;
+        const int64_t e0 = (int64_t)DC_GUARD(P, w, (s_base[P.n_beams] + 31) / 32, 4) * 32;
+        int b = 0;
+        while (b + 1 < P.n_beams && s_base[b + 1] <= e0) ++b;
+        const int32_t vi = __ldg(a.items + e0 + lane);
+        tile_unit<MERGED, LAT>(a, t, vi, e0, b, sW, s_row[warp], s_val[warp], lane);
+    }
+}
+
 // voxels per lane in the pair-count pass (measured on thorax9: 2 -> 0.722 ms,
 // 3 -> 0.725 ms, 4 -> 0.796 ms; one voxel per lane, the pair kernel's count
 // mode, took 0.847 ms)
@@ -1239,6 +1481,40 @@ cudaError_t launch_fill(const dc_plan* p, const int64_t* rowptr, int32_t* cols, 
     k_sum_beams<<<grid_for((int64_t)p->V), 256, 0, p->stream>>>(p->d_part, p->n_beams, 1, 1, p->V, dose, p->V);
     count_launches(1);
     return cudaGetLastError();
+}
+
+template <typename K>
+static cudaError_t launch_persistent(const dc_plan* p, K kern, size_t sm, const DoseArgs& a, const PatchTiles& t)
+{
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, sm);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(p->d_work + 1, 0, sizeof(int32_t), p->stream);
+    if (e != cudaSuccess) return e;
+    kern<<<sms * (per_sm > 0 ? per_sm : 1), kThreads, sm, p->stream>>>(a, t);
+    count_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mark_patches(const dc_plan* p, const PatchTiles& t)
+{
+    return launch_persistent(p, k_mark_patches, 0, make_args(p), t);
+}
+
+cudaError_t launch_tile_fill(const dc_plan* p, const PatchTiles& t)
+{
+    const DoseArgs a = make_args(p);
+    const bool item = p->coeffs.density_correction && p->lateral_mode != DC_LATERAL_ISO;
+    const size_t sm = p->merged ? 0 : 2 * sizeof(float4) * p->coeffs.w_n;
+    if (p->merged)
+        return item ? launch_persistent(p, k_tile_fill<true, kItem>, sm, a, t)
+                    : launch_persistent(p, k_tile_fill<true, kIso>, sm, a, t);
+    return item ? launch_persistent(p, k_tile_fill<false, kItem>, sm, a, t)
+                : launch_persistent(p, k_tile_fill<false, kIso>, sm, a, t);
 }
 
 cudaError_t launch_dose_vjp(const dc_plan* p, const float* fluence, const float* wv, float* g_water, float* g_dens,

@@ -4,14 +4,17 @@
 // accumulation in tensor memory.
 //
 // Storage.  Each beam's voxel list (k_bin.cu: voxels grouped by their cell in
-// the beam's eye view) is cut into row-blocks of 128 voxels.  A row-block's
-// nonzeros in the beam's columns are covered by K-chunks of 16 consecutive
-// beamlets starting at a multiple of 8; every chunk is a dense 128 x 16 BF16
-// tile stored in the UMMA "no swizzle" K-major core-matrix layout
+// the beam's eye view) is cut into row-blocks of 128 voxels.  The beam's
+// beamlets are numbered as tile columns in 4 x 4 patches (patch_col below), and
+// a row-block's nonzeros are covered by K-chunks of 16 tile columns: one per
+// patch that holds a pair of the row-block.  Every chunk is a dense 128 x 16
+// BF16 tile stored in the UMMA "no swizzle" K-major core-matrix layout
 // (8 x 8 cores of 128 contiguous bytes; core (m/8, k/8) at ((m/8) * 2 + k/8) * 128),
 // so one 4 KB bulk copy puts it in shared memory ready for tcgen05.mma.  The
-// fluence matrix is converted per call into the matching K-major layout of
-// 16 x 64 tiles, contiguous for every 8-aligned chunk start.
+// tiles are written by the pair kernels straight from the pair evaluation
+// (k_dose.cu: k_mark_patches, k_tile_fill).  The fluence matrix is converted
+// per call into the matching K-major layout of 16 x 64 tiles, contiguous for
+// every 8-aligned chunk start.
 //
 // Kernel.  One CTA (4 warps) per row-block at a time: thread 0 streams the
 // chunks' A and F tiles through a ring of shared-memory stages with
@@ -136,29 +139,6 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar)
                  : "memory");
 }
 
-// ---------------------------------------------------------------------------
-// CSR -> tiles.  One CTA of 128 threads per row-block; thread t owns row t.
-
-struct TileArgs {
-    const int64_t* rowptr;
-    const int32_t* cols;
-    const uint16_t* vals;        // BF16 bits
-    const int32_t* items;
-    const int64_t* base;         // start of each beam's list
-    const int32_t* n_items;
-    const int32_t* rb_first;     // [n_beams + 1] first row-block of each beam (host-computed)
-    const int4* beam;            // [n_beams + 1] (first beamlet, M, N, first tile column) of each beam
-    int n_beams;
-    const int32_t* bcount;       // [n_beams][V] pairs of each (beam, voxel): a row's segment of each beam
-    int64_t V;
-    int32_t* nchunk;             // count pass output [n_rb]
-    uint32_t* marks;             // count pass output, fill pass input: [n_rb][mark_words] occupied k-blocks
-    int mark_words;
-    const int64_t* chunk_off;    // fill pass: first chunk of each row-block
-    int32_t* chunk_kb;           // fill pass: k-block (beamlet / 8) of each chunk
-    uint16_t* tiles;             // fill pass: [chunks][128 * 16]
-};
-
 constexpr int kMaxKB = 4096;   // k-blocks of one beam (32768 tile columns)
 
 // Tile column order: each beam's beamlets in 4 x 4 patches of its M x N
@@ -174,129 +154,46 @@ __host__ __device__ __forceinline__ int patch_col(int n, int m, int M)
 }
 __host__ __device__ __forceinline__ int patch_cols(int M, int N) { return ((M + 3) >> 2) * ((N + 3) >> 2) * 16; }
 
-// A warp takes one row of the row-block at a time and reads its segment 32
-// consecutive entries per step, so the loads of the column indices and values
-// are whole lines.  (With one thread per row, every 4-byte load of the 32
-// lanes touched its own sector: on a 1.7 G-entry plan the tile fill read
-// 27 GB from DRAM for 10 GB of matrix and took 24 ms.)
-static_assert(kRB == 4 * 32, "four warps of 32 rows each: lane i of warp w owns row w + 4 i");
-template <bool FILL>
-__global__ void __launch_bounds__(kRB) k_tiles(const TileArgs a)
+// ---------------------------------------------------------------------------
+// Chunk lists of the block-sparse matrix.  The pair kernels (k_dose.cu) set,
+// per row-block, the bit of every 4 x 4 beamlet patch holding one of its
+// pairs; each marked patch is one chunk (16 tile columns, two k-blocks).
+// Per row-block: the chunks before each bitmap word, and the chunk count.
+__global__ void __launch_bounds__(256) k_patch_cover(const uint32_t* __restrict__ marks, int words, int n_rb,
+                                                     uint16_t* __restrict__ wpre, int32_t* __restrict__ nchunk)
 {
-    __shared__ uint32_t mark[kMaxKB / 32];
-    // fill pass: per k-block, 2 * (its chunk) + (1 if it is the chunk's second half)
-    __shared__ int16_t chunk_of[kMaxKB];
-    __shared__ int s_nc;
-    const int rb = blockIdx.x;
-    int b = 0;
-    while (b + 1 < a.n_beams && a.rb_first[b + 1] <= rb) ++b;
-    const int j = rb - a.rb_first[b];
-    const int nit = a.n_items[b];
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int4 bm = a.beam[b];
-    const int c0 = bm.x, M = bm.y, nbl = bm.y * bm.z;
-    // n = l / M as a multiply-high: exact for l, M <= 2^15 (a beam has at most
-    // 32768 beamlets), since then l (ceil(2^32 / M) M - 2^32) < 2^32; M = 1
-    // (where ceil(2^32 / M) does not fit) is taken apart
-    const uint32_t mdiv = M > 1 ? 0xffffffffu / (uint32_t)M + 1u : 0u;
-    auto row_of = [&](int l) { return M > 1 ? (int)__umulhi((uint32_t)l, mdiv) : l; };
-    const int kb0 = bm.w / 8, nkb = (a.beam[b + 1].w - bm.w) / 8;
-    for (int q = t; q < kMaxKB / 32; q += blockDim.x) mark[q] = 0;
-    __syncthreads();
-    // the warp's rows are warp, warp + 4, ..., and lane i finds the segment of
-    // row warp + 4 i at once for all of them: it starts after the segments of
-    // the beams before b and holds bcount[b][v] entries (columns ascending,
-    // all of this beam); len = 0 for padding rows
-    int64_t my_r0 = 0;
-    int my_len = 0;
-    {
-        const int e = j * kRB + warp + (kRB / 32) * lane;
-        const int v = e < nit ? a.items[a.base[b] + e] : -1;
-        if (v >= 0) {
-            int64_t r0 = a.rowptr[v];
-            for (int bb = 0; bb < b; ++bb) r0 += a.bcount[(size_t)bb * a.V + v];
-            my_r0 = r0;
-            my_len = a.bcount[(size_t)b * a.V + v];
+    for (int rb = blockIdx.x * blockDim.x + threadIdx.x; rb < n_rb; rb += gridDim.x * blockDim.x) {
+        int acc = 0;
+        for (int w = 0; w < words; ++w) {
+            wpre[(size_t)rb * words + w] = (uint16_t)acc;
+            acc += __popc(marks[(size_t)rb * words + w]);
         }
+        nchunk[rb] = acc;
     }
-    auto segment = [&](int i, int64_t& r0, int& len) {
-        r0 = __shfl_sync(0xffffffffu, my_r0, i);
-        len = __shfl_sync(0xffffffffu, my_len, i);
-    };
-    uint32_t* gmark = a.marks + (size_t)rb * a.mark_words;
-    if (FILL) {
-        // the count pass left this row-block's occupied k-blocks
-        for (int q = t; q < a.mark_words; q += blockDim.x) mark[q] = gmark[q];
-    } else for (int i = 0; i < 32; ++i) {
-        int64_t r0;
-        int len;
-        segment(i, r0, len);
-#pragma unroll 2
-        for (int q0 = 0; q0 < len; q0 += 32) {
-            const int q = q0 + lane;
-            int kb = -1;
-            if (q < len) {
-                const int l = a.cols[r0 + q] - c0;
-                if ((unsigned)l < (unsigned)nbl) {   // always: the segment holds this beam's columns only
-                    const int n = row_of(l);
-                    kb = patch_col(n, l - n * M, M) / 8;
-                }
+}
+
+// The first k-block of every chunk (twice its patch, in the all-beams tile
+// column numbering), a warp per row-block.
+__global__ void __launch_bounds__(256) k_patch_list(const uint32_t* __restrict__ marks,
+                                                    const uint16_t* __restrict__ wpre, int words, int n_rb,
+                                                    const int32_t* __restrict__ rb_first, const int4* __restrict__ beam,
+                                                    int n_beams, const int64_t* __restrict__ chunk_off,
+                                                    int32_t* __restrict__ chunk_kb)
+{
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int rb = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; rb < n_rb; rb += nwarps) {
+        int b = 0;
+        while (b + 1 < n_beams && rb_first[b + 1] <= rb) ++b;
+        const int kb0 = beam[b].w / 8;
+        for (int w = lane; w < words; w += 32) {
+            uint32_t m = marks[(size_t)rb * words + w];
+            int64_t c = chunk_off[rb] + wpre[(size_t)rb * words + w];
+            while (m) {
+                const int bit = __ffs((int)m) - 1;
+                m &= m - 1u;
+                chunk_kb[c++] = kb0 + 2 * (32 * w + bit);
             }
-            // neighbouring entries mostly share a k-block: one shared-memory
-            // atomic per change along the lanes
-            const int prev = __shfl_up_sync(0xffffffffu, kb, 1);
-            if (kb >= 0 && (lane == 0 || kb != prev)) atomicOr(&mark[kb >> 5], 1u << (kb & 31));
-        }
-    }
-    __syncthreads();
-    if (t == 0) {
-        // greedy cover of the marked k-blocks by pairs of consecutive k-blocks
-        int nc = 0, kb = 0;
-        while (kb < nkb) {
-            if (mark[kb >> 5] & (1u << (kb & 31))) {
-                if (FILL) {
-                    a.chunk_kb[a.chunk_off[rb] + nc] = kb0 + kb;
-                    chunk_of[kb] = (int16_t)(2 * nc);
-                    if (kb + 1 < nkb) chunk_of[kb + 1] = (int16_t)(2 * nc + 1);
-                }
-                ++nc;
-                kb += 2;
-            } else {
-                ++kb;
-            }
-        }
-        s_nc = nc;
-        if (!FILL) a.nchunk[rb] = nc;
-    }
-    if (!FILL) {
-        for (int q = t; q < a.mark_words; q += blockDim.x) gmark[q] = mark[q];
-        return;
-    }
-    __syncthreads();
-    // zero this row-block's tiles, then scatter the BF16 values
-    uint16_t* tiles = a.tiles + (size_t)a.chunk_off[rb] * (kRB * kKC);
-    uint4* tz = reinterpret_cast<uint4*>(tiles);
-    const int nz = s_nc * (kTileA / 16);
-    for (int q = t; q < nz; q += blockDim.x) tz[q] = make_uint4(0, 0, 0, 0);
-    __syncthreads();
-    for (int i = 0; i < 32; ++i) {
-        const int row = warp + (kRB / 32) * i;
-        int64_t r0;
-        int len;
-        segment(i, r0, len);
-#pragma unroll 2
-        for (int q0 = 0; q0 < len; q0 += 32) {
-            const int q = q0 + lane;
-            if (q >= len) continue;
-            const int l = a.cols[r0 + q] - c0;
-            if ((unsigned)l >= (unsigned)nbl) continue;
-            const int n = row_of(l);
-            const int pc = patch_col(n, l - n * M, M);
-            const int code = chunk_of[pc / 8];
-            const int k = (pc & 7) + 8 * (code & 1);   // column within the chunk, 0..15
-            // element (m = row, k) of the K-major core-matrix layout
-            const int off = ((row >> 3) * 2 + (k >> 3)) * 64 + (row & 7) * 8 + (k & 7);
-            tiles[(size_t)(code >> 1) * (kRB * kKC) + off] = a.vals[r0 + q];
         }
     }
 }
@@ -753,7 +650,7 @@ cudaError_t sp_buffer(dc_plan* p, int slot, T*& ptr, size_t bytes)
     return e;
 }
 
-dc_status spmm_prepare(dc_plan* p, const int64_t* rowptr, const int32_t* cols, const uint16_t* vals)
+dc_status spmm_prepare(dc_plan* p)
 {
     const int nb = p->n_beams;
     std::vector<int32_t> n_items(nb);
@@ -786,26 +683,19 @@ dc_status spmm_prepare(dc_plan* p, const int64_t* rowptr, const int32_t* cols, c
                             p->stream));
     DC_CUDA(cudaMemcpyAsync(p->d_sp_first, beam.data(), (nb + 1) * sizeof(int4), cudaMemcpyHostToDevice,
                             p->stream));
-    TileArgs ta{};
-    ta.rowptr = rowptr;
-    ta.cols = cols;
-    ta.vals = vals;
-    ta.items = p->d_items;
-    ta.base = p->d_base;
-    ta.n_items = p->d_nitems;
-    ta.rb_first = p->d_sp_rbfirst;
-    ta.beam = p->d_sp_first;
-    ta.n_beams = nb;
-    ta.bcount = p->d_bcount;
-    ta.V = p->V;
-    ta.nchunk = p->d_sp_nchunk;
-    int max_kb = 0;
-    for (int b = 0; b < nb; ++b) max_kb = std::max(max_kb, patch_cols(p->M[b], p->N[b]) / 8);
-    ta.mark_words = (max_kb + 31) / 32;
-    DC_CUDA(sp_buffer(p, 8, p->d_sp_marks, (size_t)std::max(n_rb, 1) * ta.mark_words * sizeof(uint32_t)));
-    ta.marks = p->d_sp_marks;
+    // the chunks of each row-block: the 4 x 4 patches holding one of its pairs
+    int max_patch = 0;
+    for (int b = 0; b < nb; ++b) max_patch = std::max(max_patch, patch_cols(p->M[b], p->N[b]) / 16);
+    const int words = (max_patch + 31) / 32;
+    const size_t nmark = (size_t)std::max(n_rb, 1) * words;
+    DC_CUDA(sp_buffer(p, 8, p->d_sp_marks, nmark * sizeof(uint32_t)));
+    DC_CUDA(sp_buffer(p, 9, p->d_sp_wpre, nmark * sizeof(uint16_t)));
+    DC_CUDA(cudaMemsetAsync(p->d_sp_marks, 0, nmark * sizeof(uint32_t), p->stream));
+    PatchTiles pt{p->d_sp_marks, p->d_sp_wpre, p->d_sp_rbfirst, p->d_sp_off, nullptr, words};
     if (n_rb > 0) {
-        k_tiles<false><<<n_rb, kRB, 0, p->stream>>>(ta);
+        DC_CUDA(launch_mark_patches(p, pt));
+        k_patch_cover<<<gsize(n_rb), 256, 0, p->stream>>>(p->d_sp_marks, words, n_rb, p->d_sp_wpre,
+                                                           p->d_sp_nchunk);
         count_launches(1);
         DC_CUDA(cudaGetLastError());
     }
@@ -821,13 +711,15 @@ dc_status spmm_prepare(dc_plan* p, const int64_t* rowptr, const int32_t* cols, c
                             p->stream));
     DC_CUDA(sp_buffer(p, 4, p->d_sp_kb, (size_t)(p->sp_chunks + 1) * sizeof(int32_t)));
     DC_CUDA(sp_buffer(p, 5, p->d_sp_tiles, (size_t)(p->sp_chunks + 1) * kTileA));
-    ta.chunk_off = p->d_sp_off;
-    ta.chunk_kb = p->d_sp_kb;
-    ta.tiles = reinterpret_cast<uint16_t*>(p->d_sp_tiles);
     if (n_rb > 0) {
-        k_tiles<true><<<n_rb, kRB, 0, p->stream>>>(ta);
+        k_patch_list<<<gsize((int64_t)n_rb * 32), 256, 0, p->stream>>>(p->d_sp_marks, p->d_sp_wpre, words, n_rb,
+                                                                        p->d_sp_rbfirst, p->d_sp_first, nb,
+                                                                        p->d_sp_off, p->d_sp_kb);
         count_launches(1);
         DC_CUDA(cudaGetLastError());
+        DC_CUDA(cudaMemsetAsync(p->d_sp_tiles, 0, (size_t)p->sp_chunks * kTileA, p->stream));
+        pt.tiles = reinterpret_cast<uint16_t*>(p->d_sp_tiles);
+        DC_CUDA(launch_tile_fill(p, pt));
     }
     {
         // inverse of the beam lists (the reduction of several beams' partial
