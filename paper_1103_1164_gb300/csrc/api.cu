@@ -860,8 +860,9 @@ static dc_status check_device_status(dc_plan* p)
         DC_CUDA(cudaStreamSynchronize(p->stream));
         if (c != 0) {
             static const char* what[] = {"", "depth-table sample", "A-row sample", "water-table sample",
-                                         "voxel-list work unit", "beamlet record or fluence", "CSR row segment"};
-            set_error(std::string("bounds check: a pair kernel's ") + (c > 0 && c < 7 ? what[c] : "index") +
+                                         "voxel-list work unit", "beamlet record or fluence", "CSR row segment",
+                                         "patch bitmap word"};
+            set_error(std::string("bounds check: a pair kernel's ") + (c > 0 && c < 8 ? what[c] : "index") +
                       " index was out of range (DC_BOUNDS_CHECK build)");
             return DC_ECUDA;
         }

@@ -97,6 +97,10 @@ for seed, kw in ((95, dict(n=(13, 11, 9), vox=0.35, n_beams=3, couch=True)),
     out[f"rowptr{{seed}}"] = rowptr
     out[f"cols{{seed}}"] = cols
     out[f"vals{{seed}}"] = vals
+    # the SpMM tiles come from their own pair passes (mark, tile fill)
+    dc.dc_fspb_spmm_prepare(plan)
+    F = np.random.default_rng(seed).uniform(0, 1, (plan.n_beamlets, 4)).astype(np.float32)
+    out[f"spmm{{seed}}"] = dc.dc_fspb_spmm(plan, F)
     dc.dc_fspb_device_status(plan)
 np.savez({out!r}, **out)
 print("run ok")
