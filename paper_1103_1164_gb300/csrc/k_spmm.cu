@@ -485,23 +485,39 @@ __global__ void __launch_bounds__(kSpmmThreads) k_spmm(const SpmmArgs a)
 }
 
 // Y[v][q] = sum over beams of the partial rows, in beam order, with
-// Neumaier-compensated summation.
+// Neumaier-compensated summation.  A warp per voxel: the lanes find the
+// voxel's list positions of all beams at once, then add the partial rows
+// column by column (lane l: columns 2l, 2l + 1), so the row reads are whole
+// lines.  (One thread per output element, each looking up the positions
+// itself, took 9.5 ms on a 12.6 M-voxel, 9-beam plan at k = 64.)
+__device__ __forceinline__ void neumaier_add(float& s, float& c, float x)
+{
+    const float t = s + x;
+    c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
+    s = t;
+}
+
 __global__ void __launch_bounds__(256) k_spmm_reduce(const float* __restrict__ P, const int32_t* __restrict__ inv,
                                                      int n_beams, int64_t V, int k, float* __restrict__ Y)
 {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < V * k; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t v = e / k;
-        const int q = (int)(e % k);
-        float s = 0.f, c = 0.f;
+    const int lane = threadIdx.x & 31, q = 2 * lane;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; v < V; v += nwarps) {
+        // the voxel's position in each beam's list (at most 64 beams: two per lane)
+        const int32_t pa = lane < n_beams ? __ldg(inv + (size_t)lane * V + v) : -1;
+        const int32_t pb = lane + 32 < n_beams ? __ldg(inv + (size_t)(lane + 32) * V + v) : -1;
+        float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
+#pragma unroll 4
         for (int b = 0; b < n_beams; ++b) {
-            const int32_t pos = __ldg(inv + (size_t)b * V + v);
+            const int32_t pos = __shfl_sync(0xffffffffu, b < 32 ? pa : pb, b & 31);
             if (pos < 0) continue;
-            const float x = __ldg(P + (size_t)pos * k + q);
-            const float tsum = s + x;
-            c += fabsf(s) >= fabsf(x) ? (s - tsum) + x : (x - tsum) + s;
-            s = tsum;
+            const float* row = P + (size_t)pos * k;
+            if (q < k) neumaier_add(s0, c0, __ldg(row + q));
+            if (q + 1 < k) neumaier_add(s1, c1, __ldg(row + q + 1));
         }
-        Y[e] = s + c;
+        float* y = Y + (size_t)v * k;
+        if (q < k) y[q] = s0 + c0;
+        if (q + 1 < k) y[q + 1] = s1 + c1;
     }
 }
 
@@ -822,7 +838,7 @@ cudaError_t spmm_run(dc_plan* p, const float* F, int k, float* Y)
         if (e != cudaSuccess) return e;
     }
     if (!direct) {
-        k_spmm_reduce<<<gsize(p->V * k), 256, 0, p->stream>>>(p->d_sp_p, p->d_sp_inv, p->n_beams, p->V, k, Y);
+        k_spmm_reduce<<<gsize(p->V * 32), 256, 0, p->stream>>>(p->d_sp_p, p->d_sp_inv, p->n_beams, p->V, k, Y);
         count_launches(1);
         e = cudaGetLastError();
     }
@@ -935,7 +951,7 @@ cudaError_t spmm_run_static(dc_plan* p, const float* F, int k, float* Y)
         if (e != cudaSuccess) return e;
     }
     if (!direct) {
-        k_spmm_reduce<<<gsize(p->V * k), 256, 0, p->stream>>>(sc.part, p->d_sp_inv, p->n_beams, p->V, k, Y);
+        k_spmm_reduce<<<gsize(p->V * 32), 256, 0, p->stream>>>(sc.part, p->d_sp_inv, p->n_beams, p->V, k, Y);
         count_launches(1);
         e = cudaGetLastError();
     }
