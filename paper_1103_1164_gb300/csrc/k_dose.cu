@@ -39,6 +39,10 @@ constexpr int kRingLd = kRing + 1;
 constexpr int row_max(int mode) { return mode == 2 ? 16 : 32; }
 
 enum Mode { kDose = 0, kCount = 1, kFill = 2, kGrad = 3 };
+// fluence vectors per pass of the multi-fluence dose (the staging below
+// rotates the order of their NF / 4 float4 by the lane's low two bits)
+constexpr int kMultiFluence = 16;
+static_assert(kMultiFluence / 4 == 4, "four float4 of fluences per beamlet record");
 
 __device__ __forceinline__ float ex2(float x)
 {
@@ -394,7 +398,7 @@ __device__ __forceinline__ void flush_stage(const DoseArgs& a, const int2* st, i
 template <int MODE, int NF, bool MERGED, int LAT, int PREC = 0>
 __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi, const int64_t e0, const int b,
                                              const float4* __restrict__ sW, int2* sst, float4* srow,
-                                             const int lane)
+                                             const int lane, float4* sflu = nullptr)
 {
     const PlanView& P = a.P;
     const int64_t V = (int64_t)P.nx * P.ny * P.nz;
@@ -488,6 +492,20 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
             // theta weight (which only the table set-up uses)
             if (MODE != kCount && NF == 1) q2.w = __ldg(a.fluence + ib);
             srow[3 * lane + 2] = q2;
+            if (MODE == kDose && NF > 1) {
+                // the beamlet's NF fluences beside its record (zero past a.nf),
+                // as NF / 4 float4 whose order is rotated by the lane (fewer
+                // bank conflicts among the lanes' stores)
+                float4* f4 = sflu + (NF / 4) * lane;
+#pragma unroll
+                for (int j = 0; j < NF / 4; ++j) {
+                    float f[4];
+#pragma unroll
+                    for (int h = 0; h < 4; ++h)
+                        f[h] = 4 * j + h < a.nf ? __ldg(a.fluence + ((4 * j + h) * (uint32_t)a.ldf + ib)) : 0.f;
+                    f4[j ^ (lane & 3)] = make_float4(f[0], f[1], f[2], f[3]);
+                }
+            }
         }
         __syncwarp();
         // two beamlets per trip: their independent loads and arithmetic
@@ -514,10 +532,15 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
                     if (NF == 1) {
                         acc[0] = fmaf(rq[2].w, D, acc[0]);
                     } else {
+                        const float4* f4 = sflu + (NF / 4) * (m - m0);
 #pragma unroll
-                        for (int q = 0; q < NF; ++q)
-                            if (q < a.nf)
-                                acc[q] = fmaf(__ldg(a.fluence + (q * (uint32_t)a.ldf + DC_GUARD(P, i, P.B, 5))), D, acc[q]);
+                        for (int q4 = 0; q4 < NF / 4; ++q4) {
+                            const float4 f = f4[q4 ^ ((m - m0) & 3)];
+                            acc[4 * q4] = fmaf(f.x, D, acc[4 * q4]);
+                            acc[4 * q4 + 1] = fmaf(f.y, D, acc[4 * q4 + 1]);
+                            acc[4 * q4 + 2] = fmaf(f.z, D, acc[4 * q4 + 2]);
+                            acc[4 * q4 + 3] = fmaf(f.w, D, acc[4 * q4 + 3]);
+                        }
                     }
                 }
             } else {
@@ -594,6 +617,8 @@ __global__ void __launch_bounds__(kThreads, min_ctas<MODE, NF>()) k_pairs(const 
         for (int q = threadIdx.x; q < ngrad; q += blockDim.x) sgrad[q] = 0.f;
     }
     __shared__ float4 s_row[kWarps][3 * row_max(MODE)];
+    // several fluence vectors: each staged beamlet's fluences (NF per record)
+    __shared__ float4 s_flu[NF > 1 ? kWarps : 1][NF > 1 ? row_max(MODE) * NF / 4 : 1];
     // the water tables are read from shared memory unless merged into the depth tables
     if (MODE != kCount && !MERGED)
         for (int q = threadIdx.x; q < 2 * P.w_n; q += blockDim.x) sW[q] = __ldg(P.water + q);
@@ -610,7 +635,8 @@ __global__ void __launch_bounds__(kThreads, min_ctas<MODE, NF>()) k_pairs(const 
         int b = 0;
         while (b + 1 < P.n_beams && s_base[b + 1] <= e0) ++b;
         const int32_t vi = __ldg(a.items + e0 + lane);
-        process_unit<MODE, NF, MERGED, LAT, PREC>(a, vi, e0, b, sW, sst, s_row[warp], lane);
+        process_unit<MODE, NF, MERGED, LAT, PREC>(a, vi, e0, b, sW, sst, s_row[warp], lane,
+                                                  NF > 1 ? s_flu[NF > 1 ? warp : 0] : nullptr);
     }
     if (MODE == kGrad) {
         __syncthreads();
