@@ -502,10 +502,19 @@ __global__ void __launch_bounds__(256) k_spmm_reduce(const float* __restrict__ P
 {
     const int lane = threadIdx.x & 31, q = 2 * lane;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t v = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; v < V; v += nwarps) {
-        // the voxel's position in each beam's list (at most 64 beams: two per lane)
-        const int32_t pa = lane < n_beams ? __ldg(inv + (size_t)lane * V + v) : -1;
-        const int32_t pb = lane + 32 < n_beams ? __ldg(inv + (size_t)(lane + 32) * V + v) : -1;
+    // the voxel's position in each beam's list (at most 64 beams: two per
+    // lane), looked up one voxel ahead so that the lookup of the next voxel
+    // overlaps the sums of this one
+    int64_t v = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    auto lookup = [&](int64_t u, int32_t& a, int32_t& b) {
+        a = u < V && lane < n_beams ? __ldg(inv + (size_t)lane * V + u) : -1;
+        b = u < V && lane + 32 < n_beams ? __ldg(inv + (size_t)(lane + 32) * V + u) : -1;
+    };
+    int32_t na, nb;
+    lookup(v, na, nb);
+    for (; v < V; v += nwarps) {
+        const int32_t pa = na, pb = nb;
+        lookup(v + nwarps, na, nb);
         float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
 #pragma unroll 4
         for (int b = 0; b < n_beams; ++b) {
