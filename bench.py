@@ -1192,6 +1192,7 @@ def run_batch_form(args, dc, torch, stream, peak_pairs):
 
 
 def run_batch_multi_fluence(args, dc, torch, inputs, net, k=64):
+    peaks, _ = measured_peaks()
     """The 16 head-and-neck plans with k fluence vectors each (uniform [0, 1],
     seeded), the north star's two forms of the multi-fluence dose, plan after
     plan: plain = axis-stencil lateral densities and the FP32 direct
@@ -1219,6 +1220,7 @@ def run_batch_multi_fluence(args, dc, torch, inputs, net, k=64):
     acc = {"plain_ms": 0.0, "surrogate_density_ms": 0.0, "surrogate_spmm_ms": 0.0}
     errs = {}
     pairs_total = 0
+    bytes_alg = bytes_tiles = 0
     for j, p in enumerate(inputs):
         rho = torch.from_numpy(p.rho).cuda()
         plan = dc.dc_fspb_create_from(p, device_density=rho)
@@ -1239,7 +1241,16 @@ def run_batch_multi_fluence(args, dc, torch, inputs, net, k=64):
         dc.dc_fspb_spmm(plan, F, Y)
         acc["surrogate_density_ms"] += wall(per_density)
         acc["surrogate_spmm_ms"] += wall(lambda: dc.dc_fspb_spmm(plan, F, Y))
-        pairs_total += dc.dc_fspb_pair_count(plan)
+        npairs = dc.dc_fspb_pair_count(plan)
+        pairs_total += npairs
+        chunks, _ = dc.dc_fspb_spmm_info(plan)
+        # per set of k: the matrix's algorithmic bytes (2 B value + 4 B column per
+        # nonzero), the FP32 output, the BF16 fluences; the bytes the SpMM streams
+        # (4 KB tiles and their indices, the FP32 partial rows of every beam
+        # written and read back, the output)
+        bytes_alg += npairs * 6 + V * k * 4 + B * k * 2
+        items = dc.dc_fspb_list_entries(plan) if len(p.beams) > 1 else 0
+        bytes_tiles += chunks * (4096 + 4) + 2 * items * k * 4 + V * k * 4 + B * k * 4
         if not args.no_cpu and j in (big, small):
             # seeded voxels, half of them above 10 % of the first column's maximum
             d0 = D[0].cpu().numpy()
@@ -1272,6 +1283,13 @@ def run_batch_multi_fluence(args, dc, torch, inputs, net, k=64):
             "sets_of_64_for_3x": sets_3x,
             "evals_per_s": {"plain": pairs_total * k / (acc["plain_ms"] * 1e-3),
                             "surrogate_bf16_one_set": pairs_total * k / (sur_one * 1e-3)},
+            "spmm_roofline": {"bound": "hbm", "achieved": bytes_alg / (per_set * 1e-3) / 1e9,
+                              "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                              "frac": bytes_alg / (per_set * 1e-3) / 1e9 / peaks.get("hbm_gbs"),
+                              "bytes": bytes_alg, "streamed_bytes": bytes_tiles,
+                              "streamed_frac": bytes_tiles / (per_set * 1e-3) / 1e9 / peaks.get("hbm_gbs"),
+                              "timing": "host wall clock per plan around dc_fspb_spmm (fluence packing, "
+                                        "the tensor-core product, the per-beam reduction)"},
             "timing": "host wall clock, synchronised, around each plan's calls; cells autotuned at set-up",
             "max_err_vs_fp64_oracle_axis_over_colmax": errs or None}
 
