@@ -326,15 +326,61 @@ dc_status dc_mlp_train(dc_mlp* m, const float* X, const float* T, int32_t n, int
     if (n < 1 || batch < 1 || epochs < 0 || !(lr > 0)) return bad("dc_mlp_train: bad n, batch, epochs or lr");
     dc_status s = stage(m, X, T, n, flags);
     if (s != DC_OK) return s;
-    for (int ep = 0; ep < epochs; ++ep) {
-        for (int b0 = 0; b0 + batch <= n; b0 += batch) {   // whole batches in the given (pre-shuffled) order
-            const int tiles = (batch + 63) / 64;
-            const int nctas = tiles < kGradCtas ? tiles : kGradCtas;
-            DC_CUDA(grad_kernel(m, nctas, X + (size_t)b0 * 48, T + (size_t)b0 * 3, batch));
-            ++m->step;
-            DC_CUDA(launch_mlp_adam(m->stream, m->partial, nctas, m->theta, m->m1, m->m2, nullptr, lr, 0.9f, 0.999f,
-                                    1e-8f, m->step));
+    // whole batches in the given (pre-shuffled) order: a gradient and an Adam
+    // launch per step, on stream `st`
+    auto steps = [&](cudaStream_t st) -> cudaError_t {
+        const int tiles = (batch + 63) / 64;
+        const int nctas = tiles < kGradCtas ? tiles : kGradCtas;
+        for (int ep = 0; ep < epochs; ++ep)
+            for (int b0 = 0; b0 + batch <= n; b0 += batch) {
+                const cudaStream_t own = m->stream;
+                m->stream = st;
+                cudaError_t e = grad_kernel(m, nctas, X + (size_t)b0 * 48, T + (size_t)b0 * 3, batch);
+                m->stream = own;
+                if (e != cudaSuccess) return e;
+                ++m->step;
+                e = launch_mlp_adam(st, m->partial, nctas, m->theta, m->m1, m->m2, nullptr, lr, 0.9f, 0.999f, 1e-8f,
+                                    m->step);
+                if (e != cudaSuccess) return e;
+            }
+        return cudaSuccess;
+    };
+    const int64_t n_steps = (int64_t)epochs * (n / batch);
+    if (n_steps < 8) {
+        DC_CUDA(steps(m->stream));
+    } else {
+        // many small launches: captured once as a CUDA graph (on a stream of
+        // its own, ordered after and before the trainer's stream), so that
+        // they run back to back without a host launch in between
+        cudaStream_t cs = nullptr;
+        cudaEvent_t ev = nullptr;
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        const int64_t step0 = m->step;
+        cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ev, m->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev, 0);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            const cudaError_t ec = steps(cs);
+            const cudaError_t ee = cudaStreamEndCapture(cs, &g);
+            e = ec != cudaSuccess ? ec : ee;
         }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+        bool launched = false;
+        if (e == cudaSuccess) {
+            e = cudaGraphLaunch(ge, cs);
+            launched = e == cudaSuccess;
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(ev, cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(m->stream, ev, 0);
+        if (!launched) m->step = step0;   // the captured steps never ran
+        if (ge) cudaGraphExecDestroy(ge);         // freed when the replay ends
+        if (g) cudaGraphDestroy(g);
+        if (ev) cudaEventDestroy(ev);
+        if (cs) cudaStreamDestroy(cs);
+        if (e != cudaSuccess) return cuda_fail(e, "dc_mlp_train");
     }
     if (loss) return grad_pass(m, X, T, n, loss);
     DC_CUDA(cudaStreamSynchronize(m->stream));
