@@ -86,10 +86,12 @@ import sys, numpy as np
 sys.path.insert(0, {root!r})
 from paper_1103_1164_gb300 import dc_fspb as dc, synth
 out = {{}}
-for seed, kw in ((95, dict(n=(13, 11, 9), vox=0.35, n_beams=3, couch=True)),
-                 (96, dict(n=(17, 9, 7), vox=0.3, n_beams=2, beamlet=0.2, beamlet_y=0.5)),
-                 (97, dict(n=(10, 12, 14), vox=0.25, n_beams=1, field=3.0))):
-    p = synth.small_plan(seed, **kw)
+cases = [(95, dict(n=(13, 11, 9), vox=0.35, n_beams=3, couch=True)),
+         (96, dict(n=(17, 9, 7), vox=0.3, n_beams=2, beamlet=0.2, beamlet_y=0.5)),
+         (97, dict(n=(10, 12, 14), vox=0.25, n_beams=1, field=3.0)),
+         (98, None)]                     # the thorax plan at 3/8 scale: 9 fields, 5,601 beamlets
+for seed, kw in cases:
+    p = synth.small_plan(seed, **kw) if kw is not None else synth.config2(0.375)
     plan = dc.dc_fspb_create_from(p)
     out[f"dose{{seed}}"] = dc.dc_fspb_dose(plan, p.fluence)
     d, rowptr, cols, vals = dc.dc_fspb_dose_and_matrix(plan, p.fluence)
@@ -109,8 +111,8 @@ print("run ok")
 
 def test_bounds_checked_build_runs_clean_and_identical(dc, tmp_path):
     # the DC_BOUNDS_CHECK build guards every index of the pair kernels; on
-    # tiny ragged grids it must report no violation and give the normal
-    # build's results bit for bit
+    # tiny ragged grids and a reduced thorax plan it must report no violation
+    # and give the normal build's results bit for bit
     import subprocess
     import sys
     from paper_1103_1164_gb300 import build
