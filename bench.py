@@ -1192,9 +1192,8 @@ def run_batch_form(args, dc, torch, stream, peak_pairs):
 
 
 def run_batch_multi_fluence(args, dc, torch, inputs, net, k=64):
-    peaks, _ = measured_peaks()
     """The 16 head-and-neck plans with k fluence vectors each (uniform [0, 1],
-    seeded), the north star's two forms of the multi-fluence dose, plan after
+    seeded), the two forms of the multi-fluence dose, plan after
     plan: plain = axis-stencil lateral densities and the FP32 direct
     evaluation of the k vectors (dc_fspb_dose_batch); surrogate + BF16 = the
     network's lateral densities, the BF16 dose-deposition matrix
@@ -1205,6 +1204,7 @@ def run_batch_multi_fluence(args, dc, torch, inputs, net, k=64):
     sets at which it is 3x faster; its error against the FP64 oracle's axis
     form on seeded voxels of the largest and the smallest plan, every column."""
     from paper_1103_1164_gb300 import surrogate
+    peaks, _ = measured_peaks()
     gen = torch.Generator(device="cuda")
     gen.manual_seed(1005)
     big = int(np.argmax([p.grid.nx * p.grid.ny * p.grid.nz for p in inputs]))
