@@ -827,17 +827,28 @@ __device__ __forceinline__ int unit_row_block(const PatchTiles& t, const DoseArg
     return __ldg(t.rb_first + b) + (int)(off >> 7);
 }
 
-__device__ __forceinline__ void mark_unit(const DoseArgs& a, const PatchTiles& t, const int64_t e0, const int b,
-                                          float4* srow, const int lane)
+// NV consecutive units of one row-block at once, as count_units takes them:
+// lane l holds entry l of each, and every staged beamlet record is tested
+// against all of the lane's voxels.
+template <int NV>
+__device__ __forceinline__ void mark_units(const DoseArgs& a, const PatchTiles& t, const int64_t e0, const int b,
+                                           float4* srow, const int lane)
 {
     const PlanView& P = a.P;
     const BeamDev& bm = P.beams[b];
     const float sad = __ldg(&bm.sad);
     const int M = __ldg(&bm.M), N = __ldg(&bm.N), first = __ldg(&bm.first);
     const float hfx = __ldg(&bm.half_fx), hfy = __ldg(&bm.half_fy);
-    const CountVoxel c = count_voxel(P, bm, __ldg(a.items + e0 + lane), sad);
-    int nlo, nhi;
-    count_rows(P, c, N, hfy, nlo, nhi);
+    CountVoxel c[NV];
+    int nlo = INT_MAX, nhi = INT_MIN;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        c[k] = count_voxel(P, bm, __ldg(a.items + e0 + 32 * k + lane), sad);
+        int lo, hi;
+        count_rows(P, c[k], N, hfy, lo, hi);
+        nlo = min(nlo, lo);
+        nhi = max(nhi, hi);
+    }
     const int wnlo = __reduce_min_sync(0xffffffffu, nlo);
     const int wnhi = __reduce_max_sync(0xffffffffu, nhi);
     int row0;
@@ -846,8 +857,14 @@ __device__ __forceinline__ void mark_unit(const DoseArgs& a, const PatchTiles& t
     const int MB = (M + 3) >> 2;
     int last = -1;
     for (int n = wnlo; n <= wnhi; ++n) {
-        int mlo, mhi;
-        count_cols(P, c, n, M, hfx, hfy, mlo, mhi);
+        int mlo = INT_MAX, mhi = INT_MIN;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            int lo, hi;
+            count_cols(P, c[k], n, M, hfx, hfy, lo, hi);
+            mlo = min(mlo, lo);
+            mhi = max(mhi, hi);
+        }
         const int wmlo = __reduce_min_sync(0xffffffffu, mlo);
         const int wmhi = __reduce_max_sync(0xffffffffu, mhi);
         const uint32_t row = (uint32_t)(first + n * M);
@@ -864,7 +881,10 @@ __device__ __forceinline__ void mark_unit(const DoseArgs& a, const PatchTiles& t
             __syncwarp();
             for (int m = m0; m <= m1; ++m) {
                 const float4* rq = srow + 3 * (m - m0);
-                const bool in = pair_test(P, c.ln, rq[0], rq[1], rq[2]).in;
+                const float4 q0 = rq[0], q1 = rq[1], q2 = rq[2];
+                bool in = false;
+#pragma unroll
+                for (int k = 0; k < NV; ++k) in = in || pair_test(P, c[k].ln, q0, q1, q2).in;
                 if (__any_sync(0xffffffffu, in)) {
                     const int patch = (n >> 2) * MB + (m >> 2);
                     if (patch != last) {
@@ -877,6 +897,7 @@ __device__ __forceinline__ void mark_unit(const DoseArgs& a, const PatchTiles& t
     }
 }
 
+// two units per warp where they share a beam and a row-block (one at a time otherwise)
 __global__ void __launch_bounds__(kThreads, 4) k_mark_patches(const DoseArgs a, const PatchTiles t)
 {
     __shared__ int64_t s_base[kMaxBeams + 1];
@@ -885,16 +906,28 @@ __global__ void __launch_bounds__(kThreads, 4) k_mark_patches(const DoseArgs a, 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int q = threadIdx.x; q <= P.n_beams; q += blockDim.x) s_base[q] = a.base[q];
     __syncthreads();
-    const int total = a.work[0];
+    const int units = a.work[0];
+    const int groups = (units + 1) / 2;
     for (;;) {
         int w = 0;
         if (lane == 0) w = atomicAdd(a.work + 1, 1);
         w = __shfl_sync(0xffffffffu, w, 0);
-        if (w >= total) break;
-        const int64_t e0 = (int64_t)DC_GUARD(P, w, (s_base[P.n_beams] + 31) / 32, 4) * 32;
+        if (w >= groups) break;
+        const int u0 = 2 * w;
+        const int64_t e0 = (int64_t)DC_GUARD(P, u0, (s_base[P.n_beams] + 31) / 32, 4) * 32;
         int b = 0;
         while (b + 1 < P.n_beams && s_base[b + 1] <= e0) ++b;
-        mark_unit(a, t, e0, b, s_row[warp], lane);
+        if (u0 + 1 < units && e0 + 64 <= s_base[b + 1] && ((e0 - s_base[b]) >> 7) == ((e0 + 32 - s_base[b]) >> 7)) {
+            mark_units<2>(a, t, e0, b, s_row[warp], lane);
+        } else {
+            mark_units<1>(a, t, e0, b, s_row[warp], lane);
+            if (u0 + 1 < units) {
+                const int64_t e1 = e0 + 32;
+                int b1 = b;
+                while (b1 + 1 < P.n_beams && s_base[b1 + 1] <= e1) ++b1;
+                mark_units<1>(a, t, e1, b1, s_row[warp], lane);
+            }
+        }
     }
 }
 
