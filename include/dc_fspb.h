@@ -185,8 +185,14 @@ dc_status dc_fspb_dose(dc_plan* plan, const float* fluence, float* dose, uint32_
 
 /*
  * Eq. (1) for k fluence vectors at once: dose[q][v] = sum_i fluence[q][i] D_i(r_v),
- * each D_i(r_v) evaluated once and applied to all k vectors (1 <= k <= 64).
+ * each D_i(r_v) evaluated once and applied to all k vectors (1 <= k <= 64):
+ * one pass of 16, 32 or 64 vectors (the smallest that holds k), with the
+ * beamlets' fluences staged beside their records.  For k > 1 each vector's
+ * dose is the same, bit for bit, whatever k it is computed with.
  *   fluence [k][B]; dose [k][V].
+ * Scratch: per-beam partial doses, n_beams * width * V floats (width 16, 32
+ * or 64), kept by the plan.
+ * Errors: DC_EINVAL (NULL pointers, k outside [1, 64]), DC_ENOMEM, DC_ECUDA.
  */
 dc_status dc_fspb_dose_batch(dc_plan* plan, const float* fluence, int32_t k, float* dose,
                              uint32_t flags);

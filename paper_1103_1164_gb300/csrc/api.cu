@@ -670,8 +670,8 @@ dc_status dc_fspb_dose_batch(dc_plan* plan, const float* fluence, int32_t k, flo
     if (!plan || !fluence || !dose) return invalid("dc_fspb_dose: NULL argument");
     if (k < 1 || k > 64) return invalid("dc_fspb_dose_batch: k must be in [1, 64]");
     const size_t nf = (size_t)k * plan->B, nd = (size_t)k * plan->V;
-    // per-beam partial doses: 16 fluence vectors per pass when k > 1
-    dc_status ps = ensure_part(plan, (size_t)plan->n_beams * (k > 1 ? 16 : 1) * plan->V);
+    // per-beam partial doses of one pass (up to 64 fluence vectors)
+    dc_status ps = ensure_part(plan, (size_t)plan->n_beams * dose_pass_width(k) * plan->V);
     if (ps != DC_OK) return ps;
     // a single-fluence pass records the pair counts of the matrix pattern
     // while the pattern is unknown (every pair test is made there anyway)

@@ -200,6 +200,9 @@ cudaError_t launch_binning(const dc_plan* p);
 // second traversal; see launch_rowsum)
 cudaError_t launch_dose(const dc_plan* p, const float* fluence, int nf, int ldf, float* dose,
                         int64_t ldd, bool record_counts = false);
+// fluence vectors that one pass of launch_dose takes for nf vectors (1, 16,
+// 32 or 64); the per-beam partial doses hold n_beams * width * V floats
+int dose_pass_width(int nf);
 cudaError_t launch_count(const dc_plan* p, int32_t* counts);
 // rowcount[v] = sum over beams of the per-beam pair counts already in d_bcount
 cudaError_t launch_rowsum(const dc_plan* p, int32_t* counts);

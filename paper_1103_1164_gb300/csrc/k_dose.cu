@@ -34,15 +34,16 @@ constexpr float kLog2e = 1.4426950408889634f;
 // needs moving when only its head is written out
 constexpr int kRing = 16;
 constexpr int kRingLd = kRing + 1;
-// beamlet records of a row window staged per warp at a time (fewer in the
-// fill, whose CSR staging shares the CTA's shared memory)
-constexpr int row_max(int mode) { return mode == 2 ? 16 : 32; }
+// beamlet records of a row window staged per warp at a time: fewer in the
+// fill, whose CSR staging shares the CTA's shared memory, and with more than
+// 32 fluence vectors, whose staging does
+constexpr int row_max(int mode, int nf = 1) { return mode == 2 || nf > 32 ? 16 : 32; }
 
 enum Mode { kDose = 0, kCount = 1, kFill = 2, kGrad = 3 };
-// fluence vectors per pass of the multi-fluence dose (the staging below
-// rotates the order of their NF / 4 float4 by the lane's low two bits)
-constexpr int kMultiFluence = 16;
-static_assert(kMultiFluence / 4 == 4, "four float4 of fluences per beamlet record");
+// fluence vectors per pass of the dose kernel: 1, or 16, 32 or 64 staged
+// beside each beamlet record (as NF / 4 float4, whose order the staging
+// rotates by the lane's low two bits)
+constexpr bool valid_nf(int nf) { return nf == 1 || nf == 16 || nf == 32 || nf == 64; }
 
 __device__ __forceinline__ float ex2(float x)
 {
@@ -479,8 +480,8 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
         // the records of the row's window go to shared memory with one
         // coalesced load per lane, so the traversal reads them without a
         // global-memory round trip per beamlet
-        for (int m0 = wmlo; m0 <= wmhi; m0 += row_max(MODE)) {
-        const int m1 = min(wmhi, m0 + row_max(MODE) - 1);
+        for (int m0 = wmlo; m0 <= wmhi; m0 += row_max(MODE, NF)) {
+        const int m1 = min(wmhi, m0 + row_max(MODE, NF) - 1);
         __syncwarp();
         if (m0 + lane <= m1) {
             const uint32_t ib = DC_GUARD(P, row + (uint32_t)(m0 + lane), P.B, 5);
@@ -594,9 +595,13 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
 // Persistent CTAs take units from a global counter.
 // Register budgets: 48 per thread for the single-fluence dose (5 CTAs per
 // SM), 64 for the pair count and the CSR fill (4 CTAs; the fill's extra state
-// would otherwise be recomputed in the hot loop), 80 for 16 fluence vectors.
+// would otherwise be recomputed in the hot loop), 80 for 16 fluence vectors,
+// 128 for 32 or 64 (their accumulators).
 template <int MODE, int NF>
-constexpr int min_ctas() { return MODE == kCount || MODE == kFill || MODE == kGrad ? 4 : (NF == 1 ? 5 : 3); }
+constexpr int min_ctas()
+{
+    return MODE == kCount || MODE == kFill || MODE == kGrad ? 4 : (NF == 1 ? 5 : (NF == 16 ? 3 : 2));
+}
 
 template <int MODE, int NF, bool MERGED, int LAT, int PREC>
 __global__ void __launch_bounds__(kThreads, min_ctas<MODE, NF>()) k_pairs(const DoseArgs a)
@@ -616,9 +621,10 @@ __global__ void __launch_bounds__(kThreads, min_ctas<MODE, NF>()) k_pairs(const 
         sst = reinterpret_cast<int2*>(sgrad);
         for (int q = threadIdx.x; q < ngrad; q += blockDim.x) sgrad[q] = 0.f;
     }
-    __shared__ float4 s_row[kWarps][3 * row_max(MODE)];
+    static_assert(valid_nf(NF) || MODE != kDose, "16, 32 or 64 fluence vectors per pass");
+    __shared__ float4 s_row[kWarps][3 * row_max(MODE, NF)];
     // several fluence vectors: each staged beamlet's fluences (NF per record)
-    __shared__ float4 s_flu[NF > 1 ? kWarps : 1][NF > 1 ? row_max(MODE) * NF / 4 : 1];
+    __shared__ float4 s_flu[NF > 1 ? kWarps : 1][NF > 1 ? row_max(MODE, NF) * NF / 4 : 1];
     // the water tables are read from shared memory unless merged into the depth tables
     if (MODE != kCount && !MERGED)
         for (int q = threadIdx.x; q < 2 * P.w_n; q += blockDim.x) sW[q] = __ldg(P.water + q);
@@ -1461,6 +1467,14 @@ cudaError_t launch_batch(cudaStream_t s, const DoseArgs* h_args, const DoseArgs*
     return cudaGetLastError();
 }
 
+// One pass evaluates each pair once for all of its fluence vectors: on the
+// 16 head-and-neck plans' largest grid, 64 vectors took 145 ms as four passes
+// of 16 and 80 ms as one pass of 64 (the same doses bit for bit).
+int dose_pass_width(int nf)
+{
+    return nf <= 1 ? 1 : (nf <= 16 ? 16 : (nf <= 32 ? 32 : 64));
+}
+
 cudaError_t launch_dose(const dc_plan* p, const float* fluence, int nf, int ldf, float* dose,
                         int64_t ldd, bool record_counts)
 {
@@ -1472,14 +1486,16 @@ cudaError_t launch_dose(const dc_plan* p, const float* fluence, int nf, int ldf,
         if (e != cudaSuccess) return e;
         a.count_out = p->d_bcount;
     }
-    for (int q0 = 0; q0 < nf; q0 += 16) {
+    const int width = dose_pass_width(nf);
+    for (int q0 = 0; q0 < nf; q0 += width) {
         a.fluence = fluence + (size_t)q0 * ldf;
-        a.nf = nf - q0 < 16 ? nf - q0 : 16;
-        const int nfs = a.nf == 1 ? 1 : 16;
+        a.nf = nf - q0 < width ? nf - q0 : width;
+        const int nfs = a.nf == 1 ? 1 : width;
         if (p->part_cap < (size_t)p->n_beams * nfs * p->V) return cudaErrorInvalidValue;
         cudaError_t e = cudaMemsetAsync(p->d_part, 0, sizeof(float) * (size_t)p->n_beams * nfs * p->V, p->stream);
         if (e != cudaSuccess) return e;
-        e = nfs == 1 ? run<kDose, 1>(p, a) : run<kDose, 16>(p, a);
+        e = nfs == 1 ? run<kDose, 1>(p, a)
+                     : (nfs == 16 ? run<kDose, 16>(p, a) : (nfs == 32 ? run<kDose, 32>(p, a) : run<kDose, 64>(p, a)));
         if (e != cudaSuccess) return e;
         k_sum_beams<<<grid_for((int64_t)a.nf * p->V), 256, 0, p->stream>>>(p->d_part, p->n_beams, nfs, a.nf, p->V,
                                                                           dose + (size_t)q0 * ldd, ldd);

@@ -140,13 +140,19 @@ def test_dose_matrix_matches_oracle(dc, oracle_mod):
 
 
 def test_dose_batch_equals_single(dc):
+    # k = 3, 17, 40, 64 take the passes of 16, 32 and 64 fluence vectors
     p = synth.small_plan(10, n_beams=2)
     plan = dc.dc_fspb_create_from(p)
     rng = np.random.default_rng(5)
-    for k in (1, 3, 17, 40):
-        F = rng.uniform(0, 1, (k, plan.n_beamlets)).astype(np.float32)
+    F64 = rng.uniform(0, 1, (64, plan.n_beamlets)).astype(np.float32)
+    full = dc.dc_fspb_dose_batch(plan, F64)
+    for k in (1, 3, 17, 40, 64):
+        F = np.ascontiguousarray(F64[:k])
         got = dc.dc_fspb_dose_batch(plan, F)
-        for q in (0, k - 1):
+        # every pass width sums the same pairs in the same order for each vector
+        if k > 1:
+            assert np.array_equal(got, full[:k]), k
+        for q in sorted({0, k // 2, k - 1}):
             one = dc.dc_fspb_dose(plan, np.ascontiguousarray(F[q]))
             assert np.abs(got[q] - one).max() <= 1e-6 * max(1.0, float(np.abs(one).max()))
 
