@@ -21,7 +21,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -56,13 +55,13 @@ L2_FLUSH_BYTES = 256 << 20
 # reads; the summaries are under profiles/); reported only while they are unchanged.
 KERNEL_TRAFFIC = {
     # k_pairs<kFill, 1> (the step's fill + eq. 1) and k_pairs<kDose> on thorax9
-    "fill": (1182118912 + 5323690496, {
-        "paper_1103_1164_gb300/csrc/k_dose.cu": "64add85012b7bc4893516c2ba0730c24ee9eb3f215193cba0ab55344430ee2bd",
-        "paper_1103_1164_gb300/csrc/dc_views.cuh": "f1be087b7a0acad7b8f7cef88a48640b076f1fa27a2cd95059a18729a05be3a6",
+    "fill": (1182519296 + 5323322624, {
+        "paper_1103_1164_gb300/csrc/k_dose.cu": "5d055c97e41799cec66cb70fd651222cfbbc9d1e055d0292647a3f3c08c35e5d",
+        "paper_1103_1164_gb300/csrc/dc_views.cuh": "786376aaf34c342ec1f8614b14b49cfb72da1465ac3fd3094fb0956611314095",
     }),
-    "dose": (110451200 + 21174784, {
-        "paper_1103_1164_gb300/csrc/k_dose.cu": "64add85012b7bc4893516c2ba0730c24ee9eb3f215193cba0ab55344430ee2bd",
-        "paper_1103_1164_gb300/csrc/dc_views.cuh": "f1be087b7a0acad7b8f7cef88a48640b076f1fa27a2cd95059a18729a05be3a6",
+    "dose": (110442240 + 20924416, {
+        "paper_1103_1164_gb300/csrc/k_dose.cu": "5d055c97e41799cec66cb70fd651222cfbbc9d1e055d0292647a3f3c08c35e5d",
+        "paper_1103_1164_gb300/csrc/dc_views.cuh": "786376aaf34c342ec1f8614b14b49cfb72da1465ac3fd3094fb0956611314095",
     }),
 }
 
@@ -747,6 +746,14 @@ def run_surrogate_form(args, dc, torch, stream, peaks, k=64):
     t_spmm = time_on_stream(torch, stream, lambda: dc.dc_fspb_spmm(plan, F, Y), reps, flush)
     dc.dc_fspb_device_status(plan)
     err = float(((Y.t() - plain).abs().max(1).values / plain.abs().max(1).values).max())
+    # the direct tensor-core form (no matrix): the BF16 pair values and
+    # fluences of every pair multiplied on the tensor cores, per set of 64
+    dc.dc_fspb_set_precision(plan, dc.DC_PRECISION_BF16)
+    dose_tc = torch.empty_like(dose)
+    dc.dc_fspb_dose_batch(plan, Ft, dose_tc)
+    t_direct = time_on_stream(torch, stream, lambda: dc.dc_fspb_dose_batch(plan, Ft, dose_tc), reps, flush)
+    dc.dc_fspb_set_precision(plan, dc.DC_PRECISION_FP32)
+    dc.dc_fspb_device_status(plan)
     # the network's factor pass alone (k_mlp_factors: 48 nearest taps and the
     # network per (voxel, beam) entry), against the BF16 tensor peak
     entries = dc.dc_fspb_list_entries(plan)
@@ -775,10 +782,15 @@ def run_surrogate_form(args, dc, torch, stream, peaks, k=64):
         vox = np.sort(np.random.default_rng(21).choice(plan.n_voxels, 3000, replace=False))
         want = oracle_multi_fluence(p1, F.cpu().numpy(), lateral_mode=1, voxels=vox)
         oracle_err = {"surrogate_bf16": column_error(Y.cpu().numpy()[vox], want),
+                      "surrogate_bf16_direct": column_error(dose_tc.t().cpu().numpy()[vox], want),
                       "plain_fp32_axis": column_error(plain.t().cpu().numpy()[vox], want),
                       "voxels": int(vox.size)}
-    per_set = t_plain - 3.0 * t_spmm
-    sets_3x = math.ceil((3.0 * (t_set_mlp + t_prep) - t_set_axis) / per_set) if per_set > 0 else None
+
+    def surrogate_ms(n):
+        # the faster surrogate + BF16 form for n sets of 64 fluences per density
+        return min(t_set_mlp + t_prep + n * t_spmm, t_set_mlp + n * t_direct)
+
+    sets_3x = next((n for n in range(1, 1001) if t_set_axis + n * t_plain >= 3.0 * surrogate_ms(n)), None)
     return {"workload": f"slab64 64^3 @0.25cm, 1 beam, {plan.n_beamlets} beamlets, {k} fluences U[0,1]; "
                         f"network 48-64-64-3 SiLU trained on {n_tr} stencils from 200 random phantoms",
             "samples_generate_s": t_gen, "train_s": t_train, "train_loss": loss,
@@ -786,11 +798,15 @@ def run_surrogate_form(args, dc, torch, stream, peaks, k=64):
             "plain_fp32_axis": {"set_density_ms": t_set_axis, "dose_64_ms": t_plain},
             "surrogate_bf16": {"set_density_ms": t_set_mlp, "spmm_prepare_ms": t_prep, "spmm_64_ms": t_spmm,
                                "fallbacks": dc.dc_fspb_lateral_fallbacks(plan)},
-            "speedup_one_set_of_64": (t_set_axis + t_plain) / (t_set_mlp + t_prep + t_spmm),
-            "speedup_per_further_set_of_64": t_plain / t_spmm,
+            "surrogate_bf16_direct": {"set_density_ms": t_set_mlp, "dose_64_ms": t_direct},
+            "speedup_one_set_of_64": (t_set_axis + t_plain) / surrogate_ms(1),
+            "speedup_one_set_by_form": {"matrix_spmm": (t_set_axis + t_plain) / (t_set_mlp + t_prep + t_spmm),
+                                        "direct_tensor_core": (t_set_axis + t_plain) / (t_set_mlp + t_direct)},
+            "speedup_per_further_set_of_64": t_plain / min(t_spmm, t_direct),
             "sets_of_64_for_3x": sets_3x,
-            "accounting": "per density: factors (+ matrix build for the BF16 form); per set of 64 "
-                          "fluences: the direct batch or the SpMM",
+            "accounting": "per density: factors (+ matrix build for the matrix form); per set of 64 "
+                          "fluences: the direct batch, the SpMM or the direct tensor-core pass; the "
+                          "surrogate figures take the faster form for the number of sets",
             "max_err_vs_plain_over_colmax": err,
             "max_err_vs_fp64_oracle_over_colmax": oracle_err,
             "network_kernels": mlp}
@@ -1199,13 +1215,16 @@ def run_batch_multi_fluence(args, dc, torch, inputs, net, k=64):
     seeded), the two forms of the multi-fluence dose, plan after
     plan: plain = axis-stencil lateral densities and the FP32 direct
     evaluation of the k vectors (dc_fspb_dose_batch); surrogate + BF16 = the
-    network's lateral densities, the BF16 dose-deposition matrix
-    (dc_fspb_spmm_prepare) and the tensor-core SpMM (dc_fspb_spmm).  Host wall
-    clock around each plan's calls (both forms synchronise), cells autotuned at
-    set-up.  The surrogate form's cost per density (factors + matrix) and per
-    further set of k vectors (the SpMM) are reported apart, with the number of
-    sets at which it is 3x faster; its error against the FP64 oracle's axis
-    form on seeded voxels of the largest and the smallest plan, every column."""
+    network's lateral densities with, either, the BF16 dose-deposition matrix
+    (dc_fspb_spmm_prepare) and the tensor-core SpMM (dc_fspb_spmm), or the
+    direct tensor-core form (dc_fspb_dose_batch in the reduced-precision
+    setting: the pair values and fluences in BF16, their products on the
+    tensor cores, no matrix).  Host wall clock around each plan's calls (all
+    forms synchronise), cells autotuned at set-up.  The surrogate forms' cost
+    per density (factors, + matrix) and per set of k vectors are reported
+    apart, with the number of sets at which the faster of them is 3x faster;
+    their error against the FP64 oracle's axis form on seeded voxels of the
+    largest and the smallest plan, every column."""
     from paper_1103_1164_gb300 import surrogate
     peaks, _ = measured_peaks()
     gen = torch.Generator(device="cuda")
@@ -1220,7 +1239,8 @@ def run_batch_multi_fluence(args, dc, torch, inputs, net, k=64):
         torch.cuda.synchronize()
         return 1e3 * (time.perf_counter() - t0)
 
-    acc = {"plain_ms": 0.0, "surrogate_density_ms": 0.0, "surrogate_spmm_ms": 0.0}
+    acc = {"plain_ms": 0.0, "surrogate_density_ms": 0.0, "surrogate_spmm_ms": 0.0, "surrogate_factors_ms": 0.0,
+           "surrogate_direct_ms": 0.0}
     errs = {}
     pairs_total = 0
     bytes_alg = bytes_tiles = 0
@@ -1254,6 +1274,15 @@ def run_batch_multi_fluence(args, dc, torch, inputs, net, k=64):
         bytes_alg += npairs * 6 + V * k * 4 + B * k * 2
         items = dc.dc_fspb_list_entries(plan) if len(p.beams) > 1 else 0
         bytes_tiles += chunks * (4096 + 4) + 2 * items * k * 4 + V * k * 4 + B * k * 4
+        # the direct tensor-core form (after the matrix's figures: a new density
+        # drops the tiles): per density the network's factors, per
+        # set the BF16 evaluation of every pair for the k vectors
+        acc["surrogate_factors_ms"] += wall(lambda: dc.dc_fspb_set_density(plan, rho))
+        dc.dc_fspb_set_precision(plan, dc.DC_PRECISION_BF16)
+        Dt = torch.empty(k, V, device="cuda")
+        dc.dc_fspb_dose_batch(plan, Ft, Dt)
+        acc["surrogate_direct_ms"] += wall(lambda: dc.dc_fspb_dose_batch(plan, Ft, Dt))
+        dc.dc_fspb_set_precision(plan, dc.DC_PRECISION_FP32)
         if not args.no_cpu and j in (big, small):
             # seeded voxels, half of them above 10 % of the first column's maximum
             d0 = D[0].cpu().numpy()
@@ -1265,24 +1294,37 @@ def run_batch_multi_fluence(args, dc, torch, inputs, net, k=64):
             colmax = D.abs().max(1).values.cpu().numpy().astype(np.float64)
             e = np.abs(Y.cpu().numpy()[vox].astype(np.float64) - want).max(0) / colmax
             ep = np.abs(D.t().cpu().numpy()[vox].astype(np.float64) - want).max(0) / colmax
+            et = np.abs(Dt.t().cpu().numpy()[vox].astype(np.float64) - want).max(0) / colmax
             errs["largest" if j == big else "smallest"] = {"voxels": int(vox.size),
                                                            "surrogate_bf16": float(e.max()),
+                                                           "surrogate_bf16_direct": float(et.max()),
                                                            "plain_fp32_axis": float(ep.max())}
-        del plan, D, Y, F, Ft, rho
+        del plan, D, Dt, Y, F, Ft, rho
         torch.cuda.empty_cache()
     sur_one = acc["surrogate_density_ms"] + acc["surrogate_spmm_ms"]
     per_set = acc["surrogate_spmm_ms"]
+    direct_one = acc["surrogate_factors_ms"] + acc["surrogate_direct_ms"]
+
+    def surrogate_ms(n):
+        # the faster surrogate + BF16 form for n sets of k vectors per density
+        return min(acc["surrogate_density_ms"] + n * per_set,
+                   acc["surrogate_factors_ms"] + n * acc["surrogate_direct_ms"])
+
     sets_3x = None
     for n in range(1, 1001):
-        if n * acc["plain_ms"] >= 3.0 * (acc["surrogate_density_ms"] + n * per_set):
+        if n * acc["plain_ms"] >= 3.0 * surrogate_ms(n):
             sets_3x = n
             break
     return {"workload": f"the 16 plans, {k} fluence vectors U[0,1] each ({pairs_total} pairs per vector)",
             "plain_fp32_axis_ms": acc["plain_ms"],
             "surrogate_bf16": {"per_density_ms": acc["surrogate_density_ms"],
                                "per_set_of_64_ms": per_set, "one_set_ms": sur_one},
-            "speedup_one_set": acc["plain_ms"] / sur_one,
-            "speedup_per_further_set": acc["plain_ms"] / per_set,
+            "surrogate_bf16_direct": {"per_density_ms": acc["surrogate_factors_ms"],
+                                      "per_set_of_64_ms": acc["surrogate_direct_ms"], "one_set_ms": direct_one},
+            "speedup_one_set": acc["plain_ms"] / surrogate_ms(1),
+            "speedup_one_set_by_form": {"matrix_spmm": acc["plain_ms"] / sur_one,
+                                        "direct_tensor_core": acc["plain_ms"] / direct_one},
+            "speedup_per_further_set": acc["plain_ms"] / min(per_set, acc["surrogate_direct_ms"]),
             "sets_of_64_for_3x": sets_3x,
             "evals_per_s": {"plain": pairs_total * k / (acc["plain_ms"] * 1e-3),
                             "surrogate_bf16_one_set": pairs_total * k / (sur_one * 1e-3)},

@@ -372,9 +372,15 @@ dc_status dc_fspb_dose_vjp(dc_plan* plan, const float* fluence, const float* wei
  * and the sum of eq. (1) stay FP32.  Its error against the FP64 oracle is
  * measured against the surrogate bar of 1 % of the maximum dose, not
  * guaranteed.  It applies to dc_fspb_dose (and dc_fspb_dose_batch with k = 1)
- * and to the plan's share of a multi-plan batch; the matrix calls, the SpMM and
- * k > 1 stay FP32.  Takes effect at the next call; a batch picks it up at its
- * next run.  Errors: DC_EINVAL (NULL plan, unknown value).
+ * and to the plan's share of a multi-plan batch.  dc_fspb_dose_batch with
+ * k > 1 takes the tensor-core form instead: each pair value D_i(r_v) (FP32
+ * exponentials, as in DC_PRECISION_FP32) and each fluence are rounded to BF16
+ * (nearest even), and their products for all k <= 64 vectors are summed by
+ * mma.m16n8k16 with FP32 accumulators, 16 beamlets of 32 voxels at a time, in
+ * one pass; the per-beam sums stay FP32, in beam order.  The matrix calls and
+ * the SpMM do not depend on the setting.  Takes effect at the next call; a
+ * batch picks it up at its next run.  Errors: DC_EINVAL (NULL plan, unknown
+ * value).
  */
 #define DC_PRECISION_FP32 0
 #define DC_PRECISION_BF16 1

@@ -670,9 +670,18 @@ dc_status dc_fspb_dose_batch(dc_plan* plan, const float* fluence, int32_t k, flo
     if (!plan || !fluence || !dose) return invalid("dc_fspb_dose: NULL argument");
     if (k < 1 || k > 64) return invalid("dc_fspb_dose_batch: k must be in [1, 64]");
     const size_t nf = (size_t)k * plan->B, nd = (size_t)k * plan->V;
-    // per-beam partial doses of one pass (up to 64 fluence vectors)
-    dc_status ps = ensure_part(plan, (size_t)plan->n_beams * dose_pass_width(k) * plan->V);
+    // per-beam partial doses of one pass (up to 64 fluence vectors); the
+    // tensor-core form (reduced precision, k > 1) also packs the fluences
+    const bool tc = k > 1 && plan->precision == DC_PRECISION_BF16;
+    dc_status ps = ensure_part(plan, (size_t)plan->n_beams * (tc ? 64 : dose_pass_width(k)) * plan->V);
     if (ps != DC_OK) return ps;
+    if (tc && plan->sp_fp_cap < (size_t)plan->B * 64) {
+        if (plan->d_sp_fp) cudaFree(plan->d_sp_fp);
+        plan->d_sp_fp = nullptr;
+        plan->sp_fp_cap = 0;
+        DC_CUDA(dc::dev_malloc(&plan->d_sp_fp, (size_t)plan->B * 64 * sizeof(uint16_t)));
+        plan->sp_fp_cap = (size_t)plan->B * 64;
+    }
     // a single-fluence pass records the pair counts of the matrix pattern
     // while the pattern is unknown (every pair test is made there anyway)
     const bool record = k == 1 && plan->pairs < 0 && !plan->counts_fresh;

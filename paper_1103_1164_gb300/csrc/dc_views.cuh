@@ -110,6 +110,7 @@ struct DoseArgs {
     float* dose;            // [nf][ldd]
     int64_t ldd;
     float* part;            // dose: per-beam partial dose [n_beams][NF][V]
+    const uint4* fpack;     // dose, tensor-core form: the fluences as BF16 [B][64] (zero past nf)
     int32_t* bcount;        // count: per-beam pair counts [n_beams][V]; fill reads them
     int32_t* count_out;     // dose with one fluence vector: where to record the same counts (or null)
     const int64_t* rowptr;  // fill

@@ -45,6 +45,30 @@ enum Mode { kDose = 0, kCount = 1, kFill = 2, kGrad = 3 };
 // rotates by the lane's low two bits)
 constexpr bool valid_nf(int nf) { return nf == 1 || nf == 16 || nf == 32 || nf == 64; }
 
+// PREC 2, the tensor-core form of the multi-fluence dose (64 vectors): per
+// warp and chunk of 16 beamlets, Y[32 voxels][64] += D[32][16] F[16][64] as
+// mma.m16n8k16 with BF16 operands (D and F rounded to nearest even) and FP32
+// accumulators in registers.  D is staged as BF16 pairs of neighbouring
+// beamlets per voxel row (words [tile of 16 rows][beamlet pair][row]), F as
+// BF16 pairs of neighbouring beamlets per vector (words [beamlet pair][vector]);
+// the padded strides keep the per-beamlet stores and the fragment loads free of
+// bank conflicts (the second 16-row tile starts on the other 16 banks).
+constexpr int kTcRowD = 24;
+constexpr int kTcTileD = 8 * kTcRowD + 16;
+constexpr int kTcRowF = 72;
+constexpr int kTcOffF = kTcTileD + 8 * kTcRowD;
+constexpr int kTcWords = kTcOffF + 8 * kTcRowF;   // per warp
+
+__device__ __forceinline__ void mma_bf16(float* d, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                         uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
 __device__ __forceinline__ float ex2(float x)
 {
     float y;
@@ -399,8 +423,13 @@ __device__ __forceinline__ void flush_stage(const DoseArgs& a, const int2* st, i
 template <int MODE, int NF, bool MERGED, int LAT, int PREC = 0>
 __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi, const int64_t e0, const int b,
                                              const float4* __restrict__ sW, int2* sst, float4* srow,
-                                             const int lane, float4* sflu = nullptr)
+                                             const int lane, float4* sflu = nullptr, uint32_t* stc = nullptr)
 {
+    // the tensor-core form of 64 fluence vectors; its pair values in FP32
+    // exponentials like the plain form
+    constexpr bool TC = MODE == kDose && PREC == 2;
+    constexpr int EP = PREC == 1 ? 1 : 0;
+    static_assert(!TC || NF == 64, "the tensor-core form takes 64 fluence vectors");
     const PlanView& P = a.P;
     const int64_t V = (int64_t)P.nx * P.ny * P.nz;
     Lane ln;
@@ -493,7 +522,7 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
             // theta weight (which only the table set-up uses)
             if (MODE != kCount && NF == 1) q2.w = __ldg(a.fluence + ib);
             srow[3 * lane + 2] = q2;
-            if (MODE == kDose && NF > 1) {
+            if (MODE == kDose && NF > 1 && !TC) {
                 // the beamlet's NF fluences beside its record (zero past a.nf),
                 // as NF / 4 float4 whose order is rotated by the lane (fewer
                 // bank conflicts among the lanes' stores)
@@ -507,6 +536,32 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
                     f4[j ^ (lane & 3)] = make_float4(f[0], f[1], f[2], f[3]);
                 }
             }
+        }
+        if (TC) {
+            // the chunk's 64 BF16 fluences of beamlets m0 + 2j and m0 + 2j + 1
+            // as pairs (lane: pair j, vectors nb .. nb + 15); zero past m1
+            const int j = lane >> 2, nb = (lane & 3) * 16;
+            const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+            uint4 f0 = z, f1 = z, g0 = z, g1 = z;
+            if (m0 + 2 * j <= m1) {
+                const uint4* src = a.fpack + (size_t)DC_GUARD(P, row + (uint32_t)(m0 + 2 * j), P.B, 5) * 8 + nb / 8;
+                f0 = __ldg(src);
+                f1 = __ldg(src + 1);
+            }
+            if (m0 + 2 * j + 1 <= m1) {
+                const uint4* src = a.fpack + (size_t)DC_GUARD(P, row + (uint32_t)(m0 + 2 * j + 1), P.B, 5) * 8 + nb / 8;
+                g0 = __ldg(src);
+                g1 = __ldg(src + 1);
+            }
+            uint4* dst = reinterpret_cast<uint4*>(stc + kTcOffF + j * kTcRowF + nb);
+            dst[0] = make_uint4(__byte_perm(f0.x, g0.x, 0x5410), __byte_perm(f0.x, g0.x, 0x7632),
+                                __byte_perm(f0.y, g0.y, 0x5410), __byte_perm(f0.y, g0.y, 0x7632));
+            dst[1] = make_uint4(__byte_perm(f0.z, g0.z, 0x5410), __byte_perm(f0.z, g0.z, 0x7632),
+                                __byte_perm(f0.w, g0.w, 0x5410), __byte_perm(f0.w, g0.w, 0x7632));
+            dst[2] = make_uint4(__byte_perm(f1.x, g1.x, 0x5410), __byte_perm(f1.x, g1.x, 0x7632),
+                                __byte_perm(f1.y, g1.y, 0x5410), __byte_perm(f1.y, g1.y, 0x7632));
+            dst[3] = make_uint4(__byte_perm(f1.z, g1.z, 0x5410), __byte_perm(f1.z, g1.z, 0x7632),
+                                __byte_perm(f1.w, g1.w, 0x5410), __byte_perm(f1.w, g1.w, 0x7632));
         }
         __syncwarp();
         // two beamlets per trip: their independent loads and arithmetic
@@ -526,10 +581,19 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
                               reinterpret_cast<float*>(sst), gl, gc);
                 continue;
             }
+            if (TC) {
+                // D (zero outside the pair) into the lane's row of the chunk's tile
+                float D = 0.f;
+                if (pt.in) D = pair_eval<MERGED, LAT, 0>(P, ln, i, sad, sW, pt);
+                const int c = m - m0;
+                reinterpret_cast<__nv_bfloat16*>(stc)[2 * ((lane >> 4) * kTcTileD + (c >> 1) * kTcRowD + (lane & 15)) +
+                                                      (c & 1)] = __float2bfloat16_rn(D);
+                continue;
+            }
             if (MODE == kDose) {
                 if (NF == 1) cnt += pt.in ? 1 : 0;
                 if (pt.in) {
-                    const float D = pair_eval<MERGED, LAT, PREC>(P, ln, i, sad, sW, pt);
+                    const float D = pair_eval<MERGED, LAT, EP>(P, ln, i, sad, sW, pt);
                     if (NF == 1) {
                         acc[0] = fmaf(rq[2].w, D, acc[0]);
                     } else {
@@ -555,6 +619,27 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
                 if (__any_sync(0xffffffffu, cnt >= kRing)) flush_stage(a, sst, lane, cnt, pos, pend, mis, false);
             }
         }
+        if (TC) {
+            // Y[32][64] += D[32][16] F[16][64]: two 16-row tiles, eight 8-vector tiles
+            __syncwarp();
+            const int g = lane >> 2, t4 = lane & 3;
+            uint32_t fa[2][4];
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                const uint32_t* d0 = stc + t * kTcTileD;
+                fa[t][0] = d0[t4 * kTcRowD + g];
+                fa[t][1] = d0[t4 * kTcRowD + g + 8];
+                fa[t][2] = d0[(t4 + 4) * kTcRowD + g];
+                fa[t][3] = d0[(t4 + 4) * kTcRowD + g + 8];
+            }
+            const uint32_t* sf = stc + kTcOffF;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const uint32_t b0 = sf[t4 * kTcRowF + 8 * u + g], b1 = sf[(t4 + 4) * kTcRowF + 8 * u + g];
+#pragma unroll
+                for (int t = 0; t < 2; ++t) mma_bf16(acc + (t * 8 + u) * 4, fa[t][0], fa[t][1], fa[t][2], fa[t][3], b0, b1);
+            }
+        }
         }
     }
     if (MODE == kGrad) {
@@ -575,6 +660,23 @@ __device__ __forceinline__ void process_unit(const DoseArgs& a, const int32_t vi
             atomicAdd(sgd + 4 * P.f_n, gc[0]);
             atomicAdd(sgd + 4 * P.f_n + 1, gc[1]);
         }
+    } else if (TC) {
+        // accumulator (tile t, vectors 8u .. 8u + 7, element 2h + e) is row
+        // 16t + 8h + g (that lane's voxel), vector 8u + 2 t4 + e
+        const int g = lane >> 2, t4 = lane & 3;
+#pragma unroll
+        for (int t = 0; t < 2; ++t)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int vr = __shfl_sync(0xffffffffu, vi, 16 * t + 8 * h + g);
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        const int n = 8 * u + 2 * t4 + e;
+                        if (vr >= 0 && n < a.nf) a.part[((size_t)b * NF + n) * V + vr] = acc[(t * 8 + u) * 4 + 2 * h + e];
+                    }
+            }
     } else if (MODE == kFill) {
         flush_stage(a, sst, lane, cnt, pos, pend, mis, true);
         if (NF == 1 && ln.valid) a.part[(size_t)b * V + v] = acc[0];
@@ -622,9 +724,17 @@ __global__ void __launch_bounds__(kThreads, min_ctas<MODE, NF>()) k_pairs(const 
         for (int q = threadIdx.x; q < ngrad; q += blockDim.x) sgrad[q] = 0.f;
     }
     static_assert(valid_nf(NF) || MODE != kDose, "16, 32 or 64 fluence vectors per pass");
+    constexpr bool TC = MODE == kDose && PREC == 2;
     __shared__ float4 s_row[kWarps][3 * row_max(MODE, NF)];
-    // several fluence vectors: each staged beamlet's fluences (NF per record)
-    __shared__ float4 s_flu[NF > 1 ? kWarps : 1][NF > 1 ? row_max(MODE, NF) * NF / 4 : 1];
+    // several fluence vectors: each staged beamlet's fluences (NF per record),
+    // or the tensor-core form's operand tiles
+    __shared__ float4 s_flu[NF > 1 && !TC ? kWarps : 1][NF > 1 && !TC ? row_max(MODE, NF) * NF / 4 : 1];
+    __shared__ __align__(16) uint32_t s_tc[TC ? kWarps : 1][TC ? kTcWords : 4];
+    if (TC) {
+        // columns past a partial chunk keep earlier (finite) pair values, which
+        // meet zero fluences; nothing may be left uninitialised
+        for (int q = threadIdx.x & 31; q < kTcOffF; q += 32) s_tc[threadIdx.x >> 5][q] = 0u;
+    }
     // the water tables are read from shared memory unless merged into the depth tables
     if (MODE != kCount && !MERGED)
         for (int q = threadIdx.x; q < 2 * P.w_n; q += blockDim.x) sW[q] = __ldg(P.water + q);
@@ -642,7 +752,8 @@ __global__ void __launch_bounds__(kThreads, min_ctas<MODE, NF>()) k_pairs(const 
         while (b + 1 < P.n_beams && s_base[b + 1] <= e0) ++b;
         const int32_t vi = __ldg(a.items + e0 + lane);
         process_unit<MODE, NF, MERGED, LAT, PREC>(a, vi, e0, b, sW, sst, s_row[warp], lane,
-                                                  NF > 1 ? s_flu[NF > 1 ? warp : 0] : nullptr);
+                                                  NF > 1 && !TC ? s_flu[NF > 1 && !TC ? warp : 0] : nullptr,
+                                                  TC ? s_tc[TC ? warp : 0] : nullptr);
     }
     if (MODE == kGrad) {
         __syncthreads();
@@ -1394,6 +1505,28 @@ cudaError_t run_variant(const dc_plan* p, const DoseArgs& a)
     return cudaGetLastError();
 }
 
+// The tensor-core form of 64 fluence vectors (PREC 2) for the plan's lateral
+// form and tables.
+cudaError_t run_tc(const dc_plan* p, const DoseArgs& a)
+{
+    const bool item = p->coeffs.density_correction && p->lateral_mode != DC_LATERAL_ISO;
+    if (p->merged)
+        return item ? run_variant<kDose, 64, true, kItem, 2>(p, a) : run_variant<kDose, 64, true, kIso, 2>(p, a);
+    return item ? run_variant<kDose, 64, false, kItem, 2>(p, a) : run_variant<kDose, 64, false, kIso, 2>(p, a);
+}
+
+// The fluences of the tensor-core form: fpack[i][n] = BF16(F[n][i]) (round to
+// nearest even), zero for n >= nf.
+__global__ void __launch_bounds__(256) k_pack_fluence_bf16(const float* __restrict__ F, int nf, int ldf, int B,
+                                                           __nv_bfloat16* __restrict__ fpack)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)B * 64;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int n = (int)(e / B), i = (int)(e % B);
+        fpack[(size_t)i * 64 + n] = __float2bfloat16_rn(n < nf ? __ldg(F + (size_t)n * ldf + i) : 0.f);
+    }
+}
+
 template <int MODE, int NF>
 cudaError_t run(const dc_plan* p, const DoseArgs& a)
 {
@@ -1481,6 +1614,28 @@ cudaError_t launch_dose(const dc_plan* p, const float* fluence, int nf, int ldf,
     DoseArgs a = make_args(p);
     a.ldf = ldf;
     a.part = p->d_part;
+    if (nf > 1 && p->precision == DC_PRECISION_BF16) {
+        // the reduced-precision form of several vectors: the pair values and
+        // fluences rounded to BF16 and applied on the tensor cores, one pass
+        if (nf > 64 || p->part_cap < (size_t)p->n_beams * 64 * p->V || p->sp_fp_cap < (size_t)p->B * 64)
+            return cudaErrorInvalidValue;
+        k_pack_fluence_bf16<<<grid_for((int64_t)p->B * 64), 256, 0, p->stream>>>(
+            fluence, nf, ldf, p->B, static_cast<__nv_bfloat16*>(p->d_sp_fp));
+        count_launches(1);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        a.fluence = fluence;
+        a.nf = nf;
+        a.fpack = static_cast<const uint4*>(p->d_sp_fp);
+        e = cudaMemsetAsync(p->d_part, 0, sizeof(float) * (size_t)p->n_beams * 64 * p->V, p->stream);
+        if (e != cudaSuccess) return e;
+        e = run_tc(p, a);
+        if (e != cudaSuccess) return e;
+        k_sum_beams<<<grid_for((int64_t)nf * p->V), 256, 0, p->stream>>>(p->d_part, p->n_beams, 64, nf, p->V, dose,
+                                                                        ldd);
+        count_launches(1);
+        return cudaGetLastError();
+    }
     if (record_counts && nf == 1) {
         cudaError_t e = cudaMemsetAsync(p->d_bcount, 0, sizeof(int32_t) * (size_t)p->n_beams * p->V, p->stream);
         if (e != cudaSuccess) return e;

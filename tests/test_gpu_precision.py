@@ -108,3 +108,52 @@ def test_surrogate_bf16_head_neck_batch_against_oracle(dc, oracle_mod):
         err = np.abs(d[vox] - want)
         dmax = float(d.max())
         assert np.all(err <= SURROGATE_TOL * dmax + amb), (j, float((err / dmax).max()))
+
+
+def _bf16_round(x):
+    """Round-to-nearest-even to BF16, returned as float64 (library-independent)."""
+    b = np.asarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) >> 16
+    return (b.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("k,seed,kw", [(2, 80, dict(n_beams=3, couch=True)),
+                                       (17, 81, dict(n=(26, 22, 18), vox=0.3, n_beams=3, roi=2.0, field=4.0)),
+                                       (64, 82, dict(beamlet=0.2, beamlet_y=0.5, field=2.0, n_beams=2))])
+def test_bf16_tensor_core_dose_batch(dc, oracle_mod, k, seed, kw):
+    # dc_fspb_dose_batch with k > 1 in the reduced-precision setting: the pair
+    # values and fluences rounded to BF16, their products summed on the tensor
+    # cores.  Data path: the exact product of the library's BF16 matrix entries
+    # (the same FP32 pair values, rounded the same way) and the BF16 fluences,
+    # in FP64 here, up to FP32 summation order.  Method: the FP64 oracle's
+    # matrix times the unrounded fluences, the BF16 bar of 1 % of each
+    # vector's maximum dose (rows with an ambiguous pair left out).
+    from scipy import sparse
+    p = synth.small_plan(seed, **kw)
+    plan = dc.dc_fspb_create_from(p)
+    V, B = plan.n_voxels, plan.n_beamlets
+    rng = np.random.default_rng(seed)
+    F = rng.uniform(0, 1, (k, B)).astype(np.float32)
+    rowptr, cols, vals = dc.dc_fspb_dose_matrix(plan, dc.DC_BF16)
+    Mb = sparse.csr_matrix(((vals.astype(np.uint32) << 16).view(np.float32).astype(np.float64), cols, rowptr),
+                           shape=(V, B))
+    f32 = dc.dc_fspb_dose_batch(plan, F).reshape(k, V).astype(np.float64)
+    dc.dc_fspb_set_precision(plan, dc.DC_PRECISION_BF16)
+    got = dc.dc_fspb_dose_batch(plan, F).reshape(k, V).astype(np.float64)
+    dc.dc_fspb_device_status(plan)
+    assert np.all(np.isfinite(got))
+    exact = np.asarray((Mb @ _bf16_round(F).T).T)
+    colmax = np.abs(exact).max(1, keepdims=True) + 1e-30
+    assert np.all(np.abs(got - exact) <= 1e-4 * colmax), float((np.abs(got - exact) / colmax).max())
+    op = oracle_mod.OraclePlan(p)
+    o_ptr, o_cols, o_vals, o_flags = op.matrix()
+    Mo = sparse.csr_matrix((o_vals * (o_flags & 1), o_cols, o_ptr), shape=(op.V, op.B))
+    want = np.asarray((Mo @ F.astype(np.float64).T).T)
+    amb_rows = np.zeros(op.V, bool)
+    amb_rows[np.repeat(np.arange(op.V), np.diff(o_ptr))[(o_flags & 2).astype(bool)]] = True
+    err = np.abs(got - want) / (np.abs(want).max(1, keepdims=True) + 1e-30)
+    assert err[:, ~amb_rows].max() <= 1e-2, float(err[:, ~amb_rows].max())
+    assert np.abs(got - f32).max() > 0                     # the tensor-core form ran
+    # a single vector keeps the direct form's own reduced-precision kernel
+    one = dc.dc_fspb_dose_batch(plan, np.ascontiguousarray(F[:1])).reshape(-1)
+    assert np.array_equal(one, dc.dc_fspb_dose(plan, np.ascontiguousarray(F[0])).reshape(-1))
