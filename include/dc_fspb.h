@@ -190,8 +190,9 @@ dc_status dc_fspb_dose(dc_plan* plan, const float* fluence, float* dose, uint32_
  * beamlets' fluences staged beside their records.  For k > 1 each vector's
  * dose is the same, bit for bit, whatever k it is computed with.
  *   fluence [k][B]; dose [k][V].
- * Scratch: per-beam partial doses, n_beams * width * V floats (width 16, 32
- * or 64), kept by the plan.
+ * Scratch, kept by the plan: per-beam partial doses, n_beams * width * V
+ * floats (width 16, 32 or 64; 64 in the tensor-core form of
+ * DC_PRECISION_BF16), and in that form the fluences packed as B * 64 BF16.
  * Errors: DC_EINVAL (NULL pointers, k outside [1, 64]), DC_ENOMEM, DC_ECUDA.
  */
 dc_status dc_fspb_dose_batch(dc_plan* plan, const float* fluence, int32_t k, float* dose,
