@@ -1365,34 +1365,17 @@ def dc_view(torch, ptr, n):
 
 
 def run_e2e(args, dc, p, plan, pairs, torch):
-    """The benchmark step through the C ABI with page-locked host buffers: every
-    H2D/D2H copy of the step's inputs and results is inside the timed region
-    (host wall clock over the same number of steps as the device-timed value).
-    Variants: the matrix values in BF16, and the dose alone (no matrix).
-    The buffers are NumPy arrays registered with the CUDA runtime for this
-    measurement and released after it."""
+    """The benchmark step through the C ABI with page-locked host buffers (from
+    PyTorch's pinned allocator): every H2D/D2H copy of the step's inputs and
+    results is inside the timed region (host wall clock over the same number
+    of steps as the device-timed value).  Variants: the matrix values in BF16,
+    and the dose alone (no matrix)."""
     V, B = plan.n_voxels, plan.n_beamlets
-    cudart = torch.cuda.cudart()
-    registered = []
+    dtypes = {np.float32: torch.float32, np.int32: torch.int32, np.int64: torch.int64, np.uint16: torch.int16}
 
     def pin(shape, dt):
-        a = np.zeros(shape, dt)
-        rc = int(cudart.cudaHostRegister(a.ctypes.data, max(a.nbytes, 1), 0))
-        if rc != 0:
-            raise RuntimeError(f"cudaHostRegister failed ({rc})")
-        registered.append(a)
-        return a
+        return torch.empty(shape, dtype=dtypes[dt], pin_memory=True).numpy().view(dt)
 
-    try:
-        return _e2e_timed(args, dc, p, plan, pairs, torch, pin)
-    finally:
-        torch.cuda.synchronize()
-        for a in registered:
-            cudart.cudaHostUnregister(a.ctypes.data)
-
-
-def _e2e_timed(args, dc, p, plan, pairs, torch, pin):
-    V, B = plan.n_voxels, plan.n_beamlets
     rho_h = pin(p.rho.shape, np.float32)
     rho_h[...] = p.rho
     flu_h = pin((B,), np.float32)
